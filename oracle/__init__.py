@@ -1,0 +1,29 @@
+"""Oracle for the exact fast Matérn kernel MVM and the GP solve built on it.
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by ``__graft_entry__.smoke()``
+and by the ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py``.  The
+product package never imports it, and it never imports the product package.
+Everything here is plain FP64 on the CPU:
+
+* ``mvm_brute``  O1, the definition of K V (C, OpenMP, compensated sums);
+* ``kmat``       the dense matrix K for small N;
+* ``mvm_dc``     O2, the paper's ECDF decomposition evaluated literally by a
+  re-sorting divide and conquer (C);
+* ``structure``  O3, canonical sort permutations and the dominance-level
+  arrays (numpy);
+* ``solve``      O4, conjugate gradients (Algorithm 2 with the identity
+  preconditioner), dense solves and the GLS fixed-effects step (numpy).
+"""
+
+from .core import (  # noqa: F401
+    L1,
+    PRODUCT,
+    build,
+    kernel,
+    kmat,
+    max_threads,
+    mvm_brute,
+    mvm_dc,
+    mvm_dc_product32_printed,
+    phi,
+)

@@ -1,0 +1,50 @@
+"""Pins for the oracle's CG and GLS (O4): against LAPACK dense solves and the
+exact special cases of the GLS estimator."""
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import solve
+
+
+@pytest.mark.parametrize("nu,kind", [(0.5, 0), (1.5, 1), (2.5, 1)])
+def test_cg_matches_dense_solve(orc, nu, kind):
+    p = workloads.small(31, 400, 2, nu=nu, ell=[0.1, 0.3], nrhs=3)
+    sigma2 = 0.01
+    K = orc.kmat(p.X, nu, p.ell, kind=kind)
+
+    def A(B):
+        return orc.mvm_brute(p.X, B, nu, p.ell, kind=kind) + sigma2 * B
+
+    x, iters = solve.cg(A, p.V, 1e-10, 5000)
+    ref = solve.dense_solve(K, sigma2, p.V)
+    assert (iters > 0).all()
+    res = solve.true_residual(A, x, p.V)
+    assert (res <= 2e-10).all()
+    cond = np.linalg.cond(K + sigma2 * np.eye(K.shape[0]))
+    assert np.linalg.norm(x - ref) / np.linalg.norm(ref) < cond * 1e-10
+
+
+def test_gls_exact_mean_is_recovered(orc):
+    """y = H beta* exactly: the GLS estimator returns beta* and alpha = 0."""
+    p = workloads.small(32, 300, 2, nu=1.5, ell=[0.2, 0.2])
+    H = np.column_stack([np.ones(p.N), p.X])
+    beta_star = np.array([1.5, -0.7, 2.25])
+    y = H @ beta_star
+    A = orc.kmat(p.X, 1.5, p.ell, kind=1) + 0.01 * np.eye(p.N)
+    alpha, beta = solve.gls(lambda B: np.linalg.solve(A, B), y, H)
+    assert np.allclose(beta, beta_star, rtol=1e-9)
+    assert np.abs(alpha).max() < 1e-8 * np.abs(y).max()
+
+
+def test_gls_normal_equations(orc):
+    """The GLS beta satisfies H^T A^{-1} (y - H beta) = 0, and alpha solves
+    A alpha = y - H beta."""
+    p = workloads.small(33, 250, 3, nu=2.5, ell=[0.3, 0.3, 0.3])
+    H = np.column_stack([np.ones(p.N), p.X])
+    y = p.V[:, 0] + H @ np.array([1.0, 0.5, -0.3, 0.2])
+    A = orc.kmat(p.X, 2.5, p.ell, kind=1) + 0.01 * np.eye(p.N)
+    alpha, beta = solve.gls(lambda B: np.linalg.solve(A, B), y, H)
+    assert np.linalg.norm(H.T @ alpha) < 1e-8 * np.linalg.norm(H.T @ np.linalg.solve(A, y))
+    assert np.linalg.norm(A @ alpha - (y - H @ beta)) < 1e-10 * np.linalg.norm(y)
