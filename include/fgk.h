@@ -1,0 +1,188 @@
+/*
+ * libfgk — exact fast Matérn-kernel matrix-vector products and GP solves on
+ * one NVIDIA GB300 (sm_103a).
+ *
+ * The library computes, exactly up to rounding,
+ *
+ *     Y = K V,   K_ij = s2 * K(x_i - x_j),                  (Sec. 2, eq. Ky)
+ *
+ * for the half-integer Matérn kernels nu = 1/2, 3/2, 5/2 (App. C.1,
+ * eqs. matern_1_2, matern_3_2, matern_5_2) combined over d <= 3 coordinates
+ * either through the L1 norm, K(u) = k(sum_k |u_k| / ell_k) (eq. L1_kernel),
+ * or as a product, K(u) = prod_k k(|u_k| / ell_k) (eq. product_kernel), with
+ * one lengthscale per dimension (eq. scaled_kernel read per dimension).  It
+ * does so by the paper's decomposition of the kernel sum into weighted
+ * empirical CDFs (Propositions 1 and 2, eqs. L1_decomposition and
+ * product_decomposition), evaluated over a dominance structure whose sorted
+ * subsets are computed once per point set and kept on the device (Sec. 2.2.3).
+ * On top of the product it solves (K + sigma^2 I) alpha = y by conjugate
+ * gradients (App. A.1, Algorithm 2 with the identity preconditioner), with an
+ * optional generalised-least-squares fixed-effects mean (Sec. 3.2,
+ * Algorithm 1's GLS step).
+ *
+ * Conventions for every entry point:
+ *  - Pointers documented "device" must be device memory of the current CUDA
+ *    device; "host" means ordinary host memory.  The caller owns every
+ *    pointer it passes; the library never frees or keeps them past the call
+ *    (fgk_build copies what it needs).
+ *  - Arrays of points and vectors are row-major: X is N x d, V and Y are
+ *    N x nrhs (the nrhs values of one point are contiguous), in the caller's
+ *    original point order.
+ *  - Work is enqueued on the given stream (NULL = legacy default stream);
+ *    calls on one handle must be ordered on one stream (a handle owns one
+ *    workspace).  fgk_build and fgk_cg_solve synchronise that stream before
+ *    returning; fgk_matvec does not.
+ *  - Return value: FGK_OK (0) on success, a negative FGK_ERR_* code on
+ *    failure (nothing is thrown across the ABI); fgk_last_error() then gives
+ *    a message for the calling thread.  FGK_NOT_CONVERGED (1) is a soft
+ *    result of fgk_cg_solve.
+ */
+#ifndef FGK_H
+#define FGK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* cudaStream_t, spelled without the CUDA headers (same underlying type). */
+typedef struct CUstream_st *fgk_stream_t;
+
+typedef struct fgk_plan *fgk_handle;
+
+enum fgk_status {
+    FGK_OK = 0,
+    FGK_NOT_CONVERGED = 1,  /* CG stopped at maxit above tol; outputs hold the best iterate */
+    FGK_ERR_INVALID = -1,   /* an argument is out of range */
+    FGK_ERR_NONFINITE = -2, /* NaN or Inf in an input */
+    FGK_ERR_OOM = -3,       /* device allocation failed */
+    FGK_ERR_CUDA = -4,      /* a CUDA call failed; the message names it */
+    FGK_ERR_BREAKDOWN = -5, /* CG met p^T A p <= 0: the system is not positive definite */
+    FGK_ERR_TIMEOUT = -6,   /* a bounded device-side wait gave up */
+    FGK_ERR_INTERNAL = -7   /* a device-side consistency check failed */
+};
+
+enum fgk_kind { FGK_L1 = 0, FGK_PRODUCT = 1 };
+enum fgk_precision { FGK_F64 = 0, FGK_F32 = 1, FGK_MIXED = 2 };
+
+/* Device allocator used for the handle's memory and workspace.  alloc must
+ * return device memory usable on `stream` (NULL on failure); free releases
+ * it.  Default (or after passing NULL, NULL): cudaMallocAsync/cudaFreeAsync.
+ * The setting is process-wide and applies to allocations made after it. */
+typedef void *(*fgk_alloc_fn)(size_t bytes, fgk_stream_t stream, void *ctx);
+typedef void (*fgk_free_fn)(void *ptr, fgk_stream_t stream, void *ctx);
+int fgk_set_allocator(fgk_alloc_fn alloc, fgk_free_fn free_fn, void *ctx);
+
+/* Build the cached sort and dominance structure of a point set
+ * (Sec. 2.1: sorting then fast sum updating; Sec. 2.2.3: the sorted subsets
+ * of the divide and conquer stored in a data structure; eq. scaled_kernel
+ * for ell and outscale2).
+ *   X          device, N x d FP64 row-major; finite (else FGK_ERR_NONFINITE).
+ *   N          1 <= N <= 2^30.
+ *   d          1, 2 or 3.
+ *   two_nu     2 nu: 1, 3 or 5.
+ *   ell        host, d lengthscales, finite and > 0.
+ *   outscale2  varsigma^2 > 0 (1 when the kernel has no outputscale).
+ *   kind       FGK_L1 or FGK_PRODUCT (identical when two_nu == 1 or d == 1).
+ *   out        host; receives the handle (NULL on failure).
+ * The handle owns device memory of about fgk_bytes_estimate(...) bytes and
+ * must be released with fgk_destroy. */
+int fgk_build(const double *X, int64_t N, int d, int two_nu, const double *ell, double outscale2,
+              int kind, fgk_stream_t stream, fgk_handle *out);
+
+/* Y = K V (eq. Ky for nrhs columns at once; the kernel sum of eq. kde for
+ * every z in the point set).
+ *   V, Y       device, N x nrhs row-major, original point order; FP64 when
+ *              precision == FGK_F64, FP32 when precision == FGK_F32.  V must
+ *              be finite; V and Y must not overlap.
+ *   nrhs       >= 1.
+ *   precision  FGK_F64 (FP64 scans) or FGK_F32 (FP32 scans, FP32 in/out).
+ * Asynchronous on `stream`. */
+int fgk_matvec(fgk_handle h, const void *V, int nrhs, void *Y, int precision, fgk_stream_t stream);
+
+/* Per-solve report of fgk_cg_solve (host memory, filled on return). */
+typedef struct {
+    int32_t iterations;     /* CG iterations, summed over refinement sweeps */
+    int32_t refinements;    /* FP64 true-residual evaluations */
+    int32_t mvm_f32;        /* products taken with FP32 scans */
+    int32_t mvm_f64;        /* products taken with FP64 scans */
+    double max_true_resid;  /* max over solved columns of ||b - A x|| / ||b||, FP64 */
+    double *true_resid;     /* optional host array of nrhs + L doubles (columns
+                               [y, H]); written when not NULL */
+} fgk_cg_info;
+
+/* Solve (K + sigma2 I) alpha = y (eq. gp_mean_system) for nrhs columns by
+ * conjugate gradients (Algorithm 2, identity preconditioner, zero start),
+ * optionally with a linear fixed-effects mean m(x) = H beta estimated by
+ * generalised least squares, beta = (H^T A^{-1} H)^{-1} H^T A^{-1} y
+ * (Sec. 3.2), in which case alpha = A^{-1} (y - H beta) (eq. gp_mean).
+ *   y          device, N x nrhs FP64 row-major, original point order.
+ *   sigma2     noise variance >= 0.
+ *   H, L       fixed effects: H == NULL && L == 0: none; H == NULL && L == -1:
+ *              the default H = [1, x_1, ..., x_d] (L = 1 + d, unscaled x);
+ *              H != NULL: device N x L FP64 row-major, 1 <= L <= 8.
+ *   tol        stop when every column's true relative residual
+ *              ||b - A x||_2 / ||b||_2 (recomputed in FP64) is <= tol.
+ *   maxit      cap on CG iterations (all sweeps together).
+ *   mode       FGK_F64: FP64 scans throughout; FGK_MIXED: FP32 scans inside
+ *              CG with FP64 inner products and vectors, the residual
+ *              recomputed with FP64 scans and the solution corrected
+ *              (iterative refinement).
+ *   alpha      device, N x nrhs FP64 (output).
+ *   beta       device, L x nrhs FP64 (output) or NULL; ignored without H.
+ *   info       host, may be NULL.
+ * Returns FGK_OK, FGK_NOT_CONVERGED, FGK_ERR_BREAKDOWN (p^T A p <= 0, e.g.
+ * the indefinite L1 kernel at nu >= 3/2, d >= 2) or an error.  Synchronises
+ * `stream`. */
+int fgk_cg_solve(fgk_handle h, const double *y, int nrhs, double sigma2, const double *H, int L, double tol,
+                 int maxit, int mode, double *alpha, double *beta, fgk_cg_info *info, fgk_stream_t stream);
+
+/* Upper estimate, in bytes, of the device memory a handle for these sizes
+ * holds after fgk_build plus the workspace of fgk_cg_solve with nrhs
+ * columns (used for admission against a memory budget).  0 if invalid. */
+size_t fgk_bytes_estimate(int64_t N, int d, int two_nu, int kind, int nrhs);
+
+/* Release a handle and its device memory (stream-ordered on the stream of
+ * its last call).  NULL is ignored. */
+int fgk_destroy(fgk_handle h);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char *fgk_last_error(void);
+
+/* ---- inspection (tests and tools): copies of the cached structure ---- */
+
+typedef struct {
+    int64_t N;
+    int32_t d, two_nu, kind;
+    int32_t L;          /* ceil(log2 N) */
+    int32_t n_levels;   /* 1 (d=1), L (d=2), L(L+1)/2 (d=3) */
+    double outscale2;
+    double ell[3];
+    size_t device_bytes; /* held by the handle now */
+} fgk_plan_info;
+
+int fgk_get_info(fgk_handle h, fgk_plan_info *out);
+
+/* perm: host, N int32: the stable ascending order of the scaled coordinate
+ * x'_dim = x_dim * sqrt(2 nu) / ell_dim (ties by original index). */
+int fgk_get_permutation(fgk_handle h, int dim, int32_t *perm);
+
+/* Copy level `level` of the structure to host arrays (any may be NULL):
+ *   q     N uint32: point index in x'_1 order, per entry;
+ *   roles N uint8: bit 0 = role in the first split dimension, bit 1 = role
+ *         in the second (d = 3);
+ *   dl64, dl32  N gaps of the sweep coordinate to the previous entry of the
+ *         same segment (0 at a segment start);
+ *   off64, off32  N x (d-1) row-major offsets |x' - split| per split dim;
+ *   seg_size  the level's segment size (power of two).
+ * Synchronous. */
+int fgk_get_level(fgk_handle h, int level, uint32_t *q, uint8_t *roles, double *dl64, float *dl32,
+                  double *off64, float *off32, int64_t *seg_size);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FGK_H */

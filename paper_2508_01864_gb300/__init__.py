@@ -1,0 +1,26 @@
+"""GB300-native exact fast Matérn-kernel MVM and GP solve (arXiv 2508.01864).
+
+The compute path is libfgk (hand-written CUDA for sm_103a behind a C ABI,
+``include/fgk.h``); ``fgk`` is its thin Python binding.
+"""
+
+from .fgk import (  # noqa: F401
+    FGK_F32,
+    FGK_F64,
+    FGK_L1,
+    FGK_MIXED,
+    FGK_PRODUCT,
+    FgkError,
+    Handle,
+    fgk_build,
+    fgk_bytes_estimate,
+    fgk_cg_solve,
+    fgk_destroy,
+    fgk_get_info,
+    fgk_get_level,
+    fgk_get_permutation,
+    fgk_last_error,
+    fgk_matvec,
+    load,
+    use_torch_allocator,
+)

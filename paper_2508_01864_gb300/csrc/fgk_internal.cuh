@@ -1,0 +1,160 @@
+// Internal declarations shared by the libfgk translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "fgk.h"
+
+namespace fgk {
+
+// ---------------------------------------------------------------- errors
+void set_error(const char *fmt, ...);
+void clear_error();
+
+// Status carried through internal calls; converted to the C codes at the ABI.
+#define FGK_TRY(expr)                      \
+    do {                                   \
+        int _rc = (expr);                  \
+        if (_rc != FGK_OK) return _rc;     \
+    } while (0)
+
+#define FGK_CUDA(expr)                                                                        \
+    do {                                                                                      \
+        cudaError_t _e = (expr);                                                              \
+        if (_e != cudaSuccess) {                                                              \
+            ::fgk::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(_e), __FILE__, \
+                             __LINE__);                                                       \
+            return FGK_ERR_CUDA;                                                              \
+        }                                                                                     \
+    } while (0)
+
+#define FGK_LAUNCH_CHECK() FGK_CUDA(cudaGetLastError())
+
+// ---------------------------------------------------------------- memory
+void *dev_alloc(size_t bytes, cudaStream_t s);
+void dev_free(void *p, cudaStream_t s);
+
+// A device buffer owned by a plan (freed in the plan's destructor path).
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+// ---------------------------------------------------------------- device error word
+// Set by kernels whose bounded waits expire or whose checks fail (never a trap).
+enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_INTERNAL = 2 };
+
+// ---------------------------------------------------------------- constants
+constexpr int kMaxD = 3;
+constexpr int kMaxH = 8;
+
+// Level-scan tiling: a CTA owns kTile consecutive entries of one level.
+constexpr int kScanThreads = 128;
+constexpr int kScanEPT = 8;  // entries per thread (power of two)
+constexpr int kTile = kScanThreads * kScanEPT;
+
+// One unit of scan work: tile `tile` of level `level`.  For levels whose
+// segments are longer than a tile, `seg_tile0`/`seg_ntiles` give the tile
+// range of the segment and `agg` indexes the aggregate/carry slot.
+struct WorkItem {
+    int32_t level;
+    int32_t tile;
+    int32_t agg;        // -1 for short-segment levels
+    int32_t seg_tile0;  // first tile of this tile's segment (long levels)
+    int32_t seg_ntiles; // tiles in this tile's segment (long levels)
+    int32_t log2S;      // segment size of the level
+};
+
+// ---------------------------------------------------------------- plan
+struct Plan {
+    int64_t N = 0;
+    int d = 0, two_nu = 0, kind = 0, P = 0;
+    double s2 = 1.0;
+    double ell[kMaxD] = {0, 0, 0};
+    double a[kMaxD] = {0, 0, 0};  // sqrt(2 nu) / ell_k
+    int L = 0;
+    int nlev = 0;
+    cudaStream_t stream = nullptr;
+
+    // sort results (device)
+    int32_t *perm[kMaxD] = {nullptr, nullptr, nullptr};  // position in x'_k order -> point
+    int32_t *rank1 = nullptr;                            // point -> position in x'_1 order
+    double *xq[kMaxD] = {nullptr, nullptr, nullptr};     // x'_k of the point at q (x'_1 order)
+    double *xraw_q = nullptr;                            // N x d unscaled x in x'_1 order
+
+    // structure: nlev x N entries, level-major
+    uint32_t *lv_q = nullptr;  // q | r1 << 31 | r2 << 30
+    float *lv_dl32 = nullptr;
+    double *lv_dl64 = nullptr;
+    float *lv_off32 = nullptr;   // (d-1) arrays of nlev x N, dimension-major
+    double *lv_off64 = nullptr;
+    std::vector<int> lev_log2S;  // host
+
+    // scan work lists (device + host copies)
+    std::vector<WorkItem> items_host;
+    WorkItem *items = nullptr;     // all items
+    WorkItem *long_items = nullptr;
+    int n_items = 0, n_long = 0;
+    int n_long_segments = 0;
+    std::vector<int32_t> long_seg_host;  // [first agg, n tiles] per long segment
+    int32_t *long_seg = nullptr;
+
+    int *dev_err = nullptr;  // device error word
+
+    std::vector<Buf> owned;
+    size_t bytes_held = 0;
+
+    // workspace (grown on demand)
+    Buf ws;
+    int ws_users = 0;
+};
+
+int plan_alloc(Plan *p, void **ptr, size_t bytes);  // plan-owned allocation
+int check_dev_error(Plan *p, const char *where);    // reads and clears the error word (syncs)
+
+// ---------------------------------------------------------------- build steps
+int build_sort(Plan *p, const double *X);     // K0 + K1 (fgk_sort.cu)
+int build_levels(Plan *p);                    // K2 (fgk_struct.cu)
+int build_worklists(Plan *p);                 // host work lists for the scans (fgk_scan_*.cu)
+
+// ---------------------------------------------------------------- product
+// Y_q = s2 (V_q + sum_levels ...) for vectors in x'_1 order (q order).
+// Vin: FP64 or FP32 (vin_f64), Yout of the scan precision (f64 flag), both
+// N x nrhs row-major in q order.  Workspace is taken from p->ws.
+int mvm_q_f64(Plan *p, const double *Vq, int nrhs, double *Yq, cudaStream_t s);
+int mvm_q_f32(Plan *p, const void *Vq, bool vin_f64, int nrhs, float *Yq, cudaStream_t s);
+size_t mvm_ws_bytes(const Plan *p, int nrhs, bool f64);
+
+int ensure_ws(Plan *p, size_t bytes, cudaStream_t s);
+
+// gather/scatter between the caller's point order and q order
+int to_q_order(const Plan *p, const void *src, void *dst, int nrhs, int elem_bytes, cudaStream_t s);
+int from_q_order(const Plan *p, const void *src, void *dst, int nrhs, int elem_bytes, cudaStream_t s);
+
+// CG / refinement / GLS (fgk_solve.cu)
+int cg_solve(Plan *p, const double *y, int nrhs, double sigma2, const double *H, int L, double tol, int maxit,
+             int mode, double *alpha, double *beta, fgk_cg_info *info, cudaStream_t s);
+size_t solve_ws_bytes(const Plan *p, int ncols);
+
+inline int ceil_log2_i64(int64_t n) {
+    int l = 0;
+    while ((int64_t(1) << l) < n) ++l;
+    return l;
+}
+
+inline unsigned grid_for(int64_t n, int threads) {
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+}  // namespace fgk
+
+// The public opaque handle is the plan itself.
+struct fgk_plan : public fgk::Plan {};

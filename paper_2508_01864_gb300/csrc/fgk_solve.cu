@@ -1,0 +1,545 @@
+// K5-K7: the GP solve (K + sigma^2 I) alpha = y (eq. gp_mean_system) on top of
+// the product, with optional GLS fixed effects.
+//
+// CG (App. A.1, Algorithm 2 with the identity preconditioner and a zero
+// initial guess) runs on a block of columns at once; every column has its own
+// alpha_j = rho_j / p_j^T A p_j and beta_j = rho'_j / rho_j and stops on its
+// own once ||r_j|| is below its threshold (then its updates are masked).
+// Vectors, inner products and scalars are FP64 and stay on the device; the
+// host only reads a small status word every few iterations.  One iteration
+// (product, two reductions, three vector updates) is captured once into a
+// CUDA graph and replayed.
+//
+// Refinement.  The solve runs in sweeps: the residual R = B - A X is
+// recomputed with FP64 scans, CG solves A D = R to a relative threshold, and
+// X += D.  In FP64 mode the first sweep normally meets the tolerance and the
+// recomputation only confirms it; in mixed mode CG applies A with FP32 scans
+// (FP32 moments, FP64 vectors and inner products) and the FP64 sweeps correct
+// the solution until the true residual meets the tolerance (iterative
+// refinement).  The reported residuals are always the FP64 true residuals.
+//
+// Fixed effects (Sec. 3.2, the GLS step of Algorithm 1): the block is
+// [y, H]; with alpha_y = A^{-1} y and alpha_H = A^{-1} H,
+// beta = (H^T alpha_H)^{-1} H^T alpha_y and alpha = alpha_y - alpha_H beta.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "fgk_internal.cuh"
+
+namespace fgk {
+
+namespace {
+
+constexpr int kRedBlocks = 304;  // 2 x 152 SMs
+constexpr int kRedThreads = 256;
+constexpr int kMaxCols = 64;
+
+struct ColState {
+    double rho[kMaxCols];
+    double alpha[kMaxCols];
+    double beta[kMaxCols];
+    double thr2[kMaxCols];
+    int active[kMaxCols];
+    int iters[kMaxCols];
+    int n_active;
+    int breakdown;
+};
+
+// partial[b * ncols + j] = sum over this block's rows of a_ij * b_ij
+template <class TA, class TB>
+__device__ __forceinline__ void block_col_dots(const TA *__restrict__ a, const TB *__restrict__ b, double sb,
+                                               const double *__restrict__ c, int64_t N, int ncols,
+                                               double *__restrict__ partial) {
+    // sum_i a_ij * (b_ij + sb * c_ij)  (c may be NULL when sb == 0)
+    __shared__ double red[kRedThreads];
+    for (int j = 0; j < ncols; ++j) {
+        double acc = 0.0;
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t t = i * ncols + j;
+            double bb = (double)b[t];
+            if (c) bb += sb * c[t];
+            acc += (double)a[t] * bb;
+        }
+        red[threadIdx.x] = acc;
+        __syncthreads();
+        for (int s = kRedThreads / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) partial[blockIdx.x * ncols + j] = red[0];
+        __syncthreads();
+    }
+}
+
+__global__ void k_col_dots(const double *__restrict__ a, const double *__restrict__ b, int64_t N, int ncols,
+                           double *__restrict__ partial) {
+    block_col_dots<double, double>(a, b, 0.0, nullptr, N, ncols, partial);
+}
+
+__global__ void k_finalize_sums(const double *__restrict__ partial, int nblk, int ncols, double *__restrict__ out) {
+    const int j = threadIdx.x;
+    if (j >= ncols) return;
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += partial[b * ncols + j];
+    out[j] = s;
+}
+
+// pw_j = p_j^T (w_j + sigma2 p_j)
+template <class W>
+__global__ void k_dot_pAp(const double *__restrict__ p, const W *__restrict__ w, double sigma2, int64_t N, int ncols,
+                          double *__restrict__ partial, const ColState *__restrict__ st) {
+    if (st->n_active == 0) return;
+    block_col_dots<double, W>(p, w, sigma2, p, N, ncols, partial);
+}
+
+__global__ void k_alpha(const double *__restrict__ partial, int nblk, int ncols, ColState *__restrict__ st) {
+    const int j = threadIdx.x;
+    if (j >= ncols || st->n_active == 0) return;
+    double pw = 0.0;
+    for (int b = 0; b < nblk; ++b) pw += partial[b * ncols + j];
+    double a = 0.0;
+    if (st->active[j]) {
+        if (!(pw > 0.0)) {
+            st->active[j] = 0;
+            atomicOr(&st->breakdown, 1);
+        } else {
+            a = st->rho[j] / pw;
+        }
+    }
+    st->alpha[j] = a;
+}
+
+// x += alpha p; r -= alpha (w + sigma2 p); partial sums of r^2
+template <class W>
+__global__ void k_update_xr(double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
+                            const W *__restrict__ w, double sigma2, int64_t N, int ncols, double *__restrict__ partial,
+                            const ColState *__restrict__ st) {
+    if (st->n_active == 0) return;
+    __shared__ double red[kRedThreads];
+    for (int j = 0; j < ncols; ++j) {
+        const double a = st->alpha[j];
+        const bool act = st->active[j] != 0;
+        double acc = 0.0;
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t t = i * ncols + j;
+            double rv = r[t];
+            if (act) {
+                const double pv = p[t];
+                x[t] += a * pv;
+                rv -= a * ((double)w[t] + sigma2 * pv);
+                r[t] = rv;
+            }
+            acc += rv * rv;
+        }
+        red[threadIdx.x] = acc;
+        __syncthreads();
+        for (int s = kRedThreads / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) partial[blockIdx.x * ncols + j] = red[0];
+        __syncthreads();
+    }
+}
+
+__global__ void k_beta(const double *__restrict__ partial, int nblk, int ncols, ColState *__restrict__ st) {
+    __shared__ int s_act;
+    if (threadIdx.x == 0) s_act = 0;
+    __syncthreads();
+    const int j = threadIdx.x;
+    if (st->n_active != 0 && j < ncols) {
+        double rr = 0.0;
+        for (int b = 0; b < nblk; ++b) rr += partial[b * ncols + j];
+        double be = 0.0;
+        if (st->active[j]) {
+            st->iters[j] += 1;
+            be = st->rho[j] > 0.0 ? rr / st->rho[j] : 0.0;
+            st->rho[j] = rr;
+            if (rr <= st->thr2[j]) st->active[j] = 0;
+        }
+        st->beta[j] = be;
+        if (st->active[j]) atomicAdd(&s_act, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && st->n_active != 0) st->n_active = s_act;
+}
+
+__global__ void k_update_p(double *__restrict__ p, const double *__restrict__ r, int64_t N, int ncols,
+                           const ColState *__restrict__ st) {
+    if (st->n_active == 0) return;
+    const int64_t n = N * ncols;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(t % ncols);
+        if (st->active[j]) p[t] = r[t] + st->beta[j] * p[t];
+    }
+}
+
+// R = B - (Y + sigma2 X) with Y = K X
+__global__ void k_residual(const double *__restrict__ B, const double *__restrict__ Y, const double *__restrict__ X,
+                           double sigma2, int64_t n, double *__restrict__ R) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        R[t] = B[t] - (Y[t] + sigma2 * X[t]);
+}
+
+__global__ void k_axpy_all(double *__restrict__ X, const double *__restrict__ D, int64_t n) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        X[t] += D[t];
+}
+
+// B (q order, N x ncols) = [y | H]; H == NULL with L > 0 means [1, x].
+__global__ void k_assemble_rhs(const double *__restrict__ y, int nrhs, const double *__restrict__ H, int L,
+                               const double *__restrict__ xraw_q, int d, const int32_t *__restrict__ perm1, int64_t N,
+                               double *__restrict__ B, int *__restrict__ bad) {
+    const int ncols = nrhs + L;
+    const int64_t n = N * ncols;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = t / ncols;
+        const int j = (int)(t - q * ncols);
+        const int64_t i = perm1[q];
+        double v;
+        if (j < nrhs) v = y[i * nrhs + j];
+        else if (H) v = H[i * L + (j - nrhs)];
+        else v = (j == nrhs) ? 1.0 : xraw_q[q * d + (j - nrhs - 1)];
+        if (!isfinite(v)) atomicOr(bad, 1);
+        B[t] = v;
+    }
+}
+
+// GLS: C = H^T [alpha_y | alpha_H] (L x ncols) -> beta (L x nrhs) by Cholesky
+// of G = H^T alpha_H (symmetric positive definite in exact arithmetic);
+// single thread, L <= 8.
+__global__ void k_gls_beta(const double *__restrict__ C, int L, int nrhs, double *__restrict__ beta,
+                           int *__restrict__ bad) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int ncols = nrhs + L;
+    double G[kMaxH][kMaxH];
+    for (int a = 0; a < L; ++a)
+        for (int b = 0; b < L; ++b) G[a][b] = 0.5 * (C[a * ncols + nrhs + b] + C[b * ncols + nrhs + a]);
+    // Cholesky G = U^T U (upper), in place
+    for (int k = 0; k < L; ++k) {
+        double s = G[k][k];
+        for (int m = 0; m < k; ++m) s -= G[m][k] * G[m][k];
+        if (!(s > 0.0)) {
+            *bad = 1;
+            return;
+        }
+        G[k][k] = sqrt(s);
+        for (int c = k + 1; c < L; ++c) {
+            double t = G[k][c];
+            for (int m = 0; m < k; ++m) t -= G[m][k] * G[m][c];
+            G[k][c] = t / G[k][k];
+        }
+    }
+    for (int r = 0; r < nrhs; ++r) {
+        double z[kMaxH];
+        for (int k = 0; k < L; ++k) {  // U^T z = g
+            double t = C[k * ncols + r];
+            for (int m = 0; m < k; ++m) t -= G[m][k] * z[m];
+            z[k] = t / G[k][k];
+        }
+        for (int k = L - 1; k >= 0; --k) {  // U b = z
+            double t = z[k];
+            for (int m = k + 1; m < L; ++m) t -= G[k][m] * beta[m * nrhs + r];
+            beta[k * nrhs + r] = t / G[k][k];
+        }
+    }
+}
+
+// C[l * ncols + j] partials: sum_q H_ql X_qj, H taken from B's columns
+__global__ void k_hT_x(const double *__restrict__ B, const double *__restrict__ X, int64_t N, int nrhs, int L,
+                       double *__restrict__ partial) {
+    const int ncols = nrhs + L;
+    __shared__ double red[kRedThreads];
+    for (int l = 0; l < L; ++l)
+        for (int j = 0; j < ncols; ++j) {
+            double acc = 0.0;
+            for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N;
+                 q += (int64_t)gridDim.x * blockDim.x)
+                acc += B[q * ncols + nrhs + l] * X[q * ncols + j];
+            red[threadIdx.x] = acc;
+            __syncthreads();
+            for (int s = kRedThreads / 2; s > 0; s >>= 1) {
+                if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) partial[blockIdx.x * (L * ncols) + l * ncols + j] = red[0];
+            __syncthreads();
+        }
+}
+
+// alpha (caller order) = X_y - X_H beta, read through rank1
+__global__ void k_output_alpha(const double *__restrict__ X, int ncols, int nrhs, int L,
+                               const double *__restrict__ beta, const int32_t *__restrict__ rank1, int64_t N,
+                               double *__restrict__ alpha) {
+    const int64_t n = N * nrhs;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / nrhs;
+        const int r = (int)(t - i * nrhs);
+        const int64_t q = rank1[i];
+        double v = X[q * ncols + r];
+        for (int l = 0; l < L; ++l) v -= X[q * ncols + nrhs + l] * beta[l * nrhs + r];
+        alpha[t] = v;
+    }
+}
+
+double env_double(const char *name, double dflt) {
+    const char *s = getenv(name);
+    if (!s || !*s) return dflt;
+    char *end = nullptr;
+    double v = strtod(s, &end);
+    return (end && end != s) ? v : dflt;
+}
+
+}  // namespace
+
+size_t solve_ws_bytes(const Plan *p, int ncols) {
+    const size_t vec = (size_t)p->N * ncols * 8;
+    return 7 * vec + (size_t)kRedBlocks * kMaxCols * kMaxH * 8 + sizeof(ColState) + 4096;
+}
+
+int cg_solve(Plan *p, const double *y, int nrhs, double sigma2, const double *H, int L, double tol, int maxit,
+             int mode, double *alpha, double *beta, fgk_cg_info *info, cudaStream_t user_s) {
+    const int64_t N = p->N;
+    const int ncols = nrhs + std::max(L, 0);
+    if (ncols > kMaxCols) {
+        set_error("fgk_cg_solve: nrhs + L = %d exceeds %d", ncols, kMaxCols);
+        return FGK_ERR_INVALID;
+    }
+    // a private stream: the legacy default stream cannot be captured into a graph
+    cudaStream_t s;
+    FGK_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    cudaEvent_t ev;
+    FGK_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    FGK_CUDA(cudaEventRecord(ev, user_s));
+    FGK_CUDA(cudaStreamWaitEvent(s, ev, 0));
+    cudaStream_t saved = p->stream;
+    p->stream = s;
+
+    const size_t vec = (size_t)N * ncols;
+    const bool mixed = mode == FGK_MIXED;
+    size_t bytes = 6 * vec * 8 + (mixed ? vec * 4 : 0) + (size_t)kRedBlocks * kMaxCols * kMaxH * 8 +
+                   sizeof(ColState) + 1024;
+    char *w = (char *)dev_alloc(bytes, s);
+    if (!w) {
+        p->stream = saved;
+        set_error("fgk_cg_solve: workspace allocation of %zu bytes failed", bytes);
+        cudaStreamDestroy(s);
+        cudaEventDestroy(ev);
+        return FGK_ERR_OOM;
+    }
+    auto carve = [&](size_t nbytes) {
+        char *r = w;
+        w += (nbytes + 255) / 256 * 256;
+        return (void *)r;
+    };
+    double *B = (double *)carve(vec * 8);
+    double *X = (double *)carve(vec * 8);
+    double *D = (double *)carve(vec * 8);
+    double *Rv = (double *)carve(vec * 8);
+    double *Pv = (double *)carve(vec * 8);
+    double *W64 = (double *)carve(vec * 8);
+    float *W32 = mixed ? (float *)carve(vec * 4) : nullptr;
+    double *partial = (double *)carve((size_t)kRedBlocks * kMaxCols * kMaxH * 8);
+    ColState *st = (ColState *)carve(sizeof(ColState));
+
+    int rc = FGK_OK;
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraph_t graph = nullptr;
+    std::vector<double> bnorm(ncols), rnorm(ncols), sums(std::max(ncols, L * ncols));
+    int iters_total = 0, refinements = 0, n_f32 = 0, n_f64 = 0;
+    bool converged = false, breakdown = false;
+    const double inner_floor = env_double("FGK_MIXED_INNER_TOL", 1e-5);
+    const int check_every = 8;
+    int hbad = 0;
+    double *dsum = partial + (size_t)kRedBlocks * kMaxCols * kMaxH - 2 * kMaxCols * kMaxH;  // tail scratch
+
+    auto colnorms = [&](const double *A, std::vector<double> &out) -> int {
+        k_col_dots<<<kRedBlocks, kRedThreads, 0, s>>>(A, A, N, ncols, partial);
+        FGK_LAUNCH_CHECK();
+        k_finalize_sums<<<1, kMaxCols, 0, s>>>(partial, kRedBlocks, ncols, dsum);
+        FGK_LAUNCH_CHECK();
+        FGK_CUDA(cudaMemcpyAsync(out.data(), dsum, ncols * 8, cudaMemcpyDeviceToHost, s));
+        FGK_CUDA(cudaStreamSynchronize(s));
+        for (auto &v : out) v = std::sqrt(v);
+        return FGK_OK;
+    };
+    // residual R = B - A X with FP64 scans
+    auto true_residual = [&]() -> int {
+        FGK_TRY(mvm_q_f64(p, X, ncols, W64, s));
+        k_residual<<<kRedBlocks, kRedThreads, 0, s>>>(B, W64, X, sigma2, (int64_t)vec, Rv);
+        FGK_LAUNCH_CHECK();
+        ++refinements;
+        ++n_f64;
+        return colnorms(Rv, rnorm);
+    };
+    auto one_iteration = [&]() -> int {
+        if (mixed) {
+            FGK_TRY(mvm_q_f32(p, Pv, true, ncols, W32, s));
+            k_dot_pAp<float><<<kRedBlocks, kRedThreads, 0, s>>>(Pv, W32, sigma2, N, ncols, partial, st);
+        } else {
+            FGK_TRY(mvm_q_f64(p, Pv, ncols, W64, s));
+            k_dot_pAp<double><<<kRedBlocks, kRedThreads, 0, s>>>(Pv, W64, sigma2, N, ncols, partial, st);
+        }
+        FGK_LAUNCH_CHECK();
+        k_alpha<<<1, kMaxCols, 0, s>>>(partial, kRedBlocks, ncols, st);
+        FGK_LAUNCH_CHECK();
+        if (mixed)
+            k_update_xr<float><<<kRedBlocks, kRedThreads, 0, s>>>(D, Rv, Pv, W32, sigma2, N, ncols, partial, st);
+        else
+            k_update_xr<double><<<kRedBlocks, kRedThreads, 0, s>>>(D, Rv, Pv, W64, sigma2, N, ncols, partial, st);
+        FGK_LAUNCH_CHECK();
+        k_beta<<<1, kMaxCols, 0, s>>>(partial, kRedBlocks, ncols, st);
+        FGK_LAUNCH_CHECK();
+        k_update_p<<<kRedBlocks, kRedThreads, 0, s>>>(Pv, Rv, N, ncols, st);
+        FGK_LAUNCH_CHECK();
+        return FGK_OK;
+    };
+
+    do {
+        FGK_CUDA(cudaMemsetAsync(p->dev_err, 0, sizeof(int), s));
+        k_assemble_rhs<<<kRedBlocks, kRedThreads, 0, s>>>(y, nrhs, H, std::max(L, 0), p->xraw_q, p->d, p->perm[0], N,
+                                                          B, p->dev_err);
+        rc = cudaGetLastError() == cudaSuccess ? FGK_OK : FGK_ERR_CUDA;
+        if (rc) break;
+        FGK_CUDA(cudaMemcpyAsync(&hbad, p->dev_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        FGK_CUDA(cudaStreamSynchronize(s));
+        if (hbad) {
+            FGK_CUDA(cudaMemsetAsync(p->dev_err, 0, sizeof(int), s));
+            set_error("fgk_cg_solve: y or H holds a NaN or an infinity");
+            rc = FGK_ERR_NONFINITE;
+            break;
+        }
+        if ((rc = colnorms(B, bnorm))) break;
+        FGK_CUDA(cudaMemsetAsync(X, 0, vec * 8, s));
+        FGK_CUDA(cudaMemcpyAsync(Rv, B, vec * 8, cudaMemcpyDeviceToDevice, s));
+        rnorm = bnorm;
+        // warm the product once so its workspace exists before graph capture
+        if (mixed) {
+            if ((rc = mvm_q_f32(p, B, true, ncols, W32, s))) break;
+        }
+        if ((rc = mvm_q_f64(p, B, ncols, W64, s))) break;
+        const int max_sweeps = 30;
+        for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+            // converged?  (zero right-hand sides count as converged)
+            bool all = true;
+            for (int j = 0; j < ncols; ++j)
+                if (rnorm[j] > tol * bnorm[j]) all = false;
+            if (all) {
+                converged = true;
+                break;
+            }
+            if (iters_total >= maxit) break;
+            // sweep set-up: D = 0, r = p = R, rho = ||R||^2, thresholds
+            ColState hs;
+            std::memset(&hs, 0, sizeof(hs));
+            int nact = 0;
+            for (int j = 0; j < ncols; ++j) {
+                hs.rho[j] = rnorm[j] * rnorm[j];
+                double target = 0.5 * tol * bnorm[j];
+                if (mixed) target = std::max(target, inner_floor * rnorm[j]);
+                hs.thr2[j] = target * target;
+                hs.active[j] = rnorm[j] > tol * bnorm[j] ? 1 : 0;
+                nact += hs.active[j];
+            }
+            hs.n_active = nact;
+            FGK_CUDA(cudaMemcpyAsync(st, &hs, sizeof(hs), cudaMemcpyHostToDevice, s));
+            FGK_CUDA(cudaMemsetAsync(D, 0, vec * 8, s));
+            FGK_CUDA(cudaMemcpyAsync(Pv, Rv, vec * 8, cudaMemcpyDeviceToDevice, s));
+            if (!gexec) {
+                FGK_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+                int crc = one_iteration();
+                cudaError_t ce = cudaStreamEndCapture(s, &graph);
+                if (crc) {
+                    rc = crc;
+                    break;
+                }
+                FGK_CUDA(ce);
+                FGK_CUDA(cudaGraphInstantiate(&gexec, graph, 0));
+            }
+            int sweep_iters = 0;
+            ColState snap;
+            while (iters_total < maxit) {
+                const int k = std::min(check_every, maxit - iters_total);
+                for (int it = 0; it < k; ++it) FGK_CUDA(cudaGraphLaunch(gexec, s));
+                FGK_CUDA(cudaMemcpyAsync(&snap, st, sizeof(ColState), cudaMemcpyDeviceToHost, s));
+                FGK_CUDA(cudaStreamSynchronize(s));
+                int mx = 0;
+                for (int j = 0; j < ncols; ++j) mx = std::max(mx, snap.iters[j]);
+                iters_total += mx - sweep_iters;
+                sweep_iters = mx;
+                if (mixed) n_f32 += k; else n_f64 += k;
+                if (snap.breakdown) breakdown = true;
+                if (snap.n_active == 0 || breakdown) break;
+            }
+            if (breakdown) break;
+            k_axpy_all<<<kRedBlocks, kRedThreads, 0, s>>>(X, D, (int64_t)vec);
+            if ((rc = cudaGetLastError() == cudaSuccess ? FGK_OK : FGK_ERR_CUDA)) break;
+            if ((rc = true_residual())) break;
+        }
+        if (rc) break;
+        // GLS fixed effects
+        double *beta_dev = nullptr;
+        if (L > 0) {
+            beta_dev = partial;  // L x nrhs at the head of the scratch
+            double *part2 = partial + kMaxH * kMaxCols;
+            const int nb = 64;
+            k_hT_x<<<nb, kRedThreads, 0, s>>>(B, X, N, nrhs, L, part2);
+            FGK_LAUNCH_CHECK();
+            double *Cm = dsum;
+            k_finalize_sums<<<1, kMaxCols * kMaxH, 0, s>>>(part2, nb, L * ncols, Cm);
+            FGK_LAUNCH_CHECK();
+            FGK_CUDA(cudaMemsetAsync(p->dev_err, 0, sizeof(int), s));
+            k_gls_beta<<<1, 32, 0, s>>>(Cm, L, nrhs, beta_dev, p->dev_err);
+            FGK_LAUNCH_CHECK();
+            FGK_CUDA(cudaMemcpyAsync(&hbad, p->dev_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+            FGK_CUDA(cudaStreamSynchronize(s));
+            if (hbad) {
+                FGK_CUDA(cudaMemsetAsync(p->dev_err, 0, sizeof(int), s));
+                set_error("fgk_cg_solve: H^T A^{-1} H is not positive definite (collinear fixed effects?)");
+                rc = FGK_ERR_INVALID;
+                break;
+            }
+            if (beta) FGK_CUDA(cudaMemcpyAsync(beta, beta_dev, (size_t)L * nrhs * 8, cudaMemcpyDeviceToDevice, s));
+        }
+        k_output_alpha<<<kRedBlocks, kRedThreads, 0, s>>>(X, ncols, nrhs, std::max(L, 0), beta_dev, p->rank1, N,
+                                                           alpha);
+        FGK_LAUNCH_CHECK();
+        FGK_CUDA(cudaStreamSynchronize(s));
+    } while (0);
+
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    dev_free((void *)B, s);
+    cudaStreamSynchronize(s);
+    p->stream = saved;
+    cudaEventDestroy(ev);
+    cudaStreamDestroy(s);
+    if (info) {
+        info->iterations = iters_total;
+        info->refinements = refinements;
+        info->mvm_f32 = n_f32;
+        info->mvm_f64 = n_f64;
+        double mx = 0.0;
+        for (int j = 0; j < ncols; ++j) {
+            double r = bnorm[j] > 0 ? rnorm[j] / bnorm[j] : 0.0;
+            mx = std::max(mx, r);
+            if (info->true_resid) info->true_resid[j] = r;
+        }
+        info->max_true_resid = mx;
+    }
+    if (rc) return rc;
+    if (breakdown) {
+        set_error("fgk_cg_solve: p^T A p <= 0 met; the system is not positive definite");
+        return FGK_ERR_BREAKDOWN;
+    }
+    if (!converged) {
+        set_error("fgk_cg_solve: tolerance not reached within maxit = %d iterations", maxit);
+        return FGK_NOT_CONVERGED;
+    }
+    return FGK_OK;
+}
+
+}  // namespace fgk

@@ -1,0 +1,288 @@
+"""Thin Python binding of libfgk (``include/fgk.h``), same names as the C ABI.
+
+Argument marshalling only: torch tensors are checked for device, dtype and
+layout and passed to the library as raw pointers together with the current
+torch CUDA stream.  Every step of the product and the solve runs inside
+libfgk's CUDA kernels; there is no fallback path.  If the shared library is
+missing, ``load()`` raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libfgk.so")
+
+FGK_OK = 0
+FGK_NOT_CONVERGED = 1
+FGK_L1, FGK_PRODUCT = 0, 1
+FGK_F64, FGK_F32, FGK_MIXED = 0, 1, 2
+
+_STATUS = {
+    0: "FGK_OK", 1: "FGK_NOT_CONVERGED", -1: "FGK_ERR_INVALID", -2: "FGK_ERR_NONFINITE", -3: "FGK_ERR_OOM",
+    -4: "FGK_ERR_CUDA", -5: "FGK_ERR_BREAKDOWN", -6: "FGK_ERR_TIMEOUT", -7: "FGK_ERR_INTERNAL",
+}
+
+
+class FgkError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+        self.name = _STATUS.get(code, str(code))
+
+
+class fgk_cg_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("refinements", ctypes.c_int32), ("mvm_f32", ctypes.c_int32),
+                ("mvm_f64", ctypes.c_int32), ("max_true_resid", ctypes.c_double),
+                ("true_resid", ctypes.POINTER(ctypes.c_double))]
+
+
+class fgk_plan_info(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("d", ctypes.c_int32), ("two_nu", ctypes.c_int32), ("kind", ctypes.c_int32),
+                ("L", ctypes.c_int32), ("n_levels", ctypes.c_int32), ("outscale2", ctypes.c_double),
+                ("ell", ctypes.c_double * 3), ("device_bytes", ctypes.c_size_t)]
+
+
+EXPORTS = ["fgk_set_allocator", "fgk_build", "fgk_matvec", "fgk_cg_solve", "fgk_bytes_estimate", "fgk_destroy",
+           "fgk_last_error", "fgk_get_info", "fgk_get_permutation", "fgk_get_level"]
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load libfgk.so (built by ``paper_2508_01864_gb300.build``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise FileNotFoundError(f"libfgk.so not found at {p}; run paper_2508_01864_gb300.build.build() first")
+        lib = ctypes.CDLL(p)
+        vp, i64, i32, dbl, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+        lib.fgk_set_allocator.argtypes = [vp, vp, vp]
+        lib.fgk_set_allocator.restype = i32
+        lib.fgk_build.argtypes = [vp, i64, i32, i32, ctypes.POINTER(dbl), dbl, i32, vp, ctypes.POINTER(vp)]
+        lib.fgk_build.restype = i32
+        lib.fgk_matvec.argtypes = [vp, vp, i32, vp, i32, vp]
+        lib.fgk_matvec.restype = i32
+        lib.fgk_cg_solve.argtypes = [vp, vp, i32, dbl, vp, i32, dbl, i32, i32, vp, vp, ctypes.POINTER(fgk_cg_info),
+                                     vp]
+        lib.fgk_cg_solve.restype = i32
+        lib.fgk_bytes_estimate.argtypes = [i64, i32, i32, i32, i32]
+        lib.fgk_bytes_estimate.restype = sz
+        lib.fgk_destroy.argtypes = [vp]
+        lib.fgk_destroy.restype = i32
+        lib.fgk_last_error.argtypes = []
+        lib.fgk_last_error.restype = ctypes.c_char_p
+        lib.fgk_get_info.argtypes = [vp, ctypes.POINTER(fgk_plan_info)]
+        lib.fgk_get_info.restype = i32
+        lib.fgk_get_permutation.argtypes = [vp, i32, vp]
+        lib.fgk_get_permutation.restype = i32
+        lib.fgk_get_level.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, ctypes.POINTER(i64)]
+        lib.fgk_get_level.restype = i32
+        _lib = lib
+        return lib
+
+
+def _check(rc: int, allow_soft: bool = False) -> int:
+    if rc == FGK_OK or (allow_soft and rc == FGK_NOT_CONVERGED):
+        return rc
+    msg = load().fgk_last_error()
+    raise FgkError(rc, msg.decode() if msg else "")
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _two_nu(nu) -> int:
+    t = int(round(2 * float(nu)))
+    if t not in (1, 3, 5):
+        raise ValueError(f"nu must be 1/2, 3/2 or 5/2, got {nu}")
+    return t
+
+
+def _kind(kind) -> int:
+    if isinstance(kind, str):
+        return {"l1": FGK_L1, "product": FGK_PRODUCT}[kind.lower()]
+    return int(kind)
+
+
+def _dev_f64_2d(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float64:
+        raise TypeError(f"{name} must be float64")
+    if t.dim() == 1:
+        t = t.unsqueeze(1)
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous (row-major)")
+    return t
+
+
+@dataclass
+class Handle:
+    ptr: int
+    N: int
+    d: int
+    two_nu: int
+    kind: int
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        fgk_destroy(self)
+
+
+def fgk_build(X: torch.Tensor, nu, ell, outscale2: float = 1.0, kind="l1", stream=None) -> Handle:
+    """Build the cached sort and dominance structure (see include/fgk.h)."""
+    lib = load()
+    X = _dev_f64_2d(X, "X")
+    N, d = X.shape
+    ellv = [float(e) for e in torch.as_tensor(ell, dtype=torch.float64).reshape(-1).broadcast_to((d,)).tolist()]
+    ell_arr = (ctypes.c_double * d)(*ellv)
+    out = ctypes.c_void_p()
+    _check(lib.fgk_build(X.data_ptr(), N, d, _two_nu(nu), ell_arr, float(outscale2), _kind(kind), _stream(stream),
+                         ctypes.byref(out)))
+    return Handle(out.value, N, d, _two_nu(nu), _kind(kind))
+
+
+def fgk_matvec(h: Handle, V: torch.Tensor, precision="f64", out: torch.Tensor | None = None, stream=None):
+    """Y = K V (asynchronous on the stream)."""
+    lib = load()
+    prec = {"f64": FGK_F64, "f32": FGK_F32}[precision] if isinstance(precision, str) else int(precision)
+    dt = torch.float64 if prec == FGK_F64 else torch.float32
+    if not V.is_cuda or V.dtype != dt or not V.is_contiguous():
+        raise TypeError(f"V must be a contiguous CUDA {dt} tensor")
+    squeeze = V.dim() == 1
+    V2 = V.unsqueeze(1) if squeeze else V
+    if V2.shape[0] != h.N:
+        raise ValueError("V has the wrong number of rows")
+    if out is None:
+        out = torch.empty_like(V2)
+    _check(lib.fgk_matvec(h.ptr, V2.data_ptr(), V2.shape[1], out.data_ptr(), prec, _stream(stream)))
+    return out.squeeze(1) if squeeze else out
+
+
+def fgk_cg_solve(h: Handle, y: torch.Tensor, sigma2: float, H: torch.Tensor | None = None, L: int = 0,
+                 tol: float = 1e-8, maxit: int = 100000, mode="f64", stream=None, want_beta: bool = True):
+    """Solve (K + sigma2 I) alpha = y, optionally with GLS fixed effects.
+
+    Returns (alpha, beta or None, info dict, status) where status is FGK_OK or
+    FGK_NOT_CONVERGED; errors raise FgkError."""
+    lib = load()
+    y2 = _dev_f64_2d(y, "y")
+    nrhs = y2.shape[1]
+    m = {"f64": FGK_F64, "mixed": FGK_MIXED}[mode] if isinstance(mode, str) else int(mode)
+    Hp = 0
+    if H is not None:
+        H = _dev_f64_2d(H, "H")
+        L = H.shape[1]
+        Hp = H.data_ptr()
+    Leff = L if L >= 0 else 1 + h.d
+    alpha = torch.empty_like(y2)
+    beta = torch.empty((Leff, nrhs), dtype=torch.float64, device=y2.device) if (Leff > 0 and want_beta) else None
+    ncols = nrhs + max(Leff, 0)
+    res = (ctypes.c_double * ncols)()
+    info = fgk_cg_info()
+    info.true_resid = ctypes.cast(res, ctypes.POINTER(ctypes.c_double))
+    rc = lib.fgk_cg_solve(h.ptr, y2.data_ptr(), nrhs, float(sigma2), Hp, int(L), float(tol), int(maxit), m,
+                          alpha.data_ptr(), beta.data_ptr() if beta is not None else 0, ctypes.byref(info),
+                          _stream(stream))
+    _check(rc, allow_soft=True)
+    d = {"iterations": info.iterations, "refinements": info.refinements, "mvm_f32": info.mvm_f32,
+         "mvm_f64": info.mvm_f64, "max_true_resid": info.max_true_resid, "true_resid": list(res)}
+    if y.dim() == 1:
+        alpha = alpha.squeeze(1)
+    return alpha, beta, d, rc
+
+
+def fgk_bytes_estimate(N: int, d: int, nu, kind="l1", nrhs: int = 1) -> int:
+    return int(load().fgk_bytes_estimate(int(N), int(d), _two_nu(nu), _kind(kind), int(nrhs)))
+
+
+def fgk_destroy(h: Handle) -> None:
+    if h is not None and h.ptr:
+        _check(load().fgk_destroy(h.ptr))
+        h.ptr = 0
+
+
+def fgk_last_error() -> str:
+    m = load().fgk_last_error()
+    return m.decode() if m else ""
+
+
+def fgk_get_info(h: Handle) -> dict:
+    info = fgk_plan_info()
+    _check(load().fgk_get_info(h.ptr, ctypes.byref(info)))
+    return {"N": info.N, "d": info.d, "two_nu": info.two_nu, "kind": info.kind, "L": info.L,
+            "n_levels": info.n_levels, "outscale2": info.outscale2, "ell": list(info.ell)[:info.d],
+            "device_bytes": info.device_bytes}
+
+
+def fgk_get_permutation(h: Handle, dim: int):
+    import numpy as np
+
+    perm = np.empty(h.N, dtype=np.int32)
+    _check(load().fgk_get_permutation(h.ptr, int(dim), perm.ctypes.data))
+    return perm
+
+
+def fgk_get_level(h: Handle, level: int) -> dict:
+    import numpy as np
+
+    N, nof = h.N, max(h.d - 1, 0)
+    q = np.empty(N, dtype=np.uint32)
+    roles = np.empty(N, dtype=np.uint8)
+    dl64 = np.empty(N, dtype=np.float64)
+    dl32 = np.empty(N, dtype=np.float32)
+    off64 = np.empty((N, max(nof, 1)), dtype=np.float64)
+    off32 = np.empty((N, max(nof, 1)), dtype=np.float32)
+    S = ctypes.c_int64()
+    _check(load().fgk_get_level(h.ptr, int(level), q.ctypes.data, roles.ctypes.data, dl64.ctypes.data,
+                                dl32.ctypes.data, off64.ctypes.data if nof else 0, off32.ctypes.data if nof else 0,
+                                ctypes.byref(S)))
+    out = {"S": int(S.value), "q": q, "roles": roles, "dl64": dl64, "dl32": dl32}
+    if nof:
+        out["off64"] = off64[:, :nof]
+        out["off32"] = off32[:, :nof]
+    return out
+
+
+# ------------------------------------------------------------ torch allocator hook
+_ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_T = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+_hooks = []
+
+
+def use_torch_allocator(enable: bool = True) -> None:
+    """Route libfgk's device allocations through torch's caching allocator."""
+    lib = load()
+    if not enable:
+        _check(lib.fgk_set_allocator(None, None, None))
+        return
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                      int(stream) if stream else 0)
+        except Exception:  # allocation failure is reported to the library as NULL
+            return None
+
+    def _free(ptr, stream, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    a, f = _ALLOC_T(_alloc), _FREE_T(_free)
+    _hooks[:] = [a, f]
+    _check(lib.fgk_set_allocator(ctypes.cast(a, ctypes.c_void_p), ctypes.cast(f, ctypes.c_void_p), None))

@@ -19,3 +19,16 @@ def orc():
 
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def fgk_mod():
+    """The libfgk binding, built in-tree; GPU tests fail (not skip) without CUDA."""
+    import torch
+
+    assert torch.cuda.is_available(), "these tests need a CUDA GPU"
+    from paper_2508_01864_gb300 import build, fgk
+
+    build.build()
+    fgk.load()
+    return fgk

@@ -1,0 +1,86 @@
+"""The C ABI without a GPU: the library builds, loads, exports every function
+that include/fgk.h declares, and rejects invalid arguments before touching
+the device."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2508_01864_gb300 import build, fgk
+
+    build.build()
+    return fgk.load()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "fgk.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = set(re.findall(r"\b(fgk_[a-z_0-9]+)\s*\(", src))
+    return sorted(n for n in names if not n.endswith("_fn"))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ["fgk_build", "fgk_matvec", "fgk_cg_solve", "fgk_bytes_estimate", "fgk_destroy", "fgk_last_error",
+              "fgk_set_allocator"]:
+        assert n in names
+
+
+def test_exports_every_declared_symbol(lib):
+    for n in declared_functions():
+        assert hasattr(lib, n), n
+    from paper_2508_01864_gb300 import fgk
+
+    assert sorted(fgk.EXPORTS) == declared_functions()
+
+
+def test_bytes_estimate(lib):
+    from paper_2508_01864_gb300 import fgk
+
+    assert fgk.fgk_bytes_estimate(0, 2, 1.5) == 0
+    assert fgk.fgk_bytes_estimate(1000, 4, 1.5) == 0
+    small = fgk.fgk_bytes_estimate(10_000, 2, 1.5, "product", 1)
+    big = fgk.fgk_bytes_estimate(200_000, 2, 1.5, "product", 1)
+    d3 = fgk.fgk_bytes_estimate(200_000, 3, 2.5, "product", 5)
+    assert 0 < small < big < d3
+    # the structure of d=3 holds about L(L+1)/2 entries per point
+    assert d3 > 200_000 * 18 * 19 // 2 * 16
+
+
+def test_invalid_arguments_rejected_without_gpu(lib):
+    out = ctypes.c_void_p()
+    ell = (ctypes.c_double * 3)(0.1, 0.1, 0.1)
+    # N = 0, d = 4, two_nu = 2, ell <= 0, kind = 7: all rejected before any CUDA call
+    assert lib.fgk_build(1, 0, 2, 3, ell, 1.0, 0, None, ctypes.byref(out)) == -1
+    assert b"N" in lib.fgk_last_error()
+    assert lib.fgk_build(1, 10, 4, 3, ell, 1.0, 0, None, ctypes.byref(out)) == -1
+    assert lib.fgk_build(1, 10, 2, 2, ell, 1.0, 0, None, ctypes.byref(out)) == -1
+    bad_ell = (ctypes.c_double * 3)(0.1, -1.0, 0.1)
+    assert lib.fgk_build(1, 10, 2, 3, bad_ell, 1.0, 0, None, ctypes.byref(out)) == -1
+    assert lib.fgk_build(1, 10, 2, 3, ell, 1.0, 7, None, ctypes.byref(out)) == -1
+    assert lib.fgk_build(1, 10, 2, 3, ell, 0.0, 0, None, ctypes.byref(out)) == -1
+    assert out.value is None
+    assert lib.fgk_matvec(None, 1, 1, 1, 0, None) == -1
+    assert lib.fgk_destroy(None) == 0
+    assert lib.fgk_set_allocator(1, None, None) == -1
+    assert lib.fgk_set_allocator(None, None, None) == 0
+
+
+def test_binding_fails_loudly_without_library(tmp_path):
+    from paper_2508_01864_gb300 import fgk
+
+    with pytest.raises(FileNotFoundError):
+        fgk.load.__wrapped__ if hasattr(fgk.load, "__wrapped__") else None
+        saved = fgk._lib
+        fgk._lib = None
+        try:
+            fgk.load(str(tmp_path / "missing.so"))
+        finally:
+            fgk._lib = saved

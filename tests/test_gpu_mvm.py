@@ -1,0 +1,170 @@
+"""GPU parity of the build (sort permutations, dominance levels: bit-exact)
+and of the product K V (FP64 within 1e-12, FP32 within 1e-5 normwise
+relative error per column) against the oracle, through the C ABI."""
+
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from oracle import structure
+from gpu_util import colwise_relerr, to_dev
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 1e-5
+
+
+def build(fgk, p, kind):
+    return fgk.fgk_build(to_dev(p.X), p.nu, p.ell, outscale2=p.s2, kind=kind)
+
+
+STRUCT_CASES = [
+    (1, 1, "uniform"), (2, 2, "uniform"), (5, 2, "lattice"), (37, 2, "dups"), (1000, 2, "uniform"),
+    (1025, 2, "lattice"), (3000, 2, "dups"), (5000, 2, "uniform"), (2, 3, "uniform"), (33, 3, "lattice"),
+    (700, 3, "negzero"), (2500, 3, "uniform"), (4097, 3, "dups"), (3000, 1, "dups"), (9, 1, "negzero"),
+]
+
+
+@pytest.mark.parametrize("N,d,pattern", STRUCT_CASES)
+def test_structure_bit_exact(fgk_mod, N, d, pattern):
+    fgk = fgk_mod
+    p = workloads.small(N + 13 * d, N, d, nu=2.5, ell=[0.13, 0.29, 0.41][:d], pattern=pattern)
+    perms, _ = structure.permutations(p.X, p.nu, p.ell)
+    levs = structure.levels(p.X, p.nu, p.ell)
+    with build(fgk, p, "product") as h:
+        info = fgk.fgk_get_info(h)
+        assert info["n_levels"] == len(levs) == structure.n_levels(N, d)
+        for k in range(d):
+            assert np.array_equal(fgk.fgk_get_permutation(h, k), perms[k].astype(np.int32)), f"perm {k}"
+        for li, ref in enumerate(levs):
+            got = fgk.fgk_get_level(h, li)
+            assert got["S"] == ref["S"]
+            assert np.array_equal(got["q"], ref["q"]), f"level {li} q"
+            roles = np.zeros(N, dtype=np.uint8)
+            if d >= 2:
+                roles |= ref["r1"]
+            if d == 3:
+                roles |= ref["r2"] << 1
+            assert np.array_equal(got["roles"], roles), f"level {li} roles"
+            assert np.array_equal(got["dl64"].view(np.uint64), ref["dl64"].view(np.uint64)), f"level {li} dl64"
+            assert np.array_equal(got["dl32"].view(np.uint32), ref["dl32"].view(np.uint32)), f"level {li} dl32"
+            if d >= 2:
+                assert np.array_equal(got["off64"].view(np.uint64), ref["off64"].view(np.uint64)), f"level {li} off"
+                assert np.array_equal(got["off32"].view(np.uint32), ref["off32"].view(np.uint32))
+
+
+MVM_CASES = [
+    # N, d, pattern, nrhs
+    (1, 1, "uniform", 1), (2, 2, "uniform", 2), (3, 3, "uniform", 1), (7, 1, "lattice", 2),
+    (64, 2, "lattice", 1), (100, 3, "dups", 3), (1000, 1, "uniform", 2), (1500, 2, "negzero", 1),
+    (2500, 2, "dups", 2), (3001, 3, "uniform", 2), (5000, 1, "dups", 1), (5000, 2, "uniform", 3),
+    (2049, 3, "lattice", 1), (600, 2, "wide", 2),
+]
+
+
+@pytest.mark.parametrize("N,d,pattern,nrhs", MVM_CASES)
+@pytest.mark.parametrize("nu", [0.5, 1.5, 2.5])
+@pytest.mark.parametrize("kind", ["l1", "product"])
+def test_mvm_parity(fgk_mod, orc, N, d, pattern, nrhs, nu, kind):
+    fgk = fgk_mod
+    if kind == "product" and (nu == 0.5 or d == 1) and N > 100:
+        pytest.skip("same kernel as the L1 case")
+    ell = [0.2, 0.35, 0.5][:d] if pattern != "wide" else [10.0, 20.0, 30.0][:d]
+    p = workloads.small(7 * N + d, N, d, nu=nu, ell=ell, nrhs=nrhs, pattern=pattern, s2=1.7)
+    kcode = 0 if kind == "l1" else 1
+    ref = orc.mvm_brute(p.X, p.V, nu, p.ell, s2=p.s2, kind=kcode)
+    with build(fgk, p, kind) as h:
+        y64 = fgk.fgk_matvec(h, to_dev(p.V), "f64").cpu().numpy()
+        y32 = fgk.fgk_matvec(h, to_dev(p.V, torch.float32), "f32").cpu().numpy()
+    e64 = colwise_relerr(y64, ref)
+    e32 = colwise_relerr(y32, ref)
+    assert (e64 <= TOL64).all(), e64
+    assert (e32 <= TOL32).all(), e32
+
+
+def test_mvm_c1_full(fgk_mod, orc):
+    """The d=1 configuration at full size (N=4096, nu=1/2, ell=0.2)."""
+    fgk = fgk_mod
+    p = workloads.c1()
+    ref = orc.mvm_brute(p.X, p.V, p.nu, p.ell)
+    with build(fgk, p, "l1") as h:
+        for prec, tol, dt in (("f64", TOL64, torch.float64), ("f32", TOL32, torch.float32)):
+            y = fgk.fgk_matvec(h, to_dev(p.V, dt), prec).cpu().numpy()
+            assert (colwise_relerr(y, ref) <= tol).all()
+
+
+def sampled_rows(N, k, seed):
+    rng = np.random.default_rng(seed)
+    rows = rng.choice(N, size=min(k, N), replace=False)
+    return np.sort(np.concatenate([rows, [0, N - 1]]))
+
+
+@pytest.mark.parametrize("kind", ["product", "l1"])
+def test_mvm_c2_full_size_sampled(fgk_mod, orc, kind):
+    """d=2, N=200000, nu=3/2, ell=(0.1,0.3): every output row is computed on
+    the GPU, 400 sampled rows are checked against the brute-force oracle."""
+    fgk = fgk_mod
+    p = workloads.c2()
+    rng = np.random.default_rng(22)
+    V = rng.standard_normal((p.N, 2))
+    rows = sampled_rows(p.N, 400, 5)
+    ref = orc.mvm_brute(p.X, V, p.nu, p.ell, kind=0 if kind == "l1" else 1, rows=rows)
+    with build(fgk, p, kind) as h:
+        y64 = fgk.fgk_matvec(h, to_dev(V), "f64").cpu().numpy()[rows]
+        y32 = fgk.fgk_matvec(h, to_dev(V, torch.float32), "f32").cpu().numpy()[rows]
+    assert (colwise_relerr(y64, ref) <= TOL64).all()
+    assert (colwise_relerr(y32, ref) <= TOL32).all()
+
+
+def test_mvm_c3_full_size_sampled(fgk_mod, orc):
+    """d=3, N=500000, nu=5/2, product kernel on the Gaussian-mixture points."""
+    fgk = fgk_mod
+    p = workloads.c3()
+    rng = np.random.default_rng(33)
+    V = rng.standard_normal((p.N, 1))
+    rows = sampled_rows(p.N, 150, 6)
+    ref = orc.mvm_brute(p.X, V, p.nu, p.ell, kind=1, rows=rows)
+    with build(fgk, p, "product") as h:
+        y64 = fgk.fgk_matvec(h, to_dev(V), "f64").cpu().numpy()[rows]
+        y32 = fgk.fgk_matvec(h, to_dev(V, torch.float32), "f32").cpu().numpy()[rows]
+    assert (colwise_relerr(y64, ref) <= TOL64).all()
+    assert (colwise_relerr(y32, ref) <= TOL32).all()
+
+
+def test_nonfinite_input_rejected(fgk_mod):
+    fgk = fgk_mod
+    X = np.random.default_rng(1).uniform(size=(50, 2))
+    X[17, 1] = np.nan
+    with pytest.raises(fgk.FgkError) as e:
+        fgk.fgk_build(to_dev(X), 1.5, [0.2, 0.2])
+    assert e.value.code == -2
+    X[17, 1] = np.inf
+    with pytest.raises(fgk.FgkError):
+        fgk.fgk_build(to_dev(X), 1.5, [0.2, 0.2])
+
+
+def test_invalid_arguments(fgk_mod):
+    fgk = fgk_mod
+    X = to_dev(np.random.default_rng(2).uniform(size=(20, 2)))
+    with pytest.raises(fgk.FgkError):
+        fgk.fgk_build(X, 1.0, [0.2, 0.2])
+    with pytest.raises(fgk.FgkError):
+        fgk.fgk_build(X, 1.5, [0.2, 0.0])
+    with fgk.fgk_build(X, 1.5, [0.2, 0.2]) as h:
+        with pytest.raises(TypeError):
+            fgk.fgk_matvec(h, torch.zeros(20, dtype=torch.float32, device="cuda"), "f64")
+
+
+def test_permutation_equivariance_and_linearity(fgk_mod):
+    fgk = fgk_mod
+    p = workloads.small(77, 3000, 2, nu=1.5, ell=[0.1, 0.3], nrhs=2)
+    perm = np.random.default_rng(3).permutation(p.N)
+    with fgk.fgk_build(to_dev(p.X), p.nu, p.ell, kind="product") as h1, \
+            fgk.fgk_build(to_dev(p.X[perm]), p.nu, p.ell, kind="product") as h2:
+        y1 = fgk.fgk_matvec(h1, to_dev(p.V)).cpu().numpy()
+        y2 = fgk.fgk_matvec(h2, to_dev(p.V[perm])).cpu().numpy()
+        assert np.allclose(y2, y1[perm], rtol=1e-12, atol=1e-12 * np.abs(y1).max())
+        comb = fgk.fgk_matvec(h1, to_dev(2 * p.V[:, :1] - 3 * p.V[:, 1:])).cpu().numpy()
+        assert np.allclose(comb, 2 * y1[:, :1] - 3 * y1[:, 1:], atol=1e-12 * np.abs(y1).max())
