@@ -102,10 +102,17 @@ int fgk_build(const double *X, int64_t N, int d, int two_nu, const double *ell, 
  * Asynchronous on `stream`. */
 int fgk_matvec(fgk_handle h, const void *V, int nrhs, void *Y, int precision, fgk_stream_t stream);
 
+/* Y = K V with V and Y in the plan's internal point order: row q holds the
+ * point perm_1[q] (fgk_get_permutation(h, 0, ...)), i.e. the points sorted
+ * by their first scaled coordinate.  Iterative methods that keep their
+ * vectors in this order (as fgk_cg_solve does) skip the two permutations of
+ * fgk_matvec.  Arguments otherwise as fgk_matvec.  Asynchronous. */
+int fgk_matvec_q(fgk_handle h, const void *Vq, int nrhs, void *Yq, int precision, fgk_stream_t stream);
+
 /* Per-solve report of fgk_cg_solve (host memory, filled on return). */
 typedef struct {
-    int32_t iterations;     /* CG iterations, summed over refinement sweeps */
-    int32_t refinements;    /* FP64 true-residual evaluations */
+    int32_t iterations;     /* CG iterations (the most any column took) */
+    int32_t refinements;    /* FP64 true-residual evaluations (residual replacements) */
     int32_t mvm_f32;        /* products taken with FP32 scans */
     int32_t mvm_f64;        /* products taken with FP64 scans */
     double max_true_resid;  /* max over solved columns of ||b - A x|| / ||b||, FP64 */
@@ -125,11 +132,14 @@ typedef struct {
  *              H != NULL: device N x L FP64 row-major, 1 <= L <= 8.
  *   tol        stop when every column's true relative residual
  *              ||b - A x||_2 / ||b||_2 (recomputed in FP64) is <= tol.
- *   maxit      cap on CG iterations (all sweeps together).
+ *   maxit      cap on CG iterations.
  *   mode       FGK_F64: FP64 scans throughout; FGK_MIXED: FP32 scans inside
  *              CG with FP64 inner products and vectors, the residual
- *              recomputed with FP64 scans and the solution corrected
- *              (iterative refinement).
+ *              recomputed with FP64 scans whenever the
+ *              recursive residual has dropped by a factor (env
+ *              FGK_MIXED_DELTA, default 0.1) and substituted for it, the
+ *              FP64 solution being corrected in place (iterative refinement
+ *              without restarting the Krylov space).
  *   alpha      device, N x nrhs FP64 (output).
  *   beta       device, L x nrhs FP64 (output) or NULL; ignored without H.
  *   info       host, may be NULL.
@@ -150,6 +160,20 @@ int fgk_destroy(fgk_handle h);
 
 /* Message for the last failing call on this thread ("" if none). */
 const char *fgk_last_error(void);
+
+/* ---- instrumentation (tools) ---- */
+
+/* Number of CUDA kernels the library has launched in this process (each
+ * replay of a captured CG iteration counts its kernels). */
+uint64_t fgk_kernel_launches(void);
+
+/* CUDA-event timing of the main scan kernel (the output pass of the level
+ * scans).  enable = 1 clears the totals and starts bracketing every launch
+ * of that kernel made outside graph capture with events on its stream;
+ * enable = 0 stops; enable = -1 only reads.  total_ms and launches (either
+ * may be NULL) receive the accumulated elapsed time and launch count, after
+ * waiting for the recorded events. */
+int fgk_scan_timing(int enable, double *total_ms, int64_t *launches);
 
 /* ---- inspection (tests and tools): copies of the cached structure ---- */
 

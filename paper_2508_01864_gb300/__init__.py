@@ -20,7 +20,10 @@ from .fgk import (  # noqa: F401
     fgk_get_level,
     fgk_get_permutation,
     fgk_last_error,
+    fgk_kernel_launches,
     fgk_matvec,
+    fgk_matvec_q,
+    fgk_scan_timing,
     load,
     use_torch_allocator,
 )

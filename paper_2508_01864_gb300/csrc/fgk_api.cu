@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 
 #include "fgk_internal.cuh"
@@ -20,6 +21,38 @@ void set_error(const char *fmt, ...) {
     va_end(ap);
 }
 void clear_error() { g_err[0] = 0; }
+
+// ---------------------------------------------------------------- launch counter / scan timing
+static std::atomic<int64_t> g_launches{0};
+void add_kernel_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+uint64_t kernel_launch_count() { return (uint64_t)g_launches.load(std::memory_order_relaxed); }
+
+static std::mutex g_timing_mu;
+static std::atomic<bool> g_timing_on{false};
+static std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_timing_events;
+static double g_timing_ms = 0.0;
+static int64_t g_timing_n = 0;
+
+bool scan_timing_enabled() { return g_timing_on.load(std::memory_order_relaxed); }
+void scan_timing_record(cudaEvent_t start, cudaEvent_t stop) {
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    g_timing_events.emplace_back(start, stop);
+}
+// folds recorded event pairs into the totals (synchronises on each pair)
+static int timing_drain() {
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    for (auto &e : g_timing_events) {
+        FGK_CUDA(cudaEventSynchronize(e.second));
+        float ms = 0.f;
+        FGK_CUDA(cudaEventElapsedTime(&ms, e.first, e.second));
+        g_timing_ms += ms;
+        ++g_timing_n;
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
+    g_timing_events.clear();
+    return FGK_OK;
+}
 
 // ---------------------------------------------------------------- allocator
 static std::mutex g_alloc_mu;
@@ -336,11 +369,42 @@ int fgk_matvec(fgk_handle h, const void *V, int nrhs, void *Y, int precision, fg
     void *Yq = tmp + ((vb + 255) / 256) * 256;
     int rc = to_q_order(p, V, Vq, nrhs, eb, s);
     if (rc == FGK_OK)
-        rc = precision == FGK_F64 ? mvm_q_f64(p, (const double *)Vq, nrhs, (double *)Yq, s)
-                                  : mvm_q_f32(p, Vq, false, nrhs, (float *)Yq, s);
+        rc = precision == FGK_F64 ? mvm_q_f64(p, (const double *)Vq, nrhs, (double *)Yq, s, nullptr)
+                                  : mvm_q_f32(p, Vq, false, nrhs, (float *)Yq, s, nullptr);
     if (rc == FGK_OK) rc = from_q_order(p, Yq, Y, nrhs, eb, s);
     dev_free(tmp, s);
     return rc;
+}
+
+int fgk_matvec_q(fgk_handle h, const void *Vq, int nrhs, void *Yq, int precision, fgk_stream_t stream) {
+    clear_error();
+    if (!h || !Vq || !Yq || nrhs < 1 || (precision != FGK_F64 && precision != FGK_F32)) {
+        set_error("fgk_matvec_q: bad argument");
+        return FGK_ERR_INVALID;
+    }
+    Plan *p = h;
+    cudaStream_t s = (cudaStream_t)stream;
+    p->stream = s;
+    return precision == FGK_F64 ? mvm_q_f64(p, (const double *)Vq, nrhs, (double *)Yq, s, nullptr)
+                                : mvm_q_f32(p, Vq, false, nrhs, (float *)Yq, s, nullptr);
+}
+
+uint64_t fgk_kernel_launches(void) { return kernel_launch_count(); }
+
+int fgk_scan_timing(int enable, double *total_ms, int64_t *launches) {
+    clear_error();
+    int rc = timing_drain();
+    if (rc != FGK_OK) return rc;
+    if (total_ms) *total_ms = g_timing_ms;
+    if (launches) *launches = g_timing_n;
+    if (enable >= 0) {
+        if (enable == 1 && !g_timing_on.load()) {
+            g_timing_ms = 0.0;
+            g_timing_n = 0;
+        }
+        g_timing_on.store(enable == 1);
+    }
+    return FGK_OK;
 }
 
 int fgk_cg_solve(fgk_handle h, const double *y, int nrhs, double sigma2, const double *H, int L, double tol,

@@ -34,7 +34,18 @@ void clear_error();
         }                                                                                     \
     } while (0)
 
-#define FGK_LAUNCH_CHECK() FGK_CUDA(cudaGetLastError())
+// Every kernel launch is followed by FGK_LAUNCH_CHECK(), which also counts it.
+void add_kernel_launches(int64_t n);
+uint64_t kernel_launch_count();
+#define FGK_LAUNCH_CHECK()                    \
+    do {                                      \
+        ::fgk::add_kernel_launches(1);        \
+        FGK_CUDA(cudaGetLastError());         \
+    } while (0)
+
+// Optional CUDA-event timing of the main scan kernel (tools; off by default).
+bool scan_timing_enabled();
+void scan_timing_record(cudaEvent_t start, cudaEvent_t stop);
 
 // ---------------------------------------------------------------- memory
 void *dev_alloc(size_t bytes, cudaStream_t s);
@@ -127,8 +138,10 @@ int build_worklists(Plan *p);                 // host work lists for the scans (
 // Y_q = s2 (V_q + sum_levels ...) for vectors in x'_1 order (q order).
 // Vin: FP64 or FP32 (vin_f64), Yout of the scan precision (f64 flag), both
 // N x nrhs row-major in q order.  Workspace is taken from p->ws.
-int mvm_q_f64(Plan *p, const double *Vq, int nrhs, double *Yq, cudaStream_t s);
-int mvm_q_f32(Plan *p, const void *Vq, bool vin_f64, int nrhs, float *Yq, cudaStream_t s);
+// gate (device, may be NULL): when it points at 0 every kernel of the product
+// returns at once (used inside captured CG iterations after convergence).
+int mvm_q_f64(Plan *p, const double *Vq, int nrhs, double *Yq, cudaStream_t s, const int *gate);
+int mvm_q_f32(Plan *p, const void *Vq, bool vin_f64, int nrhs, float *Yq, cudaStream_t s, const int *gate);
 size_t mvm_ws_bytes(const Plan *p, int nrhs, bool f64);
 
 int ensure_ws(Plan *p, size_t bytes, cudaStream_t s);

@@ -37,9 +37,11 @@
 // so a segment is scanned in parallel: each thread folds kScanEPT entries,
 // threads of one segment combine by warp shuffles and shared memory, and
 // segments longer than a tile receive the aggregate of their earlier
-// (forward) or later (backward) tiles from a separate carry pass.  e^{-T} is
-// carried as a product of per-entry factors over a logarithmic-depth tree,
-// never as a long sequential chain.
+// (forward) or later (backward) tiles from a separate carry pass.  The decay
+// of a run is recomputed as e^{-T} from its summed gap T whenever runs are
+// composed, never carried as a product of per-entry factors: a factor near 1
+// holds the decay 1 - e^{-g} to only ~eps/g relative accuracy, and a product
+// of thousands of them would turn that into a visible error in the distance.
 #pragma once
 
 #include <type_traits>
@@ -57,7 +59,7 @@ struct Traits {
     static constexpr int NA = (KIND == FGK_PRODUCT && NOFF > 0 && P > 1) ? ipow_c(P, NOFF) : 1;
     static constexpr int MOM = NA * P;
     static constexpr int NCH = 1 << NOFF;
-    static constexpr int AG = 2 + MOM;  // T, E = e^{-T}, moments
+    static constexpr int AG = 1 + MOM;  // summed gap T, then the moments
 };
 
 template <class R>
@@ -75,6 +77,7 @@ struct ScanArgs {
     R *agg;        // SCAN_AGG: tile aggregates out; SCAN_OUT: carries in
     R s2;
     int *err;
+    const int *gate;  // NULL, or a device int: 0 = skip the whole product
 };
 
 template <class R>
@@ -211,25 +214,23 @@ __device__ __forceinline__ R read_query(const R *M, const R *o, const R *eo) {
     }
 }
 
-// x = prev then x   (prev precedes x in the walk direction)
+// x = prev then x   (prev precedes x in the walk direction): the moments of
+// prev are stepped across x's span T (decay e^{-T}) and added to x's.
 template <class R, int P, int AG>
 __device__ __forceinline__ void compose_after(R *x, const R *prev) {
-    R tmp[AG - 2];
+    R tmp[AG - 1];
 #pragma unroll
-    for (int m = 0; m < AG - 2; ++m) tmp[m] = prev[2 + m];
-    step_all<R, P, AG - 2>(tmp, x[0], x[1]);
+    for (int m = 0; m < AG - 1; ++m) tmp[m] = prev[1 + m];
+    step_all<R, P, AG - 1>(tmp, x[0], exp_neg<R>(x[0]));
 #pragma unroll
-    for (int m = 0; m < AG - 2; ++m) x[2 + m] += tmp[m];
+    for (int m = 0; m < AG - 1; ++m) x[1 + m] += tmp[m];
     x[0] += prev[0];
-    x[1] *= prev[1];
 }
 
 template <class R, int AG>
 __device__ __forceinline__ void set_identity(R *x) {
-    x[0] = R(0);
-    x[1] = R(1);
 #pragma unroll
-    for (int m = 2; m < AG; ++m) x[m] = R(0);
+    for (int m = 0; m < AG; ++m) x[m] = R(0);
 }
 
 constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -266,6 +267,7 @@ __global__ void __launch_bounds__(kScanThreads) k_level_scan(ScanArgs<R> A) {
     R *s_w = (R *)(smem + Lay::w_off);
     R *s_wex = (R *)(smem + Lay::wex_off);
 
+    if (A.gate && *A.gate == 0) return;
     const WorkItem wi = A.items[blockIdx.x];
     const int64_t N = A.N;
     const int64_t base = (int64_t)wi.tile * kTile;
@@ -330,9 +332,8 @@ __global__ void __launch_bounds__(kScanThreads) k_level_scan(ScanArgs<R> A) {
                         const int j = j0 + i;
                         const R g = dir == 0 ? s_dl[j] : s_dl[j + 1];
                         const R eg = dir == 0 ? s_edl[j] : s_edl[j + 1];
-                        step_all<R, P, MOM>(cur + 2, g, eg);
+                        step_all<R, P, MOM>(cur + 1, g, eg);
                         cur[0] += g;
-                        cur[1] *= eg;
                         if (j < cnt) {
                             const int role = NOFF == 0 ? 0 : (int)(s_q[j] >> (32 - NOFF));
                             if (role == c) {
@@ -342,7 +343,7 @@ __global__ void __launch_bounds__(kScanThreads) k_level_scan(ScanArgs<R> A) {
                                     o[k] = s_o[k * kTile + j];
                                     eo[k] = s_eo[k * kTile + j];
                                 }
-                                insert_src<R, P, NOFF, KIND>(cur + 2, v[i], o, eo);
+                                insert_src<R, P, NOFF, KIND>(cur + 1, v[i], o, eo);
                             }
                         }
                     }
@@ -418,7 +419,7 @@ __global__ void __launch_bounds__(kScanThreads) k_level_scan(ScanArgs<R> A) {
                 // 3. walk again from the carried-in moments and read the queries
                 R st[MOM];
 #pragma unroll
-                for (int m = 0; m < MOM; ++m) st[m] = excl[2 + m];
+                for (int m = 0; m < MOM; ++m) st[m] = excl[1 + m];
 #pragma unroll
                 for (int ii = 0; ii < EPT; ++ii) {
                     const int i = dir == 0 ? ii : EPT - 1 - ii;
@@ -462,7 +463,8 @@ __global__ void __launch_bounds__(kScanThreads) k_level_scan(ScanArgs<R> A) {
 // after it (backward).  One thread per (segment, direction, rhs, channel).
 template <class R, int P, int NOFF, int KIND>
 __global__ void k_carry_scan(const R *__restrict__ agg, R *__restrict__ carry, const int32_t *__restrict__ segs,
-                             int nseg, int nrhs) {
+                             int nseg, int nrhs, const int *__restrict__ gate) {
+    if (gate && *gate == 0) return;
     using Tr = Traits<P, NOFF, KIND>;
     constexpr int AG = Tr::AG, NCH = Tr::NCH;
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -491,7 +493,9 @@ __global__ void k_carry_scan(const R *__restrict__ agg, R *__restrict__ carry, c
 }
 
 template <class R>
-__global__ void k_diag_init(const void *__restrict__ V, int vin_f64, int64_t n, R s2, R *__restrict__ Y) {
+__global__ void k_diag_init(const void *__restrict__ V, int vin_f64, int64_t n, R s2, R *__restrict__ Y,
+                            const int *__restrict__ gate) {
+    if (gate && *gate == 0) return;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const R v = vin_f64 ? (R)((const double *)V)[i] : (R)((const float *)V)[i];
@@ -499,7 +503,7 @@ __global__ void k_diag_init(const void *__restrict__ V, int vin_f64, int64_t n, 
 }
 
 template <class R, int P, int NOFF, int KIND>
-int run_levels(Plan *p, const void *Vq, bool vin64, int nrhs, R *Yq, R *ws, cudaStream_t s) {
+int run_levels(Plan *p, const void *Vq, bool vin64, int nrhs, R *Yq, R *ws, cudaStream_t s, const int *gate) {
     using Tr = Traits<P, NOFF, KIND>;
     using Lay = SmemLayout<R, P, NOFF, KIND>;
     static bool attr_set = false;
@@ -522,6 +526,7 @@ int run_levels(Plan *p, const void *Vq, bool vin64, int nrhs, R *Yq, R *ws, cuda
     A.Y = Yq;
     A.s2 = (R)p->s2;
     A.err = p->dev_err;
+    A.gate = gate;
     const size_t per_slot = (size_t)2 * nrhs * Tr::NCH * Tr::AG;
     R *agg = ws;
     R *carry = ws + (size_t)p->n_long * per_slot;
@@ -532,33 +537,46 @@ int run_levels(Plan *p, const void *Vq, bool vin64, int nrhs, R *Yq, R *ws, cuda
         FGK_LAUNCH_CHECK();
         const int64_t nthr = (int64_t)p->n_long_segments * 2 * nrhs * Tr::NCH;
         k_carry_scan<R, P, NOFF, KIND><<<grid_for(nthr, 128), 128, 0, s>>>(agg, carry, p->long_seg,
-                                                                           p->n_long_segments, nrhs);
+                                                                           p->n_long_segments, nrhs, gate);
         FGK_LAUNCH_CHECK();
     }
     if (p->n_items > 0) {
         A.items = p->items;
         A.agg = carry;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (scan_timing_enabled() && cudaStreamIsCapturing(s, &cs) == cudaSuccess &&
+            cs == cudaStreamCaptureStatusNone) {
+            FGK_CUDA(cudaEventCreate(&e0));
+            FGK_CUDA(cudaEventCreate(&e1));
+            FGK_CUDA(cudaEventRecord(e0, s));
+        }
         k_level_scan<R, P, NOFF, KIND, SCAN_OUT><<<p->n_items, kScanThreads, Lay::bytes, s>>>(A);
         FGK_LAUNCH_CHECK();
+        if (e0) {
+            FGK_CUDA(cudaEventRecord(e1, s));
+            scan_timing_record(e0, e1);
+        }
     }
     return FGK_OK;
 }
 
 template <class R>
 size_t scan_ws_elems(const Plan *p, int nrhs) {
-    // generous: the largest AG (product, P = 3, d = 3: 2 + 27) and 4 channels
+    // generous: the largest AG (product, P = 3, d = 3: 1 + 27) and 4 channels
     return (size_t)2 * p->n_long * 2 * nrhs * 4 * 29 + 64;
 }
 
 // dispatch over (P, d-1, kind); nu = 1/2 or d = 1 make both kinds the same kernel
 template <class R>
-int run_levels_dispatch(Plan *p, const void *Vq, bool vin64, int nrhs, R *Yq, R *ws, cudaStream_t s) {
+int run_levels_dispatch(Plan *p, const void *Vq, bool vin64, int nrhs, R *Yq, R *ws, cudaStream_t s,
+                        const int *gate) {
     const int P = p->P, NOFF = p->d - 1;
     const int kind = (P == 1 || NOFF == 0) ? FGK_L1 : p->kind;
     const int key = (P * 3 + NOFF) * 2 + kind;
     switch (key) {
 #define FGK_CASE(PP, NO, KK) \
-    case (PP * 3 + NO) * 2 + KK: return run_levels<R, PP, NO, KK>(p, Vq, vin64, nrhs, Yq, ws, s);
+    case (PP * 3 + NO) * 2 + KK: return run_levels<R, PP, NO, KK>(p, Vq, vin64, nrhs, Yq, ws, s, gate);
         FGK_CASE(1, 0, FGK_L1)
         FGK_CASE(2, 0, FGK_L1)
         FGK_CASE(3, 0, FGK_L1)

@@ -10,13 +10,17 @@
 // (product, two reductions, three vector updates) is captured once into a
 // CUDA graph and replayed.
 //
-// Refinement.  The solve runs in sweeps: the residual R = B - A X is
-// recomputed with FP64 scans, CG solves A D = R to a relative threshold, and
-// X += D.  In FP64 mode the first sweep normally meets the tolerance and the
-// recomputation only confirms it; in mixed mode CG applies A with FP32 scans
-// (FP32 moments, FP64 vectors and inner products) and the FP64 sweeps correct
-// the solution until the true residual meets the tolerance (iterative
-// refinement).  The reported residuals are always the FP64 true residuals.
+// Refinement.  X accumulates in FP64.  In mixed mode CG applies A with FP32
+// scans (FP32 moments; FP64 vectors, inner products and scalars), so its
+// recursive residual drifts from b - A X; whenever a column's recursive
+// residual has dropped by a factor delta since the last time (and whenever
+// it claims convergence), the true residual b - A X is recomputed with FP64
+// scans and replaces the recursive one, and CG continues from it with the
+// same search direction (residual replacement, "reliable updates").  This is
+// iterative refinement with the correction solved in low precision, without
+// restarting the Krylov space at every correction.  In FP64 mode the only
+// replacement is the final confirmation.  A column stops once its FP64 true
+// residual meets the tolerance; the reported residuals are those.
 //
 // Fixed effects (Sec. 3.2, the GLS step of Algorithm 1): the block is
 // [y, H]; with alpha_y = A^{-1} y and alpha_H = A^{-1} H,
@@ -184,11 +188,6 @@ __global__ void k_residual(const double *__restrict__ B, const double *__restric
         R[t] = B[t] - (Y[t] + sigma2 * X[t]);
 }
 
-__global__ void k_axpy_all(double *__restrict__ X, const double *__restrict__ D, int64_t n) {
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
-        X[t] += D[t];
-}
-
 // B (q order, N x ncols) = [y | H]; H == NULL with L > 0 means [1, x].
 __global__ void k_assemble_rhs(const double *__restrict__ y, int nrhs, const double *__restrict__ H, int L,
                                const double *__restrict__ xraw_q, int d, const int32_t *__restrict__ perm1, int64_t N,
@@ -320,7 +319,7 @@ int cg_solve(Plan *p, const double *y, int nrhs, double sigma2, const double *H,
 
     const size_t vec = (size_t)N * ncols;
     const bool mixed = mode == FGK_MIXED;
-    size_t bytes = 6 * vec * 8 + (mixed ? vec * 4 : 0) + (size_t)kRedBlocks * kMaxCols * kMaxH * 8 +
+    size_t bytes = 5 * vec * 8 + (mixed ? vec * 4 : 0) + (size_t)kRedBlocks * kMaxCols * kMaxH * 8 +
                    sizeof(ColState) + 1024;
     char *w = (char *)dev_alloc(bytes, s);
     if (!w) {
@@ -337,7 +336,6 @@ int cg_solve(Plan *p, const double *y, int nrhs, double sigma2, const double *H,
     };
     double *B = (double *)carve(vec * 8);
     double *X = (double *)carve(vec * 8);
-    double *D = (double *)carve(vec * 8);
     double *Rv = (double *)carve(vec * 8);
     double *Pv = (double *)carve(vec * 8);
     double *W64 = (double *)carve(vec * 8);
@@ -348,10 +346,14 @@ int cg_solve(Plan *p, const double *y, int nrhs, double sigma2, const double *H,
     int rc = FGK_OK;
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph = nullptr;
-    std::vector<double> bnorm(ncols), rnorm(ncols), sums(std::max(ncols, L * ncols));
+    uint64_t graph_nodes = 0;
+    std::vector<double> bnorm(ncols), rnorm(ncols), rho_ref(ncols);
+    std::vector<int> confirmed(ncols, 0);
     int iters_total = 0, refinements = 0, n_f32 = 0, n_f64 = 0;
     bool converged = false, breakdown = false;
-    const double inner_floor = env_double("FGK_MIXED_INNER_TOL", 1e-5);
+    // mixed mode: replace the recursive residual by the FP64 true residual
+    // once it has dropped by this factor since the last replacement
+    const double delta = mixed ? env_double("FGK_MIXED_DELTA", 0.1) : 0.0;
     const int check_every = 8;
     int hbad = 0;
     double *dsum = partial + (size_t)kRedBlocks * kMaxCols * kMaxH - 2 * kMaxCols * kMaxH;  // tail scratch
@@ -366,30 +368,31 @@ int cg_solve(Plan *p, const double *y, int nrhs, double sigma2, const double *H,
         for (auto &v : out) v = std::sqrt(v);
         return FGK_OK;
     };
-    // residual R = B - A X with FP64 scans
+    // R = B - A X with FP64 scans (replaces the recursive residual)
     auto true_residual = [&]() -> int {
-        FGK_TRY(mvm_q_f64(p, X, ncols, W64, s));
+        FGK_TRY(mvm_q_f64(p, X, ncols, W64, s, nullptr));
         k_residual<<<kRedBlocks, kRedThreads, 0, s>>>(B, W64, X, sigma2, (int64_t)vec, Rv);
         FGK_LAUNCH_CHECK();
         ++refinements;
         ++n_f64;
         return colnorms(Rv, rnorm);
     };
+    // one CG iteration; every kernel returns at once when no column is active
     auto one_iteration = [&]() -> int {
         if (mixed) {
-            FGK_TRY(mvm_q_f32(p, Pv, true, ncols, W32, s));
+            FGK_TRY(mvm_q_f32(p, Pv, true, ncols, W32, s, &st->n_active));
             k_dot_pAp<float><<<kRedBlocks, kRedThreads, 0, s>>>(Pv, W32, sigma2, N, ncols, partial, st);
         } else {
-            FGK_TRY(mvm_q_f64(p, Pv, ncols, W64, s));
+            FGK_TRY(mvm_q_f64(p, Pv, ncols, W64, s, &st->n_active));
             k_dot_pAp<double><<<kRedBlocks, kRedThreads, 0, s>>>(Pv, W64, sigma2, N, ncols, partial, st);
         }
         FGK_LAUNCH_CHECK();
         k_alpha<<<1, kMaxCols, 0, s>>>(partial, kRedBlocks, ncols, st);
         FGK_LAUNCH_CHECK();
         if (mixed)
-            k_update_xr<float><<<kRedBlocks, kRedThreads, 0, s>>>(D, Rv, Pv, W32, sigma2, N, ncols, partial, st);
+            k_update_xr<float><<<kRedBlocks, kRedThreads, 0, s>>>(X, Rv, Pv, W32, sigma2, N, ncols, partial, st);
         else
-            k_update_xr<double><<<kRedBlocks, kRedThreads, 0, s>>>(D, Rv, Pv, W64, sigma2, N, ncols, partial, st);
+            k_update_xr<double><<<kRedBlocks, kRedThreads, 0, s>>>(X, Rv, Pv, W64, sigma2, N, ncols, partial, st);
         FGK_LAUNCH_CHECK();
         k_beta<<<1, kMaxCols, 0, s>>>(partial, kRedBlocks, ncols, st);
         FGK_LAUNCH_CHECK();
@@ -402,8 +405,7 @@ int cg_solve(Plan *p, const double *y, int nrhs, double sigma2, const double *H,
         FGK_CUDA(cudaMemsetAsync(p->dev_err, 0, sizeof(int), s));
         k_assemble_rhs<<<kRedBlocks, kRedThreads, 0, s>>>(y, nrhs, H, std::max(L, 0), p->xraw_q, p->d, p->perm[0], N,
                                                           B, p->dev_err);
-        rc = cudaGetLastError() == cudaSuccess ? FGK_OK : FGK_ERR_CUDA;
-        if (rc) break;
+        FGK_LAUNCH_CHECK();
         FGK_CUDA(cudaMemcpyAsync(&hbad, p->dev_err, sizeof(int), cudaMemcpyDeviceToHost, s));
         FGK_CUDA(cudaStreamSynchronize(s));
         if (hbad) {
@@ -415,71 +417,84 @@ int cg_solve(Plan *p, const double *y, int nrhs, double sigma2, const double *H,
         if ((rc = colnorms(B, bnorm))) break;
         FGK_CUDA(cudaMemsetAsync(X, 0, vec * 8, s));
         FGK_CUDA(cudaMemcpyAsync(Rv, B, vec * 8, cudaMemcpyDeviceToDevice, s));
+        FGK_CUDA(cudaMemcpyAsync(Pv, B, vec * 8, cudaMemcpyDeviceToDevice, s));
         rnorm = bnorm;
-        // warm the product once so its workspace exists before graph capture
+        // warm the products once so their workspace exists before graph capture
         if (mixed) {
-            if ((rc = mvm_q_f32(p, B, true, ncols, W32, s))) break;
+            if ((rc = mvm_q_f32(p, B, true, ncols, W32, s, nullptr))) break;
         }
-        if ((rc = mvm_q_f64(p, B, ncols, W64, s))) break;
-        const int max_sweeps = 30;
-        for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-            // converged?  (zero right-hand sides count as converged)
+        if ((rc = mvm_q_f64(p, B, ncols, W64, s, nullptr))) break;
+        ColState hs;
+        std::memset(&hs, 0, sizeof(hs));
+        for (int j = 0; j < ncols; ++j) {
+            hs.rho[j] = rnorm[j] * rnorm[j];
+            rho_ref[j] = hs.rho[j];
+            const double target = 0.5 * tol * bnorm[j];
+            hs.thr2[j] = target * target;
+            confirmed[j] = rnorm[j] <= tol * bnorm[j];
+            hs.active[j] = !confirmed[j];
+            hs.n_active += hs.active[j];
+        }
+        FGK_CUDA(cudaMemcpyAsync(st, &hs, sizeof(hs), cudaMemcpyHostToDevice, s));
+        {
+            const uint64_t c0 = kernel_launch_count();
+            FGK_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            int crc = one_iteration();
+            cudaError_t ce = cudaStreamEndCapture(s, &graph);
+            graph_nodes = kernel_launch_count() - c0;
+            add_kernel_launches(-(int64_t)graph_nodes);  // counted when replayed
+            if (crc) {
+                rc = crc;
+                break;
+            }
+            FGK_CUDA(ce);
+            FGK_CUDA(cudaGraphInstantiate(&gexec, graph, 0));
+        }
+        ColState snap = hs;
+        while (true) {
             bool all = true;
-            for (int j = 0; j < ncols; ++j)
-                if (rnorm[j] > tol * bnorm[j]) all = false;
+            for (int j = 0; j < ncols; ++j) all = all && confirmed[j];
             if (all) {
                 converged = true;
                 break;
             }
             if (iters_total >= maxit) break;
-            // sweep set-up: D = 0, r = p = R, rho = ||R||^2, thresholds
-            ColState hs;
-            std::memset(&hs, 0, sizeof(hs));
-            int nact = 0;
+            const int k = std::min(check_every, maxit - iters_total);
+            const int before = *std::max_element(snap.iters, snap.iters + ncols);
+            for (int it = 0; it < k; ++it) FGK_CUDA(cudaGraphLaunch(gexec, s));
+            add_kernel_launches((int64_t)graph_nodes * k);
+            FGK_CUDA(cudaMemcpyAsync(&snap, st, sizeof(ColState), cudaMemcpyDeviceToHost, s));
+            FGK_CUDA(cudaStreamSynchronize(s));
+            const int after = *std::max_element(snap.iters, snap.iters + ncols);
+            iters_total += after - before;
+            if (mixed) n_f32 += after - before; else n_f64 += after - before;
+            if (snap.breakdown) {
+                breakdown = true;
+                break;
+            }
+            // replace the recursive residual when a column claims convergence
+            // or (mixed) has reduced its residual by delta since the last time
+            bool replace = false;
             for (int j = 0; j < ncols; ++j) {
-                hs.rho[j] = rnorm[j] * rnorm[j];
-                double target = 0.5 * tol * bnorm[j];
-                if (mixed) target = std::max(target, inner_floor * rnorm[j]);
-                hs.thr2[j] = target * target;
-                hs.active[j] = rnorm[j] > tol * bnorm[j] ? 1 : 0;
-                nact += hs.active[j];
+                if (confirmed[j]) continue;
+                if (!snap.active[j] || snap.rho[j] <= delta * delta * rho_ref[j]) replace = true;
             }
-            hs.n_active = nact;
-            FGK_CUDA(cudaMemcpyAsync(st, &hs, sizeof(hs), cudaMemcpyHostToDevice, s));
-            FGK_CUDA(cudaMemsetAsync(D, 0, vec * 8, s));
-            FGK_CUDA(cudaMemcpyAsync(Pv, Rv, vec * 8, cudaMemcpyDeviceToDevice, s));
-            if (!gexec) {
-                FGK_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-                int crc = one_iteration();
-                cudaError_t ce = cudaStreamEndCapture(s, &graph);
-                if (crc) {
-                    rc = crc;
-                    break;
-                }
-                FGK_CUDA(ce);
-                FGK_CUDA(cudaGraphInstantiate(&gexec, graph, 0));
-            }
-            int sweep_iters = 0;
-            ColState snap;
-            while (iters_total < maxit) {
-                const int k = std::min(check_every, maxit - iters_total);
-                for (int it = 0; it < k; ++it) FGK_CUDA(cudaGraphLaunch(gexec, s));
-                FGK_CUDA(cudaMemcpyAsync(&snap, st, sizeof(ColState), cudaMemcpyDeviceToHost, s));
-                FGK_CUDA(cudaStreamSynchronize(s));
-                int mx = 0;
-                for (int j = 0; j < ncols; ++j) mx = std::max(mx, snap.iters[j]);
-                iters_total += mx - sweep_iters;
-                sweep_iters = mx;
-                if (mixed) n_f32 += k; else n_f64 += k;
-                if (snap.breakdown) breakdown = true;
-                if (snap.n_active == 0 || breakdown) break;
-            }
-            if (breakdown) break;
-            k_axpy_all<<<kRedBlocks, kRedThreads, 0, s>>>(X, D, (int64_t)vec);
-            if ((rc = cudaGetLastError() == cudaSuccess ? FGK_OK : FGK_ERR_CUDA)) break;
+            if (!replace) continue;
             if ((rc = true_residual())) break;
+            snap.n_active = 0;
+            for (int j = 0; j < ncols; ++j) {
+                if (!confirmed[j] && rnorm[j] <= tol * bnorm[j]) confirmed[j] = 1;
+                snap.active[j] = !confirmed[j];
+                if (!confirmed[j]) {
+                    snap.rho[j] = rnorm[j] * rnorm[j];
+                    rho_ref[j] = snap.rho[j];
+                }
+                snap.n_active += snap.active[j];
+            }
+            FGK_CUDA(cudaMemcpyAsync(st, &snap, sizeof(ColState), cudaMemcpyHostToDevice, s));
         }
         if (rc) break;
+        if (!converged && refinements == 0 && (rc = true_residual())) break;  // report true residuals
         // GLS fixed effects
         double *beta_dev = nullptr;
         if (L > 0) {

@@ -49,8 +49,9 @@ class fgk_plan_info(ctypes.Structure):
                 ("ell", ctypes.c_double * 3), ("device_bytes", ctypes.c_size_t)]
 
 
-EXPORTS = ["fgk_set_allocator", "fgk_build", "fgk_matvec", "fgk_cg_solve", "fgk_bytes_estimate", "fgk_destroy",
-           "fgk_last_error", "fgk_get_info", "fgk_get_permutation", "fgk_get_level"]
+EXPORTS = ["fgk_set_allocator", "fgk_build", "fgk_matvec", "fgk_matvec_q", "fgk_cg_solve", "fgk_bytes_estimate",
+           "fgk_destroy", "fgk_last_error", "fgk_kernel_launches", "fgk_scan_timing", "fgk_get_info",
+           "fgk_get_permutation", "fgk_get_level"]
 
 _lock = threading.Lock()
 _lib = None
@@ -73,6 +74,12 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.fgk_build.restype = i32
         lib.fgk_matvec.argtypes = [vp, vp, i32, vp, i32, vp]
         lib.fgk_matvec.restype = i32
+        lib.fgk_matvec_q.argtypes = [vp, vp, i32, vp, i32, vp]
+        lib.fgk_matvec_q.restype = i32
+        lib.fgk_kernel_launches.argtypes = []
+        lib.fgk_kernel_launches.restype = ctypes.c_uint64
+        lib.fgk_scan_timing.argtypes = [i32, ctypes.POINTER(dbl), ctypes.POINTER(i64)]
+        lib.fgk_scan_timing.restype = i32
         lib.fgk_cg_solve.argtypes = [vp, vp, i32, dbl, vp, i32, dbl, i32, i32, vp, vp, ctypes.POINTER(fgk_cg_info),
                                      vp]
         lib.fgk_cg_solve.restype = i32
@@ -173,6 +180,33 @@ def fgk_matvec(h: Handle, V: torch.Tensor, precision="f64", out: torch.Tensor | 
         out = torch.empty_like(V2)
     _check(lib.fgk_matvec(h.ptr, V2.data_ptr(), V2.shape[1], out.data_ptr(), prec, _stream(stream)))
     return out.squeeze(1) if squeeze else out
+
+
+def fgk_matvec_q(h: Handle, Vq: torch.Tensor, precision="f32", out: torch.Tensor | None = None, stream=None):
+    """Y = K V with rows in the plan's internal order (see include/fgk.h)."""
+    lib = load()
+    prec = {"f64": FGK_F64, "f32": FGK_F32}[precision] if isinstance(precision, str) else int(precision)
+    dt = torch.float64 if prec == FGK_F64 else torch.float32
+    if not Vq.is_cuda or Vq.dtype != dt or not Vq.is_contiguous():
+        raise TypeError(f"Vq must be a contiguous CUDA {dt} tensor")
+    V2 = Vq.unsqueeze(1) if Vq.dim() == 1 else Vq
+    if out is None:
+        out = torch.empty_like(V2)
+    _check(lib.fgk_matvec_q(h.ptr, V2.data_ptr(), V2.shape[1], out.data_ptr(), prec, _stream(stream)))
+    return out
+
+
+def fgk_kernel_launches() -> int:
+    return int(load().fgk_kernel_launches())
+
+
+def fgk_scan_timing(enable: int = -1):
+    """Start (1), stop (0) or read (-1) event timing of the main scan kernel;
+    returns (total_ms, launches)."""
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    _check(load().fgk_scan_timing(int(enable), ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
 
 
 def fgk_cg_solve(h: Handle, y: torch.Tensor, sigma2: float, H: torch.Tensor | None = None, L: int = 0,

@@ -148,7 +148,7 @@ def test_nonfinite_input_rejected(fgk_mod):
 def test_invalid_arguments(fgk_mod):
     fgk = fgk_mod
     X = to_dev(np.random.default_rng(2).uniform(size=(20, 2)))
-    with pytest.raises(fgk.FgkError):
+    with pytest.raises(ValueError):
         fgk.fgk_build(X, 1.0, [0.2, 0.2])
     with pytest.raises(fgk.FgkError):
         fgk.fgk_build(X, 1.5, [0.2, 0.0])
