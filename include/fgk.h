@@ -109,6 +109,24 @@ int fgk_matvec(fgk_handle h, const void *V, int nrhs, void *Y, int precision, fg
  * fgk_matvec.  Arguments otherwise as fgk_matvec.  Asynchronous. */
 int fgk_matvec_q(fgk_handle h, const void *Vq, int nrhs, void *Yq, int precision, fgk_stream_t stream);
 
+/* The product of fgk_matvec_q for callers that must not allocate device
+ * memory during the call (their device memory is planned before they start:
+ * a serving loop whose budget is already handed out, an engine whose memory
+ * plan is fixed, a latency-critical path that cannot afford an allocator
+ * call).  The paper has no counterpart; this is an interface choice.
+ * It calls no cudaMalloc, cudaFree or allocating library routine: the
+ * scratch of the level scans lives in one 16 MiB __device__ array compiled
+ * into the library, which every GPU that loads the library holds until the
+ * process exits.  The first call on a device looks up that array's device
+ * address (make it before any stream capture).  All calls on a device share
+ * the array: calls whose work overlaps on the GPU race and must be ordered
+ * by the caller.  A product needing more scratch than the array holds
+ * (the need grows with nrhs and with the number of tiles in segments longer
+ * than a tile) returns FGK_ERR_INVALID without launching anything.
+ * Arguments, layout and precision as fgk_matvec_q; the handle comes from an
+ * earlier fgk_build.  Asynchronous. */
+int fgk_matvec_q_noalloc(fgk_handle h, const void *Vq, int nrhs, void *Yq, int precision, fgk_stream_t stream);
+
 /* Per-solve report of fgk_cg_solve (host memory, filled on return). */
 typedef struct {
     int32_t iterations;     /* CG iterations (the most any column took) */

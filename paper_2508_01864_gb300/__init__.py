@@ -23,6 +23,7 @@ from .fgk import (  # noqa: F401
     fgk_kernel_launches,
     fgk_matvec,
     fgk_matvec_q,
+    fgk_matvec_q_noalloc,
     fgk_scan_timing,
     load,
     use_torch_allocator,

@@ -49,7 +49,7 @@ class fgk_plan_info(ctypes.Structure):
                 ("ell", ctypes.c_double * 3), ("device_bytes", ctypes.c_size_t)]
 
 
-EXPORTS = ["fgk_set_allocator", "fgk_build", "fgk_matvec", "fgk_matvec_q", "fgk_cg_solve", "fgk_bytes_estimate",
+EXPORTS = ["fgk_set_allocator", "fgk_build", "fgk_matvec", "fgk_matvec_q", "fgk_matvec_q_noalloc", "fgk_cg_solve", "fgk_bytes_estimate",
            "fgk_destroy", "fgk_last_error", "fgk_kernel_launches", "fgk_scan_timing", "fgk_get_info",
            "fgk_get_permutation", "fgk_get_level"]
 
@@ -76,6 +76,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.fgk_matvec.restype = i32
         lib.fgk_matvec_q.argtypes = [vp, vp, i32, vp, i32, vp]
         lib.fgk_matvec_q.restype = i32
+        lib.fgk_matvec_q_noalloc.argtypes = [vp, vp, i32, vp, i32, vp]
+        lib.fgk_matvec_q_noalloc.restype = i32
         lib.fgk_kernel_launches.argtypes = []
         lib.fgk_kernel_launches.restype = ctypes.c_uint64
         lib.fgk_scan_timing.argtypes = [i32, ctypes.POINTER(dbl), ctypes.POINTER(i64)]
@@ -193,6 +195,20 @@ def fgk_matvec_q(h: Handle, Vq: torch.Tensor, precision="f32", out: torch.Tensor
     if out is None:
         out = torch.empty_like(V2)
     _check(lib.fgk_matvec_q(h.ptr, V2.data_ptr(), V2.shape[1], out.data_ptr(), prec, _stream(stream)))
+    return out
+
+
+def fgk_matvec_q_noalloc(h: Handle, Vq: torch.Tensor, out: torch.Tensor, precision="f32", stream=None):
+    """fgk_matvec_q without any device allocation: scratch in the library's
+    fixed array, output into the caller's ``out``."""
+    lib = load()
+    prec = {"f64": FGK_F64, "f32": FGK_F32}[precision] if isinstance(precision, str) else int(precision)
+    dt = torch.float64 if prec == FGK_F64 else torch.float32
+    for t, n in ((Vq, "Vq"), (out, "out")):
+        if not t.is_cuda or t.dtype != dt or not t.is_contiguous():
+            raise TypeError(f"{n} must be a contiguous CUDA {dt} tensor")
+    V2 = Vq.unsqueeze(1) if Vq.dim() == 1 else Vq
+    _check(lib.fgk_matvec_q_noalloc(h.ptr, V2.data_ptr(), V2.shape[1], out.data_ptr(), prec, _stream(stream)))
     return out
 
 
