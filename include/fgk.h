@@ -155,7 +155,7 @@ typedef struct {
  *              CG with FP64 inner products and vectors, the residual
  *              recomputed with FP64 scans whenever the
  *              recursive residual has dropped by a factor (env
- *              FGK_MIXED_DELTA, default 0.1) and substituted for it, the
+ *              FGK_MIXED_DELTA, default 0.5) and substituted for it, the
  *              FP64 solution being corrected in place (iterative refinement
  *              without restarting the Krylov space).
  *   alpha      device, N x nrhs FP64 (output).

@@ -236,7 +236,7 @@ int from_q_order(const Plan *p, const void *src, void *dst, int nrhs, int elem_b
 size_t plan_bytes_estimate(int64_t N, int d, int two_nu, int kind, int nrhs) {
     const int L = ceil_log2_i64(N);
     const int64_t nlev = d == 1 ? 1 : (d == 2 ? L : (int64_t)L * (L + 1) / 2);
-    const int64_t E = nlev * N;
+    const int64_t E = nlev * ((N + 63) / 64 * 64);
     size_t b = 0;
     b += (size_t)E * (4 + 4 + 8 + (size_t)(d - 1) * 12);                // levels
     b += (size_t)N * (4 * d + 4 + 8 * d + 8 * d);                         // perms, rank, xq, xraw
@@ -325,6 +325,7 @@ int fgk_build(const double *X, int64_t N, int d, int two_nu, const double *ell, 
     }
     p->L = ceil_log2_i64(N);
     p->nlev = d == 1 ? 1 : (d == 2 ? p->L : p->L * (p->L + 1) / 2);
+    p->ldN = (N + 63) / 64 * 64;
     int rc = plan_alloc(p, (void **)&p->dev_err, 16);
     if (rc == FGK_OK) rc = cudaMemsetAsync(p->dev_err, 0, 16, p->stream) == cudaSuccess ? FGK_OK : FGK_ERR_CUDA;
     if (rc == FGK_OK) rc = build_sort(p, X);
@@ -484,7 +485,7 @@ int fgk_get_level(fgk_handle h, int level, uint32_t *q, uint8_t *roles, double *
         return FGK_ERR_INVALID;
     }
     const int64_t N = h->N;
-    const size_t lo = (size_t)level * N;
+    const size_t lo = (size_t)level * h->ldN;
     cudaStream_t s = h->stream;
     if (seg_size) *seg_size = int64_t(1) << h->lev_log2S[level];
     std::vector<uint32_t> raw(N);
@@ -495,7 +496,7 @@ int fgk_get_level(fgk_handle h, int level, uint32_t *q, uint8_t *roles, double *
     std::vector<double> o64((size_t)N * std::max(nof, 1));
     std::vector<float> o32((size_t)N * std::max(nof, 1));
     for (int k = 0; k < nof; ++k) {
-        const size_t src = ((size_t)k * h->nlev + level) * N;
+        const size_t src = ((size_t)k * h->nlev + level) * h->ldN;
         FGK_CUDA(cudaMemcpyAsync(o64.data() + (size_t)k * N, h->lv_off64 + src, N * 8, cudaMemcpyDeviceToHost, s));
         FGK_CUDA(cudaMemcpyAsync(o32.data() + (size_t)k * N, h->lv_off32 + src, N * 4, cudaMemcpyDeviceToHost, s));
     }

@@ -66,7 +66,7 @@ constexpr int kMaxD = 3;
 constexpr int kMaxH = 8;
 
 // Level-scan tiling: a CTA owns kTile consecutive entries of one level.
-constexpr int kScanThreads = 128;
+constexpr int kScanThreads = 256;
 constexpr int kScanEPT = 8;  // entries per thread (power of two)
 constexpr int kTile = kScanThreads * kScanEPT;
 
@@ -91,6 +91,7 @@ struct Plan {
     double a[kMaxD] = {0, 0, 0};  // sqrt(2 nu) / ell_k
     int L = 0;
     int nlev = 0;
+    int64_t ldN = 0;  // stride between levels: N rounded up to a multiple of 64 entries
     cudaStream_t stream = nullptr;
 
     // sort results (device)
@@ -99,11 +100,11 @@ struct Plan {
     double *xq[kMaxD] = {nullptr, nullptr, nullptr};     // x'_k of the point at q (x'_1 order)
     double *xraw_q = nullptr;                            // N x d unscaled x in x'_1 order
 
-    // structure: nlev x N entries, level-major
+    // structure: nlev levels of N entries, level-major with stride ldN
     uint32_t *lv_q = nullptr;  // q | r1 << 31 | r2 << 30
     float *lv_dl32 = nullptr;
     double *lv_dl64 = nullptr;
-    float *lv_off32 = nullptr;   // (d-1) arrays of nlev x N, dimension-major
+    float *lv_off32 = nullptr;   // (d-1) arrays of nlev x ldN, dimension-major
     double *lv_off64 = nullptr;
     std::vector<int> lev_log2S;  // host
 

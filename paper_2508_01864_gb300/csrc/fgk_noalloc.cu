@@ -67,9 +67,10 @@ size_t noalloc_need(const Plan *p, int nrhs, size_t elem) {
     int na = 1;
     if (p->kind == FGK_PRODUCT && p->P > 1)
         for (int k = 0; k < noff; ++k) na *= p->P;
-    const size_t ag = 1 + (size_t)na * p->P;
-    const size_t nch = size_t(1) << noff;
-    return (size_t)2 * p->n_long * 2 * nrhs * nch * ag * elem;
+    const size_t cp = noff == 0 ? 1 : 2;
+    const size_t npass = noff == 2 ? 2 : 1;
+    const size_t ag = 1 + cp * (size_t)na * p->P;
+    return (size_t)2 * p->n_long * 2 * nrhs * npass * ag * elem;
 }
 
 }  // namespace

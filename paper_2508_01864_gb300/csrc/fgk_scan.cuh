@@ -54,27 +54,36 @@ constexpr int ipow_c(int b, int e) { return e == 0 ? 1 : b * ipow_c(b, e - 1); }
 
 enum { SCAN_AGG = 0, SCAN_OUT = 1 };
 
+// Channels: a source of role c feeds the queries of the complementary role
+// c ^ (NCH-1), so a pass handles one complementary pair {cA, cB} (d = 2: one
+// pair; d = 3: two pairs; d = 1: one self-paired channel).  A pass carries,
+// per direction, the summed gap T and the moments of its CP channels.
 template <int P, int NOFF, int KIND>
 struct Traits {
     static constexpr int NA = (KIND == FGK_PRODUCT && NOFF > 0 && P > 1) ? ipow_c(P, NOFF) : 1;
-    static constexpr int MOM = NA * P;
-    static constexpr int NCH = 1 << NOFF;
-    static constexpr int AG = 1 + MOM;  // summed gap T, then the moments
+    static constexpr int MOM = NA * P;                 // moments per channel
+    static constexpr int NCH = 1 << NOFF;              // role channels
+    static constexpr int CP = NOFF == 0 ? 1 : 2;       // channels per pass
+    static constexpr int NPASS = NOFF == 2 ? 2 : 1;    // channel-pair passes
+    static constexpr int SM = CP * MOM;                // moments per pass and direction
+    static constexpr int AG = 1 + SM;                  // aggregate: T, moments
+    static constexpr int NDIR = SM <= 12 ? 2 : 1;      // directions walked together
 };
 
 template <class R>
 struct ScanArgs {
     const uint32_t *lv_q;
     const R *lv_dl;
-    const R *lv_off;  // (d-1) blocks of nlev x N
+    const R *lv_off;  // (d-1) blocks of nlev x ldN
     int64_t N;
+    int64_t ldN;
     int nlev;
     const WorkItem *items;
     const void *V;  // q order, N x nrhs
     int vin_f64;
     int nrhs;
-    R *Y;          // q order, N x nrhs, accumulated atomically
-    R *agg;        // SCAN_AGG: tile aggregates out; SCAN_OUT: carries in
+    R *Y;      // q order, N x nrhs, accumulated atomically
+    R *agg;    // SCAN_AGG: tile aggregates out; SCAN_OUT: carries in
     R s2;
     int *err;
     const int *gate;  // NULL, or a device int: 0 = skip the whole product
@@ -134,27 +143,29 @@ __device__ __forceinline__ R csum(const R *m) {
     else return m[0] + m[1] + m[2] * (R(1) / R(3));
 }
 
+// source weights w (per unit v) for the entry's offsets: L1 adds w[q] to
+// M[q] (w[q] = e^{-s} s^q, s = sum of offsets), the product kernel adds w[a]
+// to M[a][0] (w[a] = prod_k o_k^{a_k} e^{-o_k}); d = 1 adds v to M[0].
 template <class R, int P, int NOFF, int KIND>
-__device__ __forceinline__ void insert_src(R *M, R v, const R *o, const R *eo) {
+struct SrcW {
+    static constexpr int NA = Traits<P, NOFF, KIND>::NA;
+    static constexpr int NW = NOFF == 0 ? 1 : (NA == 1 ? P : NA);
+};
+
+template <class R, int P, int NOFF, int KIND>
+__device__ __forceinline__ void src_weights(R *w, const R *o, const R *eo) {
     using Tr = Traits<P, NOFF, KIND>;
     if constexpr (NOFF == 0) {
-        M[0] += v;
+        w[0] = R(1);
     } else if constexpr (Tr::NA == 1) {
         R s = o[0], es = eo[0];
         if constexpr (NOFF == 2) {
             s += o[1];
             es *= eo[1];
         }
-        R w = v * es;
-        M[0] += w;
-        if constexpr (P > 1) {
-            w *= s;
-            M[1] += w;
-        }
-        if constexpr (P > 2) {
-            w *= s;
-            M[2] += w;
-        }
+        w[0] = es;
+#pragma unroll
+        for (int q = 1; q < P; ++q) w[q] = w[q - 1] * s;
     } else {
         R f[NOFF][P];
 #pragma unroll
@@ -165,15 +176,29 @@ __device__ __forceinline__ void insert_src(R *M, R v, const R *o, const R *eo) {
         }
 #pragma unroll
         for (int a = 0; a < Tr::NA; ++a) {
-            R w = v;
+            R x = R(1);
             int rem = a;
 #pragma unroll
             for (int k = 0; k < NOFF; ++k) {
-                w *= f[k][rem % P];
+                x *= f[k][rem % P];
                 rem /= P;
             }
-            M[a * P] += w;
+            w[a] = x;
         }
+    }
+}
+
+template <class R, int P, int NOFF, int KIND>
+__device__ __forceinline__ void add_src(R *M, R v, const R *w) {
+    using Tr = Traits<P, NOFF, KIND>;
+    if constexpr (NOFF == 0) {
+        M[0] += v;
+    } else if constexpr (Tr::NA == 1) {
+#pragma unroll
+        for (int q = 0; q < P; ++q) M[q] += v * w[q];
+    } else {
+#pragma unroll
+        for (int a = 0; a < Tr::NA; ++a) M[a * P] += v * w[a];
     }
 }
 
@@ -233,262 +258,345 @@ __device__ __forceinline__ void set_identity(R *x) {
     for (int m = 0; m < AG; ++m) x[m] = R(0);
 }
 
-constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
-
-template <class R, int P, int NOFF, int KIND>
-struct SmemLayout {
-    using Tr = Traits<P, NOFF, KIND>;
-    static constexpr int NW = kScanThreads / 32;
-    static constexpr size_t q_off = 0;
-    static constexpr size_t dl_off = align_up(q_off + sizeof(uint32_t) * (kTile + 1), 16);
-    static constexpr size_t edl_off = align_up(dl_off + sizeof(R) * (kTile + 1), 16);
-    static constexpr size_t o_off = align_up(edl_off + sizeof(R) * (kTile + 1), 16);
-    static constexpr size_t eo_off = align_up(o_off + sizeof(R) * kTile * NOFF, 16);
-    static constexpr size_t w_off = align_up(eo_off + sizeof(R) * kTile * NOFF, 16);
-    static constexpr size_t wex_off = align_up(w_off + sizeof(R) * NW * Tr::AG, 16);
-    static constexpr size_t bytes = align_up(wex_off + sizeof(R) * NW * Tr::AG, 16);
-};
-
+// One CTA = one tile of kTile consecutive entries of one level; each thread
+// owns kScanEPT consecutive entries, held in registers.  Per right-hand side
+// and channel pair: fold each thread's entries in both directions, scan the
+// folds across the threads of each segment (warp shuffles, then the warp
+// totals through shared memory), and walk the entries again from the
+// carried-in moments, reading queries and inserting sources.  Segments
+// longer than a tile receive their carry from the aggregate pass
+// (MODE == SCAN_AGG writes each tile's totals; k_carry_scan scans them).
 template <class R, int P, int NOFF, int KIND, int MODE>
 __global__ void __launch_bounds__(kScanThreads) k_level_scan(ScanArgs<R> A) {
     using Tr = Traits<P, NOFF, KIND>;
-    using Lay = SmemLayout<R, P, NOFF, KIND>;
-    constexpr int MOM = Tr::MOM, NCH = Tr::NCH, AG = Tr::AG, EPT = kScanEPT, NT = kScanThreads;
-    constexpr int NW = NT / 32;
+    constexpr int MOM = Tr::MOM, CP = Tr::CP, SMM = Tr::SM, AG = Tr::AG, NPASS = Tr::NPASS, NCH = Tr::NCH;
+    constexpr int ND = Tr::NDIR, NDP = 2 / ND;  // directions per walk, direction passes
+    constexpr int EPT = kScanEPT, NT = kScanThreads, NW = NT / 32;
     constexpr int LOG2EPT = (EPT == 8) ? 3 : (EPT == 4 ? 2 : (EPT == 16 ? 4 : 0));
+    constexpr int NO = NOFF > 0 ? NOFF : 1;
+    constexpr int NWT = SrcW<R, P, NOFF, KIND>::NW;
     static_assert((1 << LOG2EPT) == EPT, "EPT must be 4, 8 or 16");
-
-    extern __shared__ __align__(16) unsigned char smem[];
-    uint32_t *s_q = (uint32_t *)(smem + Lay::q_off);
-    R *s_dl = (R *)(smem + Lay::dl_off);
-    R *s_edl = (R *)(smem + Lay::edl_off);
-    R *s_o = (R *)(smem + Lay::o_off);
-    R *s_eo = (R *)(smem + Lay::eo_off);
-    R *s_w = (R *)(smem + Lay::w_off);
-    R *s_wex = (R *)(smem + Lay::wex_off);
+    static_assert(EPT == 8, "vector loads assume 8 entries per thread");
+    __shared__ R s_w[ND][NW][AG];
 
     if (A.gate && *A.gate == 0) return;
     const WorkItem wi = A.items[blockIdx.x];
     const int64_t N = A.N;
     const int64_t base = (int64_t)wi.tile * kTile;
-    const int cnt = (int)(N - base < (int64_t)kTile ? N - base : (int64_t)kTile);
     const int log2S = wi.log2S;
     const int64_t S = int64_t(1) << log2S;
-    const size_t lo = (size_t)wi.level * N;
+    const size_t lo = (size_t)wi.level * A.ldN;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int j0 = tid * EPT;
+    const int64_t p0 = base + j0;
+    const int nvalid = (int)(N - p0 < 0 ? 0 : (N - p0 > EPT ? EPT : N - p0));
 
-    for (int i = tid; i <= kTile; i += NT) {
-        const int64_t pos = base + i;
-        R g = R(0);
-        if (pos < N && (i < kTile || (pos & (S - 1)) != 0)) g = A.lv_dl[lo + pos];
-        s_dl[i] = g;
-        s_edl[i] = exp_neg<R>(g);
-        if (i < kTile) {
-            s_q[i] = pos < N ? A.lv_q[lo + pos] : 0u;
+    // ---- this thread's entries (the level stride keeps 8-entry groups aligned)
+    uint32_t q[EPT];
+    R g[EPT], eg[EPT], o[NO][EPT], eo[NO][EPT];
+    if (nvalid > 0) {
+        const uint4 *qp = reinterpret_cast<const uint4 *>(A.lv_q + lo + p0);
+        const uint4 qa = qp[0], qb = qp[1];
+        q[0] = qa.x; q[1] = qa.y; q[2] = qa.z; q[3] = qa.w;
+        q[4] = qb.x; q[5] = qb.y; q[6] = qb.z; q[7] = qb.w;
+        if constexpr (sizeof(R) == 4) {
+            const float4 *gp = reinterpret_cast<const float4 *>(A.lv_dl + lo + p0);
+            const float4 ga = gp[0], gb = gp[1];
+            g[0] = ga.x; g[1] = ga.y; g[2] = ga.z; g[3] = ga.w;
+            g[4] = gb.x; g[5] = gb.y; g[6] = gb.z; g[7] = gb.w;
 #pragma unroll
             for (int k = 0; k < NOFF; ++k) {
-                R o = pos < N ? A.lv_off[((size_t)k * A.nlev + wi.level) * N + pos] : R(0);
-                s_o[k * kTile + i] = o;
-                s_eo[k * kTile + i] = exp_neg<R>(o);
+                const float4 *op = reinterpret_cast<const float4 *>(A.lv_off + ((size_t)k * A.nlev) * A.ldN + lo + p0);
+                const float4 oa = op[0], ob = op[1];
+                o[k][0] = oa.x; o[k][1] = oa.y; o[k][2] = oa.z; o[k][3] = oa.w;
+                o[k][4] = ob.x; o[k][5] = ob.y; o[k][6] = ob.z; o[k][7] = ob.w;
+            }
+        } else {
+            const double2 *gp = reinterpret_cast<const double2 *>(A.lv_dl + lo + p0);
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const double2 x = gp[h];
+                g[2 * h] = x.x;
+                g[2 * h + 1] = x.y;
+            }
+#pragma unroll
+            for (int k = 0; k < NOFF; ++k) {
+                const double2 *op = reinterpret_cast<const double2 *>(A.lv_off + ((size_t)k * A.nlev) * A.ldN + lo + p0);
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const double2 x = op[h];
+                    o[k][2 * h] = x.x;
+                    o[k][2 * h + 1] = x.y;
+                }
             }
         }
     }
-    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) {
+        if (i >= nvalid) {  // padding: identity steps, no role
+            q[i] = 0;
+            g[i] = R(0);
+#pragma unroll
+            for (int k = 0; k < NOFF; ++k) o[k][i] = R(0);
+        }
+        eg[i] = exp_neg<R>(g[i]);
+#pragma unroll
+        for (int k = 0; k < NOFF; ++k) eo[k][i] = exp_neg<R>(o[k][i]);
+    }
+    // gap into my last entry when walking backward: the next entry's forward gap
+    R gn = __shfl_down_sync(0xffffffffu, g[0], 1);
+    R egn = __shfl_down_sync(0xffffffffu, eg[0], 1);
+    if (lane == 31) {
+        const int64_t pn = p0 + EPT;
+        gn = pn < N ? A.lv_dl[lo + pn] : R(0);
+        egn = exp_neg<R>(gn);
+    }
 
-    const int j0 = tid * EPT;
-    const bool multi = log2S < LOG2EPT;  // several segments inside one thread's entries
-    // scan group (in threads) for segments no longer than a tile
+    const bool multi = log2S < LOG2EPT;  // whole segments inside one thread
     const int G = multi ? 1 : (int)((S >> LOG2EPT) < (int64_t)NT ? (S >> LOG2EPT) : (int64_t)NT);
+    const int GW = G < 32 ? G : 32;
     const bool is_long = S > kTile;
 
     for (int r = 0; r < A.nrhs; ++r) {
         R v[EPT], out[EPT];
 #pragma unroll
         for (int i = 0; i < EPT; ++i) {
-            const int j = j0 + i;
             out[i] = R(0);
-            v[i] = R(0);
-            if (j < cnt) {
-                const size_t idx = (size_t)(s_q[j] & 0x3fffffffu) * A.nrhs + r;
-                v[i] = A.vin_f64 ? (R)((const double *)A.V)[idx] : (R)((const float *)A.V)[idx];
-            }
+            const size_t idx = (size_t)(q[i] & 0x3fffffffu) * A.nrhs + r;
+            v[i] = i < nvalid ? (A.vin_f64 ? (R)((const double *)A.V)[idx] : (R)((const float *)A.V)[idx]) : R(0);
         }
-#pragma unroll
-        for (int dir = 0; dir < 2; ++dir) {
-            const int vlane = dir == 0 ? lane : 31 - lane;
-            const int vwarp = dir == 0 ? warp : NW - 1 - warp;
 #pragma unroll 1
-            for (int c = 0; c < NCH; ++c) {
-                const int qrole = c ^ (NCH - 1);
-                R excl[AG];
-                set_identity<R, AG>(excl);
+        for (int pp = 0; pp < NPASS; ++pp) {
+            const int cA = pp;
+            const int cB = NOFF == 0 ? 0 : (cA ^ (NCH - 1));
+#pragma unroll
+            for (int dp = 0; dp < NDP; ++dp) {
+                R ex[ND][AG];
+#pragma unroll
+                for (int dd = 0; dd < ND; ++dd) set_identity<R, AG>(ex[dd]);
                 if (!multi) {
                     // 1. fold this thread's entries
-                    R cur[AG];
-                    set_identity<R, AG>(cur);
+                    R inc[ND][AG];
+#pragma unroll
+                    for (int dd = 0; dd < ND; ++dd) set_identity<R, AG>(inc[dd]);
 #pragma unroll
                     for (int ii = 0; ii < EPT; ++ii) {
-                        const int i = dir == 0 ? ii : EPT - 1 - ii;
-                        const int j = j0 + i;
-                        const R g = dir == 0 ? s_dl[j] : s_dl[j + 1];
-                        const R eg = dir == 0 ? s_edl[j] : s_edl[j + 1];
-                        step_all<R, P, MOM>(cur + 1, g, eg);
-                        cur[0] += g;
-                        if (j < cnt) {
-                            const int role = NOFF == 0 ? 0 : (int)(s_q[j] >> (32 - NOFF));
-                            if (role == c) {
-                                R o[NOFF > 0 ? NOFF : 1], eo[NOFF > 0 ? NOFF : 1];
 #pragma unroll
-                                for (int k = 0; k < NOFF; ++k) {
-                                    o[k] = s_o[k * kTile + j];
-                                    eo[k] = s_eo[k * kTile + j];
-                                }
-                                insert_src<R, P, NOFF, KIND>(cur + 1, v[i], o, eo);
+                        for (int dd = 0; dd < ND; ++dd) {
+                            const int dir = ND == 2 ? dd : dp;
+                            const int i = dir == 0 ? ii : EPT - 1 - ii;
+                            const R gg = dir == 0 ? g[i] : (i < EPT - 1 ? g[i + 1] : gn);
+                            const R ee = dir == 0 ? eg[i] : (i < EPT - 1 ? eg[i + 1] : egn);
+                            step_all<R, P, SMM>(inc[dd] + 1, gg, ee);
+                            inc[dd][0] += gg;
+                            const int role = NOFF == 0 ? 0 : (int)(q[i] >> (32 - NOFF));
+                            R oi[NO], eoi[NO], w[NWT];
+#pragma unroll
+                            for (int k = 0; k < NO; ++k) {
+                                oi[k] = NOFF ? o[k][i] : R(0);
+                                eoi[k] = NOFF ? eo[k][i] : R(1);
                             }
+                            src_weights<R, P, NOFF, KIND>(w, oi, eoi);
+                            add_src<R, P, NOFF, KIND>(inc[dd] + 1, role == cA ? v[i] : R(0), w);
+                            if constexpr (CP == 2) add_src<R, P, NOFF, KIND>(inc[dd] + 1 + MOM, role == cB ? v[i] : R(0), w);
                         }
                     }
-                    // 2. inclusive scan across the threads of the segment (virtual lanes)
-                    const int GW = G < 32 ? G : 32;
-                    R inc[AG];
-#pragma unroll
-                    for (int m = 0; m < AG; ++m) inc[m] = cur[m];
+                    // 2. inclusive scan over the threads of each segment (virtual lanes)
                     for (int dlt = 1; dlt < GW; dlt <<= 1) {
-                        R prev[AG];
 #pragma unroll
-                        for (int m = 0; m < AG; ++m)
-                            prev[m] = dir == 0 ? __shfl_up_sync(0xffffffffu, inc[m], dlt)
-                                               : __shfl_down_sync(0xffffffffu, inc[m], dlt);
-                        if ((vlane & (GW - 1)) >= dlt) compose_after<R, P, AG>(inc, prev);
+                        for (int dd = 0; dd < ND; ++dd) {
+                            const int dir = ND == 2 ? dd : dp;
+                            const int vlane = dir == 0 ? lane : 31 - lane;
+                            R prev[AG];
+#pragma unroll
+                            for (int m = 0; m < AG; ++m)
+                                prev[m] = dir == 0 ? __shfl_up_sync(0xffffffffu, inc[dd][m], dlt)
+                                                   : __shfl_down_sync(0xffffffffu, inc[dd][m], dlt);
+                            if ((vlane & (GW - 1)) >= dlt) compose_after<R, P, AG>(inc[dd], prev);
+                        }
                     }
-                    // exclusive within the warp group
-                    {
+#pragma unroll
+                    for (int dd = 0; dd < ND; ++dd) {
+                        const int dir = ND == 2 ? dd : dp;
+                        const int vlane = dir == 0 ? lane : 31 - lane;
                         R prev[AG];
 #pragma unroll
                         for (int m = 0; m < AG; ++m)
-                            prev[m] = dir == 0 ? __shfl_up_sync(0xffffffffu, inc[m], 1)
-                                               : __shfl_down_sync(0xffffffffu, inc[m], 1);
+                            prev[m] = dir == 0 ? __shfl_up_sync(0xffffffffu, inc[dd][m], 1)
+                                               : __shfl_down_sync(0xffffffffu, inc[dd][m], 1);
                         if ((vlane & (GW - 1)) != 0) {
 #pragma unroll
-                            for (int m = 0; m < AG; ++m) excl[m] = prev[m];
+                            for (int m = 0; m < AG; ++m) ex[dd][m] = prev[m];
                         }
                     }
+                    // 3. across warps: every thread composes the totals of the
+                    //    earlier warps of its segment (and the tile carry)
                     if (G > 32 || MODE == SCAN_AGG) {
-                        // warp totals -> exclusive prefix over the warps of each group
-                        if (vlane == 31) {
 #pragma unroll
-                            for (int m = 0; m < AG; ++m) s_w[vwarp * AG + m] = inc[m];
+                        for (int dd = 0; dd < ND; ++dd) {
+                            const int dir = ND == 2 ? dd : dp;
+                            const int vlane = dir == 0 ? lane : 31 - lane;
+                            const int vwarp = dir == 0 ? warp : NW - 1 - warp;
+                            if (vlane == 31) {
+#pragma unroll
+                                for (int m = 0; m < AG; ++m) s_w[dd][vwarp][m] = inc[dd][m];
+                            }
                         }
                         __syncthreads();
-                        if (tid == 0) {
-                            const int GWn = G > 32 ? G / 32 : 1;
-                            R run[AG];
-                            set_identity<R, AG>(run);
-                            if (MODE == SCAN_OUT && is_long) {
-                                const R *cin = A.agg + ((((size_t)wi.agg * 2 + dir) * A.nrhs + r) * NCH + c) * AG;
 #pragma unroll
-                                for (int m = 0; m < AG; ++m) run[m] = cin[m];
-                            }
-                            for (int w = 0; w < NW; ++w) {
-                                if (!is_long && (w % GWn) == 0) set_identity<R, AG>(run);
-#pragma unroll
-                                for (int m = 0; m < AG; ++m) s_wex[w * AG + m] = run[m];
-                                R t[AG];
-#pragma unroll
-                                for (int m = 0; m < AG; ++m) t[m] = s_w[w * AG + m];
-                                compose_after<R, P, AG>(t, run);
-#pragma unroll
-                                for (int m = 0; m < AG; ++m) run[m] = t[m];
-                            }
+                        for (int dd = 0; dd < ND; ++dd) {
+                            const int dir = ND == 2 ? dd : dp;
+                            const int vwarp = dir == 0 ? warp : NW - 1 - warp;
+                            const size_t cslot = ((((size_t)wi.agg * 2 + dir) * A.nrhs + r) * NPASS + pp) * AG;
                             if (MODE == SCAN_AGG) {
-                                R *aout = A.agg + ((((size_t)wi.agg * 2 + dir) * A.nrhs + r) * NCH + c) * AG;
+                                if (tid == dd * 32) {  // the tile's total
+                                    R run[AG];
+                                    set_identity<R, AG>(run);
+                                    for (int w2 = 0; w2 < NW; ++w2) {
+                                        R t[AG];
 #pragma unroll
-                                for (int m = 0; m < AG; ++m) aout[m] = run[m];
+                                        for (int m = 0; m < AG; ++m) t[m] = s_w[dd][w2][m];
+                                        compose_after<R, P, AG>(t, run);
+#pragma unroll
+                                        for (int m = 0; m < AG; ++m) run[m] = t[m];
+                                    }
+#pragma unroll
+                                    for (int m = 0; m < AG; ++m) A.agg[cslot + m] = run[m];
+                                }
+                            } else {
+                                const int GWn = G > 32 ? G / 32 : 1;
+                                const int w0 = is_long ? 0 : (vwarp / GWn) * GWn;
+                                R pre[AG];
+                                if (is_long) {
+#pragma unroll
+                                    for (int m = 0; m < AG; ++m) pre[m] = A.agg[cslot + m];
+                                } else {
+                                    set_identity<R, AG>(pre);
+                                }
+                                for (int w2 = w0; w2 < vwarp; ++w2) {
+                                    R t[AG];
+#pragma unroll
+                                    for (int m = 0; m < AG; ++m) t[m] = s_w[dd][w2][m];
+                                    compose_after<R, P, AG>(t, pre);
+#pragma unroll
+                                    for (int m = 0; m < AG; ++m) pre[m] = t[m];
+                                }
+                                compose_after<R, P, AG>(ex[dd], pre);
                             }
-                        }
-                        __syncthreads();
-                        if (MODE == SCAN_OUT && G > 32) {
-                            R wex[AG];
-#pragma unroll
-                            for (int m = 0; m < AG; ++m) wex[m] = s_wex[vwarp * AG + m];
-                            compose_after<R, P, AG>(excl, wex);
                         }
                         __syncthreads();
                     }
                 }
-                if (MODE == SCAN_AGG) continue;
-                // 3. walk again from the carried-in moments and read the queries
-                R st[MOM];
+                if constexpr (MODE == SCAN_OUT) {
+                    // 4. walk again from the carried-in moments; read, then insert
+                    R st[ND][SMM];
 #pragma unroll
-                for (int m = 0; m < MOM; ++m) st[m] = excl[1 + m];
+                    for (int dd = 0; dd < ND; ++dd)
 #pragma unroll
-                for (int ii = 0; ii < EPT; ++ii) {
-                    const int i = dir == 0 ? ii : EPT - 1 - ii;
-                    const int j = j0 + i;
-                    if (multi) {
-                        const bool seg_start = dir == 0 ? (j & (S - 1)) == 0 : ((j + 1) & (S - 1)) == 0;
-                        if (seg_start) {
+                        for (int m = 0; m < SMM; ++m) st[dd][m] = ex[dd][1 + m];
 #pragma unroll
-                            for (int m = 0; m < MOM; ++m) st[m] = R(0);
+                    for (int ii = 0; ii < EPT; ++ii) {
+#pragma unroll
+                        for (int dd = 0; dd < ND; ++dd) {
+                            const int dir = ND == 2 ? dd : dp;
+                            const int i = dir == 0 ? ii : EPT - 1 - ii;
+                            if (multi) {
+                                const int jj = j0 + i;
+                                const bool seg_start = dir == 0 ? (jj & (S - 1)) == 0 : ((jj + 1) & (S - 1)) == 0;
+                                if (seg_start) {
+#pragma unroll
+                                    for (int m = 0; m < SMM; ++m) st[dd][m] = R(0);
+                                }
+                            }
+                            const R gg = dir == 0 ? g[i] : (i < EPT - 1 ? g[i + 1] : gn);
+                            const R ee = dir == 0 ? eg[i] : (i < EPT - 1 ? eg[i + 1] : egn);
+                            step_all<R, P, SMM>(st[dd], gg, ee);
+                            const bool ok = i < nvalid;
+                            const int role = NOFF == 0 ? 0 : (int)(q[i] >> (32 - NOFF));
+                            R oi[NO], eoi[NO], w[NWT];
+#pragma unroll
+                            for (int k = 0; k < NO; ++k) {
+                                oi[k] = NOFF ? o[k][i] : R(0);
+                                eoi[k] = NOFF ? eo[k][i] : R(1);
+                            }
+                            if constexpr (CP == 1) {
+                                if (ok) out[i] += read_query<R, P, NOFF, KIND>(st[dd], oi, eoi);
+                                src_weights<R, P, NOFF, KIND>(w, oi, eoi);
+                                add_src<R, P, NOFF, KIND>(st[dd], ok ? v[i] : R(0), w);
+                            } else {
+                                const bool sa = ok && role == cA, sb = ok && role == cB;
+                                R msel[MOM];
+#pragma unroll
+                                for (int m = 0; m < MOM; ++m) msel[m] = sa ? st[dd][MOM + m] : st[dd][m];
+                                const R rd = read_query<R, P, NOFF, KIND>(msel, oi, eoi);
+                                out[i] += (sa || sb) ? rd : R(0);
+                                src_weights<R, P, NOFF, KIND>(w, oi, eoi);
+                                add_src<R, P, NOFF, KIND>(st[dd], sa ? v[i] : R(0), w);
+                                add_src<R, P, NOFF, KIND>(st[dd] + MOM, sb ? v[i] : R(0), w);
+                            }
                         }
-                    }
-                    const R g = dir == 0 ? s_dl[j] : s_dl[j + 1];
-                    const R eg = dir == 0 ? s_edl[j] : s_edl[j + 1];
-                    step_all<R, P, MOM>(st, g, eg);
-                    if (j < cnt) {
-                        const int role = NOFF == 0 ? 0 : (int)(s_q[j] >> (32 - NOFF));
-                        R o[NOFF > 0 ? NOFF : 1], eo[NOFF > 0 ? NOFF : 1];
-#pragma unroll
-                        for (int k = 0; k < NOFF; ++k) {
-                            o[k] = s_o[k * kTile + j];
-                            eo[k] = s_eo[k * kTile + j];
-                        }
-                        if (role == qrole) out[i] += read_query<R, P, NOFF, KIND>(st, o, eo);
-                        if (role == c) insert_src<R, P, NOFF, KIND>(st, v[i], o, eo);
                     }
                 }
             }
         }
-        if (MODE == SCAN_OUT) {
+        if constexpr (MODE == SCAN_OUT) {
 #pragma unroll
-            for (int i = 0; i < EPT; ++i) {
-                const int j = j0 + i;
-                if (j < cnt) atomicAdd(A.Y + (size_t)(s_q[j] & 0x3fffffffu) * A.nrhs + r, A.s2 * out[i]);
-            }
+            for (int i = 0; i < EPT; ++i)
+                if (i < nvalid) atomicAdd(A.Y + (size_t)(q[i] & 0x3fffffffu) * A.nrhs + r, A.s2 * out[i]);
         }
     }
 }
 
 // Exclusive scan of the tile aggregates of every long segment, in both
 // directions: carry[tile] = composition of the tiles before it (forward) or
-// after it (backward).  One thread per (segment, direction, rhs, channel).
+// after it (backward).  One warp per (segment, direction, rhs, channel pair)
+// scans the segment's tiles 32 at a time.
 template <class R, int P, int NOFF, int KIND>
 __global__ void k_carry_scan(const R *__restrict__ agg, R *__restrict__ carry, const int32_t *__restrict__ segs,
                              int nseg, int nrhs, const int *__restrict__ gate) {
     if (gate && *gate == 0) return;
     using Tr = Traits<P, NOFF, KIND>;
-    constexpr int AG = Tr::AG, NCH = Tr::NCH;
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t total = (int64_t)nseg * 2 * nrhs * NCH;
-    if (t >= total) return;
-    const int c = (int)(t % NCH);
-    const int r = (int)((t / NCH) % nrhs);
-    const int dir = (int)((t / ((int64_t)NCH * nrhs)) % 2);
-    const int sg = (int)(t / ((int64_t)NCH * nrhs * 2));
+    constexpr int AG = Tr::AG, NPASS = Tr::NPASS;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t total = (int64_t)nseg * 2 * nrhs * NPASS;
+    if (wid >= total) return;  // uniform per warp
+    const int pp = (int)(wid % NPASS);
+    const int r = (int)((wid / NPASS) % nrhs);
+    const int dir = (int)((wid / ((int64_t)NPASS * nrhs)) % 2);
+    const int sg = (int)(wid / ((int64_t)NPASS * nrhs * 2));
     const int a0 = segs[2 * sg], nt = segs[2 * sg + 1];
     R run[AG];
     set_identity<R, AG>(run);
-    for (int k = 0; k < nt; ++k) {
+    for (int k0 = 0; k0 < nt; k0 += 32) {
+        const int k = k0 + lane;
+        const bool valid = k < nt;
         const int slot = a0 + (dir == 0 ? k : nt - 1 - k);
-        const size_t off = ((((size_t)slot * 2 + dir) * nrhs + r) * NCH + c) * AG;
-        R x[AG];
+        const size_t off = ((((size_t)(valid ? slot : a0) * 2 + dir) * nrhs + r) * NPASS + pp) * AG;
+        R inc[AG];
 #pragma unroll
-        for (int m = 0; m < AG; ++m) {
-            x[m] = agg[off + m];
-            carry[off + m] = run[m];
+        for (int m = 0; m < AG; ++m) inc[m] = valid ? agg[off + m] : R(0);
+        for (int dlt = 1; dlt < 32; dlt <<= 1) {
+            R prev[AG];
+#pragma unroll
+            for (int m = 0; m < AG; ++m) prev[m] = __shfl_up_sync(0xffffffffu, inc[m], dlt);
+            if (lane >= dlt) compose_after<R, P, AG>(inc, prev);
         }
-        compose_after<R, P, AG>(x, run);
+        R ex[AG];
 #pragma unroll
-        for (int m = 0; m < AG; ++m) run[m] = x[m];
+        for (int m = 0; m < AG; ++m) ex[m] = __shfl_up_sync(0xffffffffu, inc[m], 1);
+        if (lane == 0) set_identity<R, AG>(ex);
+        compose_after<R, P, AG>(ex, run);
+        if (valid) {
+#pragma unroll
+            for (int m = 0; m < AG; ++m) carry[off + m] = ex[m];
+        }
+        R last[AG];
+#pragma unroll
+        for (int m = 0; m < AG; ++m) last[m] = __shfl_sync(0xffffffffu, inc[m], 31);
+        compose_after<R, P, AG>(last, run);
+#pragma unroll
+        for (int m = 0; m < AG; ++m) run[m] = last[m];
     }
 }
 
@@ -505,20 +613,12 @@ __global__ void k_diag_init(const void *__restrict__ V, int vin_f64, int64_t n, 
 template <class R, int P, int NOFF, int KIND>
 int run_levels(Plan *p, const void *Vq, bool vin64, int nrhs, R *Yq, R *ws, cudaStream_t s, const int *gate) {
     using Tr = Traits<P, NOFF, KIND>;
-    using Lay = SmemLayout<R, P, NOFF, KIND>;
-    static bool attr_set = false;
-    if (!attr_set) {
-        FGK_CUDA(cudaFuncSetAttribute(k_level_scan<R, P, NOFF, KIND, SCAN_AGG>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::bytes));
-        FGK_CUDA(cudaFuncSetAttribute(k_level_scan<R, P, NOFF, KIND, SCAN_OUT>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::bytes));
-        attr_set = true;
-    }
     ScanArgs<R> A;
     A.lv_q = p->lv_q;
     A.lv_dl = std::is_same<R, float>::value ? (const R *)p->lv_dl32 : (const R *)p->lv_dl64;
     A.lv_off = std::is_same<R, float>::value ? (const R *)p->lv_off32 : (const R *)p->lv_off64;
     A.N = p->N;
+    A.ldN = p->ldN;
     A.nlev = p->nlev;
     A.V = Vq;
     A.vin_f64 = vin64 ? 1 : 0;
@@ -527,15 +627,15 @@ int run_levels(Plan *p, const void *Vq, bool vin64, int nrhs, R *Yq, R *ws, cuda
     A.s2 = (R)p->s2;
     A.err = p->dev_err;
     A.gate = gate;
-    const size_t per_slot = (size_t)2 * nrhs * Tr::NCH * Tr::AG;
+    const size_t per_slot = (size_t)2 * nrhs * Tr::NPASS * Tr::AG;
     R *agg = ws;
     R *carry = ws + (size_t)p->n_long * per_slot;
     if (p->n_long > 0) {
         A.items = p->long_items;
         A.agg = agg;
-        k_level_scan<R, P, NOFF, KIND, SCAN_AGG><<<p->n_long, kScanThreads, Lay::bytes, s>>>(A);
+        k_level_scan<R, P, NOFF, KIND, SCAN_AGG><<<p->n_long, kScanThreads, 0, s>>>(A);
         FGK_LAUNCH_CHECK();
-        const int64_t nthr = (int64_t)p->n_long_segments * 2 * nrhs * Tr::NCH;
+        const int64_t nthr = (int64_t)p->n_long_segments * 2 * nrhs * Tr::NPASS * 32;
         k_carry_scan<R, P, NOFF, KIND><<<grid_for(nthr, 128), 128, 0, s>>>(agg, carry, p->long_seg,
                                                                            p->n_long_segments, nrhs, gate);
         FGK_LAUNCH_CHECK();
@@ -551,7 +651,7 @@ int run_levels(Plan *p, const void *Vq, bool vin64, int nrhs, R *Yq, R *ws, cuda
             FGK_CUDA(cudaEventCreate(&e1));
             FGK_CUDA(cudaEventRecord(e0, s));
         }
-        k_level_scan<R, P, NOFF, KIND, SCAN_OUT><<<p->n_items, kScanThreads, Lay::bytes, s>>>(A);
+        k_level_scan<R, P, NOFF, KIND, SCAN_OUT><<<p->n_items, kScanThreads, 0, s>>>(A);
         FGK_LAUNCH_CHECK();
         if (e0) {
             FGK_CUDA(cudaEventRecord(e1, s));
@@ -563,8 +663,8 @@ int run_levels(Plan *p, const void *Vq, bool vin64, int nrhs, R *Yq, R *ws, cuda
 
 template <class R>
 size_t scan_ws_elems(const Plan *p, int nrhs) {
-    // generous: the largest AG (product, P = 3, d = 3: 1 + 27) and 4 channels
-    return (size_t)2 * p->n_long * 2 * nrhs * 4 * 29 + 64;
+    // generous: the largest aggregate (product, P = 3, d = 3: 1 + 2 x 27) and 2 passes
+    return (size_t)2 * p->n_long * 2 * nrhs * 2 * 56 + 64;
 }
 
 // dispatch over (P, d-1, kind); nu = 1/2 or d = 1 make both kinds the same kernel

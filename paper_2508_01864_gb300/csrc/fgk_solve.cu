@@ -99,21 +99,35 @@ __global__ void k_dot_pAp(const double *__restrict__ p, const W *__restrict__ w,
     block_col_dots<double, W>(p, w, sigma2, p, N, ncols, partial);
 }
 
+// Deterministic sum of the nblk partials of column j by one warp: lanes take
+// strided partials, then a shuffle tree.
+__device__ __forceinline__ double warp_col_sum(const double *__restrict__ partial, int nblk, int ncols, int j,
+                                               int lane) {
+    double acc = 0.0;
+    for (int b = lane; b < nblk; b += 32) acc += partial[b * ncols + j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc;
+}
+
+// alpha_j = rho_j / p_j^T A p_j (one warp per column)
 __global__ void k_alpha(const double *__restrict__ partial, int nblk, int ncols, ColState *__restrict__ st) {
-    const int j = threadIdx.x;
-    if (j >= ncols || st->n_active == 0) return;
-    double pw = 0.0;
-    for (int b = 0; b < nblk; ++b) pw += partial[b * ncols + j];
-    double a = 0.0;
-    if (st->active[j]) {
-        if (!(pw > 0.0)) {
-            st->active[j] = 0;
-            atomicOr(&st->breakdown, 1);
-        } else {
-            a = st->rho[j] / pw;
+    if (st->n_active == 0) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j = warp; j < ncols; j += nw) {
+        const double pw = warp_col_sum(partial, nblk, ncols, j, lane);
+        if (lane != 0) continue;
+        double a = 0.0;
+        if (st->active[j]) {
+            if (!(pw > 0.0)) {
+                st->active[j] = 0;
+                atomicOr(&st->breakdown, 1);
+            } else {
+                a = st->rho[j] / pw;
+            }
         }
+        st->alpha[j] = a;
     }
-    st->alpha[j] = a;
 }
 
 // x += alpha p; r -= alpha (w + sigma2 p); partial sums of r^2
@@ -149,26 +163,30 @@ __global__ void k_update_xr(double *__restrict__ x, double *__restrict__ r, cons
     }
 }
 
+// beta_j = rho'_j / rho_j, convergence flags, active count (one warp per column)
 __global__ void k_beta(const double *__restrict__ partial, int nblk, int ncols, ColState *__restrict__ st) {
     __shared__ int s_act;
     if (threadIdx.x == 0) s_act = 0;
     __syncthreads();
-    const int j = threadIdx.x;
-    if (st->n_active != 0 && j < ncols) {
-        double rr = 0.0;
-        for (int b = 0; b < nblk; ++b) rr += partial[b * ncols + j];
-        double be = 0.0;
-        if (st->active[j]) {
-            st->iters[j] += 1;
-            be = st->rho[j] > 0.0 ? rr / st->rho[j] : 0.0;
-            st->rho[j] = rr;
-            if (rr <= st->thr2[j]) st->active[j] = 0;
+    const int n_active = st->n_active;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (n_active != 0) {
+        for (int j = warp; j < ncols; j += nw) {
+            const double rr = warp_col_sum(partial, nblk, ncols, j, lane);
+            if (lane != 0) continue;
+            double be = 0.0;
+            if (st->active[j]) {
+                st->iters[j] += 1;
+                be = st->rho[j] > 0.0 ? rr / st->rho[j] : 0.0;
+                st->rho[j] = rr;
+                if (rr <= st->thr2[j]) st->active[j] = 0;
+            }
+            st->beta[j] = be;
+            if (st->active[j]) atomicAdd(&s_act, 1);
         }
-        st->beta[j] = be;
-        if (st->active[j]) atomicAdd(&s_act, 1);
     }
     __syncthreads();
-    if (threadIdx.x == 0 && st->n_active != 0) st->n_active = s_act;
+    if (threadIdx.x == 0 && n_active != 0) st->n_active = s_act;
 }
 
 __global__ void k_update_p(double *__restrict__ p, const double *__restrict__ r, int64_t N, int ncols,
@@ -353,7 +371,7 @@ int cg_solve(Plan *p, const double *y, int nrhs, double sigma2, const double *H,
     bool converged = false, breakdown = false;
     // mixed mode: replace the recursive residual by the FP64 true residual
     // once it has dropped by this factor since the last replacement
-    const double delta = mixed ? env_double("FGK_MIXED_DELTA", 0.1) : 0.0;
+    const double delta = mixed ? env_double("FGK_MIXED_DELTA", 0.5) : 0.0;
     const int check_every = 8;
     int hbad = 0;
     double *dsum = partial + (size_t)kRedBlocks * kMaxCols * kMaxH - 2 * kMaxCols * kMaxH;  // tail scratch
@@ -387,14 +405,14 @@ int cg_solve(Plan *p, const double *y, int nrhs, double sigma2, const double *H,
             k_dot_pAp<double><<<kRedBlocks, kRedThreads, 0, s>>>(Pv, W64, sigma2, N, ncols, partial, st);
         }
         FGK_LAUNCH_CHECK();
-        k_alpha<<<1, kMaxCols, 0, s>>>(partial, kRedBlocks, ncols, st);
+        k_alpha<<<1, 256, 0, s>>>(partial, kRedBlocks, ncols, st);
         FGK_LAUNCH_CHECK();
         if (mixed)
             k_update_xr<float><<<kRedBlocks, kRedThreads, 0, s>>>(X, Rv, Pv, W32, sigma2, N, ncols, partial, st);
         else
             k_update_xr<double><<<kRedBlocks, kRedThreads, 0, s>>>(X, Rv, Pv, W64, sigma2, N, ncols, partial, st);
         FGK_LAUNCH_CHECK();
-        k_beta<<<1, kMaxCols, 0, s>>>(partial, kRedBlocks, ncols, st);
+        k_beta<<<1, 256, 0, s>>>(partial, kRedBlocks, ncols, st);
         FGK_LAUNCH_CHECK();
         k_update_p<<<kRedBlocks, kRedThreads, 0, s>>>(Pv, Rv, N, ncols, st);
         FGK_LAUNCH_CHECK();

@@ -236,7 +236,8 @@ int build_levels(Plan *p) {
     const int64_t N = p->N;
     const int d = p->d, L = p->L;
     const int nlev = p->nlev;
-    const size_t E = (size_t)nlev * N;
+    const int64_t ldN = p->ldN;  // level stride (padded for aligned vector loads)
+    const size_t E = (size_t)nlev * ldN;
     FGK_TRY(plan_alloc(p, (void **)&p->lv_q, E * sizeof(uint32_t)));
     FGK_TRY(plan_alloc(p, (void **)&p->lv_dl32, E * sizeof(float)));
     FGK_TRY(plan_alloc(p, (void **)&p->lv_dl64, E * sizeof(double)));
@@ -267,11 +268,11 @@ int build_levels(Plan *p) {
         FGK_LAUNCH_CHECK();
         for (int l = 0; l < L; ++l) {
             p->lev_log2S[l] = L - l;
-            uint32_t *cur = p->lv_q + (size_t)l * N;
-            if (l + 1 < L) FGK_TRY(partition(cur, cur + N, N, L - l, nullptr, L - 1 - l, ws, p->dev_err, s));
-            k_attrs_d2<<<grid_for(N, 256), 256, 0, s>>>(p->xq[0], p->xq[1], N, L, l, cur, p->lv_dl64 + (size_t)l * N,
-                                                         p->lv_dl32 + (size_t)l * N, p->lv_off64 + (size_t)l * N,
-                                                         p->lv_off32 + (size_t)l * N);
+            uint32_t *cur = p->lv_q + (size_t)l * ldN;
+            if (l + 1 < L) FGK_TRY(partition(cur, cur + ldN, N, L - l, nullptr, L - 1 - l, ws, p->dev_err, s));
+            k_attrs_d2<<<grid_for(N, 256), 256, 0, s>>>(p->xq[0], p->xq[1], N, L, l, cur, p->lv_dl64 + (size_t)l * ldN,
+                                                         p->lv_dl32 + (size_t)l * ldN, p->lv_off64 + (size_t)l * ldN,
+                                                         p->lv_off32 + (size_t)l * ldN);
             FGK_LAUNCH_CHECK();
         }
     } else {
@@ -288,14 +289,15 @@ int build_levels(Plan *p) {
             k_local_rank<<<grid_for(N, 256), 256, 0, s>>>(pi_cur, N, log2S1, lr2);
             FGK_LAUNCH_CHECK();
             // inner chain starts from the x'_3 order split into outer segments
-            FGK_CUDA(cudaMemcpyAsync(p->lv_q + (size_t)lev * N, rho_cur, N * sizeof(uint32_t),
+            FGK_CUDA(cudaMemcpyAsync(p->lv_q + (size_t)lev * ldN, rho_cur, N * sizeof(uint32_t),
                                      cudaMemcpyDeviceToDevice, s));
             for (int l2 = 0; l2 < L - l1; ++l2) {
                 const int log2S = L - l1 - l2;
                 p->lev_log2S[lev + l2] = log2S;
-                uint32_t *cur = p->lv_q + (size_t)(lev + l2) * N;
-                if (l2 + 1 < L - l1) FGK_TRY(partition(cur, cur + N, N, log2S, lr2, log2S - 1, ws, p->dev_err, s));
-                size_t o = (size_t)(lev + l2) * N;
+                uint32_t *cur = p->lv_q + (size_t)(lev + l2) * ldN;
+                if (l2 + 1 < L - l1)
+                    FGK_TRY(partition(cur, cur + ldN, N, log2S, lr2, log2S - 1, ws, p->dev_err, s));
+                size_t o = (size_t)(lev + l2) * ldN;
                 k_attrs_d3<<<grid_for(N, 256), 256, 0, s>>>(
                     p->xq[0], p->xq[1], p->xq[2], pi_cur, lr2, N, L, l1, l2, cur, p->lv_dl64 + o, p->lv_dl32 + o,
                     p->lv_off64 + o, p->lv_off32 + o, p->lv_off64 + E + o, p->lv_off32 + E + o);

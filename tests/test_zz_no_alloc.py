@@ -43,7 +43,9 @@ def test_noalloc_rejects_products_beyond_its_scratch(fgk_mod):
     fgk = fgk_mod
     p = workloads.c2(N=200000)
     with fgk.fgk_build(to_dev(p.X), p.nu, p.ell, kind="product") as h:
-        nrhs = 64
+        # 512 FP64 columns: the tile aggregates and carries of the 7+ long
+        # levels alone are far beyond 16 MiB
+        nrhs = 512
         Vq = torch.zeros(p.N, nrhs, dtype=torch.float64, device="cuda")
         Yq = torch.empty_like(Vq)
         assert raw_noalloc(fgk, h, Vq, Yq, "f64") == -1
