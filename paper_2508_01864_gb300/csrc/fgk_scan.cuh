@@ -54,6 +54,11 @@ constexpr int ipow_c(int b, int e) { return e == 0 ? 1 : b * ipow_c(b, e - 1); }
 
 enum { SCAN_AGG = 0, SCAN_OUT = 1 };
 
+// resident CTAs per SM the scan kernels are compiled for (register budget)
+#ifndef FGK_SCAN_MINB
+#define FGK_SCAN_MINB 1
+#endif
+
 // Channels: a source of role c feeds the queries of the complementary role
 // c ^ (NCH-1), so a pass handles one complementary pair {cA, cB} (d = 2: one
 // pair; d = 3: two pairs; d = 1: one self-paired channel).  A pass carries,
@@ -267,7 +272,7 @@ __device__ __forceinline__ void set_identity(R *x) {
 // longer than a tile receive their carry from the aggregate pass
 // (MODE == SCAN_AGG writes each tile's totals; k_carry_scan scans them).
 template <class R, int P, int NOFF, int KIND, int MODE>
-__global__ void __launch_bounds__(kScanThreads) k_level_scan(ScanArgs<R> A) {
+__global__ void __launch_bounds__(kScanThreads, FGK_SCAN_MINB) k_level_scan(ScanArgs<R> A) {
     using Tr = Traits<P, NOFF, KIND>;
     constexpr int MOM = Tr::MOM, CP = Tr::CP, SMM = Tr::SM, AG = Tr::AG, NPASS = Tr::NPASS, NCH = Tr::NCH;
     constexpr int ND = Tr::NDIR, NDP = 2 / ND;  // directions per walk, direction passes
