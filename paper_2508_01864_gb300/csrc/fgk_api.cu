@@ -371,7 +371,7 @@ int fgk_matvec(fgk_handle h, const void *V, int nrhs, void *Y, int precision, fg
     int rc = to_q_order(p, V, Vq, nrhs, eb, s);
     if (rc == FGK_OK)
         rc = precision == FGK_F64 ? mvm_q_f64(p, (const double *)Vq, nrhs, (double *)Yq, s, nullptr)
-                                  : mvm_q_f32(p, Vq, false, nrhs, (float *)Yq, s, nullptr);
+                                  : mvm_q_f32(p, (const float *)Vq, nrhs, (float *)Yq, s, nullptr);
     if (rc == FGK_OK) rc = from_q_order(p, Yq, Y, nrhs, eb, s);
     dev_free(tmp, s);
     return rc;
@@ -387,7 +387,7 @@ int fgk_matvec_q(fgk_handle h, const void *Vq, int nrhs, void *Yq, int precision
     cudaStream_t s = (cudaStream_t)stream;
     p->stream = s;
     return precision == FGK_F64 ? mvm_q_f64(p, (const double *)Vq, nrhs, (double *)Yq, s, nullptr)
-                                : mvm_q_f32(p, Vq, false, nrhs, (float *)Yq, s, nullptr);
+                                : mvm_q_f32(p, (const float *)Vq, nrhs, (float *)Yq, s, nullptr);
 }
 
 uint64_t fgk_kernel_launches(void) { return kernel_launch_count(); }

@@ -141,8 +141,12 @@ int build_worklists(Plan *p);                 // host work lists for the scans (
 // N x nrhs row-major in q order.  Workspace is taken from p->ws.
 // gate (device, may be NULL): when it points at 0 every kernel of the product
 // returns at once (used inside captured CG iterations after convergence).
-int mvm_q_f64(Plan *p, const double *Vq, int nrhs, double *Yq, cudaStream_t s, const int *gate);
-int mvm_q_f32(Plan *p, const void *Vq, bool vin_f64, int nrhs, float *Yq, cudaStream_t s, const int *gate);
+// init_diag = false: Yq already holds s2 * Vq (the diagonal term), written by
+// the caller's own kernel.
+int mvm_q_f64(Plan *p, const double *Vq, int nrhs, double *Yq, cudaStream_t s, const int *gate,
+              bool init_diag = true);
+int mvm_q_f32(Plan *p, const float *Vq, int nrhs, float *Yq, cudaStream_t s, const int *gate,
+              bool init_diag = true);
 size_t mvm_ws_bytes(const Plan *p, int nrhs, bool f64);
 
 int ensure_ws(Plan *p, size_t bytes, cudaStream_t s);

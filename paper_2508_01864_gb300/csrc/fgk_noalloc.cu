@@ -100,13 +100,13 @@ extern "C" int fgk_matvec_q_noalloc(fgk_handle h, const void *Vq, int nrhs, void
     FGK_TRY(noalloc_scratch(&scratch));
     const int64_t n = p->N * nrhs;
     if (precision == FGK_F64) {
-        k_diag_init<double><<<grid_for(n, 256), 256, 0, s>>>(Vq, 1, n, p->s2, (double *)Yq, nullptr);
+        k_diag_init<double><<<grid_for(n, 256), 256, 0, s>>>((const double *)Vq, n, p->s2, (double *)Yq, nullptr);
         FGK_LAUNCH_CHECK();
         if (p->nlev == 0) return FGK_OK;
-        return run_levels_dispatch<double>(p, Vq, true, nrhs, (double *)Yq, (double *)scratch, s, nullptr);
+        return run_levels_dispatch<double>(p, (const double *)Vq, nrhs, (double *)Yq, (double *)scratch, s, nullptr);
     }
-    k_diag_init<float><<<grid_for(n, 256), 256, 0, s>>>(Vq, 0, n, (float)p->s2, (float *)Yq, nullptr);
+    k_diag_init<float><<<grid_for(n, 256), 256, 0, s>>>((const float *)Vq, n, (float)p->s2, (float *)Yq, nullptr);
     FGK_LAUNCH_CHECK();
     if (p->nlev == 0) return FGK_OK;
-    return run_levels_dispatch<float>(p, Vq, false, nrhs, (float *)Yq, (float *)scratch, s, nullptr);
+    return run_levels_dispatch<float>(p, (const float *)Vq, nrhs, (float *)Yq, (float *)scratch, s, nullptr);
 }

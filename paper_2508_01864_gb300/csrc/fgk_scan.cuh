@@ -56,7 +56,7 @@ enum { SCAN_AGG = 0, SCAN_OUT = 1 };
 
 // resident CTAs per SM the scan kernels are compiled for (register budget)
 #ifndef FGK_SCAN_MINB
-#define FGK_SCAN_MINB 1
+#define FGK_SCAN_MINB 2
 #endif
 
 // Channels: a source of role c feeds the queries of the complementary role
@@ -84,8 +84,7 @@ struct ScanArgs {
     int64_t ldN;
     int nlev;
     const WorkItem *items;
-    const void *V;  // q order, N x nrhs
-    int vin_f64;
+    const R *V;  // q order, N x nrhs, in the scan precision
     int nrhs;
     R *Y;      // q order, N x nrhs, accumulated atomically
     R *agg;    // SCAN_AGG: tile aggregates out; SCAN_OUT: carries in
@@ -368,7 +367,7 @@ __global__ void __launch_bounds__(kScanThreads, FGK_SCAN_MINB) k_level_scan(Scan
         for (int i = 0; i < EPT; ++i) {
             out[i] = R(0);
             const size_t idx = (size_t)(q[i] & 0x3fffffffu) * A.nrhs + r;
-            v[i] = i < nvalid ? (A.vin_f64 ? (R)((const double *)A.V)[idx] : (R)((const float *)A.V)[idx]) : R(0);
+            v[i] = i < nvalid ? A.V[idx] : R(0);
         }
 #pragma unroll 1
         for (int pp = 0; pp < NPASS; ++pp) {
@@ -606,17 +605,15 @@ __global__ void k_carry_scan(const R *__restrict__ agg, R *__restrict__ carry, c
 }
 
 template <class R>
-__global__ void k_diag_init(const void *__restrict__ V, int vin_f64, int64_t n, R s2, R *__restrict__ Y,
-                            const int *__restrict__ gate) {
+__global__ void k_diag_init(const R *__restrict__ V, int64_t n, R s2, R *__restrict__ Y, const int *__restrict__ gate) {
     if (gate && *gate == 0) return;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const R v = vin_f64 ? (R)((const double *)V)[i] : (R)((const float *)V)[i];
-    Y[i] = s2 * v;
+    Y[i] = s2 * V[i];
 }
 
 template <class R, int P, int NOFF, int KIND>
-int run_levels(Plan *p, const void *Vq, bool vin64, int nrhs, R *Yq, R *ws, cudaStream_t s, const int *gate) {
+int run_levels(Plan *p, const R *Vq, int nrhs, R *Yq, R *ws, cudaStream_t s, const int *gate) {
     using Tr = Traits<P, NOFF, KIND>;
     ScanArgs<R> A;
     A.lv_q = p->lv_q;
@@ -626,7 +623,6 @@ int run_levels(Plan *p, const void *Vq, bool vin64, int nrhs, R *Yq, R *ws, cuda
     A.ldN = p->ldN;
     A.nlev = p->nlev;
     A.V = Vq;
-    A.vin_f64 = vin64 ? 1 : 0;
     A.nrhs = nrhs;
     A.Y = Yq;
     A.s2 = (R)p->s2;
@@ -674,14 +670,14 @@ size_t scan_ws_elems(const Plan *p, int nrhs) {
 
 // dispatch over (P, d-1, kind); nu = 1/2 or d = 1 make both kinds the same kernel
 template <class R>
-int run_levels_dispatch(Plan *p, const void *Vq, bool vin64, int nrhs, R *Yq, R *ws, cudaStream_t s,
+int run_levels_dispatch(Plan *p, const R *Vq, int nrhs, R *Yq, R *ws, cudaStream_t s,
                         const int *gate) {
     const int P = p->P, NOFF = p->d - 1;
     const int kind = (P == 1 || NOFF == 0) ? FGK_L1 : p->kind;
     const int key = (P * 3 + NOFF) * 2 + kind;
     switch (key) {
 #define FGK_CASE(PP, NO, KK) \
-    case (PP * 3 + NO) * 2 + KK: return run_levels<R, PP, NO, KK>(p, Vq, vin64, nrhs, Yq, ws, s, gate);
+    case (PP * 3 + NO) * 2 + KK: return run_levels<R, PP, NO, KK>(p, Vq, nrhs, Yq, ws, s, gate);
         FGK_CASE(1, 0, FGK_L1)
         FGK_CASE(2, 0, FGK_L1)
         FGK_CASE(3, 0, FGK_L1)

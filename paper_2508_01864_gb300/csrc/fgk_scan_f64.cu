@@ -4,13 +4,15 @@
 
 namespace fgk {
 
-int mvm_q_f64(Plan *p, const double *Vq, int nrhs, double *Yq, cudaStream_t s, const int *gate) {
+int mvm_q_f64(Plan *p, const double *Vq, int nrhs, double *Yq, cudaStream_t s, const int *gate, bool init_diag) {
     const int64_t n = p->N * nrhs;
-    k_diag_init<double><<<grid_for(n, 256), 256, 0, s>>>(Vq, 1, n, p->s2, Yq, gate);
-    FGK_LAUNCH_CHECK();
+    if (init_diag) {
+        k_diag_init<double><<<grid_for(n, 256), 256, 0, s>>>(Vq, n, p->s2, Yq, gate);
+        FGK_LAUNCH_CHECK();
+    }
     if (p->nlev == 0) return FGK_OK;
     FGK_TRY(ensure_ws(p, scan_ws_elems<double>(p, nrhs) * sizeof(double), s));
-    return run_levels_dispatch<double>(p, Vq, true, nrhs, Yq, (double *)p->ws.p, s, gate);
+    return run_levels_dispatch<double>(p, Vq, nrhs, Yq, (double *)p->ws.p, s, gate);
 }
 
 size_t mvm_ws_bytes(const Plan *p, int nrhs, bool f64) {

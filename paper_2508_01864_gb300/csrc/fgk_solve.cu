@@ -41,12 +41,17 @@ constexpr int kRedBlocks = 304;  // 2 x 152 SMs
 constexpr int kRedThreads = 256;
 constexpr int kMaxCols = 64;
 
+// CG state on the device.  The vector kernels of an iteration read rho and
+// active; the p-update's first block writes the new values to rho_next and
+// active_next, which the next iteration's first kernel copies over, so no
+// block ever reads a value another block of the same kernel may be writing.
 struct ColState {
     double rho[kMaxCols];
-    double alpha[kMaxCols];
+    double rho_next[kMaxCols];
     double beta[kMaxCols];
     double thr2[kMaxCols];
     int active[kMaxCols];
+    int active_next[kMaxCols];
     int iters[kMaxCols];
     int n_active;
     int breakdown;
@@ -91,14 +96,6 @@ __global__ void k_finalize_sums(const double *__restrict__ partial, int nblk, in
     out[j] = s;
 }
 
-// pw_j = p_j^T (w_j + sigma2 p_j)
-template <class W>
-__global__ void k_dot_pAp(const double *__restrict__ p, const W *__restrict__ w, double sigma2, int64_t N, int ncols,
-                          double *__restrict__ partial, const ColState *__restrict__ st) {
-    if (st->n_active == 0) return;
-    block_col_dots<double, W>(p, w, sigma2, p, N, ncols, partial);
-}
-
 // Deterministic sum of the nblk partials of column j by one warp: lanes take
 // strided partials, then a shuffle tree.
 __device__ __forceinline__ double warp_col_sum(const double *__restrict__ partial, int nblk, int ncols, int j,
@@ -110,41 +107,53 @@ __device__ __forceinline__ double warp_col_sum(const double *__restrict__ partia
     return acc;
 }
 
-// alpha_j = rho_j / p_j^T A p_j (one warp per column)
-__global__ void k_alpha(const double *__restrict__ partial, int nblk, int ncols, ColState *__restrict__ st) {
+// pw_j = p_j^T (w_j + sigma2 p_j); the first block also moves the state the
+// previous p-update left in rho_next / active_next into rho / active.
+template <class W>
+__global__ void k_dot_pAp(const double *__restrict__ p, const W *__restrict__ w, double sigma2, int64_t N, int ncols,
+                          double *__restrict__ partial, ColState *__restrict__ st) {
     if (st->n_active == 0) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int j = warp; j < ncols; j += nw) {
-        const double pw = warp_col_sum(partial, nblk, ncols, j, lane);
-        if (lane != 0) continue;
-        double a = 0.0;
-        if (st->active[j]) {
-            if (!(pw > 0.0)) {
-                st->active[j] = 0;
-                atomicOr(&st->breakdown, 1);
-            } else {
-                a = st->rho[j] / pw;
-            }
-        }
-        st->alpha[j] = a;
+    if (blockIdx.x == 0 && threadIdx.x < ncols) {
+        st->rho[threadIdx.x] = st->rho_next[threadIdx.x];
+        st->active[threadIdx.x] = st->active_next[threadIdx.x];
     }
+    block_col_dots<double, W>(p, w, sigma2, p, N, ncols, partial);
 }
 
-// x += alpha p; r -= alpha (w + sigma2 p); partial sums of r^2
+// alpha_j = rho_j / p_j^T A p_j (every block from the partials), then
+// x += alpha p, r -= alpha (w + sigma2 p), and partial sums of r^2.
+// p^T A p <= 0 on an active column flags a breakdown (the column is left
+// untouched; the host stops the solve).
 template <class W>
 __global__ void k_update_xr(double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
-                            const W *__restrict__ w, double sigma2, int64_t N, int ncols, double *__restrict__ partial,
-                            const ColState *__restrict__ st) {
+                            const W *__restrict__ w, double sigma2, int64_t N, int ncols,
+                            const double *__restrict__ pw_partial, int nblk, double *__restrict__ partial,
+                            ColState *__restrict__ st) {
     if (st->n_active == 0) return;
+    __shared__ double s_alpha[kMaxCols];
     __shared__ double red[kRedThreads];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j = warp; j < ncols; j += nw) {
+        const double pw = warp_col_sum(pw_partial, nblk, ncols, j, lane);
+        if (lane == 0) {
+            double a = 0.0;
+            if (st->active[j]) {
+                if (pw > 0.0)
+                    a = st->rho[j] / pw;
+                else if (blockIdx.x == 0)
+                    atomicOr(&st->breakdown, 1);
+            }
+            s_alpha[j] = a;
+        }
+    }
+    __syncthreads();
     for (int j = 0; j < ncols; ++j) {
-        const double a = st->alpha[j];
-        const bool act = st->active[j] != 0;
+        const double a = s_alpha[j];
         double acc = 0.0;
         for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
             const int64_t t = i * ncols + j;
             double rv = r[t];
-            if (act) {
+            if (a != 0.0) {
                 const double pv = p[t];
                 x[t] += a * pv;
                 rv -= a * ((double)w[t] + sigma2 * pv);
@@ -163,39 +172,72 @@ __global__ void k_update_xr(double *__restrict__ x, double *__restrict__ r, cons
     }
 }
 
-// beta_j = rho'_j / rho_j, convergence flags, active count (one warp per column)
-__global__ void k_beta(const double *__restrict__ partial, int nblk, int ncols, ColState *__restrict__ st) {
-    __shared__ int s_act;
-    if (threadIdx.x == 0) s_act = 0;
-    __syncthreads();
-    const int n_active = st->n_active;
+// beta_j = rho'_j / rho_j and the stop test (every block from the partials);
+// p = r + beta p on the columns still active; then, on every column, the FP32
+// copy of p for the mixed product and W = s2 p, the diagonal term the next
+// product starts from.
+// The first block records the new state for the next iteration.
+template <class W>
+__global__ void k_update_p(double *__restrict__ p, float *__restrict__ p32, W *__restrict__ w,
+                           const double *__restrict__ r, double s2, int64_t N, int ncols,
+                           const double *__restrict__ rr_partial, int nblk, ColState *__restrict__ st) {
+    if (st->n_active == 0) return;
+    __shared__ double s_beta[kMaxCols];
+    __shared__ int s_act[kMaxCols];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (n_active != 0) {
-        for (int j = warp; j < ncols; j += nw) {
-            const double rr = warp_col_sum(partial, nblk, ncols, j, lane);
-            if (lane != 0) continue;
-            double be = 0.0;
-            if (st->active[j]) {
-                st->iters[j] += 1;
-                be = st->rho[j] > 0.0 ? rr / st->rho[j] : 0.0;
-                st->rho[j] = rr;
-                if (rr <= st->thr2[j]) st->active[j] = 0;
+    for (int j = warp; j < ncols; j += nw) {
+        const double rr = warp_col_sum(rr_partial, nblk, ncols, j, lane);
+        if (lane == 0) {
+            const int act = st->active[j];
+            const double rho = st->rho[j];
+            const int still = act && rr > st->thr2[j];
+            s_beta[j] = act ? (rho > 0.0 ? rr / rho : 0.0) : 0.0;
+            s_act[j] = still;
+            if (blockIdx.x == 0) {
+                st->rho_next[j] = act ? rr : rho;
+                st->active_next[j] = still;
+                st->beta[j] = s_beta[j];
+                if (act) st->iters[j] += 1;
             }
-            st->beta[j] = be;
-            if (st->active[j]) atomicAdd(&s_act, 1);
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0 && n_active != 0) st->n_active = s_act;
-}
-
-__global__ void k_update_p(double *__restrict__ p, const double *__restrict__ r, int64_t N, int ncols,
-                           const ColState *__restrict__ st) {
-    if (st->n_active == 0) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        int n = 0;
+        for (int j = 0; j < ncols; ++j) n += s_act[j];
+        st->n_active = n;
+    }
     const int64_t n = N * ncols;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
         const int j = (int)(t % ncols);
-        if (st->active[j]) p[t] = r[t] + st->beta[j] * p[t];
+        double pv = p[t];
+        if (s_act[j]) {
+            pv = r[t] + s_beta[j] * pv;
+            p[t] = pv;
+        }
+        if (p32) {
+            const float pf = (float)pv;
+            p32[t] = pf;
+            w[t] = (W)(s2 * (double)pf);
+        } else {
+            w[t] = (W)(s2 * pv);
+        }
+    }
+}
+
+// the FP32 copy of p and W = s2 p before the first product of a solve
+template <class W>
+__global__ void k_init_p(const double *__restrict__ p, float *__restrict__ p32, W *__restrict__ w, double s2,
+                         int64_t n) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const double pv = p[t];
+        if (p32) {
+            const float pf = (float)pv;
+            p32[t] = pf;
+            w[t] = (W)(s2 * (double)pf);
+        } else {
+            w[t] = (W)(s2 * pv);
+        }
     }
 }
 
@@ -337,8 +379,8 @@ int cg_solve(Plan *p, const double *y, int nrhs, double sigma2, const double *H,
 
     const size_t vec = (size_t)N * ncols;
     const bool mixed = mode == FGK_MIXED;
-    size_t bytes = 5 * vec * 8 + (mixed ? vec * 4 : 0) + (size_t)kRedBlocks * kMaxCols * kMaxH * 8 +
-                   sizeof(ColState) + 1024;
+    size_t bytes = 5 * vec * 8 + (mixed ? 2 * vec * 4 : 0) + (size_t)kRedBlocks * kMaxCols * (kMaxH + 1) * 8 +
+                   sizeof(ColState) + 4096;
     char *w = (char *)dev_alloc(bytes, s);
     if (!w) {
         p->stream = saved;
@@ -358,7 +400,9 @@ int cg_solve(Plan *p, const double *y, int nrhs, double sigma2, const double *H,
     double *Pv = (double *)carve(vec * 8);
     double *W64 = (double *)carve(vec * 8);
     float *W32 = mixed ? (float *)carve(vec * 4) : nullptr;
+    float *P32 = mixed ? (float *)carve(vec * 4) : nullptr;
     double *partial = (double *)carve((size_t)kRedBlocks * kMaxCols * kMaxH * 8);
+    double *partial2 = (double *)carve((size_t)kRedBlocks * kMaxCols * 8);
     ColState *st = (ColState *)carve(sizeof(ColState));
 
     int rc = FGK_OK;
@@ -395,26 +439,37 @@ int cg_solve(Plan *p, const double *y, int nrhs, double sigma2, const double *H,
         ++n_f64;
         return colnorms(Rv, rnorm);
     };
-    // one CG iteration; every kernel returns at once when no column is active
+    // one CG iteration; every kernel returns at once when no column is active.
+    // The product starts from W = s2 p, written by the previous p-update.
     auto one_iteration = [&]() -> int {
         if (mixed) {
-            FGK_TRY(mvm_q_f32(p, Pv, true, ncols, W32, s, &st->n_active));
+            FGK_TRY(mvm_q_f32(p, P32, ncols, W32, s, &st->n_active, false));
             k_dot_pAp<float><<<kRedBlocks, kRedThreads, 0, s>>>(Pv, W32, sigma2, N, ncols, partial, st);
+            FGK_LAUNCH_CHECK();
+            k_update_xr<float><<<kRedBlocks, kRedThreads, 0, s>>>(X, Rv, Pv, W32, sigma2, N, ncols, partial,
+                                                                 kRedBlocks, partial2, st);
+            FGK_LAUNCH_CHECK();
+            k_update_p<float><<<kRedBlocks, kRedThreads, 0, s>>>(Pv, P32, W32, Rv, p->s2, N, ncols, partial2,
+                                                                kRedBlocks, st);
+            FGK_LAUNCH_CHECK();
         } else {
-            FGK_TRY(mvm_q_f64(p, Pv, ncols, W64, s, &st->n_active));
+            FGK_TRY(mvm_q_f64(p, Pv, ncols, W64, s, &st->n_active, false));
             k_dot_pAp<double><<<kRedBlocks, kRedThreads, 0, s>>>(Pv, W64, sigma2, N, ncols, partial, st);
+            FGK_LAUNCH_CHECK();
+            k_update_xr<double><<<kRedBlocks, kRedThreads, 0, s>>>(X, Rv, Pv, W64, sigma2, N, ncols, partial,
+                                                                  kRedBlocks, partial2, st);
+            FGK_LAUNCH_CHECK();
+            k_update_p<double><<<kRedBlocks, kRedThreads, 0, s>>>(Pv, nullptr, W64, Rv, p->s2, N, ncols,
+                                                                 partial2, kRedBlocks, st);
+            FGK_LAUNCH_CHECK();
         }
-        FGK_LAUNCH_CHECK();
-        k_alpha<<<1, 256, 0, s>>>(partial, kRedBlocks, ncols, st);
-        FGK_LAUNCH_CHECK();
+        return FGK_OK;
+    };
+    auto init_p = [&]() -> int {
         if (mixed)
-            k_update_xr<float><<<kRedBlocks, kRedThreads, 0, s>>>(X, Rv, Pv, W32, sigma2, N, ncols, partial, st);
+            k_init_p<float><<<kRedBlocks, kRedThreads, 0, s>>>(Pv, P32, W32, p->s2, (int64_t)vec);
         else
-            k_update_xr<double><<<kRedBlocks, kRedThreads, 0, s>>>(X, Rv, Pv, W64, sigma2, N, ncols, partial, st);
-        FGK_LAUNCH_CHECK();
-        k_beta<<<1, 256, 0, s>>>(partial, kRedBlocks, ncols, st);
-        FGK_LAUNCH_CHECK();
-        k_update_p<<<kRedBlocks, kRedThreads, 0, s>>>(Pv, Rv, N, ncols, st);
+            k_init_p<double><<<kRedBlocks, kRedThreads, 0, s>>>(Pv, nullptr, W64, p->s2, (int64_t)vec);
         FGK_LAUNCH_CHECK();
         return FGK_OK;
     };
@@ -437,20 +492,23 @@ int cg_solve(Plan *p, const double *y, int nrhs, double sigma2, const double *H,
         FGK_CUDA(cudaMemcpyAsync(Rv, B, vec * 8, cudaMemcpyDeviceToDevice, s));
         FGK_CUDA(cudaMemcpyAsync(Pv, B, vec * 8, cudaMemcpyDeviceToDevice, s));
         rnorm = bnorm;
-        // warm the products once so their workspace exists before graph capture
+        // warm the products once so their workspace exists before graph capture,
+        // then set the product's starting point W = s2 p
+        if ((rc = init_p())) break;
         if (mixed) {
-            if ((rc = mvm_q_f32(p, B, true, ncols, W32, s, nullptr))) break;
+            if ((rc = mvm_q_f32(p, P32, ncols, W32, s, nullptr))) break;
         }
-        if ((rc = mvm_q_f64(p, B, ncols, W64, s, nullptr))) break;
+        if ((rc = mvm_q_f64(p, Pv, ncols, W64, s, nullptr))) break;
+        if ((rc = init_p())) break;
         ColState hs;
         std::memset(&hs, 0, sizeof(hs));
         for (int j = 0; j < ncols; ++j) {
-            hs.rho[j] = rnorm[j] * rnorm[j];
+            hs.rho[j] = hs.rho_next[j] = rnorm[j] * rnorm[j];
             rho_ref[j] = hs.rho[j];
             const double target = 0.5 * tol * bnorm[j];
             hs.thr2[j] = target * target;
             confirmed[j] = rnorm[j] <= tol * bnorm[j];
-            hs.active[j] = !confirmed[j];
+            hs.active[j] = hs.active_next[j] = !confirmed[j];
             hs.n_active += hs.active[j];
         }
         FGK_CUDA(cudaMemcpyAsync(st, &hs, sizeof(hs), cudaMemcpyHostToDevice, s));
@@ -495,16 +553,16 @@ int cg_solve(Plan *p, const double *y, int nrhs, double sigma2, const double *H,
             bool replace = false;
             for (int j = 0; j < ncols; ++j) {
                 if (confirmed[j]) continue;
-                if (!snap.active[j] || snap.rho[j] <= delta * delta * rho_ref[j]) replace = true;
+                if (!snap.active_next[j] || snap.rho_next[j] <= delta * delta * rho_ref[j]) replace = true;
             }
             if (!replace) continue;
             if ((rc = true_residual())) break;
             snap.n_active = 0;
             for (int j = 0; j < ncols; ++j) {
                 if (!confirmed[j] && rnorm[j] <= tol * bnorm[j]) confirmed[j] = 1;
-                snap.active[j] = !confirmed[j];
+                snap.active[j] = snap.active_next[j] = !confirmed[j];
                 if (!confirmed[j]) {
-                    snap.rho[j] = rnorm[j] * rnorm[j];
+                    snap.rho[j] = snap.rho_next[j] = rnorm[j] * rnorm[j];
                     rho_ref[j] = snap.rho[j];
                 }
                 snap.n_active += snap.active[j];
