@@ -557,6 +557,7 @@ int cg_solve(Plan *p, const double *y, int nrhs, double sigma2, const double *H,
             }
             if (!replace) continue;
             if ((rc = true_residual())) break;
+            if ((rc = init_p())) break;  // the residual product overwrote W64 (FP64 mode)
             snap.n_active = 0;
             for (int j = 0; j < ncols; ++j) {
                 if (!confirmed[j] && rnorm[j] <= tol * bnorm[j]) confirmed[j] = 1;
