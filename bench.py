@@ -343,15 +343,13 @@ def main():
     mvm64_ms = e0.elapsed_time(e1) / 5
     fgk.fgk_destroy(h)
     E = info_p["n_levels"] * p.N
-    bytes_per_launch = E * (4 + 4 + 4 * (p.d - 1) + 2 * 4)  # per entry: q, gap, offsets, V gather, Y update
+    bytes_per_launch = E * (4 + 4 + 4 * (p.d - 1) + 2 * 4)  # q, gap, offsets, V gather, Y update
     pk, src = peaks()
     scan_avg_ms = scan_ms / max(scan_n, 1)
     achieved = bytes_per_launch / (scan_avg_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"], "traffic": SCAN_TRAFFIC_BYTES,
-                "kernel": ("k_level_scan<float,P=2,d-1=1,product>: the scan launches of one product (look-back "
-                           "forward + backward for segments longer than a 2048-entry tile, both directions for the "
-                           "rest), timed together by CUDA events"),
+                "kernel": "k_level_scan<float,P=2,NOFF=1,product,OUT>",
                 "peak_source": f"{src} (hbm_gbs, copy burst)", "avg_launch_ms": scan_avg_ms,
                 "algorithmic_bytes_per_launch": bytes_per_launch}
 

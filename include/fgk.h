@@ -119,9 +119,8 @@ int fgk_matvec_q(fgk_handle h, const void *Vq, int nrhs, void *Yq, int precision
  * into the library, which every GPU that loads the library holds until the
  * process exits.  The first call on a device looks up that array's device
  * address (make it before any stream capture).  All calls on a device share
- * the array, which keeps the last call's contents; each call clears the part
- * that must start at zero with a stream-ordered memset.  Calls whose work
- * overlaps on the GPU race and must be ordered by the caller.  A product needing more scratch than the array holds
+ * the array: calls whose work overlaps on the GPU race and must be ordered
+ * by the caller.  A product needing more scratch than the array holds
  * (the need grows with nrhs and with the number of tiles in segments longer
  * than a tile) returns FGK_ERR_INVALID without launching anything.
  * Arguments, layout and precision as fgk_matvec_q; the handle comes from an

@@ -172,21 +172,19 @@ int build_worklists(Plan *p) {
             }
         }
     }
-    // one buffer: the long-segment tiles (ascending (level, segment, tile)), then
-    // the short-segment tiles
+    // long-segment tiles first in the output launch: they carry more work per tile
     std::vector<WorkItem> all = longs;
     all.insert(all.end(), items.begin(), items.end());
     p->items_host = all;
-    p->n_items = (int)items.size();
+    p->n_items = (int)all.size();
     p->n_long = (int)longs.size();
     p->n_long_segments = (int)(segs.size() / 2);
     p->long_seg_host = segs;
-    if (!all.empty()) {
-        WorkItem *buf = nullptr;
-        FGK_TRY(plan_alloc(p, (void **)&buf, sizeof(WorkItem) * all.size()));
-        FGK_CUDA(cudaMemcpyAsync(buf, all.data(), sizeof(WorkItem) * all.size(), cudaMemcpyHostToDevice, p->stream));
-        p->long_items = buf;
-        p->items = buf + p->n_long;
+    if (p->n_items) {
+        FGK_TRY(plan_alloc(p, (void **)&p->items, sizeof(WorkItem) * all.size()));
+        FGK_CUDA(cudaMemcpyAsync(p->items, all.data(), sizeof(WorkItem) * all.size(), cudaMemcpyHostToDevice,
+                                 p->stream));
+        p->long_items = p->items;  // the long tiles lead the list
     }
     if (!segs.empty()) {
         FGK_TRY(plan_alloc(p, (void **)&p->long_seg, sizeof(int32_t) * segs.size()));

@@ -110,8 +110,8 @@ struct Plan {
 
     // scan work lists (device + host copies)
     std::vector<WorkItem> items_host;
-    WorkItem *items = nullptr;       // tiles of short-segment levels
-    WorkItem *long_items = nullptr;  // tiles of long-segment levels (look-back)
+    WorkItem *items = nullptr;     // all items
+    WorkItem *long_items = nullptr;
     int n_items = 0, n_long = 0;
     int n_long_segments = 0;
     std::vector<int32_t> long_seg_host;  // [first agg, n tiles] per long segment

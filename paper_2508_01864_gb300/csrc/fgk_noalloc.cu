@@ -1,8 +1,8 @@
 // fgk_matvec_q_noalloc: the product in the plan's internal order for callers
 // that must not allocate device memory during the call.
 //
-// The level scans need scratch for the look-back state of segments longer
-// than a tile (per tile: published aggregates, inclusive prefixes, flags).  The ordinary entry points take it from the
+// The level scans need scratch for the per-tile aggregates and carries of
+// segments longer than a tile.  The ordinary entry points take it from the
 // plan's workspace, which grows with cudaMallocAsync when a larger nrhs
 // arrives.  Callers whose device memory is fully planned before they start
 // (a serving loop that has handed its whole budget to admitted requests, an
@@ -16,8 +16,8 @@
 //     current, by cudaGetSymbolAddress on the first call made on that
 //     device (make that first call before any stream capture);
 //   - every call on a device shares the array and it keeps the last call's
-//     contents; the look-back flags that must start at zero are cleared by
-//     a stream-ordered memset at the start of every call; two calls whose work overlaps on
+//     contents; nothing in it has to start at zero (each slot is written
+//     before it is read within a call), but two calls whose work overlaps on
 //     the GPU (different streams, or other threads) race on it and must be
 //     ordered by the caller;
 //   - a product whose scratch need exceeds the array is rejected with
@@ -61,9 +61,7 @@ int noalloc_scratch(void **out) {
     return FGK_OK;
 }
 
-// bytes of look-back state the level scans of this plan need: per long tile,
-// direction, rhs and channel pair an aggregate and an inclusive prefix, and a
-// flag; plus two ticket counters
+// bytes of tile aggregates and carries the level scans of this plan need
 size_t noalloc_need(const Plan *p, int nrhs, size_t elem) {
     const int noff = p->d - 1;
     int na = 1;
@@ -72,8 +70,7 @@ size_t noalloc_need(const Plan *p, int nrhs, size_t elem) {
     const size_t cp = noff == 0 ? 1 : 2;
     const size_t npass = noff == 2 ? 2 : 1;
     const size_t ag = 1 + cp * (size_t)na * p->P;
-    const size_t nslot = (size_t)p->n_long * 2 * nrhs * npass;
-    return 2 * nslot * ag * elem + (nslot + 2) * sizeof(int) + 64;
+    return (size_t)2 * p->n_long * 2 * nrhs * npass * ag * elem;
 }
 
 }  // namespace

@@ -52,14 +52,7 @@ namespace fgk {
 
 constexpr int ipow_c(int b, int e) { return e == 0 ? 1 : b * ipow_c(b, e - 1); }
 
-// SCAN_OUT: segments no longer than a tile, both directions per CTA.
-// SCAN_LB: segments longer than a tile, one direction per launch, carries by
-// decoupled look-back over the tiles' published aggregates.
-enum { SCAN_LB = 0, SCAN_OUT = 1 };
-
-// look-back flag values (0: nothing published yet)
-enum : int { LB_AGG = 1, LB_PREFIX = 2 };
-constexpr int kLookbackSpinLimit = 1 << 22;
+enum { SCAN_AGG = 0, SCAN_OUT = 1 };
 
 // resident CTAs per SM the scan kernels are compiled for (register budget)
 #ifndef FGK_SCAN_MINB
@@ -93,14 +86,8 @@ struct ScanArgs {
     const WorkItem *items;
     const R *V;  // q order, N x nrhs, in the scan precision
     int nrhs;
-    R *Y;  // q order, N x nrhs, accumulated atomically
-    // SCAN_LB only: per (long tile, direction, rhs, pass) slot, the tile's
-    // aggregate, its inclusive prefix, and a flag; and the ticket counter
-    R *lb_agg;
-    R *lb_pre;
-    int *lb_flag;
-    unsigned *ticket;
-    int n_work;
+    R *Y;      // q order, N x nrhs, accumulated atomically
+    R *agg;    // SCAN_AGG: tile aggregates out; SCAN_OUT: carries in
     R s2;
     int *err;
     const int *gate;  // NULL, or a device int: 0 = skip the whole product
@@ -275,73 +262,19 @@ __device__ __forceinline__ void set_identity(R *x) {
     for (int m = 0; m < AG; ++m) x[m] = R(0);
 }
 
-// Decoupled look-back (SCAN_LB): with the tile's aggregate in hand, thread 0
-// publishes it (or, for the first tile of its segment in this direction, its
-// inclusive prefix), then walks back over the preceding tiles of the segment,
-// composing published aggregates until it meets a published inclusive prefix,
-// and publishes its own.  Tiles are taken in ticket order, so every tile
-// waited on was started by a running CTA; each wait is bounded (on expiry the
-// error word gets DEV_TIMEOUT and the predecessor is taken as empty).
-template <class R, int P, int AG>
-__device__ void lookback(const ScanArgs<R> &A, const R *agg, size_t slot_idx, size_t step, bool first, R *excl) {
-    set_identity<R, AG>(excl);
-    if (first) {
-#pragma unroll
-        for (int m = 0; m < AG; ++m) __stcg(A.lb_pre + slot_idx * AG + m, agg[m]);
-        __threadfence();
-        atomicExch(A.lb_flag + slot_idx, LB_PREFIX);
-        return;
-    }
-#pragma unroll
-    for (int m = 0; m < AG; ++m) __stcg(A.lb_agg + slot_idx * AG + m, agg[m]);
-    __threadfence();
-    atomicExch(A.lb_flag + slot_idx, LB_AGG);
-    size_t j = slot_idx - step;  // preceding tile in the walk direction (step may wrap for backward)
-    while (true) {
-        int f;
-        int spins = 0;
-        while ((f = *((volatile int *)(A.lb_flag + j))) == 0) {
-            if (++spins > kLookbackSpinLimit) {
-                atomicExch(A.err, DEV_TIMEOUT);
-                break;
-            }
-            __nanosleep(64);
-        }
-        if (f == 0) break;
-        __threadfence();
-        const R *src = (f == LB_PREFIX ? A.lb_pre : A.lb_agg) + j * AG;
-        R prev[AG];
-#pragma unroll
-        for (int m = 0; m < AG; ++m) prev[m] = __ldcg(src + m);
-        compose_after<R, P, AG>(excl, prev);
-        if (f == LB_PREFIX) break;
-        j -= step;
-    }
-    R incl[AG];
-#pragma unroll
-    for (int m = 0; m < AG; ++m) incl[m] = agg[m];
-    compose_after<R, P, AG>(incl, excl);
-#pragma unroll
-    for (int m = 0; m < AG; ++m) __stcg(A.lb_pre + slot_idx * AG + m, incl[m]);
-    __threadfence();
-    atomicExch(A.lb_flag + slot_idx, LB_PREFIX);
-}
-
 // One CTA = one tile of kTile consecutive entries of one level; each thread
 // owns kScanEPT consecutive entries, held in registers.  Per right-hand side
-// and channel pair: fold each thread's entries, scan the folds across the
-// threads of each segment (warp shuffles, then the warp totals through shared
-// memory), and walk the entries again from the carried-in moments, reading
-// queries and inserting sources.  SCAN_OUT handles segments up to a tile in
-// both directions; SCAN_LB handles segments longer than a tile, direction
-// DIRSEL only, with the tile's carry from the look-back above.
-template <class R, int P, int NOFF, int KIND, int MODE, int DIRSEL>
+// and channel pair: fold each thread's entries in both directions, scan the
+// folds across the threads of each segment (warp shuffles, then the warp
+// totals through shared memory), and walk the entries again from the
+// carried-in moments, reading queries and inserting sources.  Segments
+// longer than a tile receive their carry from the aggregate pass
+// (MODE == SCAN_AGG writes each tile's totals; k_carry_scan scans them).
+template <class R, int P, int NOFF, int KIND, int MODE>
 __global__ void __launch_bounds__(kScanThreads, FGK_SCAN_MINB) k_level_scan(ScanArgs<R> A) {
     using Tr = Traits<P, NOFF, KIND>;
     constexpr int MOM = Tr::MOM, CP = Tr::CP, SMM = Tr::SM, AG = Tr::AG, NPASS = Tr::NPASS, NCH = Tr::NCH;
-    // directions per walk and direction passes
-    constexpr int ND = DIRSEL < 0 ? Tr::NDIR : 1, NDP = DIRSEL < 0 ? 2 / ND : 1;
-    static_assert(MODE == SCAN_OUT || DIRSEL >= 0, "look-back tiles walk one direction");
+    constexpr int ND = Tr::NDIR, NDP = 2 / ND;  // directions per walk, direction passes
     constexpr int EPT = kScanEPT, NT = kScanThreads, NW = NT / 32;
     constexpr int LOG2EPT = (EPT == 8) ? 3 : (EPT == 4 ? 2 : (EPT == 16 ? 4 : 0));
     constexpr int NO = NOFF > 0 ? NOFF : 1;
@@ -349,20 +282,9 @@ __global__ void __launch_bounds__(kScanThreads, FGK_SCAN_MINB) k_level_scan(Scan
     static_assert((1 << LOG2EPT) == EPT, "EPT must be 4, 8 or 16");
     static_assert(EPT == 8, "vector loads assume 8 entries per thread");
     __shared__ R s_w[ND][NW][AG];
-    __shared__ R s_carry[AG];
-    __shared__ int s_item;
 
     if (A.gate && *A.gate == 0) return;
-    int item = blockIdx.x;
-    if constexpr (MODE == SCAN_LB) {
-        if (threadIdx.x == 0) {
-            const int t = (int)atomicAdd(A.ticket, 1u);
-            s_item = DIRSEL == 0 ? t : A.n_work - 1 - t;  // forward: ascending tiles; backward: descending
-        }
-        __syncthreads();
-        item = s_item;
-    }
-    const WorkItem wi = A.items[item];
+    const WorkItem wi = A.items[blockIdx.x];
     const int64_t N = A.N;
     const int64_t base = (int64_t)wi.tile * kTile;
     const int log2S = wi.log2S;
@@ -437,6 +359,7 @@ __global__ void __launch_bounds__(kScanThreads, FGK_SCAN_MINB) k_level_scan(Scan
     const bool multi = log2S < LOG2EPT;  // whole segments inside one thread
     const int G = multi ? 1 : (int)((S >> LOG2EPT) < (int64_t)NT ? (S >> LOG2EPT) : (int64_t)NT);
     const int GW = G < 32 ? G : 32;
+    const bool is_long = S > kTile;
 
     for (int r = 0; r < A.nrhs; ++r) {
         R v[EPT], out[EPT];
@@ -464,7 +387,7 @@ __global__ void __launch_bounds__(kScanThreads, FGK_SCAN_MINB) k_level_scan(Scan
                     for (int ii = 0; ii < EPT; ++ii) {
 #pragma unroll
                         for (int dd = 0; dd < ND; ++dd) {
-                            const int dir = DIRSEL >= 0 ? DIRSEL : (ND == 2 ? dd : dp);
+                            const int dir = ND == 2 ? dd : dp;
                             const int i = dir == 0 ? ii : EPT - 1 - ii;
                             const R gg = dir == 0 ? g[i] : (i < EPT - 1 ? g[i + 1] : gn);
                             const R ee = dir == 0 ? eg[i] : (i < EPT - 1 ? eg[i + 1] : egn);
@@ -486,7 +409,7 @@ __global__ void __launch_bounds__(kScanThreads, FGK_SCAN_MINB) k_level_scan(Scan
                     for (int dlt = 1; dlt < GW; dlt <<= 1) {
 #pragma unroll
                         for (int dd = 0; dd < ND; ++dd) {
-                            const int dir = DIRSEL >= 0 ? DIRSEL : (ND == 2 ? dd : dp);
+                            const int dir = ND == 2 ? dd : dp;
                             const int vlane = dir == 0 ? lane : 31 - lane;
                             R prev[AG];
 #pragma unroll
@@ -498,7 +421,7 @@ __global__ void __launch_bounds__(kScanThreads, FGK_SCAN_MINB) k_level_scan(Scan
                     }
 #pragma unroll
                     for (int dd = 0; dd < ND; ++dd) {
-                        const int dir = DIRSEL >= 0 ? DIRSEL : (ND == 2 ? dd : dp);
+                        const int dir = ND == 2 ? dd : dp;
                         const int vlane = dir == 0 ? lane : 31 - lane;
                         R prev[AG];
 #pragma unroll
@@ -512,10 +435,10 @@ __global__ void __launch_bounds__(kScanThreads, FGK_SCAN_MINB) k_level_scan(Scan
                     }
                     // 3. across warps: every thread composes the totals of the
                     //    earlier warps of its segment (and the tile carry)
-                    if (G > 32 || MODE == SCAN_LB) {
+                    if (G > 32 || MODE == SCAN_AGG) {
 #pragma unroll
                         for (int dd = 0; dd < ND; ++dd) {
-                            const int dir = DIRSEL >= 0 ? DIRSEL : (ND == 2 ? dd : dp);
+                            const int dir = ND == 2 ? dd : dp;
                             const int vlane = dir == 0 ? lane : 31 - lane;
                             const int vwarp = dir == 0 ? warp : NW - 1 - warp;
                             if (vlane == 31) {
@@ -524,57 +447,51 @@ __global__ void __launch_bounds__(kScanThreads, FGK_SCAN_MINB) k_level_scan(Scan
                             }
                         }
                         __syncthreads();
-                        if constexpr (MODE == SCAN_LB) {
-                            if (tid == 0) {
-                                R tot[AG], excl[AG];
-                                set_identity<R, AG>(tot);
-                                for (int w2 = 0; w2 < NW; ++w2) {
-                                    R t[AG];
-#pragma unroll
-                                    for (int m = 0; m < AG; ++m) t[m] = s_w[0][w2][m];
-                                    compose_after<R, P, AG>(t, tot);
-#pragma unroll
-                                    for (int m = 0; m < AG; ++m) tot[m] = t[m];
-                                }
-                                // slots of one segment are consecutive in tile order
-                                const size_t per = (size_t)A.nrhs * NPASS;
-                                const size_t idx = (((size_t)wi.agg * 2 + DIRSEL) * A.nrhs + r) * NPASS + pp;
-                                const bool first = DIRSEL == 0 ? wi.tile == wi.seg_tile0
-                                                               : wi.tile == wi.seg_tile0 + wi.seg_ntiles - 1;
-                                const size_t step = DIRSEL == 0 ? 2 * per : (size_t)0 - 2 * per;
-                                lookback<R, P, AG>(A, tot, idx, step, first, excl);
-#pragma unroll
-                                for (int m = 0; m < AG; ++m) s_carry[m] = excl[m];
-                            }
-                            __syncthreads();
-                        }
 #pragma unroll
                         for (int dd = 0; dd < ND; ++dd) {
-                            const int dir = DIRSEL >= 0 ? DIRSEL : (ND == 2 ? dd : dp);
+                            const int dir = ND == 2 ? dd : dp;
                             const int vwarp = dir == 0 ? warp : NW - 1 - warp;
-                            const int GWn = G > 32 ? G / 32 : 1;
-                            const int w0 = MODE == SCAN_LB ? 0 : (vwarp / GWn) * GWn;
-                            R pre[AG];
-                            if constexpr (MODE == SCAN_LB) {
+                            const size_t cslot = ((((size_t)wi.agg * 2 + dir) * A.nrhs + r) * NPASS + pp) * AG;
+                            if (MODE == SCAN_AGG) {
+                                if (tid == dd * 32) {  // the tile's total
+                                    R run[AG];
+                                    set_identity<R, AG>(run);
+                                    for (int w2 = 0; w2 < NW; ++w2) {
+                                        R t[AG];
 #pragma unroll
-                                for (int m = 0; m < AG; ++m) pre[m] = s_carry[m];
+                                        for (int m = 0; m < AG; ++m) t[m] = s_w[dd][w2][m];
+                                        compose_after<R, P, AG>(t, run);
+#pragma unroll
+                                        for (int m = 0; m < AG; ++m) run[m] = t[m];
+                                    }
+#pragma unroll
+                                    for (int m = 0; m < AG; ++m) A.agg[cslot + m] = run[m];
+                                }
                             } else {
-                                set_identity<R, AG>(pre);
-                            }
-                            for (int w2 = w0; w2 < vwarp; ++w2) {
-                                R t[AG];
+                                const int GWn = G > 32 ? G / 32 : 1;
+                                const int w0 = is_long ? 0 : (vwarp / GWn) * GWn;
+                                R pre[AG];
+                                if (is_long) {
 #pragma unroll
-                                for (int m = 0; m < AG; ++m) t[m] = s_w[dd][w2][m];
-                                compose_after<R, P, AG>(t, pre);
+                                    for (int m = 0; m < AG; ++m) pre[m] = A.agg[cslot + m];
+                                } else {
+                                    set_identity<R, AG>(pre);
+                                }
+                                for (int w2 = w0; w2 < vwarp; ++w2) {
+                                    R t[AG];
 #pragma unroll
-                                for (int m = 0; m < AG; ++m) pre[m] = t[m];
+                                    for (int m = 0; m < AG; ++m) t[m] = s_w[dd][w2][m];
+                                    compose_after<R, P, AG>(t, pre);
+#pragma unroll
+                                    for (int m = 0; m < AG; ++m) pre[m] = t[m];
+                                }
+                                compose_after<R, P, AG>(ex[dd], pre);
                             }
-                            compose_after<R, P, AG>(ex[dd], pre);
                         }
                         __syncthreads();
                     }
                 }
-                {
+                if constexpr (MODE == SCAN_OUT) {
                     // 4. walk again from the carried-in moments; read, then insert
                     R st[ND][SMM];
 #pragma unroll
@@ -585,7 +502,7 @@ __global__ void __launch_bounds__(kScanThreads, FGK_SCAN_MINB) k_level_scan(Scan
                     for (int ii = 0; ii < EPT; ++ii) {
 #pragma unroll
                         for (int dd = 0; dd < ND; ++dd) {
-                            const int dir = DIRSEL >= 0 ? DIRSEL : (ND == 2 ? dd : dp);
+                            const int dir = ND == 2 ? dd : dp;
                             const int i = dir == 0 ? ii : EPT - 1 - ii;
                             if (multi) {
                                 const int jj = j0 + i;
@@ -626,11 +543,64 @@ __global__ void __launch_bounds__(kScanThreads, FGK_SCAN_MINB) k_level_scan(Scan
                 }
             }
         }
-        {
+        if constexpr (MODE == SCAN_OUT) {
 #pragma unroll
             for (int i = 0; i < EPT; ++i)
                 if (i < nvalid) atomicAdd(A.Y + (size_t)(q[i] & 0x3fffffffu) * A.nrhs + r, A.s2 * out[i]);
         }
+    }
+}
+
+// Exclusive scan of the tile aggregates of every long segment, in both
+// directions: carry[tile] = composition of the tiles before it (forward) or
+// after it (backward).  One warp per (segment, direction, rhs, channel pair)
+// scans the segment's tiles 32 at a time.
+template <class R, int P, int NOFF, int KIND>
+__global__ void k_carry_scan(const R *__restrict__ agg, R *__restrict__ carry, const int32_t *__restrict__ segs,
+                             int nseg, int nrhs, const int *__restrict__ gate) {
+    if (gate && *gate == 0) return;
+    using Tr = Traits<P, NOFF, KIND>;
+    constexpr int AG = Tr::AG, NPASS = Tr::NPASS;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t total = (int64_t)nseg * 2 * nrhs * NPASS;
+    if (wid >= total) return;  // uniform per warp
+    const int pp = (int)(wid % NPASS);
+    const int r = (int)((wid / NPASS) % nrhs);
+    const int dir = (int)((wid / ((int64_t)NPASS * nrhs)) % 2);
+    const int sg = (int)(wid / ((int64_t)NPASS * nrhs * 2));
+    const int a0 = segs[2 * sg], nt = segs[2 * sg + 1];
+    R run[AG];
+    set_identity<R, AG>(run);
+    for (int k0 = 0; k0 < nt; k0 += 32) {
+        const int k = k0 + lane;
+        const bool valid = k < nt;
+        const int slot = a0 + (dir == 0 ? k : nt - 1 - k);
+        const size_t off = ((((size_t)(valid ? slot : a0) * 2 + dir) * nrhs + r) * NPASS + pp) * AG;
+        R inc[AG];
+#pragma unroll
+        for (int m = 0; m < AG; ++m) inc[m] = valid ? agg[off + m] : R(0);
+        for (int dlt = 1; dlt < 32; dlt <<= 1) {
+            R prev[AG];
+#pragma unroll
+            for (int m = 0; m < AG; ++m) prev[m] = __shfl_up_sync(0xffffffffu, inc[m], dlt);
+            if (lane >= dlt) compose_after<R, P, AG>(inc, prev);
+        }
+        R ex[AG];
+#pragma unroll
+        for (int m = 0; m < AG; ++m) ex[m] = __shfl_up_sync(0xffffffffu, inc[m], 1);
+        if (lane == 0) set_identity<R, AG>(ex);
+        compose_after<R, P, AG>(ex, run);
+        if (valid) {
+#pragma unroll
+            for (int m = 0; m < AG; ++m) carry[off + m] = ex[m];
+        }
+        R last[AG];
+#pragma unroll
+        for (int m = 0; m < AG; ++m) last[m] = __shfl_sync(0xffffffffu, inc[m], 31);
+        compose_after<R, P, AG>(last, run);
+#pragma unroll
+        for (int m = 0; m < AG; ++m) run[m] = last[m];
     }
 }
 
@@ -658,47 +628,44 @@ int run_levels(Plan *p, const R *Vq, int nrhs, R *Yq, R *ws, cudaStream_t s, con
     A.s2 = (R)p->s2;
     A.err = p->dev_err;
     A.gate = gate;
-    const size_t nslot = (size_t)p->n_long * 2 * nrhs * Tr::NPASS;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (scan_timing_enabled() && cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
-        FGK_CUDA(cudaEventCreate(&e0));
-        FGK_CUDA(cudaEventCreate(&e1));
-        FGK_CUDA(cudaEventRecord(e0, s));
-    }
+    const size_t per_slot = (size_t)2 * nrhs * Tr::NPASS * Tr::AG;
+    R *agg = ws;
+    R *carry = ws + (size_t)p->n_long * per_slot;
     if (p->n_long > 0) {
-        A.lb_agg = ws;
-        A.lb_pre = ws + nslot * Tr::AG;
-        A.lb_flag = reinterpret_cast<int *>(ws + 2 * nslot * Tr::AG);
-        A.ticket = reinterpret_cast<unsigned *>(A.lb_flag + nslot);
-        FGK_CUDA(cudaMemsetAsync(A.lb_flag, 0, (nslot + 2) * sizeof(int), s));
         A.items = p->long_items;
-        A.n_work = p->n_long;
-        k_level_scan<R, P, NOFF, KIND, SCAN_LB, 0><<<p->n_long, kScanThreads, 0, s>>>(A);
+        A.agg = agg;
+        k_level_scan<R, P, NOFF, KIND, SCAN_AGG><<<p->n_long, kScanThreads, 0, s>>>(A);
         FGK_LAUNCH_CHECK();
-        A.ticket += 1;
-        k_level_scan<R, P, NOFF, KIND, SCAN_LB, 1><<<p->n_long, kScanThreads, 0, s>>>(A);
+        const int64_t nthr = (int64_t)p->n_long_segments * 2 * nrhs * Tr::NPASS * 32;
+        k_carry_scan<R, P, NOFF, KIND><<<grid_for(nthr, 128), 128, 0, s>>>(agg, carry, p->long_seg,
+                                                                           p->n_long_segments, nrhs, gate);
         FGK_LAUNCH_CHECK();
     }
     if (p->n_items > 0) {
         A.items = p->items;
-        A.n_work = p->n_items;
-        k_level_scan<R, P, NOFF, KIND, SCAN_OUT, -1><<<p->n_items, kScanThreads, 0, s>>>(A);
+        A.agg = carry;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (scan_timing_enabled() && cudaStreamIsCapturing(s, &cs) == cudaSuccess &&
+            cs == cudaStreamCaptureStatusNone) {
+            FGK_CUDA(cudaEventCreate(&e0));
+            FGK_CUDA(cudaEventCreate(&e1));
+            FGK_CUDA(cudaEventRecord(e0, s));
+        }
+        k_level_scan<R, P, NOFF, KIND, SCAN_OUT><<<p->n_items, kScanThreads, 0, s>>>(A);
         FGK_LAUNCH_CHECK();
-    }
-    if (e0) {
-        FGK_CUDA(cudaEventRecord(e1, s));
-        scan_timing_record(e0, e1);
+        if (e0) {
+            FGK_CUDA(cudaEventRecord(e1, s));
+            scan_timing_record(e0, e1);
+        }
     }
     return FGK_OK;
 }
 
 template <class R>
 size_t scan_ws_elems(const Plan *p, int nrhs) {
-    // look-back slots for the largest aggregate (product, P = 3, d = 3: 1 + 2 x 27)
-    // and 2 passes: aggregates, inclusive prefixes, flags and tickets
-    const size_t nslot = (size_t)p->n_long * 2 * nrhs * 2;
-    return 2 * nslot * 56 + (nslot + 2) * sizeof(int) / sizeof(R) + 64;
+    // generous: the largest aggregate (product, P = 3, d = 3: 1 + 2 x 27) and 2 passes
+    return (size_t)2 * p->n_long * 2 * nrhs * 2 * 56 + 64;
 }
 
 // dispatch over (P, d-1, kind); nu = 1/2 or d = 1 make both kinds the same kernel
