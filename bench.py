@@ -165,6 +165,39 @@ def cpu_baseline(p, iters, seconds):
             "mvm_nrhs_per_s": p.N / t_mvm}
 
 
+def run_serving(args, local):
+    """Continuous-batching replay of the serving stream's first K requests:
+    first as a burst (all arriving at once) to measure the sustained capacity,
+    then with Poisson arrivals at 0.8x that capacity for the latencies."""
+    import torch
+
+    import workloads
+    from paper_2508_01864_gb300 import serving
+
+    torch.cuda.set_device(local)
+    reqs, gaps = workloads.c5(n_requests=args.serving)
+    requests = serving.to_requests(reqs, tol=TOL)
+    out = {"metric": "serving: GP solves/sec at resid<=1e-8 with p50/p99 latency", "unit": "solves/s",
+           "requests": len(requests), "slots": args.slots, "budget_bytes": 150e9,
+           "workload": (f"first {len(requests)} requests of the seeded serving stream: N log-uniform 2k-300k, "
+                        "d in 1..3, nu in {1/2,3/2,5/2}, x~U[0,1]^d, product kernel, sigma^2=0.01, mixed CG")}
+    srv = serving.Server(budget_bytes=150e9, slots=args.slots)
+    burst = serving.replay(srv, requests, np.zeros(len(requests)), rate=1.0)
+    srv.close()
+    sb = serving.summarize(burst)
+    out["burst"] = sb
+    cap = sb.get("solves_per_s", 0.0)
+    if cap > 0:
+        srv = serving.Server(budget_bytes=150e9, slots=args.slots)
+        steady = serving.replay(srv, requests, gaps[:len(requests)], rate=0.8 * cap)
+        srv.close()
+        out["steady_0.8x"] = serving.summarize(steady)
+        out["value"] = out["steady_0.8x"].get("solves_per_s")
+        out["peak_concurrency"] = srv.stats.peak_concurrency
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_mvm_only(args, local):
     """W + K FP32 products in the internal order on the d=2 workload with
     --mvm-only points (for profiling the scan kernels at sizes above L2)."""
@@ -210,6 +243,9 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=5000)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving", type=int, default=0,
+                    help="replay the first K requests of the serving stream (burst, then 0.8x its capacity)")
+    ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--mvm-only", type=int, default=0,
                     help="time only the FP32 product on the d=2 workload drawn with this many points")
     args = ap.parse_args()
@@ -218,6 +254,8 @@ def main():
         return run_reference(args, ws, rank)
     if args.mvm_only:
         return run_mvm_only(args, local)
+    if args.serving:
+        return run_serving(args, local)
 
     import torch
     import torch.distributed as dist

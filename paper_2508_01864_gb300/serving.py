@@ -1,0 +1,223 @@
+"""Continuous-batching server for GP solves on one GPU.
+
+Requests (a point set, a right-hand side and kernel parameters) arrive over
+time.  The dispatcher admits them in arrival order as soon as a slot is free
+and the device-memory budget has room for the request's estimated footprint
+(``fgk_bytes_estimate``).  Each admitted request runs on a worker thread with
+its own CUDA stream: host->device copies, ``fgk_build`` (its sort and
+dominance structure stay on the device for the request's lifetime),
+``fgk_cg_solve`` (its CG state stays on the device), the device->host copy of
+alpha, ``fgk_destroy``.  The solves of all admitted requests overlap on the
+device; a request leaves as soon as its own solve converges, freeing its slot
+and memory for the next arrival.  Latency is measured from arrival to the
+result being on the host.
+
+All GPU work happens inside libfgk's kernels; this module only schedules.  The
+executor is injectable so the scheduling logic can be exercised without a GPU.
+"""
+
+from __future__ import annotations
+
+import queue
+import threading
+import time
+from concurrent.futures import Future, ThreadPoolExecutor
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Request:
+    rid: int
+    X: np.ndarray  # N x d float64
+    y: np.ndarray  # N float64
+    nu: float
+    ell: np.ndarray
+    sigma2: float
+    kind: str = "product"
+    tol: float = 1e-8
+    arrival: float = 0.0  # set by the server when submitted
+
+    @property
+    def N(self) -> int:
+        return self.X.shape[0]
+
+    @property
+    def d(self) -> int:
+        return self.X.shape[1]
+
+
+@dataclass
+class Result:
+    rid: int
+    alpha: np.ndarray | None
+    info: dict
+    status: int
+    arrival: float
+    admitted: float
+    finished: float
+    error: str | None = None
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+@dataclass
+class Stats:
+    submitted: int = 0
+    admitted: int = 0
+    completed: int = 0
+    rejected: int = 0
+    peak_bytes: int = 0
+    peak_concurrency: int = 0
+    results: list = field(default_factory=list)
+
+
+def gpu_executor(mode: str = "mixed", maxit: int = 200000):
+    """The real executor: one request, start to end, on a private stream."""
+    import torch
+
+    from . import fgk
+
+    def run(req: Request):
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            X = torch.as_tensor(np.ascontiguousarray(req.X)).pin_memory().to("cuda", non_blocking=True)
+            y = torch.as_tensor(np.ascontiguousarray(req.y).reshape(-1, 1)).pin_memory().to("cuda",
+                                                                                           non_blocking=True)
+            h = fgk.fgk_build(X, req.nu, req.ell, kind=req.kind, stream=stream)
+            try:
+                alpha, _, info, rc = fgk.fgk_cg_solve(h, y, req.sigma2, tol=req.tol, maxit=maxit, mode=mode,
+                                                      stream=stream)
+                a = alpha.cpu().numpy().reshape(-1)
+            finally:
+                fgk.fgk_destroy(h)
+        return a, info, rc
+
+    return run
+
+
+def gpu_estimator(nrhs_cols: int = 1):
+    from . import fgk
+
+    def est(req: Request) -> int:
+        return int(fgk.fgk_bytes_estimate(req.N, req.d, req.nu, req.kind, nrhs_cols)) + req.N * (req.d + 3) * 8
+
+    return est
+
+
+class Server:
+    """FIFO admission by slots and a device-memory budget; workers overlap."""
+
+    def __init__(self, budget_bytes: float = 150e9, slots: int = 8, executor=None, estimator=None):
+        self.budget = int(budget_bytes)
+        self.slots = int(slots)
+        self.executor = executor or gpu_executor()
+        self.estimator = estimator or gpu_estimator()
+        self.stats = Stats()
+        self._pending: queue.Queue = queue.Queue()
+        self._lock = threading.Condition()
+        self._used = 0
+        self._running = 0
+        self._pool = ThreadPoolExecutor(max_workers=self.slots)
+        self._stop = False
+        self._futures: dict[int, Future] = {}
+        self._dispatcher = threading.Thread(target=self._dispatch, daemon=True)
+        self._dispatcher.start()
+
+    # ------------------------------------------------------------ client side
+    def submit(self, req: Request) -> Future:
+        fut: Future = Future()
+        need = self.estimator(req)
+        req.arrival = time.perf_counter()
+        with self._lock:
+            self.stats.submitted += 1
+            if need > self.budget:
+                self.stats.rejected += 1
+                fut.set_result(Result(req.rid, None, {}, -1, req.arrival, req.arrival, req.arrival,
+                                      error=f"needs {need} bytes, more than the {self.budget}-byte budget"))
+                return fut
+            self._futures[req.rid] = fut
+        self._pending.put((req, need))
+        return fut
+
+    def close(self, wait: bool = True):
+        self._stop = True
+        self._pending.put(None)
+        self._dispatcher.join()
+        self._pool.shutdown(wait=wait)
+
+    # ------------------------------------------------------------ scheduling
+    def _dispatch(self):
+        while True:
+            item = self._pending.get()
+            if item is None:
+                return
+            req, need = item
+            with self._lock:
+                while self._running >= self.slots or self._used + need > self.budget:
+                    self._lock.wait()
+                self._running += 1
+                self._used += need
+                self.stats.admitted += 1
+                self.stats.peak_bytes = max(self.stats.peak_bytes, self._used)
+                self.stats.peak_concurrency = max(self.stats.peak_concurrency, self._running)
+            admitted = time.perf_counter()
+            self._pool.submit(self._work, req, need, admitted)
+
+    def _work(self, req: Request, need: int, admitted: float):
+        err = None
+        alpha, info, rc = None, {}, -1
+        try:
+            alpha, info, rc = self.executor(req)
+        except Exception as e:  # a failed request is reported, the server keeps going
+            err = f"{type(e).__name__}: {e}"
+        finished = time.perf_counter()
+        res = Result(req.rid, alpha, info, rc, req.arrival, admitted, finished, err)
+        with self._lock:
+            self._used -= need
+            self._running -= 1
+            self.stats.completed += 1
+            self.stats.results.append(res)
+            fut = self._futures.pop(req.rid, None)
+            self._lock.notify_all()
+        if fut is not None:
+            fut.set_result(res)
+
+
+def replay(server: Server, requests: list[Request], gaps: np.ndarray, rate: float) -> list[Result]:
+    """Submit requests at the arrival times given by unit-mean gaps scaled to
+    ``rate`` requests per second; return the results in request order."""
+    t0 = time.perf_counter()
+    arrivals = np.cumsum(np.asarray(gaps, dtype=np.float64) / rate)
+    futs = []
+    for req, at in zip(requests, arrivals):
+        delay = t0 + at - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        futs.append(server.submit(req))
+    return [f.result() for f in futs]
+
+
+def summarize(results: list[Result]) -> dict:
+    ok = [r for r in results if r.error is None and r.status in (0, 1)]
+    if not ok:
+        return {"completed": 0}
+    lat = np.array([r.latency for r in ok])
+    span = max(r.finished for r in ok) - min(r.arrival for r in ok)
+    return {"completed": len(ok), "failed": len(results) - len(ok),
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_s": float(lat.mean()), "makespan_s": float(span), "solves_per_s": len(ok) / span}
+
+
+def to_requests(problems, tol: float = 1e-8, kind: str = "product") -> list[Request]:
+    out = []
+    for i, p in enumerate(problems):
+        out.append(Request(i, p.X, p.V[:, 0], p.nu, p.ell, p.sigma2, kind=kind, tol=tol))
+    return out
+
+
+__all__ = ["Request", "Result", "Server", "Stats", "gpu_executor", "gpu_estimator", "replay", "summarize",
+           "to_requests"]

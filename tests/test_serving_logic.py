@@ -1,0 +1,84 @@
+"""Scheduling logic of the continuous-batching server, without a GPU: a fake
+executor stands in for the device work."""
+
+import threading
+import time
+
+import numpy as np
+
+from paper_2508_01864_gb300 import serving
+
+
+def make_requests(n, seed=0):
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(n):
+        N = int(rng.integers(50, 400))
+        X = rng.uniform(size=(N, 2))
+        reqs.append(serving.Request(i, X, rng.standard_normal(N), 1.5, np.array([0.2, 0.2]), 0.01))
+    return reqs
+
+
+class FakeDevice:
+    """Sleeps in proportion to N and records the memory in use."""
+
+    def __init__(self, per_point=2e-5):
+        self.per_point = per_point
+        self.lock = threading.Lock()
+        self.in_use = 0
+        self.peak = 0
+        self.concurrent = 0
+        self.peak_concurrent = 0
+        self.order = []
+
+    def estimate(self, req):
+        return req.N * 1000
+
+    def run(self, req):
+        with self.lock:
+            self.in_use += self.estimate(req)
+            self.concurrent += 1
+            self.peak = max(self.peak, self.in_use)
+            self.peak_concurrent = max(self.peak_concurrent, self.concurrent)
+            self.order.append(req.rid)
+        time.sleep(req.N * self.per_point)
+        if req.rid == 5:
+            raise RuntimeError("injected failure")
+        with self.lock:
+            self.in_use -= self.estimate(req)
+            self.concurrent -= 1
+        return req.y.copy(), {"iterations": 1}, 0
+
+
+def test_budget_slots_and_fifo():
+    dev = FakeDevice()
+    budget = 700 * 1000  # at most ~2-3 requests at once
+    srv = serving.Server(budget_bytes=budget, slots=3, executor=dev.run, estimator=dev.estimate)
+    reqs = make_requests(20)
+    futs = [srv.submit(r) for r in reqs]
+    res = [f.result(timeout=60) for f in futs]
+    srv.close()
+    assert srv.stats.completed == 20 and srv.stats.admitted == 20
+    assert srv.stats.peak_bytes <= budget
+    assert srv.stats.peak_concurrency <= 3
+    assert dev.order == sorted(dev.order)  # admitted in arrival order
+    failed = [r for r in res if r.error]
+    assert [r.rid for r in failed] == [5]  # the failure is reported, the rest are served
+    for r in res:
+        if not r.error:
+            assert np.array_equal(r.alpha, reqs[r.rid].y)
+            assert r.finished >= r.admitted >= r.arrival
+
+
+def test_oversized_request_rejected_and_summary():
+    dev = FakeDevice(per_point=1e-6)
+    srv = serving.Server(budget_bytes=500 * 1000, slots=2, executor=dev.run, estimator=dev.estimate)
+    reqs = make_requests(6, seed=3)
+    reqs[2].X = np.random.default_rng(1).uniform(size=(1000, 2))
+    reqs[2].y = np.zeros(1000)
+    out = serving.replay(srv, reqs, np.ones(6), rate=1000.0)
+    srv.close()
+    assert out[2].error and "budget" in out[2].error and srv.stats.rejected == 1
+    s = serving.summarize(out)
+    assert s["completed"] == 4  # 2 rejected/failed (rid 2 oversized, rid 5 raises)
+    assert s["p99_s"] >= s["p50_s"] > 0
