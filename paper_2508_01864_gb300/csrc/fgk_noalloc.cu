@@ -61,7 +61,9 @@ int noalloc_scratch(void **out) {
     return FGK_OK;
 }
 
-// bytes of tile aggregates and carries the level scans of this plan need
+// bytes of tile aggregates and carries the level scans of this plan need:
+// per long tile, direction, rhs and pass, an aggregate and a carry of
+// 1 + (channels per pass) x (offset groups per pass) x P values
 size_t noalloc_need(const Plan *p, int nrhs, size_t elem) {
     const int noff = p->d - 1;
     int na = 1;
@@ -69,8 +71,10 @@ size_t noalloc_need(const Plan *p, int nrhs, size_t elem) {
         for (int k = 0; k < noff; ++k) na *= p->P;
     const size_t cp = noff == 0 ? 1 : 2;
     const size_t npass = noff == 2 ? 2 : 1;
-    const size_t ag = 1 + cp * (size_t)na * p->P;
-    return (size_t)2 * p->n_long * 2 * nrhs * npass * ag * elem;
+    const size_t gp = (na > 1 && cp * na * p->P > 12) ? 1 : na;  // as the scan kernels split them
+    const size_t ngp = na / gp;
+    const size_t ag = 1 + cp * gp * p->P;
+    return (size_t)2 * p->n_long * 2 * nrhs * npass * ngp * ag * elem;
 }
 
 }  // namespace

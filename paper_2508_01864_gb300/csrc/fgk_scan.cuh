@@ -70,10 +70,19 @@ struct Traits {
     static constexpr int NCH = 1 << NOFF;              // role channels
     static constexpr int CP = NOFF == 0 ? 1 : 2;       // channels per pass
     static constexpr int NPASS = NOFF == 2 ? 2 : 1;    // channel-pair passes
-    static constexpr int SM = CP * MOM;                // moments per pass and direction
+    // The product kernel's moments fall into NA groups (one per power pattern
+    // of the offsets) that the step never mixes, so groups can be scanned in
+    // separate passes; a pass carries GP groups of P moments per channel.
+    static constexpr int GP = (NA > 1 && CP * NA * P > 12) ? 1 : NA;
+    static constexpr int NGP = NA / GP;                // group passes
+    static constexpr int GM = GP * P;                  // moments per channel in a pass
+    static constexpr int SM = CP * GM;                 // moments per pass and direction
     static constexpr int AG = 1 + SM;                  // aggregate: T, moments
     static constexpr int NDIR = SM <= 12 ? 2 : 1;      // directions walked together
+    static constexpr int NPT = NPASS * NGP;            // passes per right-hand side
+    static constexpr int NWC = NOFF == 0 ? 1 : (NA == 1 ? P : GP);  // per-entry coefficients of a pass
 };
+
 
 template <class R>
 struct ScanArgs {
@@ -147,20 +156,33 @@ __device__ __forceinline__ R csum(const R *m) {
     else return m[0] + m[1] + m[2] * (R(1) / R(3));
 }
 
-// source weights w (per unit v) for the entry's offsets: L1 adds w[q] to
-// M[q] (w[q] = e^{-s} s^q, s = sum of offsets), the product kernel adds w[a]
-// to M[a][0] (w[a] = prod_k o_k^{a_k} e^{-o_k}); d = 1 adds v to M[0].
-template <class R, int P, int NOFF, int KIND>
-struct SrcW {
-    static constexpr int NA = Traits<P, NOFF, KIND>::NA;
-    static constexpr int NW = NOFF == 0 ? 1 : (NA == 1 ? P : NA);
-};
+// o^e and u_e(o) = e^{-o} sum_{p>=e} c_p C(p,e) o^{p-e} for a run-time e < P
+template <class R, int P>
+__device__ __forceinline__ R pow_sel(R o, int e) {
+    return e == 0 ? R(1) : (e == 1 ? o : o * o);
+}
+template <class R, int P>
+__device__ __forceinline__ R ucoef_sel(R o, R eo, int e) {
+    if constexpr (P == 2) {
+        return e == 0 ? eo * (R(1) + o) : eo;
+    } else {
+        const R third = R(1) / R(3);
+        return e == 0 ? eo * (R(1) + o + third * o * o) : (e == 1 ? eo * (R(1) + R(2) * third * o) : eo * third);
+    }
+}
 
+// Per-entry coefficients of one pass (groups a0 .. a0+GP-1), from the
+// entry's offsets o and e^{-o}:
+//   insertion w: L1   w[q] = e^{-s} s^q (s = sum of offsets), added to M[q];
+//                product w[g] = prod_k o_k^{a_k} e^{-o_k}, added to M[g][0];
+//   readout   u: L1   u[q] = u_q(s); product u[g] = prod_k u_{a_k}(o_k).
+// d = 1 needs neither (v is added to M[0], the query reads sum_q c_q M[q]).
 template <class R, int P, int NOFF, int KIND>
-__device__ __forceinline__ void src_weights(R *w, const R *o, const R *eo) {
+__device__ __forceinline__ void pass_coef(int a0, const R *o, const R *eo, R *w, R *u) {
     using Tr = Traits<P, NOFF, KIND>;
     if constexpr (NOFF == 0) {
         w[0] = R(1);
+        u[0] = R(1);
     } else if constexpr (Tr::NA == 1) {
         R s = o[0], es = eo[0];
         if constexpr (NOFF == 2) {
@@ -170,30 +192,27 @@ __device__ __forceinline__ void src_weights(R *w, const R *o, const R *eo) {
         w[0] = es;
 #pragma unroll
         for (int q = 1; q < P; ++q) w[q] = w[q - 1] * s;
+        ucoef<R, P>(s, es, u);
     } else {
-        R f[NOFF][P];
 #pragma unroll
-        for (int k = 0; k < NOFF; ++k) {
-            f[k][0] = eo[k];
-#pragma unroll
-            for (int j = 1; j < P; ++j) f[k][j] = f[k][j - 1] * o[k];
-        }
-#pragma unroll
-        for (int a = 0; a < Tr::NA; ++a) {
-            R x = R(1);
-            int rem = a;
-#pragma unroll
-            for (int k = 0; k < NOFF; ++k) {
-                x *= f[k][rem % P];
-                rem /= P;
+        for (int g = 0; g < Tr::GP; ++g) {
+            const int a = a0 + g;
+            const int e0 = NOFF == 1 ? a : a % P;
+            R ww = eo[0] * pow_sel<R, P>(o[0], e0);
+            R uu = ucoef_sel<R, P>(o[0], eo[0], e0);
+            if constexpr (NOFF == 2) {
+                const int e1 = a / P;
+                ww *= eo[1] * pow_sel<R, P>(o[1], e1);
+                uu *= ucoef_sel<R, P>(o[1], eo[1], e1);
             }
-            w[a] = x;
+            w[g] = ww;
+            u[g] = uu;
         }
     }
 }
 
 template <class R, int P, int NOFF, int KIND>
-__device__ __forceinline__ void add_src(R *M, R v, const R *w) {
+__device__ __forceinline__ void add_pass(R *M, R v, const R *w) {
     using Tr = Traits<P, NOFF, KIND>;
     if constexpr (NOFF == 0) {
         M[0] += v;
@@ -202,43 +221,24 @@ __device__ __forceinline__ void add_src(R *M, R v, const R *w) {
         for (int q = 0; q < P; ++q) M[q] += v * w[q];
     } else {
 #pragma unroll
-        for (int a = 0; a < Tr::NA; ++a) M[a * P] += v * w[a];
+        for (int g = 0; g < Tr::GP; ++g) M[g * P] += v * w[g];
     }
 }
 
 template <class R, int P, int NOFF, int KIND>
-__device__ __forceinline__ R read_query(const R *M, const R *o, const R *eo) {
+__device__ __forceinline__ R read_pass(const R *M, const R *u) {
     using Tr = Traits<P, NOFF, KIND>;
     if constexpr (NOFF == 0) {
         return csum<R, P>(M);
     } else if constexpr (Tr::NA == 1) {
-        R s = o[0], es = eo[0];
-        if constexpr (NOFF == 2) {
-            s += o[1];
-            es *= eo[1];
-        }
-        R u[P];
-        ucoef<R, P>(s, es, u);
         R acc = R(0);
 #pragma unroll
         for (int q = 0; q < P; ++q) acc += u[q] * M[q];
         return acc;
     } else {
-        R u[NOFF][P];
-#pragma unroll
-        for (int k = 0; k < NOFF; ++k) ucoef<R, P>(o[k], eo[k], u[k]);
         R acc = R(0);
 #pragma unroll
-        for (int a = 0; a < Tr::NA; ++a) {
-            R c = R(1);
-            int rem = a;
-#pragma unroll
-            for (int k = 0; k < NOFF; ++k) {
-                c *= u[k][rem % P];
-                rem /= P;
-            }
-            acc += c * csum<R, P>(M + a * P);
-        }
+        for (int g = 0; g < Tr::GP; ++g) acc += u[g] * csum<R, P>(M + g * P);
         return acc;
     }
 }
@@ -273,12 +273,12 @@ __device__ __forceinline__ void set_identity(R *x) {
 template <class R, int P, int NOFF, int KIND, int MODE>
 __global__ void __launch_bounds__(kScanThreads, FGK_SCAN_MINB) k_level_scan(ScanArgs<R> A) {
     using Tr = Traits<P, NOFF, KIND>;
-    constexpr int MOM = Tr::MOM, CP = Tr::CP, SMM = Tr::SM, AG = Tr::AG, NPASS = Tr::NPASS, NCH = Tr::NCH;
+    constexpr int GM = Tr::GM, CP = Tr::CP, SMM = Tr::SM, AG = Tr::AG, NPASS = Tr::NPASS, NCH = Tr::NCH;
+    constexpr int NGP = Tr::NGP, NPT = Tr::NPT, NWC = Tr::NWC;
     constexpr int ND = Tr::NDIR, NDP = 2 / ND;  // directions per walk, direction passes
     constexpr int EPT = kScanEPT, NT = kScanThreads, NW = NT / 32;
     constexpr int LOG2EPT = (EPT == 8) ? 3 : (EPT == 4 ? 2 : (EPT == 16 ? 4 : 0));
     constexpr int NO = NOFF > 0 ? NOFF : 1;
-    constexpr int NWT = SrcW<R, P, NOFF, KIND>::NW;
     static_assert((1 << LOG2EPT) == EPT, "EPT must be 4, 8 or 16");
     static_assert(EPT == 8, "vector loads assume 8 entries per thread");
     __shared__ R s_w[ND][NW][AG];
@@ -370,7 +370,9 @@ __global__ void __launch_bounds__(kScanThreads, FGK_SCAN_MINB) k_level_scan(Scan
             v[i] = i < nvalid ? A.V[idx] : R(0);
         }
 #pragma unroll 1
-        for (int pp = 0; pp < NPASS; ++pp) {
+        for (int pq = 0; pq < NPT; ++pq) {
+            const int pp = pq / NGP;       // channel pair
+            const int a0 = NGP == 1 ? 0 : (pq % NGP) * Tr::GP;  // first offset-power group of the pass
             const int cA = pp;
             const int cB = NOFF == 0 ? 0 : (cA ^ (NCH - 1));
 #pragma unroll
@@ -394,15 +396,15 @@ __global__ void __launch_bounds__(kScanThreads, FGK_SCAN_MINB) k_level_scan(Scan
                             step_all<R, P, SMM>(inc[dd] + 1, gg, ee);
                             inc[dd][0] += gg;
                             const int role = NOFF == 0 ? 0 : (int)(q[i] >> (32 - NOFF));
-                            R oi[NO], eoi[NO], w[NWT];
+                            R oi[NO], eoi[NO], w[NWC], u[NWC];
 #pragma unroll
                             for (int k = 0; k < NO; ++k) {
                                 oi[k] = NOFF ? o[k][i] : R(0);
                                 eoi[k] = NOFF ? eo[k][i] : R(1);
                             }
-                            src_weights<R, P, NOFF, KIND>(w, oi, eoi);
-                            add_src<R, P, NOFF, KIND>(inc[dd] + 1, role == cA ? v[i] : R(0), w);
-                            if constexpr (CP == 2) add_src<R, P, NOFF, KIND>(inc[dd] + 1 + MOM, role == cB ? v[i] : R(0), w);
+                            pass_coef<R, P, NOFF, KIND>(a0, oi, eoi, w, u);
+                            add_pass<R, P, NOFF, KIND>(inc[dd] + 1, role == cA ? v[i] : R(0), w);
+                            if constexpr (CP == 2) add_pass<R, P, NOFF, KIND>(inc[dd] + 1 + GM, role == cB ? v[i] : R(0), w);
                         }
                     }
                     // 2. inclusive scan over the threads of each segment (virtual lanes)
@@ -451,7 +453,7 @@ __global__ void __launch_bounds__(kScanThreads, FGK_SCAN_MINB) k_level_scan(Scan
                         for (int dd = 0; dd < ND; ++dd) {
                             const int dir = ND == 2 ? dd : dp;
                             const int vwarp = dir == 0 ? warp : NW - 1 - warp;
-                            const size_t cslot = ((((size_t)wi.agg * 2 + dir) * A.nrhs + r) * NPASS + pp) * AG;
+                            const size_t cslot = ((((size_t)wi.agg * 2 + dir) * A.nrhs + r) * NPT + pq) * AG;
                             if (MODE == SCAN_AGG) {
                                 if (tid == dd * 32) {  // the tile's total
                                     R run[AG];
@@ -517,26 +519,25 @@ __global__ void __launch_bounds__(kScanThreads, FGK_SCAN_MINB) k_level_scan(Scan
                             step_all<R, P, SMM>(st[dd], gg, ee);
                             const bool ok = i < nvalid;
                             const int role = NOFF == 0 ? 0 : (int)(q[i] >> (32 - NOFF));
-                            R oi[NO], eoi[NO], w[NWT];
+                            R oi[NO], eoi[NO], w[NWC], u[NWC];
 #pragma unroll
                             for (int k = 0; k < NO; ++k) {
                                 oi[k] = NOFF ? o[k][i] : R(0);
                                 eoi[k] = NOFF ? eo[k][i] : R(1);
                             }
+                            pass_coef<R, P, NOFF, KIND>(a0, oi, eoi, w, u);
                             if constexpr (CP == 1) {
-                                if (ok) out[i] += read_query<R, P, NOFF, KIND>(st[dd], oi, eoi);
-                                src_weights<R, P, NOFF, KIND>(w, oi, eoi);
-                                add_src<R, P, NOFF, KIND>(st[dd], ok ? v[i] : R(0), w);
+                                if (ok) out[i] += read_pass<R, P, NOFF, KIND>(st[dd], u);
+                                add_pass<R, P, NOFF, KIND>(st[dd], ok ? v[i] : R(0), w);
                             } else {
                                 const bool sa = ok && role == cA, sb = ok && role == cB;
-                                R msel[MOM];
+                                R msel[GM];
 #pragma unroll
-                                for (int m = 0; m < MOM; ++m) msel[m] = sa ? st[dd][MOM + m] : st[dd][m];
-                                const R rd = read_query<R, P, NOFF, KIND>(msel, oi, eoi);
+                                for (int m = 0; m < GM; ++m) msel[m] = sa ? st[dd][GM + m] : st[dd][m];
+                                const R rd = read_pass<R, P, NOFF, KIND>(msel, u);
                                 out[i] += (sa || sb) ? rd : R(0);
-                                src_weights<R, P, NOFF, KIND>(w, oi, eoi);
-                                add_src<R, P, NOFF, KIND>(st[dd], sa ? v[i] : R(0), w);
-                                add_src<R, P, NOFF, KIND>(st[dd] + MOM, sb ? v[i] : R(0), w);
+                                add_pass<R, P, NOFF, KIND>(st[dd], sa ? v[i] : R(0), w);
+                                add_pass<R, P, NOFF, KIND>(st[dd] + GM, sb ? v[i] : R(0), w);
                             }
                         }
                     }
@@ -560,15 +561,15 @@ __global__ void k_carry_scan(const R *__restrict__ agg, R *__restrict__ carry, c
                              int nseg, int nrhs, const int *__restrict__ gate) {
     if (gate && *gate == 0) return;
     using Tr = Traits<P, NOFF, KIND>;
-    constexpr int AG = Tr::AG, NPASS = Tr::NPASS;
+    constexpr int AG = Tr::AG, NPT = Tr::NPT;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    const int64_t total = (int64_t)nseg * 2 * nrhs * NPASS;
+    const int64_t total = (int64_t)nseg * 2 * nrhs * NPT;
     if (wid >= total) return;  // uniform per warp
-    const int pp = (int)(wid % NPASS);
-    const int r = (int)((wid / NPASS) % nrhs);
-    const int dir = (int)((wid / ((int64_t)NPASS * nrhs)) % 2);
-    const int sg = (int)(wid / ((int64_t)NPASS * nrhs * 2));
+    const int pq = (int)(wid % NPT);
+    const int r = (int)((wid / NPT) % nrhs);
+    const int dir = (int)((wid / ((int64_t)NPT * nrhs)) % 2);
+    const int sg = (int)(wid / ((int64_t)NPT * nrhs * 2));
     const int a0 = segs[2 * sg], nt = segs[2 * sg + 1];
     R run[AG];
     set_identity<R, AG>(run);
@@ -576,7 +577,7 @@ __global__ void k_carry_scan(const R *__restrict__ agg, R *__restrict__ carry, c
         const int k = k0 + lane;
         const bool valid = k < nt;
         const int slot = a0 + (dir == 0 ? k : nt - 1 - k);
-        const size_t off = ((((size_t)(valid ? slot : a0) * 2 + dir) * nrhs + r) * NPASS + pp) * AG;
+        const size_t off = ((((size_t)(valid ? slot : a0) * 2 + dir) * nrhs + r) * NPT + pq) * AG;
         R inc[AG];
 #pragma unroll
         for (int m = 0; m < AG; ++m) inc[m] = valid ? agg[off + m] : R(0);
@@ -628,7 +629,7 @@ int run_levels(Plan *p, const R *Vq, int nrhs, R *Yq, R *ws, cudaStream_t s, con
     A.s2 = (R)p->s2;
     A.err = p->dev_err;
     A.gate = gate;
-    const size_t per_slot = (size_t)2 * nrhs * Tr::NPASS * Tr::AG;
+    const size_t per_slot = (size_t)2 * nrhs * Tr::NPT * Tr::AG;
     R *agg = ws;
     R *carry = ws + (size_t)p->n_long * per_slot;
     if (p->n_long > 0) {
@@ -636,7 +637,7 @@ int run_levels(Plan *p, const R *Vq, int nrhs, R *Yq, R *ws, cudaStream_t s, con
         A.agg = agg;
         k_level_scan<R, P, NOFF, KIND, SCAN_AGG><<<p->n_long, kScanThreads, 0, s>>>(A);
         FGK_LAUNCH_CHECK();
-        const int64_t nthr = (int64_t)p->n_long_segments * 2 * nrhs * Tr::NPASS * 32;
+        const int64_t nthr = (int64_t)p->n_long_segments * 2 * nrhs * Tr::NPT * 32;
         k_carry_scan<R, P, NOFF, KIND><<<grid_for(nthr, 128), 128, 0, s>>>(agg, carry, p->long_seg,
                                                                            p->n_long_segments, nrhs, gate);
         FGK_LAUNCH_CHECK();
@@ -664,8 +665,9 @@ int run_levels(Plan *p, const R *Vq, int nrhs, R *Yq, R *ws, cudaStream_t s, con
 
 template <class R>
 size_t scan_ws_elems(const Plan *p, int nrhs) {
-    // generous: the largest aggregate (product, P = 3, d = 3: 1 + 2 x 27) and 2 passes
-    return (size_t)2 * p->n_long * 2 * nrhs * 2 * 56 + 64;
+    // generous: the most passes x aggregate size (product, P = 3, d = 3:
+    // 2 channel pairs x 9 offset groups x (1 + 2 x 3))
+    return (size_t)2 * p->n_long * 2 * nrhs * 128 + 64;
 }
 
 // dispatch over (P, d-1, kind); nu = 1/2 or d = 1 make both kinds the same kernel
