@@ -495,10 +495,30 @@ int cg_solve(Plan *p, const double *y, int nrhs, double sigma2, const double *H,
         // warm the products once so their workspace exists before graph capture,
         // then set the product's starting point W = s2 p
         if ((rc = init_p())) break;
+        // both warm-up products are timed: a residual replacement (one FP64
+        // product) is allowed once the FP32 iterations since the last one
+        // have cost at least as much, so replacements never take more than
+        // about half of the solve
+        cudaEvent_t t0, t1, t2;
+        FGK_CUDA(cudaEventCreate(&t0));
+        FGK_CUDA(cudaEventCreate(&t1));
+        FGK_CUDA(cudaEventCreate(&t2));
+        FGK_CUDA(cudaEventRecord(t0, s));
         if (mixed) {
             if ((rc = mvm_q_f32(p, P32, ncols, W32, s, nullptr))) break;
         }
+        FGK_CUDA(cudaEventRecord(t1, s));
         if ((rc = mvm_q_f64(p, Pv, ncols, W64, s, nullptr))) break;
+        FGK_CUDA(cudaEventRecord(t2, s));
+        FGK_CUDA(cudaEventSynchronize(t2));
+        float ms32 = 0.f, ms64 = 0.f;
+        FGK_CUDA(cudaEventElapsedTime(&ms32, t0, t1));
+        FGK_CUDA(cudaEventElapsedTime(&ms64, t1, t2));
+        cudaEventDestroy(t0);
+        cudaEventDestroy(t1);
+        cudaEventDestroy(t2);
+        const int min_gap = mixed && ms32 > 0.f ? (int)std::ceil(ms64 / ms32) : 0;
+        int last_replacement = 0;
         if ((rc = init_p())) break;
         ColState hs;
         std::memset(&hs, 0, sizeof(hs));
@@ -550,12 +570,14 @@ int cg_solve(Plan *p, const double *y, int nrhs, double sigma2, const double *H,
             }
             // replace the recursive residual when a column claims convergence
             // or (mixed) has reduced its residual by delta since the last time
-            bool replace = false;
+            bool claims = false, dropped = false;
             for (int j = 0; j < ncols; ++j) {
                 if (confirmed[j]) continue;
-                if (!snap.active_next[j] || snap.rho_next[j] <= delta * delta * rho_ref[j]) replace = true;
+                if (!snap.active_next[j]) claims = true;
+                if (snap.rho_next[j] <= delta * delta * rho_ref[j]) dropped = true;
             }
-            if (!replace) continue;
+            if (!(claims || (dropped && iters_total - last_replacement >= min_gap))) continue;
+            last_replacement = iters_total;
             if ((rc = true_residual())) break;
             if ((rc = init_p())) break;  // the residual product overwrote W64 (FP64 mode)
             snap.n_active = 0;
