@@ -165,6 +165,77 @@ def cpu_baseline(p, iters, seconds):
             "mvm_nrhs_per_s": p.N / t_mvm}
 
 
+def run_batched(args, local):
+    """The batched workload: K problems (N log-uniform 1k-100k, d in {1,2},
+    nu mixed, 16 N(0,1) right-hand sides each) solved in one batch (mixed
+    precision), against the plain per-problem FP64 solve on a sample."""
+    import torch
+
+    import workloads
+    from paper_2508_01864_gb300 import batch, fgk
+
+    torch.cuda.set_device(local)
+    probs = workloads.c4(n_problems=args.batched)
+    nrhs = probs[0].V.shape[1]
+    t0 = time.perf_counter()
+    eng = batch.BatchEngine(probs, nrhs, kind="product")
+    t_setup = time.perf_counter() - t0
+    ys = [torch.as_tensor(p.V, device="cuda") for p in probs]
+    sig = [p.sigma2 for p in probs]
+    rows = sum(p.N for p in probs)
+    V = torch.randn(rows, nrhs, dtype=torch.float32, device="cuda")
+    Y = torch.empty_like(V)
+    for _ in range(3):
+        eng.matvec(V, out=Y)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(10):
+        eng.matvec(V, out=Y)
+    e1.record()
+    torch.cuda.synchronize()
+    mvm_ms = e0.elapsed_time(e1) / 10
+    times = []
+    for _ in range(max(args.steps, 1)):
+        torch.cuda.synchronize()
+        e0.record()
+        alphas, infos, rc = eng.solve(ys, sig, tol=TOL, maxit=200000)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+        assert rc == 0, infos
+    t_batch = statistics.median(times)
+    # the plain per-problem FP64 GPU solve on a sample, extrapolated by size
+    sample = list(range(min(args.f64_sample, len(probs))))
+    t_f64 = 0.0
+    for i in sample:
+        p = probs[i]
+        h = fgk.fgk_build(torch.as_tensor(p.X, device="cuda"), p.nu, p.ell, kind="product")
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        a, _, info, rc = fgk.fgk_cg_solve(h, ys[i], p.sigma2, tol=TOL, maxit=200000, mode="f64")
+        torch.cuda.synchronize()
+        t_f64 += time.perf_counter() - t1
+        fgk.fgk_destroy(h)
+    frac = sum(probs[i].N for i in sample) / rows
+    t_f64_all = t_f64 / frac if frac > 0 else float("nan")
+    solves = len(probs) * nrhs
+    out = {"metric": "batched: CG solves/sec at resid<=1e-8 (problems x rhs) and MVM N*nrhs/sec",
+           "unit": "solves/s", "value": solves / t_batch, "problems": len(probs), "nrhs": nrhs,
+           "rows": rows, "rhs_per_cta": eng.rpc, "autotune_ms": eng.timings, "setup_s": t_setup,
+           "batch_solve_s": t_batch, "max_iterations": max(i["iterations"] for i in infos),
+           "max_true_resid": max(i["max_true_resid"] for i in infos),
+           "mvm_ms": mvm_ms, "mvm_nrhs_per_s": rows * nrhs / (mvm_ms * 1e-3),
+           "f64_per_problem": {"sample_problems": len(sample), "sample_s": t_f64,
+                               "extrapolated_s": t_f64_all, "solves_per_s": solves / t_f64_all},
+           "workload": "first %d problems of the seeded batched workload (N log-uniform 1k-100k, d in {1,2}, "
+                       "nu in {1/2,3/2,5/2}, ell log-uniform 0.05-0.5, 16 N(0,1) rhs, sigma^2=0.01, product kernel)"
+                       % len(probs)}
+    eng.close()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_serving(args, local):
     """Continuous-batching replay of the serving stream's first K requests:
     first as a burst (all arriving at once) to measure the sustained capacity,
@@ -246,6 +317,10 @@ def main():
     ap.add_argument("--serving", type=int, default=0,
                     help="replay the first K requests of the serving stream (burst, then 0.8x its capacity)")
     ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--batched", type=int, default=0,
+                    help="solve the first K problems of the batched workload (16 rhs each) in one batch")
+    ap.add_argument("--f64-sample", type=int, default=4,
+                    help="batched mode: problems solved one by one in FP64 for the comparison")
     ap.add_argument("--mvm-only", type=int, default=0,
                     help="time only the FP32 product on the d=2 workload drawn with this many points")
     args = ap.parse_args()
@@ -256,6 +331,8 @@ def main():
         return run_mvm_only(args, local)
     if args.serving:
         return run_serving(args, local)
+    if args.batched:
+        return run_batched(args, local)
 
     import torch
     import torch.distributed as dist

@@ -167,6 +167,41 @@ typedef struct {
 int fgk_cg_solve(fgk_handle h, const double *y, int nrhs, double sigma2, const double *H, int L, double tol,
                  int maxit, int mode, double *alpha, double *beta, fgk_cg_info *info, fgk_stream_t stream);
 
+/* ---- batches: many problems advanced together (d <= 2) ---- */
+
+typedef struct fgk_batch_s *fgk_batch;
+
+/* Group n built plans (all d <= 2) for products and solves with nrhs columns
+ * per problem (1 <= nrhs <= 64).  The vectors of a batch are packed: problem
+ * i occupies rows [off_i, off_i + N_i) (fgk_batch_layout), each row its nrhs
+ * values, in that problem's internal order (as fgk_matvec_q).  One launch
+ * per phase of the product covers every problem; rhs_per_cta (1..nrhs, or 0
+ * for all) sets how many right-hand sides one CTA scans.  The plans must
+ * outlive the batch.  Synchronises `stream`. */
+int fgk_batch_create(const fgk_handle *handles, int n, int nrhs, int rhs_per_cta, fgk_stream_t stream,
+                     fgk_batch *out);
+
+/* row_offsets: host, n + 1 values: the first packed row of each problem and
+ * the total row count. */
+int fgk_batch_layout(fgk_batch b, int64_t *row_offsets);
+
+/* Y = K_i V_i for every problem i at once, FP32 scans; Vq, Yq device,
+ * packed (total rows x nrhs) FP32.  Asynchronous. */
+int fgk_batch_matvec_q(fgk_batch b, const float *Vq, float *Yq, fgk_stream_t stream);
+
+/* Solve (K_i + sigma2[i] I) alpha_i = y_i for every problem and column at
+ * once: mixed-precision CG as fgk_cg_solve (FP32 scans, FP64 vectors, inner
+ * products and residual replacements), no fixed effects.
+ *   y, alpha   host arrays of n device pointers, each N_i x nrhs FP64,
+ *              row-major, the problem's original point order.
+ *   sigma2     host, n values >= 0.
+ *   info       host array of n reports, or NULL.
+ * Returns as fgk_cg_solve.  Synchronises `stream`. */
+int fgk_batch_cg_solve(fgk_batch b, const double *const *y, const double *sigma2, double tol, int maxit,
+                       double *const *alpha, fgk_cg_info *info, fgk_stream_t stream);
+
+int fgk_batch_destroy(fgk_batch b);
+
 /* Upper estimate, in bytes, of the device memory a handle for these sizes
  * holds after fgk_build plus the workspace of fgk_cg_solve with nrhs
  * columns (used for admission against a memory budget).  0 if invalid. */

@@ -5,6 +5,11 @@ The compute path is libfgk (hand-written CUDA for sm_103a behind a C ABI,
 """
 
 from .fgk import (  # noqa: F401
+    Batch,
+    fgk_batch_cg_solve,
+    fgk_batch_create,
+    fgk_batch_destroy,
+    fgk_batch_matvec_q,
     FGK_F32,
     FGK_F64,
     FGK_L1,

@@ -271,7 +271,7 @@ __device__ __forceinline__ void set_identity(R *x) {
 // longer than a tile receive their carry from the aggregate pass
 // (MODE == SCAN_AGG writes each tile's totals; k_carry_scan scans them).
 template <class R, int P, int NOFF, int KIND, int MODE>
-__global__ void __launch_bounds__(kScanThreads, FGK_SCAN_MINB) k_level_scan(ScanArgs<R> A) {
+__device__ __forceinline__ void scan_tile(const ScanArgs<R> &A, const WorkItem wi, int r0, int r1) {
     using Tr = Traits<P, NOFF, KIND>;
     constexpr int GM = Tr::GM, CP = Tr::CP, SMM = Tr::SM, AG = Tr::AG, NPASS = Tr::NPASS, NCH = Tr::NCH;
     constexpr int NGP = Tr::NGP, NPT = Tr::NPT, NWC = Tr::NWC;
@@ -283,8 +283,6 @@ __global__ void __launch_bounds__(kScanThreads, FGK_SCAN_MINB) k_level_scan(Scan
     static_assert(EPT == 8, "vector loads assume 8 entries per thread");
     __shared__ R s_w[ND][NW][AG];
 
-    if (A.gate && *A.gate == 0) return;
-    const WorkItem wi = A.items[blockIdx.x];
     const int64_t N = A.N;
     const int64_t base = (int64_t)wi.tile * kTile;
     const int log2S = wi.log2S;
@@ -361,7 +359,7 @@ __global__ void __launch_bounds__(kScanThreads, FGK_SCAN_MINB) k_level_scan(Scan
     const int GW = G < 32 ? G : 32;
     const bool is_long = S > kTile;
 
-    for (int r = 0; r < A.nrhs; ++r) {
+    for (int r = r0; r < r1; ++r) {
         R v[EPT], out[EPT];
 #pragma unroll
         for (int i = 0; i < EPT; ++i) {
@@ -552,25 +550,20 @@ __global__ void __launch_bounds__(kScanThreads, FGK_SCAN_MINB) k_level_scan(Scan
     }
 }
 
-// Exclusive scan of the tile aggregates of every long segment, in both
-// directions: carry[tile] = composition of the tiles before it (forward) or
-// after it (backward).  One warp per (segment, direction, rhs, channel pair)
-// scans the segment's tiles 32 at a time.
+template <class R, int P, int NOFF, int KIND, int MODE>
+__global__ void __launch_bounds__(kScanThreads, FGK_SCAN_MINB) k_level_scan(ScanArgs<R> A) {
+    if (A.gate && *A.gate == 0) return;
+    scan_tile<R, P, NOFF, KIND, MODE>(A, A.items[blockIdx.x], 0, A.nrhs);
+}
+
+// one warp: exclusive carries of one long segment (tiles a0 .. a0+nt-1 of the
+// aggregate slots) for direction dir, right-hand side r and pass pq
 template <class R, int P, int NOFF, int KIND>
-__global__ void k_carry_scan(const R *__restrict__ agg, R *__restrict__ carry, const int32_t *__restrict__ segs,
-                             int nseg, int nrhs, const int *__restrict__ gate) {
-    if (gate && *gate == 0) return;
+__device__ __forceinline__ void carry_warp(const R *__restrict__ agg, R *__restrict__ carry, int a0, int nt, int dir,
+                                           int r, int pq, int nrhs) {
     using Tr = Traits<P, NOFF, KIND>;
     constexpr int AG = Tr::AG, NPT = Tr::NPT;
-    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    const int64_t total = (int64_t)nseg * 2 * nrhs * NPT;
-    if (wid >= total) return;  // uniform per warp
-    const int pq = (int)(wid % NPT);
-    const int r = (int)((wid / NPT) % nrhs);
-    const int dir = (int)((wid / ((int64_t)NPT * nrhs)) % 2);
-    const int sg = (int)(wid / ((int64_t)NPT * nrhs * 2));
-    const int a0 = segs[2 * sg], nt = segs[2 * sg + 1];
     R run[AG];
     set_identity<R, AG>(run);
     for (int k0 = 0; k0 < nt; k0 += 32) {
@@ -603,6 +596,23 @@ __global__ void k_carry_scan(const R *__restrict__ agg, R *__restrict__ carry, c
 #pragma unroll
         for (int m = 0; m < AG; ++m) run[m] = last[m];
     }
+}
+
+// Exclusive scan of the tile aggregates of every long segment in both
+// directions: one warp per (segment, direction, rhs, pass).
+template <class R, int P, int NOFF, int KIND>
+__global__ void k_carry_scan(const R *__restrict__ agg, R *__restrict__ carry, const int32_t *__restrict__ segs,
+                             int nseg, int nrhs, const int *__restrict__ gate) {
+    if (gate && *gate == 0) return;
+    constexpr int NPT = Traits<P, NOFF, KIND>::NPT;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t total = (int64_t)nseg * 2 * nrhs * NPT;
+    if (wid >= total) return;  // uniform per warp
+    const int pq = (int)(wid % NPT);
+    const int r = (int)((wid / NPT) % nrhs);
+    const int dir = (int)((wid / ((int64_t)NPT * nrhs)) % 2);
+    const int sg = (int)(wid / ((int64_t)NPT * nrhs * 2));
+    carry_warp<R, P, NOFF, KIND>(agg, carry, segs[2 * sg], segs[2 * sg + 1], dir, r, pq, nrhs);
 }
 
 template <class R>

@@ -51,7 +51,8 @@ class fgk_plan_info(ctypes.Structure):
 
 EXPORTS = ["fgk_set_allocator", "fgk_build", "fgk_matvec", "fgk_matvec_q", "fgk_matvec_q_noalloc", "fgk_cg_solve", "fgk_bytes_estimate",
            "fgk_destroy", "fgk_last_error", "fgk_kernel_launches", "fgk_scan_timing", "fgk_get_info",
-           "fgk_get_permutation", "fgk_get_level"]
+           "fgk_get_permutation", "fgk_get_level", "fgk_batch_create", "fgk_batch_layout", "fgk_batch_matvec_q",
+           "fgk_batch_cg_solve", "fgk_batch_destroy"]
 
 _lock = threading.Lock()
 _lib = None
@@ -97,6 +98,17 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.fgk_get_permutation.restype = i32
         lib.fgk_get_level.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, ctypes.POINTER(i64)]
         lib.fgk_get_level.restype = i32
+        lib.fgk_batch_create.argtypes = [ctypes.POINTER(vp), i32, i32, i32, vp, ctypes.POINTER(vp)]
+        lib.fgk_batch_create.restype = i32
+        lib.fgk_batch_layout.argtypes = [vp, ctypes.POINTER(i64)]
+        lib.fgk_batch_layout.restype = i32
+        lib.fgk_batch_matvec_q.argtypes = [vp, vp, vp, vp]
+        lib.fgk_batch_matvec_q.restype = i32
+        lib.fgk_batch_cg_solve.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(dbl), dbl, i32, ctypes.POINTER(vp),
+                                           ctypes.POINTER(fgk_cg_info), vp]
+        lib.fgk_batch_cg_solve.restype = i32
+        lib.fgk_batch_destroy.argtypes = [vp]
+        lib.fgk_batch_destroy.restype = i32
         _lib = lib
         return lib
 
@@ -308,6 +320,64 @@ def fgk_get_level(h: Handle, level: int) -> dict:
         out["off64"] = off64[:, :nof]
         out["off32"] = off32[:, :nof]
     return out
+
+
+# ------------------------------------------------------------ batches
+@dataclass
+class Batch:
+    ptr: int
+    handles: list
+    nrhs: int
+    rows: list  # packed row offsets, n + 1 values
+
+
+def fgk_batch_create(handles: list, nrhs: int, rhs_per_cta: int = 0, stream=None) -> Batch:
+    """Group built plans (d <= 2) for batched products and solves."""
+    lib = load()
+    arr = (ctypes.c_void_p * len(handles))(*[h.ptr for h in handles])
+    out = ctypes.c_void_p()
+    _check(lib.fgk_batch_create(arr, len(handles), int(nrhs), int(rhs_per_cta), _stream(stream), ctypes.byref(out)))
+    offs = (ctypes.c_int64 * (len(handles) + 1))()
+    _check(lib.fgk_batch_layout(out.value, offs))
+    return Batch(out.value, list(handles), int(nrhs), list(offs))
+
+
+def fgk_batch_matvec_q(b: Batch, Vq: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+    """Packed FP32 products of every problem of the batch."""
+    lib = load()
+    if not Vq.is_cuda or Vq.dtype != torch.float32 or not Vq.is_contiguous() or Vq.shape != (b.rows[-1], b.nrhs):
+        raise TypeError("Vq must be a contiguous CUDA float32 tensor of shape (total rows, nrhs)")
+    if out is None:
+        out = torch.empty_like(Vq)
+    _check(lib.fgk_batch_matvec_q(b.ptr, Vq.data_ptr(), out.data_ptr(), _stream(stream)))
+    return out
+
+
+def fgk_batch_cg_solve(b: Batch, ys: list, sigma2s, tol: float = 1e-8, maxit: int = 100000, stream=None):
+    """Mixed-precision CG for every problem and column; returns (alphas, infos, status)."""
+    lib = load()
+    n = len(b.handles)
+    ys = [_dev_f64_2d(y, "y") for y in ys]
+    alphas = [torch.empty_like(y) for y in ys]
+    yp = (ctypes.c_void_p * n)(*[y.data_ptr() for y in ys])
+    ap = (ctypes.c_void_p * n)(*[a.data_ptr() for a in alphas])
+    sg = (ctypes.c_double * n)(*[float(x) for x in sigma2s])
+    infos = (fgk_cg_info * n)()
+    res = [(ctypes.c_double * b.nrhs)() for _ in range(n)]
+    for i in range(n):
+        infos[i].true_resid = ctypes.cast(res[i], ctypes.POINTER(ctypes.c_double))
+    rc = lib.fgk_batch_cg_solve(b.ptr, yp, sg, float(tol), int(maxit), ap, infos, _stream(stream))
+    _check(rc, allow_soft=True)
+    out = [{"iterations": infos[i].iterations, "refinements": infos[i].refinements, "mvm_f32": infos[i].mvm_f32,
+            "mvm_f64": infos[i].mvm_f64, "max_true_resid": infos[i].max_true_resid, "true_resid": list(res[i])}
+           for i in range(n)]
+    return alphas, out, rc
+
+
+def fgk_batch_destroy(b: Batch) -> None:
+    if b is not None and b.ptr:
+        _check(load().fgk_batch_destroy(b.ptr))
+        b.ptr = 0
 
 
 # ------------------------------------------------------------ torch allocator hook
