@@ -174,21 +174,24 @@ __device__ __forceinline__ double warp_prob_sum(const double *__restrict__ parti
     return acc;
 }
 
-// block-wide column sums over the chunk's rows: out[j] = sum_rows f(row, j)
+// block-wide column sums over the chunk's rows: out[j] = sum_rows f(row, j).
+// Thread tid owns column tid % nrhs and every (blockDim / nrhs)-th row, so a
+// warp reads consecutive elements of the row-major block in one pass.
 template <class F>
 __device__ __forceinline__ void chunk_col_sums(const Chunk &c, int nrhs, F f, double *out, double *red) {
-    for (int j = 0; j < nrhs; ++j) {
-        double acc = 0.0;
-        for (int64_t row = c.row0 + threadIdx.x; row < c.row1; row += blockDim.x) acc += f(row, j);
-        red[threadIdx.x] = acc;
-        __syncthreads();
-        for (int s = kRedThreads / 2; s > 0; s >>= 1) {
-            if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) out[j] = red[0];
-        __syncthreads();
+    const int per = kRedThreads / nrhs;  // rows handled at once
+    const int j = threadIdx.x % nrhs, lane_row = threadIdx.x / nrhs;
+    double acc = 0.0;
+    if (lane_row < per)
+        for (int64_t row = c.row0 + lane_row; row < c.row1; row += per) acc += f(row, j);
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < nrhs) {
+        double t = 0.0;
+        for (int k = 0; k < per; ++k) t += red[k * nrhs + threadIdx.x];
+        out[threadIdx.x] = t;
     }
+    __syncthreads();
 }
 
 // p^T (w + sigma2 p) per chunk and column; the first chunk of each problem

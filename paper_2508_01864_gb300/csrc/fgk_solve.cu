@@ -57,30 +57,33 @@ struct ColState {
     int breakdown;
 };
 
-// partial[b * ncols + j] = sum over this block's rows of a_ij * b_ij
+// partial[b * ncols + j] = sum over this block's rows of a_ij * (b_ij + sb c_ij).
+// Thread tid owns column tid % ncols and a row subset, so the row-major
+// blocks are read with consecutive threads on consecutive elements.
 template <class TA, class TB>
 __device__ __forceinline__ void block_col_dots(const TA *__restrict__ a, const TB *__restrict__ b, double sb,
                                                const double *__restrict__ c, int64_t N, int ncols,
                                                double *__restrict__ partial) {
-    // sum_i a_ij * (b_ij + sb * c_ij)  (c may be NULL when sb == 0)
     __shared__ double red[kRedThreads];
-    for (int j = 0; j < ncols; ++j) {
-        double acc = 0.0;
-        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const int per = kRedThreads / ncols;
+    const int j = threadIdx.x % ncols, lr = threadIdx.x / ncols;
+    double acc = 0.0;
+    if (lr < per) {
+        for (int64_t i = (int64_t)blockIdx.x * per + lr; i < N; i += (int64_t)gridDim.x * per) {
             const int64_t t = i * ncols + j;
             double bb = (double)b[t];
             if (c) bb += sb * c[t];
             acc += (double)a[t] * bb;
         }
-        red[threadIdx.x] = acc;
-        __syncthreads();
-        for (int s = kRedThreads / 2; s > 0; s >>= 1) {
-            if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) partial[blockIdx.x * ncols + j] = red[0];
-        __syncthreads();
     }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < ncols) {
+        double s = 0.0;
+        for (int k = 0; k < per; ++k) s += red[k * ncols + threadIdx.x];
+        partial[blockIdx.x * ncols + threadIdx.x] = s;
+    }
+    __syncthreads();
 }
 
 __global__ void k_col_dots(const double *__restrict__ a, const double *__restrict__ b, int64_t N, int ncols,
@@ -147,11 +150,13 @@ __global__ void k_update_xr(double *__restrict__ x, double *__restrict__ r, cons
         }
     }
     __syncthreads();
-    for (int j = 0; j < ncols; ++j) {
-        const double a = s_alpha[j];
-        double acc = 0.0;
-        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-            const int64_t t = i * ncols + j;
+    const int per = kRedThreads / ncols;
+    const int jj = threadIdx.x % ncols, lr = threadIdx.x / ncols;
+    double acc = 0.0;
+    if (lr < per) {
+        const double a = s_alpha[jj];
+        for (int64_t i = (int64_t)blockIdx.x * per + lr; i < N; i += (int64_t)gridDim.x * per) {
+            const int64_t t = i * ncols + jj;
             double rv = r[t];
             if (a != 0.0) {
                 const double pv = p[t];
@@ -161,14 +166,13 @@ __global__ void k_update_xr(double *__restrict__ x, double *__restrict__ r, cons
             }
             acc += rv * rv;
         }
-        red[threadIdx.x] = acc;
-        __syncthreads();
-        for (int s = kRedThreads / 2; s > 0; s >>= 1) {
-            if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) partial[blockIdx.x * ncols + j] = red[0];
-        __syncthreads();
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < ncols) {
+        double t = 0.0;
+        for (int k = 0; k < per; ++k) t += red[k * ncols + threadIdx.x];
+        partial[blockIdx.x * ncols + threadIdx.x] = t;
     }
 }
 
