@@ -136,6 +136,11 @@ typedef struct {
     double max_true_resid;  /* max over solved columns of ||b - A x|| / ||b||, FP64 */
     double *true_resid;     /* optional host array of nrhs + L doubles (columns
                                [y, H]); written when not NULL */
+    int32_t restarts;       /* mixed mode: restarts (p = r on the affected
+                               columns) after an FP32 p^T A p <= 0 that FP64
+                               scans did not confirm */
+    int32_t fp64_switch;    /* fgk_cg_solve, mixed mode: 1 if too many such
+                               restarts moved the remaining iterations to FP64 scans */
 } fgk_cg_info;
 
 /* Solve (K + sigma2 I) alpha = y (eq. gp_mean_system) for nrhs columns by
@@ -157,7 +162,10 @@ typedef struct {
  *              recursive residual has dropped by a factor (env
  *              FGK_MIXED_DELTA, default 0.5) and substituted for it, the
  *              FP64 solution being corrected in place (iterative refinement
- *              without restarting the Krylov space).
+ *              without restarting the Krylov space).  An FP32 p^T A p <= 0 is
+ *              re-evaluated with FP64 scans: confirmed, it is a breakdown;
+ *              otherwise the column restarts from p = r, and after 4 such
+ *              restarts the solve continues with FP64 scans.
  *   alpha      device, N x nrhs FP64 (output).
  *   beta       device, L x nrhs FP64 (output) or NULL; ignored without H.
  *   info       host, may be NULL.

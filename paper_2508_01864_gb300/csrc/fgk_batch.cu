@@ -161,6 +161,7 @@ struct BState {
     double *rho, *rho_next, *thr2;
     int *active, *active_next, *iters;
     int *prob_active, *prob_active_next;
+    int *bd;  // per column: met p^T A p <= 0 in FP32 (cleared by the host)
     int *breakdown;
 };
 
@@ -184,14 +185,8 @@ __device__ __forceinline__ void chunk_col_sums(const Chunk &c, int nrhs, F f, do
     double acc = 0.0;
     if (lane_row < per)
         for (int64_t row = c.row0 + lane_row; row < c.row1; row += per) acc += f(row, j);
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    if (threadIdx.x < nrhs) {
-        double t = 0.0;
-        for (int k = 0; k < per; ++k) t += red[k * nrhs + threadIdx.x];
-        out[threadIdx.x] = t;
-    }
-    __syncthreads();
+    const double t = block_col_sum(acc, nrhs, red);
+    if (threadIdx.x < nrhs) out[threadIdx.x] = t;
 }
 
 // p^T (w + sigma2 p) per chunk and column; the first chunk of each problem
@@ -239,8 +234,10 @@ __global__ void k_bupdate_xr(double *__restrict__ x, double *__restrict__ r, con
             if (st.active[col]) {
                 if (pw > 0.0)
                     a = st.rho[col] / pw;
-                else if (c.first)
+                else if (c.first) {
                     atomicOr(st.breakdown, 1);
+                    st.bd[col] = 1;
+                }
             }
             s_alpha[j] = a;
         }
@@ -278,7 +275,7 @@ __global__ void k_bupdate_p(double *__restrict__ p, float *__restrict__ p32, flo
             const int col = c.prob * nrhs + j;
             const int act = st.active[col];
             const double rho = st.rho[col];
-            const int still = act && rr > st.thr2[col];
+            const int still = act && !st.bd[col] && rr > st.thr2[col];
             s_beta[j] = act ? (rho > 0.0 ? rr / rho : 0.0) : 0.0;
             s_act[j] = still;
             if (c.first) {
@@ -325,24 +322,49 @@ __global__ void k_residual_slice(const double *__restrict__ B, const double *__r
         R[t] = B[t] - (Y[t] + sigma2 * X[t]);
 }
 
-// squared column norms of a problem's slice (rows [0, n) x nrhs), one block
-__global__ void k_slice_norms2(const double *__restrict__ A, int64_t n, int nrhs, double *__restrict__ out) {
+// p_j^T (w_j + sigma2 p_j) per chunk (partials), w from FP64 scans
+__global__ void k_chunk_pap(const double *__restrict__ P, const double *__restrict__ W,
+                            const double *__restrict__ sig2, const Chunk *__restrict__ chunks, int nrhs,
+                            double *__restrict__ partial) {
     __shared__ double red[kRedThreads];
-    for (int j = 0; j < nrhs; ++j) {
-        double acc = 0.0;
-        for (int64_t row = threadIdx.x; row < n; row += blockDim.x) {
-            const double v = A[row * nrhs + j];
-            acc += v * v;
-        }
-        red[threadIdx.x] = acc;
-        __syncthreads();
-        for (int s = kRedThreads / 2; s > 0; s >>= 1) {
-            if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) out[j] = red[0];
-        __syncthreads();
-    }
+    const Chunk c = chunks[blockIdx.x];
+    const double sg = sig2[c.prob];
+    chunk_col_sums(
+        c, nrhs,
+        [&](int64_t row, int j) {
+            const int64_t t = row * nrhs + j;
+            return P[t] * (W[t] + sg * P[t]);
+        },
+        partial + (size_t)blockIdx.x * nrhs, red);
+}
+
+// p_j = r_j on the columns flagged in bd (a CG restart)
+__global__ void k_brestart(double *__restrict__ P, const double *__restrict__ R, const Chunk *__restrict__ chunks,
+                           int nrhs, const int *__restrict__ bd) {
+    const Chunk c = chunks[blockIdx.x];
+    for (int64_t t = (int64_t)c.row0 * nrhs + threadIdx.x; t < (int64_t)c.row1 * nrhs; t += blockDim.x)
+        if (bd[c.prob * nrhs + (int)(t % nrhs)]) P[t] = R[t];
+}
+
+// squared column norms per chunk (partials; summed per problem by k_prob_sums)
+__global__ void k_chunk_norms2(const double *__restrict__ A, const Chunk *__restrict__ chunks, int nrhs,
+                               double *__restrict__ partial) {
+    __shared__ double red[kRedThreads];
+    const Chunk c = chunks[blockIdx.x];
+    chunk_col_sums(
+        c, nrhs, [&](int64_t row, int j) { const double v = A[row * nrhs + j]; return v * v; },
+        partial + (size_t)blockIdx.x * nrhs, red);
+}
+
+// out[i * nrhs + j] = sum over problem i's chunks of partial[., j] (one warp each)
+__global__ void k_prob_sums(const double *__restrict__ partial, const int *__restrict__ prob_c0,
+                            const int *__restrict__ prob_nc, int n, int nrhs, double *__restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (w >= (int64_t)n * nrhs) return;
+    const int i = (int)(w / nrhs), j = (int)(w % nrhs);
+    const double t = warp_prob_sum(partial, prob_c0[i], prob_nc[i], nrhs, j, lane);
+    if (lane == 0) out[w] = t;
 }
 
 double env_double_b(const char *name, double dflt) {
@@ -585,7 +607,8 @@ int fgk_batch_cg_solve(fgk_batch b, const double *const *y, const double *sigma2
     double *Pv = (double *)take(vec * 8), *W64 = (double *)take(vec * 8);
     float *P32 = (float *)take(vec * 4), *W32 = (float *)take(vec * 4);
     double *pw_part = (double *)take((size_t)b->nchunk * nrhs * 8), *rr_part = (double *)take((size_t)b->nchunk * nrhs * 8);
-    double *sig2 = (double *)take(n * 8), *nrm = (double *)take(nrhs * 8);
+    double *sig2 = (double *)take(n * 8), *nrm = (double *)take((size_t)C * 8);
+    double *nrm_part = (double *)take((size_t)b->nchunk * nrhs * 8);
     BState st;
     st.rho = (double *)take(C * 8);
     st.rho_next = (double *)take(C * 8);
@@ -595,13 +618,19 @@ int fgk_batch_cg_solve(fgk_batch b, const double *const *y, const double *sigma2
     st.iters = (int *)take(C * 4);
     st.prob_active = (int *)take(n * 4);
     st.prob_active_next = (int *)take(n * 4);
+    st.bd = (int *)take(C * 4);
     st.breakdown = (int *)take(16);
     int rc = FGK_OK;
     for (void *q : mine)
         if (!q) rc = FGK_ERR_OOM;
-    std::vector<double> bnorm(C), rnorm(C), rho_ref(C), hrho(C), hthr2(C), hnorm(nrhs);
+    std::vector<double> bnorm(C), rnorm(C), rho_ref(C), hrho(C), hthr2(C), hnorm(C);
     std::vector<int> hact(C), hiters(C, 0), confirmed(C, 0), hpa(n), last_repl(n, 0);
-    std::vector<int> min_gap(n, 0);
+    // gap[i]: min_gap[i] while problem i's last replacement found a true
+    // residual within twice the recursive one, else 0 (the FP32 recursion was
+    // drifting: replace at every drop by delta)
+    std::vector<int> min_gap(n, 0), gap(n, 0), restarts(n, 0), hbd(C, 0);
+    constexpr int kMaxRestarts = 8;
+    int limit_prob = -1;
     int iters_total = 0, refinements = 0, n32 = 0, n64 = 0;
     bool converged = false, breakdown = false;
     cudaGraph_t graph = nullptr;
@@ -610,20 +639,31 @@ int fgk_batch_cg_solve(fgk_batch b, const double *const *y, const double *sigma2
     const double delta = env_double_b("FGK_MIXED_DELTA", 0.5);
     const int check_every = 8;
 
-    // FP64 true residual of problem i into Rv's slice; norms into rnorm
-    auto residual = [&](int i) -> int {
-        Plan *p = b->plans[i];
-        const size_t o = (size_t)b->voff[i] * nrhs, m = (size_t)p->N * nrhs;
-        FGK_TRY(mvm_q_f64(p, X + o, nrhs, W64 + o, s, nullptr));
-        k_residual_slice<<<256, 256, 0, s>>>(Bv + o, W64 + o, X + o, sigma2[i], (int64_t)m, Rv + o);
+    // squared column norms of every problem's slice of A into hnorm (one sync)
+    auto all_norms = [&](const double *A) -> int {
+        k_chunk_norms2<<<b->nchunk, kRedThreads, 0, s>>>(A, b->chunks, nrhs, nrm_part);
         FGK_LAUNCH_CHECK();
-        k_slice_norms2<<<1, kRedThreads, 0, s>>>(Rv + o, p->N, nrhs, nrm);
+        k_prob_sums<<<grid_for((int64_t)C * 32, 256), 256, 0, s>>>(nrm_part, b->prob_c0, b->prob_nc, n, nrhs, nrm);
         FGK_LAUNCH_CHECK();
-        FGK_CUDA(cudaMemcpyAsync(hnorm.data(), nrm, nrhs * 8, cudaMemcpyDeviceToHost, s));
+        FGK_CUDA(cudaMemcpyAsync(hnorm.data(), nrm, (size_t)C * 8, cudaMemcpyDeviceToHost, s));
         FGK_CUDA(cudaStreamSynchronize(s));
-        for (int j = 0; j < nrhs; ++j) rnorm[i * nrhs + j] = std::sqrt(hnorm[j]);
-        ++refinements;
-        ++n64;
+        return FGK_OK;
+    };
+    // FP64 true residuals of the listed problems into Rv's slices (the other
+    // slices keep their last residual); norms of the listed ones into rnorm
+    auto residuals = [&](const std::vector<int> &list) -> int {
+        for (int i : list) {
+            Plan *p = b->plans[i];
+            const size_t o = (size_t)b->voff[i] * nrhs, m = (size_t)p->N * nrhs;
+            FGK_TRY(mvm_q_f64(p, X + o, nrhs, W64 + o, s, nullptr));
+            k_residual_slice<<<256, 256, 0, s>>>(Bv + o, W64 + o, X + o, sigma2[i], (int64_t)m, Rv + o);
+            FGK_LAUNCH_CHECK();
+            ++refinements;
+            ++n64;
+        }
+        FGK_TRY(all_norms(Rv));
+        for (int i : list)
+            for (int j = 0; j < nrhs; ++j) rnorm[i * nrhs + j] = std::sqrt(hnorm[i * nrhs + j]);
         return FGK_OK;
     };
     auto upload_state = [&]() -> int {
@@ -653,14 +693,9 @@ int fgk_batch_cg_solve(fgk_batch b, const double *const *y, const double *sigma2
         FGK_CUDA(cudaMemcpyAsync(Rv, Bv, vec * 8, cudaMemcpyDeviceToDevice, s));
         FGK_CUDA(cudaMemcpyAsync(Pv, Bv, vec * 8, cudaMemcpyDeviceToDevice, s));
         FGK_CUDA(cudaMemsetAsync(st.breakdown, 0, 16, s));
-        for (int i = 0; i < n; ++i) {
-            const size_t o = (size_t)b->voff[i] * nrhs;
-            k_slice_norms2<<<1, kRedThreads, 0, s>>>(Bv + o, b->plans[i]->N, nrhs, nrm);
-            FGK_LAUNCH_CHECK();
-            FGK_CUDA(cudaMemcpyAsync(hnorm.data(), nrm, nrhs * 8, cudaMemcpyDeviceToHost, s));
-            FGK_CUDA(cudaStreamSynchronize(s));
-            for (int j = 0; j < nrhs; ++j) bnorm[i * nrhs + j] = std::sqrt(hnorm[j]);
-        }
+        FGK_CUDA(cudaMemsetAsync(st.bd, 0, (size_t)C * 4, s));
+        if ((rc = all_norms(Bv))) break;
+        for (int c = 0; c < C; ++c) bnorm[c] = std::sqrt(hnorm[c]);
         rnorm = bnorm;
         for (int c = 0; c < C; ++c) {
             hrho[c] = rnorm[c] * rnorm[c];
@@ -677,22 +712,29 @@ int fgk_batch_cg_solve(fgk_batch b, const double *const *y, const double *sigma2
         cudaEvent_t t0, t1;
         FGK_CUDA(cudaEventCreate(&t0));
         FGK_CUDA(cudaEventCreate(&t1));
+        // Spacing of each problem's replacements: its FP64 over its FP32 product
+        // time (each timed on its own), the rule the single-problem solve
+        // uses, so a problem converges in the batch as it does alone.  It
+        // applies only while the recursion tracks the true residual (see gap).
         FGK_CUDA(cudaEventRecord(t0, s));
-        if ((rc = batch_product(b, P32, W32, nullptr, s))) break;
+        if ((rc = batch_product(b, P32, W32, nullptr, s))) break;  // warm-up
         FGK_CUDA(cudaEventRecord(t1, s));
         FGK_CUDA(cudaEventSynchronize(t1));
-        float ms32 = 0.f;
-        FGK_CUDA(cudaEventElapsedTime(&ms32, t0, t1));
         for (int i = 0; i < n && !rc; ++i) {
             Plan *p = b->plans[i];
             const size_t o = (size_t)b->voff[i] * nrhs;
+            float ms32 = 0.f, ms64 = 0.f;
             FGK_CUDA(cudaEventRecord(t0, s));
-            rc = mvm_q_f64(p, Pv + o, nrhs, W64 + o, s, nullptr);
+            if ((rc = mvm_q_f32(p, P32 + o, nrhs, W32 + o, s, nullptr))) break;
             FGK_CUDA(cudaEventRecord(t1, s));
             FGK_CUDA(cudaEventSynchronize(t1));
-            float ms64 = 0.f;
+            FGK_CUDA(cudaEventElapsedTime(&ms32, t0, t1));
+            FGK_CUDA(cudaEventRecord(t0, s));
+            if ((rc = mvm_q_f64(p, Pv + o, nrhs, W64 + o, s, nullptr))) break;
+            FGK_CUDA(cudaEventRecord(t1, s));
+            FGK_CUDA(cudaEventSynchronize(t1));
             FGK_CUDA(cudaEventElapsedTime(&ms64, t0, t1));
-            min_gap[i] = ms32 > 0.f ? (int)std::ceil(ms64 / ms32) : 0;
+            min_gap[i] = ms32 > 0.f ? (int)std::min(1e6, std::ceil((double)ms64 / ms32)) : 0;
         }
         cudaEventDestroy(t0);
         cudaEventDestroy(t1);
@@ -747,9 +789,34 @@ int fgk_batch_cg_solve(fgk_batch b, const double *const *y, const double *sigma2
             const int after = *std::max_element(hiters.begin(), hiters.end());
             iters_total += after - before;
             n32 += after - before;
+            // FP32 breakdowns: decide with FP64 scans; restart the column if
+            // p^T A p is positive there, else stop with a breakdown
+            std::vector<int> broken(n, 0);
             if (hbreak) {
-                breakdown = true;
-                break;
+                FGK_CUDA(cudaMemcpyAsync(hbd.data(), st.bd, (size_t)C * 4, cudaMemcpyDeviceToHost, s));
+                FGK_CUDA(cudaStreamSynchronize(s));
+                for (int c = 0; c < C; ++c)
+                    if (hbd[c]) broken[c / nrhs] = 1;
+                for (int i = 0; i < n && !rc; ++i)
+                    if (broken[i]) {
+                        const size_t o = (size_t)b->voff[i] * nrhs;
+                        rc = mvm_q_f64(b->plans[i], Pv + o, nrhs, W64 + o, s, nullptr);
+                        ++n64;
+                    }
+                if (rc) break;
+                k_chunk_pap<<<b->nchunk, kRedThreads, 0, s>>>(Pv, W64, sig2, b->chunks, nrhs, nrm_part);
+                FGK_LAUNCH_CHECK();
+                k_prob_sums<<<grid_for((int64_t)C * 32, 256), 256, 0, s>>>(nrm_part, b->prob_c0, b->prob_nc, n, nrhs,
+                                                                         nrm);
+                FGK_LAUNCH_CHECK();
+                FGK_CUDA(cudaMemcpyAsync(hnorm.data(), nrm, (size_t)C * 8, cudaMemcpyDeviceToHost, s));
+                FGK_CUDA(cudaStreamSynchronize(s));
+                for (int c = 0; c < C; ++c)
+                    if (hbd[c] && !(hnorm[c] > 0.0)) breakdown = true;
+                for (int i = 0; i < n; ++i)
+                    if (broken[i] && ++restarts[i] > kMaxRestarts && limit_prob < 0) limit_prob = i;
+                if (limit_prob >= 0) breakdown = true;
+                if (breakdown) break;
             }
             bool any = false;
             std::vector<int> todo;
@@ -761,16 +828,30 @@ int fgk_batch_cg_solve(fgk_batch b, const double *const *y, const double *sigma2
                     if (!snap_act[c]) claims = true;
                     if (snap_rho[c] <= delta * delta * rho_ref[c]) dropped = true;
                 }
-                if (claims || (dropped && iters_total - last_repl[i] >= min_gap[i])) todo.push_back(i);
+                if (broken[i] || claims || (dropped && iters_total - last_repl[i] >= gap[i])) todo.push_back(i);
             }
             if (todo.empty()) continue;
             for (int c = 0; c < C; ++c) {
                 hrho[c] = snap_rho[c];
                 hact[c] = snap_act[c];
             }
+            if ((rc = residuals(todo))) break;
+            if (hbreak) {
+                k_brestart<<<b->nchunk, 256, 0, s>>>(Pv, Rv, b->chunks, nrhs, st.bd);
+                FGK_LAUNCH_CHECK();
+                k_to_f32_diag<<<b->nchunk, 256, 0, s>>>(Pv, P32, W32, b->probs, b->chunks, nrhs);
+                FGK_LAUNCH_CHECK();
+                FGK_CUDA(cudaMemsetAsync(st.bd, 0, (size_t)C * 4, s));
+                FGK_CUDA(cudaMemsetAsync(st.breakdown, 0, 16, s));
+            }
             for (int i : todo) {
-                if ((rc = residual(i))) break;
                 last_repl[i] = iters_total;
+                bool drift = false;
+                for (int j = 0; j < nrhs; ++j) {
+                    const int c = i * nrhs + j;
+                    if (!confirmed[c] && rnorm[c] > 2.0 * std::sqrt(snap_rho[c])) drift = true;
+                }
+                gap[i] = drift ? 0 : min_gap[i];
                 for (int j = 0; j < nrhs; ++j) {
                     const int c = i * nrhs + j;
                     if (!confirmed[c] && rnorm[c] <= tol * bnorm[c]) confirmed[c] = 1;
@@ -813,9 +894,17 @@ int fgk_batch_cg_solve(fgk_batch b, const double *const *y, const double *sigma2
             info[i].mvm_f32 = n32;
             info[i].mvm_f64 = n64;
             info[i].max_true_resid = mx;
+            info[i].restarts = restarts[i];
+            info[i].fp64_switch = 0;
         }
     }
     if (rc) return rc;
+    if (breakdown && limit_prob >= 0) {
+        set_error("fgk_batch_cg_solve: problem %d met p^T A p <= 0 with FP32 scans more than %d times; solve it "
+                  "on its own (fgk_cg_solve continues with FP64 scans)",
+                  limit_prob, kMaxRestarts);
+        return FGK_ERR_BREAKDOWN;
+    }
     if (breakdown) {
         set_error("fgk_batch_cg_solve: p^T A p <= 0 met; a system is not positive definite");
         return FGK_ERR_BREAKDOWN;

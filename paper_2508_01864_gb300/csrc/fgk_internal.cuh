@@ -166,6 +166,40 @@ inline int ceil_log2_i64(int64_t n) {
     return l;
 }
 
+// Column sums of a row-major block held one value per thread: thread t holds
+// a value of column t % ncols (threads at or beyond (blockDim / ncols) * ncols
+// hold 0).  Returns the column's total in threads 0..ncols-1 (other threads:
+// unspecified).  red needs blockDim.x doubles; every thread of the block calls.
+// A power-of-two ncols <= 32 folds within each warp with shuffles first (the
+// lanes of one column sit ncols apart), then sums the warps' partials; any
+// other ncols takes a shared-memory tree over the row slots.
+__device__ __forceinline__ double block_col_sum(double v, int ncols, double *red) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (ncols <= 32 && (ncols & (ncols - 1)) == 0) {
+        for (int o = 16; o >= ncols; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        const int lane = tid & 31, warp = tid >> 5;
+        if (lane < ncols) red[warp * ncols + lane] = v;
+        __syncthreads();
+        double t = 0.0;
+        if (tid < ncols)
+            for (int w = 0; w < (nt >> 5); ++w) t += red[w * ncols + tid];
+        __syncthreads();
+        return t;
+    }
+    red[tid] = v;
+    __syncthreads();
+    const int lr = tid / ncols;
+    for (int n = nt / ncols; n > 1;) {
+        const int h = (n + 1) >> 1;
+        if (lr < h && lr + h < n) red[tid] += red[tid + h * ncols];
+        __syncthreads();
+        n = h;
+    }
+    const double t = tid < ncols ? red[tid] : 0.0;
+    __syncthreads();
+    return t;
+}
+
 inline unsigned grid_for(int64_t n, int threads) {
     int64_t b = (n + threads - 1) / threads;
     if (b < 1) b = 1;

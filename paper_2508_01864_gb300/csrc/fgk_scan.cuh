@@ -273,7 +273,7 @@ __device__ __forceinline__ void set_identity(R *x) {
 template <class R, int P, int NOFF, int KIND, int MODE>
 __device__ __forceinline__ void scan_tile(const ScanArgs<R> &A, const WorkItem wi, int r0, int r1) {
     using Tr = Traits<P, NOFF, KIND>;
-    constexpr int GM = Tr::GM, CP = Tr::CP, SMM = Tr::SM, AG = Tr::AG, NPASS = Tr::NPASS, NCH = Tr::NCH;
+    constexpr int GM = Tr::GM, CP = Tr::CP, SMM = Tr::SM, AG = Tr::AG, NCH = Tr::NCH;
     constexpr int NGP = Tr::NGP, NPT = Tr::NPT, NWC = Tr::NWC;
     constexpr int ND = Tr::NDIR, NDP = 2 / ND;  // directions per walk, direction passes
     constexpr int EPT = kScanEPT, NT = kScanThreads, NW = NT / 32;

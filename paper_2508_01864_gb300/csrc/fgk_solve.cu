@@ -19,7 +19,15 @@
 // same search direction (residual replacement, "reliable updates").  This is
 // iterative refinement with the correction solved in low precision, without
 // restarting the Krylov space at every correction.  In FP64 mode the only
-// replacement is the final confirmation.  A column stops once its FP64 true
+// replacement is the final confirmation.
+//
+// FP32 breakdowns.  The FP32 product of a direction that lies mostly in the
+// small-eigenvalue subspace of a badly conditioned A can have p^T A p <= 0
+// although A is positive definite.  A column that meets it stops (masked);
+// the host recomputes p^T A p with FP64 scans: still <= 0 is a true
+// breakdown (the solve ends with FGK_ERR_BREAKDOWN); otherwise the residual
+// is replaced and the column restarts from p = r.  After kMaxRestarts such
+// restarts in one solve the remaining iterations run with FP64 scans.  A column stops once its FP64 true
 // residual meets the tolerance; the reported residuals are those.
 //
 // Fixed effects (Sec. 3.2, the GLS step of Algorithm 1): the block is
@@ -53,9 +61,12 @@ struct ColState {
     int active[kMaxCols];
     int active_next[kMaxCols];
     int iters[kMaxCols];
+    int bd[kMaxCols];  // column met p^T A p <= 0 (set by k_update_xr, cleared by the host)
     int n_active;
     int breakdown;
 };
+
+constexpr int kMaxRestarts = 4;
 
 // partial[b * ncols + j] = sum over this block's rows of a_ij * (b_ij + sb c_ij).
 // Thread tid owns column tid % ncols and a row subset, so the row-major
@@ -76,19 +87,27 @@ __device__ __forceinline__ void block_col_dots(const TA *__restrict__ a, const T
             acc += (double)a[t] * bb;
         }
     }
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    if (threadIdx.x < ncols) {
-        double s = 0.0;
-        for (int k = 0; k < per; ++k) s += red[k * ncols + threadIdx.x];
-        partial[blockIdx.x * ncols + threadIdx.x] = s;
-    }
-    __syncthreads();
+    const double s = block_col_sum(acc, ncols, red);
+    if (threadIdx.x < ncols) partial[blockIdx.x * ncols + threadIdx.x] = s;
 }
 
 __global__ void k_col_dots(const double *__restrict__ a, const double *__restrict__ b, int64_t N, int ncols,
                            double *__restrict__ partial) {
     block_col_dots<double, double>(a, b, 0.0, nullptr, N, ncols, partial);
+}
+
+// partial sums of p_j^T (w_j + sigma2 p_j)
+__global__ void k_col_pap(const double *__restrict__ p, const double *__restrict__ w, double sigma2, int64_t N,
+                          int ncols, double *__restrict__ partial) {
+    block_col_dots<double, double>(p, w, sigma2, p, N, ncols, partial);
+}
+
+// p_j = r_j on the columns flagged in bd (a CG restart)
+__global__ void k_restart_cols(double *__restrict__ p, const double *__restrict__ r, int64_t N, int ncols,
+                               const ColState *__restrict__ st) {
+    const int64_t n = N * ncols;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        if (st->bd[t % ncols]) p[t] = r[t];
 }
 
 __global__ void k_finalize_sums(const double *__restrict__ partial, int nblk, int ncols, double *__restrict__ out) {
@@ -126,7 +145,7 @@ __global__ void k_dot_pAp(const double *__restrict__ p, const W *__restrict__ w,
 // alpha_j = rho_j / p_j^T A p_j (every block from the partials), then
 // x += alpha p, r -= alpha (w + sigma2 p), and partial sums of r^2.
 // p^T A p <= 0 on an active column flags a breakdown (the column is left
-// untouched; the host stops the solve).
+// untouched and stops; the host decides what follows).
 template <class W>
 __global__ void k_update_xr(double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
                             const W *__restrict__ w, double sigma2, int64_t N, int ncols,
@@ -143,8 +162,10 @@ __global__ void k_update_xr(double *__restrict__ x, double *__restrict__ r, cons
             if (st->active[j]) {
                 if (pw > 0.0)
                     a = st->rho[j] / pw;
-                else if (blockIdx.x == 0)
+                else if (blockIdx.x == 0) {
                     atomicOr(&st->breakdown, 1);
+                    st->bd[j] = 1;
+                }
             }
             s_alpha[j] = a;
         }
@@ -167,13 +188,8 @@ __global__ void k_update_xr(double *__restrict__ x, double *__restrict__ r, cons
             acc += rv * rv;
         }
     }
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    if (threadIdx.x < ncols) {
-        double t = 0.0;
-        for (int k = 0; k < per; ++k) t += red[k * ncols + threadIdx.x];
-        partial[blockIdx.x * ncols + threadIdx.x] = t;
-    }
+    const double t = block_col_sum(acc, ncols, red);
+    if (threadIdx.x < ncols) partial[blockIdx.x * ncols + threadIdx.x] = t;
 }
 
 // beta_j = rho'_j / rho_j and the stop test (every block from the partials);
@@ -194,7 +210,7 @@ __global__ void k_update_p(double *__restrict__ p, float *__restrict__ p32, W *_
         if (lane == 0) {
             const int act = st->active[j];
             const double rho = st->rho[j];
-            const int still = act && rr > st->thr2[j];
+            const int still = act && !st->bd[j] && rr > st->thr2[j];
             s_beta[j] = act ? (rho > 0.0 ? rr / rho : 0.0) : 0.0;
             s_act[j] = still;
             if (blockIdx.x == 0) {
@@ -382,7 +398,7 @@ int cg_solve(Plan *p, const double *y, int nrhs, double sigma2, const double *H,
     p->stream = s;
 
     const size_t vec = (size_t)N * ncols;
-    const bool mixed = mode == FGK_MIXED;
+    bool mixed = mode == FGK_MIXED;
     size_t bytes = 5 * vec * 8 + (mixed ? 2 * vec * 4 : 0) + (size_t)kRedBlocks * kMaxCols * (kMaxH + 1) * 8 +
                    sizeof(ColState) + 4096;
     char *w = (char *)dev_alloc(bytes, s);
@@ -419,7 +435,9 @@ int cg_solve(Plan *p, const double *y, int nrhs, double sigma2, const double *H,
     bool converged = false, breakdown = false;
     // mixed mode: replace the recursive residual by the FP64 true residual
     // once it has dropped by this factor since the last replacement
-    const double delta = mixed ? env_double("FGK_MIXED_DELTA", 0.5) : 0.0;
+    double delta = mixed ? env_double("FGK_MIXED_DELTA", 0.5) : 0.0;
+    int restarts = 0;
+    std::vector<double> pap(ncols);
     const int check_every = 8;
     int hbad = 0;
     double *dsum = partial + (size_t)kRedBlocks * kMaxCols * kMaxH - 2 * kMaxCols * kMaxH;  // tail scratch
@@ -467,6 +485,30 @@ int cg_solve(Plan *p, const double *y, int nrhs, double sigma2, const double *H,
                                                                  partial2, kRedBlocks, st);
             FGK_LAUNCH_CHECK();
         }
+        return FGK_OK;
+    };
+    // p^T A p per column with FP64 scans (overwrites W64)
+    auto pap64 = [&]() -> int {
+        FGK_TRY(mvm_q_f64(p, Pv, ncols, W64, s, nullptr));
+        ++n_f64;
+        k_col_pap<<<kRedBlocks, kRedThreads, 0, s>>>(Pv, W64, sigma2, N, ncols, partial);
+        FGK_LAUNCH_CHECK();
+        k_finalize_sums<<<1, kMaxCols, 0, s>>>(partial, kRedBlocks, ncols, dsum);
+        FGK_LAUNCH_CHECK();
+        FGK_CUDA(cudaMemcpyAsync(pap.data(), dsum, ncols * 8, cudaMemcpyDeviceToHost, s));
+        FGK_CUDA(cudaStreamSynchronize(s));
+        return FGK_OK;
+    };
+    auto capture = [&]() -> int {
+        const uint64_t c0 = kernel_launch_count();
+        FGK_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        int crc = one_iteration();
+        cudaError_t ce = cudaStreamEndCapture(s, &graph);
+        graph_nodes = kernel_launch_count() - c0;
+        add_kernel_launches(-(int64_t)graph_nodes);  // counted when replayed
+        if (crc) return crc;
+        FGK_CUDA(ce);
+        FGK_CUDA(cudaGraphInstantiate(&gexec, graph, 0));
         return FGK_OK;
     };
     auto init_p = [&]() -> int {
@@ -521,7 +563,12 @@ int cg_solve(Plan *p, const double *y, int nrhs, double sigma2, const double *H,
         cudaEventDestroy(t0);
         cudaEventDestroy(t1);
         cudaEventDestroy(t2);
+        // The spacing only applies while the recursion tracks the true
+        // residual: when a replacement finds a true residual more than twice
+        // the recursive one, the FP32 iterations since the last one were
+        // drifting and the next replacement is not held back.
         const int min_gap = mixed && ms32 > 0.f ? (int)std::ceil(ms64 / ms32) : 0;
+        int gap = 0;  // until the first replacement has shown how well the recursion tracks
         int last_replacement = 0;
         if ((rc = init_p())) break;
         ColState hs;
@@ -536,20 +583,7 @@ int cg_solve(Plan *p, const double *y, int nrhs, double sigma2, const double *H,
             hs.n_active += hs.active[j];
         }
         FGK_CUDA(cudaMemcpyAsync(st, &hs, sizeof(hs), cudaMemcpyHostToDevice, s));
-        {
-            const uint64_t c0 = kernel_launch_count();
-            FGK_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-            int crc = one_iteration();
-            cudaError_t ce = cudaStreamEndCapture(s, &graph);
-            graph_nodes = kernel_launch_count() - c0;
-            add_kernel_launches(-(int64_t)graph_nodes);  // counted when replayed
-            if (crc) {
-                rc = crc;
-                break;
-            }
-            FGK_CUDA(ce);
-            FGK_CUDA(cudaGraphInstantiate(&gexec, graph, 0));
-        }
+        if ((rc = capture())) break;
         ColState snap = hs;
         while (true) {
             bool all = true;
@@ -568,9 +602,18 @@ int cg_solve(Plan *p, const double *y, int nrhs, double sigma2, const double *H,
             const int after = *std::max_element(snap.iters, snap.iters + ncols);
             iters_total += after - before;
             if (mixed) n_f32 += after - before; else n_f64 += after - before;
+            bool restart = false;
             if (snap.breakdown) {
-                breakdown = true;
-                break;
+                // FP64 mode: a true breakdown.  Mixed: decide with FP64 scans.
+                if (!mixed) {
+                    breakdown = true;
+                    break;
+                }
+                if ((rc = pap64())) break;
+                for (int j = 0; j < ncols; ++j)
+                    if (snap.bd[j] && !(pap[j] > 0.0)) breakdown = true;
+                if (breakdown) break;
+                restart = true;
             }
             // replace the recursive residual when a column claims convergence
             // or (mixed) has reduced its residual by delta since the last time
@@ -580,9 +623,29 @@ int cg_solve(Plan *p, const double *y, int nrhs, double sigma2, const double *H,
                 if (!snap.active_next[j]) claims = true;
                 if (snap.rho_next[j] <= delta * delta * rho_ref[j]) dropped = true;
             }
-            if (!(claims || (dropped && iters_total - last_replacement >= min_gap))) continue;
+            if (!(restart || claims || (dropped && iters_total - last_replacement >= gap))) continue;
             last_replacement = iters_total;
             if ((rc = true_residual())) break;
+            bool drift = false;
+            for (int j = 0; j < ncols; ++j)
+                if (!confirmed[j] && rnorm[j] > 2.0 * std::sqrt(snap.rho_next[j])) drift = true;
+            gap = drift ? 0 : min_gap;
+            if (restart) {
+                k_restart_cols<<<kRedBlocks, kRedThreads, 0, s>>>(Pv, Rv, N, ncols, st);
+                FGK_LAUNCH_CHECK();
+                std::memset(snap.bd, 0, sizeof(snap.bd));
+                snap.breakdown = 0;
+                if (++restarts > kMaxRestarts && mixed) {
+                    // the FP32 products cannot resolve this system: FP64 from here on
+                    mixed = false;
+                    delta = 0.0;
+                    cudaGraphExecDestroy(gexec);
+                    cudaGraphDestroy(graph);
+                    gexec = nullptr;
+                    graph = nullptr;
+                    if ((rc = capture())) break;
+                }
+            }
             if ((rc = init_p())) break;  // the residual product overwrote W64 (FP64 mode)
             snap.n_active = 0;
             for (int j = 0; j < ncols; ++j) {
@@ -640,6 +703,8 @@ int cg_solve(Plan *p, const double *y, int nrhs, double sigma2, const double *H,
         info->refinements = refinements;
         info->mvm_f32 = n_f32;
         info->mvm_f64 = n_f64;
+        info->restarts = restarts;
+        info->fp64_switch = (mode == FGK_MIXED && !mixed) ? 1 : 0;
         double mx = 0.0;
         for (int j = 0; j < ncols; ++j) {
             double r = bnorm[j] > 0 ? rnorm[j] / bnorm[j] : 0.0;

@@ -40,7 +40,8 @@ class FgkError(RuntimeError):
 class fgk_cg_info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("refinements", ctypes.c_int32), ("mvm_f32", ctypes.c_int32),
                 ("mvm_f64", ctypes.c_int32), ("max_true_resid", ctypes.c_double),
-                ("true_resid", ctypes.POINTER(ctypes.c_double))]
+                ("true_resid", ctypes.POINTER(ctypes.c_double)), ("restarts", ctypes.c_int32),
+                ("fp64_switch", ctypes.c_int32)]
 
 
 class fgk_plan_info(ctypes.Structure):
@@ -264,7 +265,8 @@ def fgk_cg_solve(h: Handle, y: torch.Tensor, sigma2: float, H: torch.Tensor | No
                           _stream(stream))
     _check(rc, allow_soft=True)
     d = {"iterations": info.iterations, "refinements": info.refinements, "mvm_f32": info.mvm_f32,
-         "mvm_f64": info.mvm_f64, "max_true_resid": info.max_true_resid, "true_resid": list(res)}
+         "mvm_f64": info.mvm_f64, "max_true_resid": info.max_true_resid, "true_resid": list(res),
+         "restarts": info.restarts, "fp64_switch": info.fp64_switch}
     if y.dim() == 1:
         alpha = alpha.squeeze(1)
     return alpha, beta, d, rc
@@ -369,7 +371,8 @@ def fgk_batch_cg_solve(b: Batch, ys: list, sigma2s, tol: float = 1e-8, maxit: in
     rc = lib.fgk_batch_cg_solve(b.ptr, yp, sg, float(tol), int(maxit), ap, infos, _stream(stream))
     _check(rc, allow_soft=True)
     out = [{"iterations": infos[i].iterations, "refinements": infos[i].refinements, "mvm_f32": infos[i].mvm_f32,
-            "mvm_f64": infos[i].mvm_f64, "max_true_resid": infos[i].max_true_resid, "true_resid": list(res[i])}
+            "mvm_f64": infos[i].mvm_f64, "max_true_resid": infos[i].max_true_resid, "true_resid": list(res[i]),
+            "restarts": infos[i].restarts, "fp64_switch": infos[i].fp64_switch}
            for i in range(n)]
     return alphas, out, rc
 

@@ -83,3 +83,29 @@ def test_batch_rejects_d3(fgk_mod):
     with fgk.fgk_build(to_dev(p.X), 1.5, [0.2] * 3) as h:
         with pytest.raises(fgk.FgkError):
             fgk.fgk_batch_create([h], 2)
+
+
+@pytest.mark.parametrize("rpc", [0, 1])
+def test_batch_cg_iterations_track_single_solver(fgk_mod, rpc):
+    """Badly conditioned small problems (smooth kernels, long length scales):
+    the FP32 recursion drifts fast there, so the batched solve has to replace
+    its residual as promptly as the single-problem solve; its iteration count
+    stays close to the single solve's for every launch shape."""
+    fgk = fgk_mod
+    probs = workloads.c4(n_problems=18)
+    sel = [probs[i] for i in (14, 17, 3)]  # d=1: nu 5/2 (N 1746, 1513), nu 3/2 (N 10165)
+    handles = [fgk.fgk_build(to_dev(p.X), p.nu, p.ell, kind="product") for p in sel]
+    b = fgk.fgk_batch_create(handles, 16, rpc)
+    try:
+        ys = [to_dev(p.V) for p in sel]
+        _, infos, rc = fgk.fgk_batch_cg_solve(b, ys, [p.sigma2 for p in sel], tol=1e-8, maxit=20000)
+        assert rc == 0
+        for p, h, y, info in zip(sel, handles, ys, infos):
+            _, _, one, rc1 = fgk.fgk_cg_solve(h, y, p.sigma2, tol=1e-8, maxit=20000, mode="mixed")
+            assert rc1 == 0
+            assert info["max_true_resid"] <= 1e-8
+            assert info["iterations"] <= 1.5 * one["iterations"] + 50, (p.name, info, one)
+    finally:
+        fgk.fgk_batch_destroy(b)
+        for h in handles:
+            fgk.fgk_destroy(h)
