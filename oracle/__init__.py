@@ -6,19 +6,22 @@ product package never imports it, and it never imports the product package.
 Everything here is plain FP64 on the CPU:
 
 * ``mvm_brute``  O1, the definition of K V (C, OpenMP, compensated sums);
-* ``kmat``       the dense matrix K for small N;
+* ``kmat``       the dense matrix K for small N; ``kcols`` selected columns;
 * ``mvm_dc``     O2, the paper's ECDF decomposition evaluated literally by a
   re-sorting divide and conquer (C);
 * ``structure``  O3, canonical sort permutations and the dominance-level
   arrays (numpy);
-* ``solve``      O4, conjugate gradients (Algorithm 2 with the identity
-  preconditioner), dense solves and the GLS fixed-effects step (numpy).
+* ``solve``      O4, conjugate gradients (Algorithm 2, with the identity or
+  the pivoted-Cholesky preconditioner of App. A.3: the rank-k pivoted
+  Cholesky factor, the Woodbury apply and the Sylvester log-determinant),
+  dense solves and the GLS fixed-effects step (numpy).
 """
 
 from .core import (  # noqa: F401
     L1,
     PRODUCT,
     build,
+    kcols,
     kernel,
     kmat,
     max_threads,

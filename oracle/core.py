@@ -50,6 +50,9 @@ def _load():
         lib.orc_kmat.restype = ctypes.c_int
         lib.orc_kmat.argtypes = [D, ctypes.c_long, ctypes.c_int, ctypes.c_int, D, ctypes.c_double,
                                  ctypes.c_int, D]
+        lib.orc_kcols.restype = ctypes.c_int
+        lib.orc_kcols.argtypes = [D, ctypes.c_long, ctypes.c_int, ctypes.c_int, D, ctypes.c_double,
+                                  ctypes.c_int, Lp, ctypes.c_long, D]
         lib.orc_mvm_dc.restype = ctypes.c_int
         lib.orc_mvm_dc.argtypes = [D, ctypes.c_long, ctypes.c_int, ctypes.c_int, D, ctypes.c_double,
                                    ctypes.c_int, D, ctypes.c_int, D]
@@ -138,6 +141,19 @@ def kmat(X, nu, ell, s2: float = 1.0, kind: int = L1) -> np.ndarray:
     if lib.orc_kmat(_dp(X), N, d, _two_nu(nu), _dp(ell), float(s2), int(kind), _dp(K)) != 0:
         raise ValueError("orc_kmat rejected its arguments")
     return K
+
+
+def kcols(X, idx, nu, ell, s2: float = 1.0, kind: int = L1) -> np.ndarray:
+    """Columns K[:, idx] (N x len(idx)) from the definition."""
+    lib = _load()
+    X, d, ell = _prep(X, ell)
+    N = X.shape[0]
+    idx = np.ascontiguousarray(np.atleast_1d(idx), dtype=np.int64)
+    C = np.empty((N, idx.size))
+    if lib.orc_kcols(_dp(X), N, d, _two_nu(nu), _dp(ell), float(s2), int(kind),
+                     idx.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), idx.size, _dp(C)) != 0:
+        raise ValueError("orc_kcols rejected its arguments")
+    return C
 
 
 def mvm_dc(X, V, nu, ell, s2: float = 1.0, kind: int = L1) -> np.ndarray:

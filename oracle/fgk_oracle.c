@@ -16,6 +16,8 @@
  *                  eq. scaled_kernel.  O(N^2), Neumaier-compensated sums,
  *                  OpenMP over output rows.
  *  orc_kmat        the dense matrix K itself (small N), same definition.
+ *  orc_kcols       selected columns K[:, idx] (the pivoted Cholesky of the
+ *                  preconditioner needs one column per step), same definition.
  *  orc_mvm_dc      O2: the paper's own algorithm, written in its order and
  *                  notation: weighted ECDFs with the generalised inequality
  *                  (eq. ECDFdelta), one per orthant delta and weight vector,
@@ -164,6 +166,20 @@ int orc_kmat(const double *X, long N, int d, int two_nu, const double *ell, doub
     double *U = scaled_coords(X, N, d, ell);
     for (long i = 0; i < N; ++i)
         for (long j = 0; j < N; ++j) K[i * N + j] = s2 * kern_pair(U + i * d, U + j * d, d, two_nu, kind);
+    free(U);
+    return 0;
+}
+
+int orc_kcols(const double *X, long N, int d, int two_nu, const double *ell, double s2, int kind,
+              const long *idx, long nidx, double *C)
+{
+    if (check_args(N, d, two_nu, ell, kind)) return -1;
+    for (long c = 0; c < nidx; ++c)
+        if (idx[c] < 0 || idx[c] >= N) return -1;
+    double *U = scaled_coords(X, N, d, ell);
+    for (long i = 0; i < N; ++i)
+        for (long c = 0; c < nidx; ++c)
+            C[i * nidx + c] = s2 * kern_pair(U + i * d, U + idx[c] * d, d, two_nu, kind);
     free(U);
     return 0;
 }

@@ -2,11 +2,21 @@
 
 TEST INFRASTRUCTURE ONLY.
 
-* ``cg``          Algorithm 2 (App. A.1) with the identity preconditioner
-                  s_P = I and a zero initial guess, several right-hand sides,
-                  each column stopped once its own relative residual
-                  ||r_j|| / ||b_j|| is at most ``tol`` (the algorithm's block
-                  test on ||R||^2 read per column and unsquared).
+* ``cg``          Algorithm 2 (App. A.1) with a zero initial guess and the
+                  preconditioner apply s_P (default: the identity), several
+                  right-hand sides, each column stopped once its own relative
+                  residual ||r_j|| / ||b_j|| is at most ``tol`` (the
+                  algorithm's block test on ||R||^2 read per column and
+                  unsquared).
+* ``pivoted_cholesky``  the rank-k pivoted Cholesky factor L of K
+                  (App. A.3, after Harbrecht et al.): at each step the pivot
+                  is the largest remaining diagonal entry (first index among
+                  equal ones) and L gains the column of K at the pivot minus
+                  what the earlier columns explain, divided by the square
+                  root of that diagonal entry.
+* ``woodbury_apply``  P^{-1} R for P = L L^T + sigma^2 I by the Woodbury
+                  formula of App. A.3.
+* ``precond_logdet``  log det P by Sylvester's determinant theorem (App. A.3).
 * ``dense_solve`` (K + sigma^2 I)^{-1} B via numpy, eq. gp_mean_system.
 * ``gls``         the generalised least-squares fixed effects
                   beta = (H^T A^{-1} H)^{-1} H^T A^{-1} y (Sec. 3.2, the GLS
@@ -20,14 +30,16 @@ from __future__ import annotations
 import numpy as np
 
 
-def cg(apply_A, B, tol: float, maxit: int):
+def cg(apply_A, B, tol: float, maxit: int, apply_Pinv=None):
+    """Algorithm 2: returns (X, iterations per column)."""
     B = np.asarray(B, dtype=np.float64)
     vec = B.ndim == 1
     B = B.reshape(B.shape[0], -1)
     n, m = B.shape
+    s_P = (lambda R: R.copy()) if apply_Pinv is None else (lambda R: np.asarray(apply_Pinv(R)).reshape(n, m))
     X = np.zeros_like(B)
     R = B - apply_A(X)
-    Pb = R.copy()
+    Pb = s_P(R)
     k = np.einsum("ij,ij->j", Pb, R)
     bnorm = np.linalg.norm(B, axis=0)
     done = np.linalg.norm(R, axis=0) <= tol * bnorm
@@ -43,11 +55,64 @@ def cg(apply_A, B, tol: float, maxit: int):
         iters[~done] += 1
         now = np.linalg.norm(R, axis=0) <= tol * bnorm
         done = done | now
+        Z = s_P(R)
         k_prev = k
-        k = np.einsum("ij,ij->j", R, R)
+        k = np.einsum("ij,ij->j", Z, R)
         beta = np.where(done, 0.0, k / np.where(k_prev == 0, 1.0, k_prev))
-        Pb = R + beta * Pb
+        Pb = Z + beta * Pb
     return (X[:, 0] if vec else X), iters
+
+
+def pivoted_cholesky(column, diag, k: int, forced=None, tie_rtol: float = 0.0):
+    """Rank-k pivoted Cholesky of the SPD matrix with diagonal ``diag`` and
+    columns ``column(i)``.  Returns (L (N x r), pivots (r,), residual
+    diagonal) with r <= k (fewer once the residual diagonal is exhausted).
+
+    ``forced``: follow these pivots instead of choosing them, after checking
+    that each is a largest remaining diagonal entry within a relative
+    ``tie_rtol`` (for comparing with a computation whose rounding may break
+    near-ties the other way)."""
+    d = np.array(diag, dtype=np.float64, copy=True)
+    N = d.size
+    L = np.zeros((N, k))
+    piv = []
+    for m in range(k):
+        top = d.max()
+        if forced is not None:
+            if m >= len(forced):
+                break
+            i = int(forced[m])
+            if not d[i] >= top * (1.0 - tie_rtol):
+                raise ValueError(f"step {m}: pivot {i} has residual {d[i]!r}, the largest is {top!r}")
+        else:
+            i = int(np.argmax(d))
+        if not d[i] > 0.0:
+            break
+        c = np.asarray(column(i), dtype=np.float64).reshape(N)
+        l = (c - L[:, :m] @ L[i, :m]) / np.sqrt(d[i])
+        L[:, m] = l
+        d = d - l * l
+        piv.append(i)
+    r = len(piv)
+    return L[:, :r], np.array(piv, dtype=np.int64), d
+
+
+def woodbury_apply(L, sigma2: float, R):
+    """(L L^T + sigma2 I)^{-1} R = R / sigma2 - L (I_k + L^T L / sigma2)^{-1} L^T R / sigma2^2."""
+    L = np.asarray(L, dtype=np.float64)
+    R = np.asarray(R, dtype=np.float64)
+    k = L.shape[1]
+    C = np.eye(k) + (L.T @ L) / sigma2
+    return R / sigma2 - (L @ np.linalg.solve(C, L.T @ R)) / (sigma2 * sigma2)
+
+
+def precond_logdet(L, sigma2: float) -> float:
+    """log det(L L^T + sigma2 I_N) = N log sigma2 + log det(I_k + L^T L / sigma2)."""
+    L = np.asarray(L, dtype=np.float64)
+    N, k = L.shape
+    sign, ld = np.linalg.slogdet(np.eye(k) + (L.T @ L) / sigma2)
+    assert sign > 0
+    return N * np.log(sigma2) + ld
 
 
 def dense_solve(K, sigma2: float, B):
