@@ -3,10 +3,12 @@
 
 One step = one pass of the whole hot path on the d=2 workload
 (N = 200000 points x ~ U[0,1]^2, nu = 3/2, ell = (0.1, 0.3), product
-kernel): build the cached sort and dominance structure, then solve
-(K + 0.01 I) alpha = y by CG to an FP64 true relative residual <= 1e-8
-(FP32 scans, FP64 vectors, FP64 residual replacement).  ``value`` is solves
-per second over all ranks (each rank solves its own replica).
+kernel): build the cached sort and dominance structure and the rank-100
+pivoted-Cholesky preconditioner (the paper's rank), then solve
+(K + 0.01 I) alpha = y by preconditioned CG to an FP64 true relative
+residual <= 1e-8 (FP32 scans, FP64 vectors, FP64 residual replacement).
+``value`` is solves per second over all ranks (each rank solves its own
+replica).  ``--precond-rank 0`` runs the unpreconditioned solve.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -35,7 +37,7 @@ METRIC = "exact Matérn MVM N·nrhs/sec & CG solves/sec at resid≤1e-8; p50/p99
 UNIT = "solves/s"
 TOL = 1e-8
 WORKLOAD = ("d=2 N=200000 nu=3/2 ell=(0.1,0.3) x~U[0,1]^2 product kernel; "
-            "CG (K+0.01I)alpha=y to FP64 true resid 1e-8; step = build + solve")
+            "CG (K+0.01I)alpha=y to FP64 true resid 1e-8; step = build + preconditioner + solve")
 # DRAM bytes per launch of the FP32 output scan on this workload from the
 # committed ncu capture (None until the kernel as built here was captured)
 SCAN_TRAFFIC_BYTES = None
@@ -310,6 +312,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="mixed", choices=["mixed", "f64"])
+    ap.add_argument("--precond-rank", type=int, default=100,
+                    help="rank of the pivoted-Cholesky preconditioner (0: none)")
     ap.add_argument("--ref-seconds", type=float, default=8.0)
     ap.add_argument("--ref-iters", type=int, default=5000)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -356,15 +360,26 @@ def main():
     flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def step():
-        h = fgk.fgk_build(X, p.nu, p.ell, kind="product")
-        alpha, _, info, rc = fgk.fgk_cg_solve(h, y, p.sigma2, tol=TOL, maxit=100000, mode=args.mode)
-        return h, alpha, info, rc
+    rank_pc = args.precond_rank
+
+    def step(Xd=X, yd=y):
+        h = fgk.fgk_build(Xd, p.nu, p.ell, kind="product")
+        pc = fgk.fgk_precond_build(h, rank_pc, p.sigma2) if rank_pc > 0 else None
+        alpha, _, info, rc = fgk.fgk_cg_solve(h, yd, p.sigma2, tol=TOL, maxit=100000, mode=args.mode, precond=pc)
+        return h, pc, alpha, info, rc
+
+    def release(h, pc):
+        if pc is not None:
+            fgk.fgk_precond_destroy(pc)
+        fgk.fgk_destroy(h)
 
     infos = []
+    pc_info = None
     for _ in range(args.warmup):
-        h, alpha, info, rc = step()
-        fgk.fgk_destroy(h)
+        h, pc, alpha, info, rc = step()
+        if pc is not None:
+            pc_info = {k: v for k, v in fgk.fgk_precond_info(pc).items() if k != "pivots"}
+        release(h, pc)
         assert rc == 0 and info["max_true_resid"] <= TOL, info
     torch.cuda.synchronize()
 
@@ -380,13 +395,13 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        h, alpha, info, rc = step()
+        h, pc, alpha, info, rc = step()
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
         infos.append(info)
         assert rc == 0 and info["max_true_resid"] <= TOL, info
-        fgk.fgk_destroy(h)
+        release(h, pc)
     torch.cuda.synchronize()
     clk = clocks.stop()
     launches = fgk.fgk_kernel_launches() - launches0
@@ -410,14 +425,13 @@ def main():
         e0.record(stream)
         Xd = Xh.to("cuda", non_blocking=True)
         yd = yh.to("cuda", non_blocking=True)
-        h = fgk.fgk_build(Xd, p.nu, p.ell, kind="product")
-        alpha, _, info, rc = fgk.fgk_cg_solve(h, yd, p.sigma2, tol=TOL, maxit=100000, mode=args.mode)
+        h, pc, alpha, info, rc = step(Xd, yd)
         ah.copy_(alpha.reshape(ah.shape), non_blocking=True)
         e1.record(stream)
         e1.synchronize()
         e2e_times.append(e0.elapsed_time(e1))
         assert rc == 0
-        fgk.fgk_destroy(h)
+        release(h, pc)
     e2e_ms = sum(e2e_times)
     if ws > 1:
         t = torch.tensor([e2e_ms], device="cuda")
@@ -457,6 +471,17 @@ def main():
     torch.cuda.synchronize()
     mvm64_ms = e0.elapsed_time(e1) / 5
     fgk.fgk_destroy(h)
+    # context: the same solve without the preconditioner (one run)
+    plain_ms = None
+    if rank_pc > 0:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        h = fgk.fgk_build(X, p.nu, p.ell, kind="product")
+        _, _, plain_info, _ = fgk.fgk_cg_solve(h, y, p.sigma2, tol=TOL, maxit=100000, mode=args.mode)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plain_ms = e0.elapsed_time(e1)
+        fgk.fgk_destroy(h)
     E = info_p["n_levels"] * p.N
     bytes_per_launch = E * (4 + 4 + 4 * (p.d - 1) + 2 * 4)  # q, gap, offsets, V gather, Y update
     pk, src = peaks()
@@ -477,7 +502,7 @@ def main():
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64" if args.mode == "mixed" else "f64",
         "data": "synthetic (seeded; stands in for the paper's uniform [0,1]^d simulations)",
-        "config": {"workload": WORKLOAD, "mode": args.mode, "parallelism": f"replicas x{ws}",
+        "config": {"workload": WORKLOAD, "mode": args.mode, "precond_rank": rank_pc, "parallelism": f"replicas x{ws}",
                    "l2": "flushed between timed steps (256 MiB write)", "global_batch": ws, "seq_len": None},
         "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99))},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -489,6 +514,8 @@ def main():
                 "f64_ms": mvm64_ms, "structure_entries": E},
         "cg": {"iterations": iters, "refinements": infos[-1]["refinements"],
                "true_resid": infos[-1]["max_true_resid"]},
+        "precond": pc_info,
+        "unpreconditioned_step_ms": plain_ms,
     }
     print(json.dumps(line), flush=True)
     if ws > 1:

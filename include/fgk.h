@@ -175,6 +175,63 @@ typedef struct {
 int fgk_cg_solve(fgk_handle h, const double *y, int nrhs, double sigma2, const double *H, int L, double tol,
                  int maxit, int mode, double *alpha, double *beta, fgk_cg_info *info, fgk_stream_t stream);
 
+/* ---- the pivoted-Cholesky preconditioner (App. A.3) ---- */
+
+typedef struct fgk_precond_s *fgk_precond;
+
+typedef struct {
+    int32_t rank_requested; /* min(rank, N) as passed to fgk_precond_build */
+    int32_t rank;           /* realised rank k (smaller once the largest residual
+                               diagonal entry of K - L L^T is at most 1e-12 s2) */
+    double sigma2;          /* the noise variance P was built for */
+    double trace_resid;     /* trace(K - L L^T): the approximation error */
+    double logdet;          /* log det P = N log sigma2 + log det(I_k + L^T L / sigma2)
+                               (Sylvester's determinant theorem, App. A.3) */
+    size_t device_bytes;    /* device memory held by the preconditioner */
+} fgk_precond_report;
+
+/* Build P = L L^T + sigma2 I, where L (N x k) is the rank-k pivoted Cholesky
+ * factor of the plan's K (App. A.3, after Harbrecht et al.): at each step the
+ * pivot is the point with the largest remaining diagonal of K - L L^T (ties:
+ * the smallest original point index), and L gains the column of K at the
+ * pivot minus what the earlier columns explain, divided by the square root of
+ * that diagonal entry.  The factor is computed in FP64 and applied from an
+ * FP32 copy; the Woodbury matrix I + L^T L / sigma2 is formed from the FP32
+ * values, so P is exactly (FP32 L)(FP32 L)^T + sigma2 I.
+ *   h       a built plan; it must outlive the preconditioner.
+ *   rank    0 <= rank <= 1024 (the paper uses 100); rank 0 gives P = sigma2 I.
+ *   sigma2  > 0, the noise variance of the systems it will precondition.
+ * Device memory: about N x rank x 12 bytes plus O(rank^2).  Synchronises
+ * `stream`.  Errors: FGK_ERR_INVALID (arguments), FGK_ERR_OOM. */
+int fgk_precond_build(fgk_handle h, int rank, double sigma2, fgk_stream_t stream, fgk_precond *out);
+
+/* The report of a built preconditioner; pivots (host, may be NULL) receives
+ * the k pivots as original point indices in the order chosen. */
+int fgk_precond_info(fgk_precond pc, fgk_precond_report *rep, int64_t *pivots);
+
+/* L (device, N x k FP64 row-major, the caller's point order: row i holds the
+ * k factor values of point i).  Asynchronous. */
+int fgk_precond_factor(fgk_precond pc, double *L, fgk_stream_t stream);
+
+/* Z = P^{-1} R by the Woodbury formula of App. A.3,
+ * P^{-1} R = R / sigma2 - L (I_k + L^T L / sigma2)^{-1} L^T R / sigma2^2.
+ * R, Z: device, N x ncols FP64 row-major, original point order,
+ * 1 <= ncols <= 64.  Asynchronous (allocates scratch on `stream`). */
+int fgk_precond_apply(fgk_precond pc, const double *R, int ncols, double *Z, fgk_stream_t stream);
+
+int fgk_precond_destroy(fgk_precond pc);
+
+/* fgk_cg_solve preconditioned by pc (Algorithm 2 with s_P = P^{-1}): every
+ * argument as fgk_cg_solve; pc == NULL is fgk_cg_solve.  pc must come from
+ * the same plan and be built for the same sigma2 (else FGK_ERR_INVALID).  The
+ * stop test stays on the unpreconditioned true residual ||b - A x|| / ||b||;
+ * in mixed mode the FP32 iterations run until the recursive residual has
+ * dropped by FGK_MIXED_DELTA (default 1e-3 here), then the FP64 true
+ * residual replaces it and every column restarts from p = P^{-1} r. */
+int fgk_cg_solve_pc(fgk_handle h, fgk_precond pc, const double *y, int nrhs, double sigma2, const double *H, int L,
+                    double tol, int maxit, int mode, double *alpha, double *beta, fgk_cg_info *info,
+                    fgk_stream_t stream);
+
 /* ---- batches: many problems advanced together (d <= 2) ---- */
 
 typedef struct fgk_batch_s *fgk_batch;

@@ -63,10 +63,14 @@ def cg(apply_A, B, tol: float, maxit: int, apply_Pinv=None):
     return (X[:, 0] if vec else X), iters
 
 
-def pivoted_cholesky(column, diag, k: int, forced=None, tie_rtol: float = 0.0):
+def pivoted_cholesky(column, diag, k: int, forced=None, tie_rtol: float = 0.0, eps: float = 1e-12):
     """Rank-k pivoted Cholesky of the SPD matrix with diagonal ``diag`` and
     columns ``column(i)``.  Returns (L (N x r), pivots (r,), residual
-    diagonal) with r <= k (fewer once the residual diagonal is exhausted).
+    diagonal) with r <= k: the factorisation stops early once the largest
+    residual diagonal entry is at most ``eps`` times the largest diagonal
+    entry of the matrix (numerically exhausted: the paper leaves this case
+    open; dividing by the square root of a rounding-level residual would only
+    add noise columns).
 
     ``forced``: follow these pivots instead of choosing them, after checking
     that each is a largest remaining diagonal entry within a relative
@@ -74,6 +78,7 @@ def pivoted_cholesky(column, diag, k: int, forced=None, tie_rtol: float = 0.0):
     near-ties the other way)."""
     d = np.array(diag, dtype=np.float64, copy=True)
     N = d.size
+    floor = eps * float(d.max()) if N else 0.0
     L = np.zeros((N, k))
     piv = []
     for m in range(k):
@@ -86,7 +91,7 @@ def pivoted_cholesky(column, diag, k: int, forced=None, tie_rtol: float = 0.0):
                 raise ValueError(f"step {m}: pivot {i} has residual {d[i]!r}, the largest is {top!r}")
         else:
             i = int(np.argmax(d))
-        if not d[i] > 0.0:
+        if not d[i] > floor:
             break
         c = np.asarray(column(i), dtype=np.float64).reshape(N)
         l = (c - L[:, :m] @ L[i, :m]) / np.sqrt(d[i])

@@ -29,6 +29,7 @@ SOURCES = [
     "fgk_solve.cu",
     "fgk_noalloc.cu",
     "fgk_batch.cu",
+    "fgk_precond.cu",
 ]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,

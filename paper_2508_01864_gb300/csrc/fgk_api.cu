@@ -408,35 +408,52 @@ int fgk_scan_timing(int enable, double *total_ms, int64_t *launches) {
     return FGK_OK;
 }
 
-int fgk_cg_solve(fgk_handle h, const double *y, int nrhs, double sigma2, const double *H, int L, double tol,
-                 int maxit, int mode, double *alpha, double *beta, fgk_cg_info *info, fgk_stream_t stream) {
+static int cg_entry(const char *name, fgk_handle h, fgk_precond pc, const double *y, int nrhs, double sigma2,
+                    const double *H, int L, double tol, int maxit, int mode, double *alpha, double *beta,
+                    fgk_cg_info *info, fgk_stream_t stream) {
     clear_error();
     if (!h || !y || !alpha) {
-        set_error("fgk_cg_solve: h, y and alpha must not be NULL");
+        set_error("%s: h, y and alpha must not be NULL", name);
         return FGK_ERR_INVALID;
     }
     if (nrhs < 1 || !(sigma2 >= 0.0) || !std::isfinite(sigma2) || !(tol > 0.0) || maxit < 1) {
-        set_error("fgk_cg_solve: need nrhs >= 1, finite sigma2 >= 0, tol > 0, maxit >= 1");
+        set_error("%s: need nrhs >= 1, finite sigma2 >= 0, tol > 0, maxit >= 1", name);
         return FGK_ERR_INVALID;
     }
     if (mode != FGK_F64 && mode != FGK_MIXED) {
-        set_error("fgk_cg_solve: mode must be FGK_F64 or FGK_MIXED");
+        set_error("%s: mode must be FGK_F64 or FGK_MIXED", name);
         return FGK_ERR_INVALID;
     }
     if (H == nullptr && L != 0 && L != -1) {
-        set_error("fgk_cg_solve: without H, L must be 0 (no fixed effects) or -1 (default [1, x])");
+        set_error("%s: without H, L must be 0 (no fixed effects) or -1 (default [1, x])", name);
         return FGK_ERR_INVALID;
     }
     if (H != nullptr && (L < 1 || L > kMaxH)) {
-        set_error("fgk_cg_solve: L = %d is outside [1, %d]", L, kMaxH);
+        set_error("%s: L = %d is outside [1, %d]", name, L, kMaxH);
         return FGK_ERR_INVALID;
     }
     Plan *p = h;
+    Precond *pcp = pc_of(pc);
+    if (pcp && (pc_plan(pcp) != p || pc_sigma2(pcp) != sigma2)) {
+        set_error("%s: the preconditioner was built for another plan or another sigma2", name);
+        return FGK_ERR_INVALID;
+    }
     if (L == -1) {
         L = 1 + p->d;
     }
     p->stream = (cudaStream_t)stream;
-    return cg_solve(p, y, nrhs, sigma2, H, L, tol, maxit, mode, alpha, beta, info, (cudaStream_t)stream);
+    return cg_solve(p, pcp, y, nrhs, sigma2, H, L, tol, maxit, mode, alpha, beta, info, (cudaStream_t)stream);
+}
+
+int fgk_cg_solve(fgk_handle h, const double *y, int nrhs, double sigma2, const double *H, int L, double tol,
+                 int maxit, int mode, double *alpha, double *beta, fgk_cg_info *info, fgk_stream_t stream) {
+    return cg_entry("fgk_cg_solve", h, nullptr, y, nrhs, sigma2, H, L, tol, maxit, mode, alpha, beta, info, stream);
+}
+
+int fgk_cg_solve_pc(fgk_handle h, fgk_precond pc, const double *y, int nrhs, double sigma2, const double *H, int L,
+                    double tol, int maxit, int mode, double *alpha, double *beta, fgk_cg_info *info,
+                    fgk_stream_t stream) {
+    return cg_entry("fgk_cg_solve_pc", h, pc, y, nrhs, sigma2, H, L, tol, maxit, mode, alpha, beta, info, stream);
 }
 
 int fgk_destroy(fgk_handle h) {

@@ -836,22 +836,37 @@ int fgk_batch_cg_solve(fgk_batch b, const double *const *y, const double *sigma2
                 hact[c] = snap_act[c];
             }
             if ((rc = residuals(todo))) break;
-            if (hbreak) {
-                k_brestart<<<b->nchunk, 256, 0, s>>>(Pv, Rv, b->chunks, nrhs, st.bd);
-                FGK_LAUNCH_CHECK();
-                k_to_f32_diag<<<b->nchunk, 256, 0, s>>>(Pv, P32, W32, b->probs, b->chunks, nrhs);
-                FGK_LAUNCH_CHECK();
-                FGK_CUDA(cudaMemsetAsync(st.bd, 0, (size_t)C * 4, s));
-                FGK_CUDA(cudaMemsetAsync(st.breakdown, 0, 16, s));
-            }
+            // restart p = r on the columns whose direction no longer fits the
+            // replaced residual (as fgk_cg_solve): an FP32 breakdown, a column
+            // that had stopped, or a true residual above twice the recursive one
+            std::vector<int> rs(C, 0);
+            bool any_rs = false;
             for (int i : todo) {
                 last_repl[i] = iters_total;
                 bool drift = false;
                 for (int j = 0; j < nrhs; ++j) {
                     const int c = i * nrhs + j;
-                    if (!confirmed[c] && rnorm[c] > 2.0 * std::sqrt(snap_rho[c])) drift = true;
+                    const bool dj = !confirmed[c] && rnorm[c] > 2.0 * std::sqrt(snap_rho[c]);
+                    drift = drift || dj;
+                    rs[c] = !confirmed[c] && ((hbreak && hbd[c]) || !snap_act[c] || dj) &&
+                            !(rnorm[c] <= tol * bnorm[c]);
+                    any_rs = any_rs || rs[c];
                 }
                 gap[i] = drift ? 0 : min_gap[i];
+            }
+            if (any_rs) {
+                FGK_CUDA(cudaMemcpyAsync(st.bd, rs.data(), (size_t)C * 4, cudaMemcpyHostToDevice, s));
+                k_brestart<<<b->nchunk, 256, 0, s>>>(Pv, Rv, b->chunks, nrhs, st.bd);
+                FGK_LAUNCH_CHECK();
+                k_to_f32_diag<<<b->nchunk, 256, 0, s>>>(Pv, P32, W32, b->probs, b->chunks, nrhs);
+                FGK_LAUNCH_CHECK();
+            }
+            if (any_rs || hbreak) {
+                FGK_CUDA(cudaMemsetAsync(st.bd, 0, (size_t)C * 4, s));
+                FGK_CUDA(cudaMemsetAsync(st.breakdown, 0, 16, s));
+                FGK_CUDA(cudaStreamSynchronize(s));  // rs is a host vector
+            }
+            for (int i : todo) {
                 for (int j = 0; j < nrhs; ++j) {
                     const int c = i * nrhs + j;
                     if (!confirmed[c] && rnorm[c] <= tol * bnorm[c]) confirmed[c] = 1;

@@ -155,9 +155,26 @@ int ensure_ws(Plan *p, size_t bytes, cudaStream_t s);
 int to_q_order(const Plan *p, const void *src, void *dst, int nrhs, int elem_bytes, cudaStream_t s);
 int from_q_order(const Plan *p, const void *src, void *dst, int nrhs, int elem_bytes, cudaStream_t s);
 
-// CG / refinement / GLS (fgk_solve.cu)
-int cg_solve(Plan *p, const double *y, int nrhs, double sigma2, const double *H, int L, double tol, int maxit,
-             int mode, double *alpha, double *beta, fgk_cg_info *info, cudaStream_t s);
+// Pivoted-Cholesky preconditioner (fgk_precond.cu).  pc_apply: Z = P^{-1} R
+// for N x ncols FP64 row-major vectors in q order (ncols <= kPcMaxCols); when
+// rz_partial is not NULL it also writes per-CTA partial sums of R .* Z per
+// column, pc_partial_blocks(pc) rows of them (partial[b * ncols + j]).
+// No host synchronisation and no allocation (after pc_reserve for ncols):
+// safe inside stream capture.
+struct Precond;
+constexpr int kPcMaxCols = 64;
+constexpr int kRedThreadsPc = 256;
+int pc_apply(const Precond *pc, const double *R, int ncols, double *Z, double *rz_partial, cudaStream_t s);
+int pc_partial_blocks(const Precond *pc);           // CTAs (rows of partials) pc_apply's rz_partial has
+int pc_check(const Precond *pc, cudaStream_t s);    // reads and clears the apply's error word (syncs)
+int pc_reserve(Precond *pc, int ncols, cudaStream_t s);  // apply scratch for ncols (allocates; not in capture)
+Precond *pc_of(fgk_precond h);  // the handle's preconditioner (NULL for NULL)
+double pc_sigma2(const Precond *pc);
+const Plan *pc_plan(const Precond *pc);
+
+// CG / refinement / GLS (fgk_solve.cu); pc may be NULL (s_P = I)
+int cg_solve(Plan *p, Precond *pc, const double *y, int nrhs, double sigma2, const double *H, int L,
+             double tol, int maxit, int mode, double *alpha, double *beta, fgk_cg_info *info, cudaStream_t s);
 size_t solve_ws_bytes(const Plan *p, int ncols);
 
 inline int ceil_log2_i64(int64_t n) {

@@ -1,0 +1,1032 @@
+// The preconditioner of the CG solve (App. A.3): P = L L^T + sigma^2 I with L
+// the rank-k pivoted Cholesky factor of K (Harbrecht et al., cited there),
+// applied by the Woodbury formula, with log det P by Sylvester's theorem.
+//
+// Build (once per plan and sigma^2).  The residual diagonal starts at
+// K_ii = s2.  Step m takes as pivot the largest residual diagonal entry (ties:
+// the smallest original point index), forms the column of K at the pivot
+// from the scaled coordinates, subtracts what columns 0..m-1 already explain
+// (sum_t L_t L_t[pivot]), divides by the square root of the pivot's residual
+// and lowers the residual diagonal by the square of the new column.  One
+// launch per step: each CTA first reduces the previous step's per-CTA
+// maxima (so every CTA agrees on the pivot without a host round trip), then
+// updates its rows and publishes its own maximum.  A step whose largest
+// residual is at most 1e-12 s2 (numerically exhausted; the paper leaves the
+// case open) records the realised rank and changes nothing.
+// L is FP64 during the build (columns of N entries, q order); the apply uses
+// an FP32 copy, and the Woodbury matrix I + L^T L / sigma^2 is formed from
+// exactly those FP32 values (their products are exact in FP64), so P is the
+// SPD matrix L32 L32^T + sigma^2 I that the apply inverts.
+//
+// Apply (Z = P^{-1} R, every CG iteration, inside the captured graph):
+//   t = L^T R          k_pc_ltr (persistent CTAs, per-CTA partials) + k_pc_tsum
+//   c = C^{-1} t / s^4  k_pc_cmul (C^{-1} formed at build from the Cholesky
+//                       factor of C: a matrix-vector product spread over
+//                       warps instead of two latency-bound triangular solves)
+//   Z = R / s^2 - L c   k_pc_apply (+ per-CTA partial sums of R .* Z)
+// Both passes over L stream it through shared memory with TMA tensor copies.
+// which is the Woodbury form P^{-1} R = R/s^2 - L (I + L^T L/s^2)^{-1} L^T R / s^4.
+// The two passes over L are FP32 arithmetic: GB300 issues FP64 at a small
+// fraction of its FP32 rate, and one FP64 multiply-add per element of L made
+// them FP64-bound (about 30x slower than its memory traffic).  FP64 accuracy
+// is kept with error-free transformations: FP64 operands split into float
+// pairs (hi + lo), products of floats made exact by a fused multiply-add
+// (two-product), and running sums carried as float pairs by Knuth's
+// two-sum; each block's pair is added in FP64.
+#include <cuda.h>  // CUtensorMap (the encoder is fetched through the runtime's driver entry point)
+
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+#include <vector>
+
+#include "fgk_internal.cuh"
+
+namespace fgk {
+
+namespace {
+
+constexpr int kPcThreads = 256;
+constexpr int kPcMaxRank = 1024;
+constexpr int kGramTile = 16;
+constexpr double kExhausted = 1e-12;  // stop once the residual diagonal is at most this x s2
+
+struct PivPart {
+    double val;
+    int64_t orig;
+    int64_t q;
+};
+
+__device__ __forceinline__ bool piv_better(const PivPart &a, const PivPart &b) {
+    return a.val > b.val || (a.val == b.val && a.orig < b.orig);
+}
+
+__device__ __forceinline__ PivPart piv_none() { return PivPart{-INFINITY, INT64_MAX, -1}; }
+
+// block-wide best of one PivPart per thread; result valid in every thread
+__device__ __forceinline__ PivPart block_best(PivPart v) {
+    __shared__ PivPart s_w[kPcThreads / 32];
+    __shared__ PivPart s_out;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        PivPart u;
+        u.val = __shfl_xor_sync(0xffffffffu, v.val, o);
+        u.orig = __shfl_xor_sync(0xffffffffu, v.orig, o);
+        u.q = __shfl_xor_sync(0xffffffffu, v.q, o);
+        if (piv_better(u, v)) v = u;
+    }
+    if (lane == 0) s_w[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        PivPart b = s_w[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            if (piv_better(s_w[w], b)) b = s_w[w];
+        s_out = b;
+    }
+    __syncthreads();
+    const PivPart r = s_out;
+    __syncthreads();
+    return r;
+}
+
+// unit-lengthscale Matern kernel k(r) = sum_p c_p r^p e^{-r}
+__device__ __forceinline__ double matern(int two_nu, double r) {
+    const double e = exp(-r);
+    if (two_nu == 1) return e;
+    if (two_nu == 3) return (1.0 + r) * e;
+    return (1.0 + r + r * r * (1.0 / 3.0)) * e;
+}
+
+struct KernArgs {
+    const double *x0, *x1, *x2;  // scaled coordinates in q order
+    int d, two_nu, kind;
+    double s2;
+};
+
+__device__ __forceinline__ double kern_q(const KernArgs &k, int64_t i, const double *xp) {
+    const double u0 = fabs(k.x0[i] - xp[0]);
+    if (k.d == 1) return k.s2 * matern(k.two_nu, u0);
+    const double u1 = fabs(k.x1[i] - xp[1]);
+    if (k.kind == FGK_L1) {
+        double r = u0 + u1;
+        if (k.d == 3) r += fabs(k.x2[i] - xp[2]);
+        return k.s2 * matern(k.two_nu, r);
+    }
+    double v = matern(k.two_nu, u0) * matern(k.two_nu, u1);
+    if (k.d == 3) v *= matern(k.two_nu, fabs(k.x2[i] - xp[2]));
+    return k.s2 * v;
+}
+
+// float-pair arithmetic (value = hi + lo): Knuth's two-sum and the
+// fused-multiply-add two-product, both exact
+struct F2 {
+    float hi, lo;
+};
+
+// (the _rn intrinsics are never contracted into fused multiply-adds, which
+// would break the exactness these steps rely on)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// acc += l * (xh + xl), l a float, x given as a float pair
+__device__ __forceinline__ void f2_fma(F2 &acc, float l, float xh, float xl) {
+    const float p = __fmul_rn(l, xh);
+    const float pe = fmaf(l, xh, -p);  // l * xh = p + pe exactly
+    float sum, err;
+    two_sum(acc.hi, p, sum, err);
+    acc.hi = sum;
+    acc.lo += err + fmaf(l, xl, pe);
+}
+
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
+    F2 r;
+    float e;
+    two_sum(a.hi, b.hi, r.hi, e);
+    r.lo = e + a.lo + b.lo;
+    return r;
+}
+
+__device__ __forceinline__ void split_f2(double x, float &hi, float &lo) {
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
+}
+
+__global__ void k_pc_init(int64_t N, double s2, const int32_t *__restrict__ perm0, double *__restrict__ dres,
+                          PivPart *__restrict__ part) {
+    PivPart best = piv_none();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        dres[i] = s2;
+        const PivPart c{s2, (int64_t)perm0[i], i};
+        if (piv_better(c, best)) best = c;
+    }
+    best = block_best(best);
+    if (threadIdx.x == 0) part[blockIdx.x] = best;
+}
+
+// step m of the pivoted Cholesky (see the file comment)
+__global__ void k_pc_step(int m, int64_t N, int64_t ldN, KernArgs ka, const int32_t *__restrict__ perm0,
+                          const PivPart *__restrict__ prev, int nprev, PivPart *__restrict__ next,
+                          double *__restrict__ L, double *__restrict__ dres, int32_t *__restrict__ piv_q,
+                          int *__restrict__ rank, double floor) {
+    __shared__ double s_lp[kPcMaxRank];
+    __shared__ double s_xp[3];
+    PivPart best = piv_none();
+    for (int b = threadIdx.x; b < nprev; b += blockDim.x)
+        if (piv_better(prev[b], best)) best = prev[b];
+    best = block_best(best);
+    if (!(best.val > floor)) {  // exhausted: rank m, nothing changes from here on
+        if (threadIdx.x == 0) {
+            if (blockIdx.x == 0) atomicMin(rank, m);
+            next[blockIdx.x] = best;
+        }
+        return;
+    }
+    const int64_t piv = best.q;
+    if (blockIdx.x == 0 && threadIdx.x == 0) piv_q[m] = (int32_t)piv;
+    for (int t = threadIdx.x; t < m; t += blockDim.x) s_lp[t] = L[(size_t)t * ldN + piv];
+    if (threadIdx.x == 0) {
+        s_xp[0] = ka.x0[piv];
+        s_xp[1] = ka.d > 1 ? ka.x1[piv] : 0.0;
+        s_xp[2] = ka.d > 2 ? ka.x2[piv] : 0.0;
+    }
+    __syncthreads();
+    const double sq = sqrt(best.val);
+    PivPart mine = piv_none();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const double kv = kern_q(ka, i, s_xp);
+        double dot = 0.0;
+        for (int t = 0; t < m; ++t) dot = fma(L[(size_t)t * ldN + i], s_lp[t], dot);
+        const double l = (kv - dot) / sq;
+        L[(size_t)m * ldN + i] = l;
+        const double dn = dres[i] - l * l;
+        dres[i] = dn;
+        const PivPart c{dn, (int64_t)perm0[i], i};
+        if (piv_better(c, mine)) mine = c;
+    }
+    mine = block_best(mine);
+    if (threadIdx.x == 0) next[blockIdx.x] = mine;
+}
+
+__global__ void k_pc_to_f32(const double *__restrict__ a, int64_t n, float *__restrict__ b) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        b[t] = (float)a[t];
+}
+
+// partial Gram blocks: Gp[z][a][b] = sum over rows of chunk z of L32[a][i] L32[b][i]
+// (products of FP32 values are exact in FP64); tiles (ta <= tb) of 16 x 16
+__global__ void k_pc_gram(const float *__restrict__ L, int64_t ldN, int64_t N, int r, int64_t rows_per_z,
+                          double *__restrict__ Gp) {
+    __shared__ float sa[kGramTile][kPcThreads + 1];
+    __shared__ float sb[kGramTile][kPcThreads + 1];
+    const int ta = blockIdx.x, tb = blockIdx.y;
+    if (ta > tb) return;
+    const int z = blockIdx.z;
+    const int a = ta * kGramTile + (threadIdx.x / kGramTile), b = tb * kGramTile + (threadIdx.x % kGramTile);
+    const int64_t i0 = (int64_t)z * rows_per_z, i1 = min(N, i0 + rows_per_z);
+    double acc = 0.0;
+    for (int64_t c0 = i0; c0 < i1; c0 += kPcThreads) {
+        const int64_t i = c0 + threadIdx.x;
+#pragma unroll
+        for (int u = 0; u < kGramTile; ++u) {
+            const int ca = ta * kGramTile + u, cb = tb * kGramTile + u;
+            sa[u][threadIdx.x] = (i < i1 && ca < r) ? L[(size_t)ca * ldN + i] : 0.f;
+            sb[u][threadIdx.x] = (i < i1 && cb < r) ? L[(size_t)cb * ldN + i] : 0.f;
+        }
+        __syncthreads();
+        const int la = threadIdx.x / kGramTile, lb = threadIdx.x % kGramTile;
+        const int n = (int)(i1 - c0 < kPcThreads ? i1 - c0 : kPcThreads);
+        for (int k = 0; k < n; ++k) acc = fma((double)sa[la][k], (double)sb[lb][k], acc);
+        __syncthreads();
+    }
+    if (a < r && b < r) Gp[((size_t)z * r + a) * r + b] = acc;
+}
+
+// C = I + G / sigma2 (G summed over the z partials, mirrored), its lower
+// Cholesky factor in place (row-major r x r), and log det P by Sylvester:
+// N log sigma2 + 2 sum_j log C_jj.  err = 1 if C is not positive definite.
+__global__ void k_pc_chol(const double *__restrict__ Gp, int nz, int r, double sigma2, int64_t N,
+                          double *__restrict__ C, double *__restrict__ logdet, int *__restrict__ err) {
+    for (int t = threadIdx.x; t < r * r; t += blockDim.x) {
+        const int a = t / r, b = t % r;
+        const int lo = min(a, b), hi = max(a, b);
+        double g = 0.0;
+        for (int z = 0; z < nz; ++z) g += Gp[((size_t)z * r + lo) * r + hi];
+        C[t] = (a == b ? 1.0 : 0.0) + g / sigma2;
+    }
+    __syncthreads();
+    __shared__ int s_bad;
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
+    for (int j = 0; j < r; ++j) {
+        if (threadIdx.x == 0) {
+            const double v = C[j * r + j];
+            if (!(v > 0.0)) s_bad = 1;
+            C[j * r + j] = v > 0.0 ? sqrt(v) : 1.0;
+        }
+        __syncthreads();
+        const double djj = C[j * r + j];
+        for (int i = j + 1 + threadIdx.x; i < r; i += blockDim.x) C[i * r + j] /= djj;
+        __syncthreads();
+        const int n = r - j - 1;
+        for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+            const int i = j + 1 + t / n, l = j + 1 + t % n;
+            if (l <= i) C[i * r + l] -= C[i * r + j] * C[l * r + j];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double ld = (double)N * log(sigma2);
+        for (int j = 0; j < r; ++j) ld += 2.0 * log(C[j * r + j]);
+        *logdet = ld;
+        *err = s_bad;
+    }
+}
+
+// C^{-1} = F^{-T} F^{-1} from the lower Cholesky factor F (row-major r x r):
+// first F^{-1} column by column (thread c: forward substitution for e_c),
+// then the symmetric product.  Finv and Cinv: r x r row-major.
+__global__ void k_pc_inverse(const double *__restrict__ F, int r, double *__restrict__ Finv,
+                             double *__restrict__ Cinv) {
+    for (int c = threadIdx.x; c < r; c += blockDim.x) {
+        for (int i = 0; i < c; ++i) Finv[i * r + c] = 0.0;
+        for (int i = c; i < r; ++i) {
+            double sacc = i == c ? 1.0 : 0.0;
+            for (int k = c; k < i; ++k) sacc -= F[i * r + k] * Finv[k * r + c];
+            Finv[i * r + c] = sacc / F[i * r + i];
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < r * r; t += blockDim.x) {
+        const int a = t / r, b = t % r;
+        double sacc = 0.0;
+        for (int k = max(a, b); k < r; ++k) sacc += Finv[k * r + a] * Finv[k * r + b];
+        Cinv[t] = sacc;
+    }
+}
+
+__global__ void k_sum(const double *__restrict__ a, int64_t n, double *__restrict__ out) {
+    __shared__ double red[1024];
+    double acc = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) acc += a[i];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
+}
+
+// ---- shared-memory staging of L by TMA
+// The rows (q order) are cut into tiles of kTR; a persistent CTA takes the
+// tiles blockIdx.x, blockIdx.x + gridDim.x, ... and streams each tile's L in
+// chunks of kMC rank indices: one 2-D tensor copy (cp.async.bulk.tensor,
+// box kTR x kMC floats, 32 KB) per chunk, issued by thread 0 and completing
+// on an mbarrier.  Two chunk buffers alternate, so the next chunk (of this
+// tile or the next) is in flight while the current one is used.  Rows and
+// rank indices outside L are filled with zeros by the copy.  Every wait is
+// bounded; on expiry the CTA records DEV_TIMEOUT in the error word and
+// returns.
+constexpr int kTR = 256;      // rows per tile (= threads per CTA)
+constexpr int kMC = 32;       // rank indices per chunk
+constexpr int kColsPass = 8;  // right-hand sides per pass over the tiles
+constexpr int kSpinLimit = 1 << 22;
+constexpr int kApplyCtas = 2 * 152;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    for (int it = 0; it < kSpinLimit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// The chunk sequence of one CTA within a pass: chunk c is rank chunk
+// c % nchunk of the CTA's tile number c / nchunk.  The buffers and barrier
+// phases follow the CTA's running chunk count g (passes included).
+struct ChunkStream {
+    float *buf;     // 2 x kMC x kTR floats
+    uint64_t *bar;  // 2 mbarriers
+    const CUtensorMap *map;
+    int nchunk, ntile_cta;
+
+    __device__ __forceinline__ int64_t tile_row0(int c) const {
+        return ((int64_t)blockIdx.x + (int64_t)(c / nchunk) * gridDim.x) * kTR;
+    }
+    __device__ __forceinline__ void issue(int g, int c) const {  // thread 0 only
+        const int b = g & 1;
+        mbar_expect_tx(bar + b, (uint32_t)(kMC * kTR * 4));
+        tma_load_2d(buf + (size_t)b * kMC * kTR, map, (int)tile_row0(c), (c % nchunk) * kMC, bar + b);
+    }
+    // every thread waits for chunk c (the use count of its buffer gives the
+    // parity); false (CTA-uniform) if a wait expired
+    __device__ __forceinline__ bool wait(int c, int *s_bad, int *err) const {
+        const uint32_t parity = (uint32_t)((c >> 1) & 1);
+        const bool ok = mbar_wait_bounded(bar + (c & 1), parity);
+        if (!ok) atomicOr(s_bad, 1);
+        __syncthreads();
+        if (*s_bad) {
+            if (threadIdx.x == 0) {
+                atomicOr(err, DEV_TIMEOUT);
+                mbar_wait_bounded(bar + (c & 1), parity);  // let a late copy land before the CTA exits
+            }
+            return false;
+        }
+        return true;
+    }
+    __device__ __forceinline__ const float *chunk(int c) const { return buf + (size_t)(c & 1) * kMC * kTR; }
+};
+
+__device__ __forceinline__ int tiles_of_cta(int64_t N) {
+    const int64_t ntile = (N + kTR - 1) / kTR;
+    return blockIdx.x < ntile ? (int)((ntile - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+}
+
+// t_part[b][m][j] = sum over the rows of CTA b's tiles of L[m][i] R[i][j].
+// R's rows of the current tile sit in shared memory as float pairs; each
+// warp owns the rank indices mm = warp, warp + 8, ... of every chunk, sums
+// over the tile's rows (lanes stride the rows) in float pairs, reduces across
+// the warp with shuffles and adds the result into s_t[m][u] (FP64).
+// NC: columns per pass (1, 2, 4 or 8); a pass with fewer real columns pads
+// with zero columns.
+template <int NC>
+__global__ void __launch_bounds__(kTR) k_pc_ltr(const __grid_constant__ CUtensorMap map, int r,
+                                                 const double *__restrict__ R, int64_t N, int ncols,
+                                                 double *__restrict__ t_part, int *__restrict__ err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float *buf = reinterpret_cast<float *>(smem_raw);
+    F2 *Rs = reinterpret_cast<F2 *>(buf + 2 * kMC * kTR);  // kTR x NC
+    F2 *s_t = Rs + kTR * NC;                               // r x NC running sums (float pairs)
+    uint64_t *bar = reinterpret_cast<uint64_t *>(s_t + (size_t)r * NC);
+    __shared__ int s_bad;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) {
+        mbar_init(bar);
+        mbar_init(bar + 1);
+        mbar_fence_init();
+        s_bad = 0;
+    }
+    const int nchunk = (r + kMC - 1) / kMC;
+    const int ntile = tiles_of_cta(N);
+    const ChunkStream cs{buf, bar, &map, nchunk, ntile};
+    const int total = nchunk * ntile;
+    int c_base = 0;  // chunks streamed by earlier passes (barrier phases keep counting)
+    for (int j0 = 0; j0 < ncols; j0 += NC) {
+        const int nc = min(NC, ncols - j0);
+        for (int t = threadIdx.x; t < r * NC; t += blockDim.x) s_t[t] = F2{0.f, 0.f};
+        __syncthreads();
+        if (total > 0 && threadIdx.x == 0) cs.issue(c_base, 0);
+        for (int c = 0; c < total; ++c) {
+            const int cc = c_base + c;
+            if (threadIdx.x == 0 && c + 1 < total) cs.issue(cc + 1, c + 1);
+            if (c % nchunk == 0) {  // a new tile: its rows of R
+                const int64_t i = cs.tile_row0(c) + threadIdx.x;
+#pragma unroll
+                for (int u = 0; u < NC; ++u) {
+                    float hi = 0.f, lo = 0.f;
+                    if (u < nc && i < N) split_f2(R[i * ncols + j0 + u], hi, lo);
+                    Rs[threadIdx.x * NC + u] = F2{hi, lo};
+                }
+            }
+            if (!cs.wait(cc, &s_bad, err)) return;
+            const float *Lc = cs.chunk(cc);
+            const int m0 = (c % nchunk) * kMC, mc = min(kMC, r - m0);
+            for (int mm = warp; mm < mc; mm += nw) {
+                F2 acc[NC];
+#pragma unroll
+                for (int u = 0; u < NC; ++u) acc[u] = F2{0.f, 0.f};
+#pragma unroll
+                for (int row = lane; row < kTR; row += 32) {
+                    const float l = Lc[mm * kTR + row];
+#pragma unroll
+                    for (int u = 0; u < NC; ++u) f2_fma(acc[u], l, Rs[row * NC + u].hi, Rs[row * NC + u].lo);
+                }
+#pragma unroll
+                for (int u = 0; u < NC; ++u) {
+                    F2 a = acc[u];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        F2 other;
+                        other.hi = __shfl_xor_sync(0xffffffffu, a.hi, o);
+                        other.lo = __shfl_xor_sync(0xffffffffu, a.lo, o);
+                        a = f2_add(a, other);
+                    }
+                    if (lane == 0) s_t[(m0 + mm) * NC + u] = f2_add(s_t[(m0 + mm) * NC + u], a);
+                }
+            }
+            __syncthreads();  // buffer reuse two chunks later; Rs rewritten at the next tile
+        }
+        c_base += total;
+        for (int t = threadIdx.x; t < r * nc; t += blockDim.x) {
+            const int m = t / nc, u = t % nc;
+            const F2 v = s_t[m * NC + u];
+            t_part[((size_t)blockIdx.x * r + m) * ncols + j0 + u] = (double)v.hi + (double)v.lo;
+        }
+        __syncthreads();
+    }
+}
+
+// t[m][j] = sum over the gridDim partials (one warp per entry)
+__global__ void k_pc_tsum(const double *__restrict__ t_part, int nb, int r, int ncols, double *__restrict__ t) {
+    const int lane = threadIdx.x & 31;
+    const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (e >= (int64_t)r * ncols) return;
+    double acc = 0.0;
+    for (int b = lane; b < nb; b += 32) acc += t_part[(size_t)b * r * ncols + e];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) t[e] = acc;
+}
+
+// c[a][j] = sum_b Cinv[a][b] t[b][j] / sigma2^2 (one warp per entry)
+__global__ void k_pc_cmul(const double *__restrict__ t, int r, int ncols, const double *__restrict__ Cinv,
+                          double sigma2, double *__restrict__ c) {
+    const int lane = threadIdx.x & 31;
+    const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (e >= (int64_t)r * ncols) return;
+    const int a = (int)(e / ncols), j = (int)(e % ncols);
+    double acc = 0.0;
+    for (int b = lane; b < r; b += 32) acc = fma(Cinv[(size_t)a * r + b], t[(size_t)b * ncols + j], acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) c[e] = acc / (sigma2 * sigma2);
+}
+
+// Z = R / sigma2 - L c (thread t: row t of the current tile) and per-CTA
+// partial sums of R .* Z per column (rz_partial[b * ncols + j], gridDim rows).
+// c is split into float pairs in shared memory per pass of up to kColsPass
+// columns; L c is summed in float pairs.
+template <int NC>
+__global__ void __launch_bounds__(kTR) k_pc_apply(const __grid_constant__ CUtensorMap map, int r,
+                                                   const double *__restrict__ R, int64_t N, int ncols,
+                                                   const double *__restrict__ c, double sigma2,
+                                                   double *__restrict__ Z, double *__restrict__ rz_partial,
+                                                   int *__restrict__ err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float *buf = reinterpret_cast<float *>(smem_raw);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(buf + 2 * kMC * kTR);
+    F2 *cs2 = reinterpret_cast<F2 *>(bar + 2);  // r x NC
+    __shared__ int s_bad;
+    __shared__ double red[kTR / 32][NC];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        mbar_init(bar);
+        mbar_init(bar + 1);
+        mbar_fence_init();
+        s_bad = 0;
+    }
+    const int nchunk = (r + kMC - 1) / kMC;
+    const int ntile = tiles_of_cta(N);
+    const ChunkStream cs{buf, bar, &map, nchunk, ntile};
+    const int total = nchunk * ntile;
+    const double inv = 1.0 / sigma2;
+    int c_base = 0;
+    for (int j0 = 0; j0 < ncols; j0 += NC) {
+        const int nc = min(NC, ncols - j0);
+        for (int t = threadIdx.x; t < r * NC; t += blockDim.x) {
+            const int m = t / NC, u = t % NC;
+            float hi = 0.f, lo = 0.f;
+            if (u < nc) split_f2(c[(size_t)m * ncols + j0 + u], hi, lo);
+            cs2[t] = F2{hi, lo};
+        }
+        __syncthreads();
+        double rz[NC];
+#pragma unroll
+        for (int u = 0; u < NC; ++u) rz[u] = 0.0;
+        // rank 0: no chunks, each tile is R / sigma2
+        for (int tt = 0; tt < (nchunk > 0 ? 0 : ntile); ++tt) {
+            const int64_t i = ((int64_t)blockIdx.x + (int64_t)tt * gridDim.x) * kTR + threadIdx.x;
+#pragma unroll
+            for (int u = 0; u < NC; ++u)
+                if (u < nc && i < N) {
+                    const int64_t t = i * ncols + j0 + u;
+                    const double rv = R[t], z = rv * inv;
+                    Z[t] = z;
+                    rz[u] += rv * z;
+                }
+        }
+        F2 acc[NC];
+#pragma unroll
+        for (int u = 0; u < NC; ++u) acc[u] = F2{0.f, 0.f};
+        if (total > 0 && threadIdx.x == 0) cs.issue(c_base, 0);
+        for (int c = 0; c < total; ++c) {
+            const int cc = c_base + c;
+            if (threadIdx.x == 0 && c + 1 < total) cs.issue(cc + 1, c + 1);
+            if (!cs.wait(cc, &s_bad, err)) return;
+            const float *Lc = cs.chunk(cc);
+            const int m0 = (c % nchunk) * kMC, mc = min(kMC, r - m0);
+            if (mc == kMC) {
+#pragma unroll 8
+                for (int mm = 0; mm < kMC; ++mm) {
+                    const float l = Lc[mm * kTR + threadIdx.x];
+                    const F2 *cm = cs2 + (m0 + mm) * NC;
+#pragma unroll
+                    for (int u = 0; u < NC; ++u) f2_fma(acc[u], l, cm[u].hi, cm[u].lo);
+                }
+            } else {
+                for (int mm = 0; mm < mc; ++mm) {
+                    const float l = Lc[mm * kTR + threadIdx.x];
+                    const F2 *cm = cs2 + (m0 + mm) * NC;
+#pragma unroll
+                    for (int u = 0; u < NC; ++u) f2_fma(acc[u], l, cm[u].hi, cm[u].lo);
+                }
+            }
+            __syncthreads();
+            if (c % nchunk == nchunk - 1) {  // the tile is complete: its rows of Z
+                const int64_t i = cs.tile_row0(c) + threadIdx.x;
+#pragma unroll
+                for (int u = 0; u < NC; ++u) {
+                    if (u < nc && i < N) {
+                        const int64_t t = i * ncols + j0 + u;
+                        const double rv = R[t];
+                        const double z = rv * inv - ((double)acc[u].hi + (double)acc[u].lo);
+                        Z[t] = z;
+                        rz[u] += rv * z;
+                    }
+                    acc[u] = F2{0.f, 0.f};
+                }
+            }
+        }
+        c_base += total;
+        if (rz_partial) {
+#pragma unroll
+            for (int u = 0; u < NC; ++u) {
+                double v = rz[u];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) red[warp][u] = v;
+            }
+            __syncthreads();
+            if ((int)threadIdx.x < nc) {
+                double tot = 0.0;
+                for (int w = 0; w < kTR / 32; ++w) tot += red[w][threadIdx.x];
+                rz_partial[(size_t)blockIdx.x * ncols + j0 + threadIdx.x] = tot;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// L in the caller's point order: out[orig * r + m] = L[m][q]
+__global__ void k_pc_factor_out(const double *__restrict__ L, int64_t ldN, int r, int64_t N,
+                                const int32_t *__restrict__ perm0, double *__restrict__ out) {
+    const int64_t n = N * r;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = t / r;
+        const int m = (int)(t % r);
+        out[(int64_t)perm0[q] * r + m] = L[(size_t)m * ldN + q];
+    }
+}
+
+}  // namespace
+
+struct Precond {
+    Plan *plan = nullptr;
+    int k_req = 0, rank = 0;
+    double sigma2 = 0.0, logdet = 0.0, trace = 0.0;
+    int64_t ldN = 0;
+    double *L64 = nullptr, *dres = nullptr, *Cf = nullptr, *Cinv = nullptr, *t_part = nullptr, *cvec = nullptr,
+           *scal = nullptr;
+    float *L32 = nullptr;
+    int32_t *piv_q = nullptr;
+    int *ints = nullptr;  // [0] rank, [1] error flag
+    int nb_ltr = 0, chunk = 0, cap_cols = 0;
+    size_t bytes = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<void *> owned;
+    double *tvec = nullptr;  // t = L^T R, r x cap_cols
+    CUtensorMap tmap;        // L32 as a 2-D tensor (rows x rank), boxes of kTR x kMC
+};
+
+// scratch of the apply for up to ncols columns (grown before any capture)
+int pc_reserve(Precond *pc, int ncols, cudaStream_t s) {
+    if (ncols < 1 || ncols > kPcMaxCols) {
+        set_error("preconditioner: ncols = %d is outside [1, %d]", ncols, kPcMaxCols);
+        return FGK_ERR_INVALID;
+    }
+    if (ncols <= pc->cap_cols) return FGK_OK;
+    const size_t kk = (size_t)std::max(pc->k_req, 1);
+    void *t = dev_alloc((size_t)pc->nb_ltr * kk * ncols * 8, s);
+    void *c = dev_alloc(kk * ncols * 8, s);
+    void *tv = dev_alloc(kk * ncols * 8, s);
+    if (!t || !c || !tv) {
+        if (t) dev_free(t, s);
+        if (c) dev_free(c, s);
+        if (tv) dev_free(tv, s);
+        set_error("preconditioner: scratch allocation failed");
+        return FGK_ERR_OOM;
+    }
+    FGK_CUDA(cudaMemsetAsync(c, 0, kk * ncols * 8, s));
+    for (auto &q : pc->owned)
+        if (q == pc->t_part || q == pc->cvec || q == pc->tvec) {
+            dev_free(q, s);
+            q = nullptr;
+        }
+    pc->owned.erase(std::remove(pc->owned.begin(), pc->owned.end(), nullptr), pc->owned.end());
+    pc->t_part = (double *)t;
+    pc->cvec = (double *)c;
+    pc->tvec = (double *)tv;
+    pc->owned.push_back(t);
+    pc->owned.push_back(c);
+    pc->owned.push_back(tv);
+    pc->bytes += (size_t)pc->nb_ltr * kk * (ncols - pc->cap_cols) * 8 + 2 * kk * (ncols - pc->cap_cols) * 8;
+    pc->cap_cols = ncols;
+    return FGK_OK;
+}
+
+double pc_sigma2(const Precond *pc) { return pc->sigma2; }
+const Plan *pc_plan(const Precond *pc) { return pc->plan; }
+
+static int cols_per_pass(int ncols) { return ncols >= 8 ? 8 : (ncols >= 3 ? (ncols == 3 || ncols == 4 ? 4 : 8) : ncols); }
+static size_t ltr_smem(int r, int nc) {
+    return (size_t)2 * kMC * kTR * 4 + (size_t)kTR * nc * 8 + (size_t)std::max(r, 1) * nc * 8 + 2 * 8;
+}
+static size_t apply_smem(int r, int nc) { return (size_t)2 * kMC * kTR * 4 + 2 * 8 + (size_t)std::max(r, 1) * nc * 8; }
+
+template <int NC>
+static int set_pc_attrs(int k) {
+    FGK_CUDA(cudaFuncSetAttribute(k_pc_ltr<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ltr_smem(k, NC)));
+    FGK_CUDA(cudaFuncSetAttribute(k_pc_apply<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)apply_smem(k, NC)));
+    return FGK_OK;
+}
+
+template <int NC>
+static int launch_pc_ltr(const Precond *pc, int r, const double *R, int ncols, int *err, cudaStream_t s);
+template <int NC>
+static int launch_pc_apply(const Precond *pc, int r, const double *R, int ncols, double *Z, double *rz_partial,
+                           int *err, cudaStream_t s);
+
+int pc_partial_blocks(const Precond *pc) { return pc->nb_ltr; }
+
+int pc_apply(const Precond *pc, const double *R, int ncols, double *Z, double *rz_partial, cudaStream_t s) {
+    if (ncols < 1 || ncols > pc->cap_cols) {
+        set_error("preconditioner apply: ncols = %d is outside [1, %d] (internal)", ncols, pc->cap_cols);
+        return FGK_ERR_INTERNAL;
+    }
+    const Plan *p = pc->plan;
+    const int r = pc->rank, nb = pc->nb_ltr;
+    int *err = pc->ints + 2;
+    const int nc = cols_per_pass(ncols);
+    if (r > 0) {
+        switch (nc) {
+            case 1: FGK_TRY(launch_pc_ltr<1>(pc, r, R, ncols, err, s)); break;
+            case 2: FGK_TRY(launch_pc_ltr<2>(pc, r, R, ncols, err, s)); break;
+            case 4: FGK_TRY(launch_pc_ltr<4>(pc, r, R, ncols, err, s)); break;
+            default: FGK_TRY(launch_pc_ltr<8>(pc, r, R, ncols, err, s)); break;
+        }
+        const unsigned nw_blocks = grid_for((int64_t)r * ncols * 32, 256);
+        k_pc_tsum<<<nw_blocks, 256, 0, s>>>(pc->t_part, nb, r, ncols, pc->tvec);
+        FGK_LAUNCH_CHECK();
+        k_pc_cmul<<<nw_blocks, 256, 0, s>>>(pc->tvec, r, ncols, pc->Cinv, pc->sigma2, pc->cvec);
+        FGK_LAUNCH_CHECK();
+    }
+    switch (nc) {
+        case 1: return launch_pc_apply<1>(pc, r, R, ncols, Z, rz_partial, err, s);
+        case 2: return launch_pc_apply<2>(pc, r, R, ncols, Z, rz_partial, err, s);
+        case 4: return launch_pc_apply<4>(pc, r, R, ncols, Z, rz_partial, err, s);
+        default: return launch_pc_apply<8>(pc, r, R, ncols, Z, rz_partial, err, s);
+    }
+}
+
+// the driver's tensor-map encoder, fetched once through the runtime
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static int encode_tiled(EncodeTiledFn *out) {
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)f;
+    });
+    if (!fn) {
+        set_error("preconditioner: cuTensorMapEncodeTiled is not available");
+        return FGK_ERR_CUDA;
+    }
+    *out = fn;
+    return FGK_OK;
+}
+
+int pc_check(const Precond *pc, cudaStream_t s) {
+    int e = 0;
+    FGK_CUDA(cudaMemcpyAsync(&e, pc->ints + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FGK_CUDA(cudaStreamSynchronize(s));
+    if (e) {
+        FGK_CUDA(cudaMemsetAsync(pc->ints + 2, 0, sizeof(int), s));
+        set_error("preconditioner apply: a bounded wait for a bulk copy expired");
+        return FGK_ERR_TIMEOUT;
+    }
+    return FGK_OK;
+}
+
+template <int NC>
+static int launch_pc_ltr(const Precond *pc, int r, const double *R, int ncols, int *err, cudaStream_t s) {
+    k_pc_ltr<NC><<<pc->nb_ltr, kTR, ltr_smem(r, NC), s>>>(pc->tmap, r, R, pc->plan->N, ncols, pc->t_part, err);
+    FGK_LAUNCH_CHECK();
+    return FGK_OK;
+}
+
+template <int NC>
+static int launch_pc_apply(const Precond *pc, int r, const double *R, int ncols, double *Z, double *rz_partial,
+                           int *err, cudaStream_t s) {
+    k_pc_apply<NC><<<pc->nb_ltr, kTR, apply_smem(r, NC), s>>>(pc->tmap, r, R, pc->plan->N, ncols, pc->cvec,
+                                                              pc->sigma2, Z, rz_partial, err);
+    FGK_LAUNCH_CHECK();
+    return FGK_OK;
+}
+
+static void pc_release(Precond *pc, cudaStream_t s) {
+    for (void *q : pc->owned) dev_free(q, s);
+    pc->owned.clear();
+}
+
+static int pc_build(Precond *pc, cudaStream_t s) {
+    Plan *p = pc->plan;
+    const int64_t N = p->N, ldN = p->ldN;
+    const int k = pc->k_req;
+    auto take = [&](size_t bytes) -> void * {
+        void *q = dev_alloc(bytes > 0 ? bytes : 16, s);
+        if (q) {
+            pc->owned.push_back(q);
+            pc->bytes += bytes;
+        }
+        return q;
+    };
+    const int steps_blocks = (int)std::min<int64_t>(2 * 152, (N + kPcThreads - 1) / kPcThreads);
+    pc->chunk = kTR;
+    pc->nb_ltr = (int)std::min<int64_t>(kApplyCtas, (N + kTR - 1) / kTR);
+    FGK_TRY(set_pc_attrs<1>(k));
+    FGK_TRY(set_pc_attrs<2>(k));
+    FGK_TRY(set_pc_attrs<4>(k));
+    FGK_TRY(set_pc_attrs<8>(k));
+    pc->ldN = ldN;
+    pc->L64 = (double *)take((size_t)k * ldN * 8);
+    pc->L32 = (float *)take((size_t)k * ldN * 4);
+    pc->dres = (double *)take((size_t)N * 8);
+    pc->piv_q = (int32_t *)take((size_t)k * 4);
+    pc->ints = (int *)take(16);
+    PivPart *part0 = (PivPart *)take((size_t)steps_blocks * sizeof(PivPart));
+    PivPart *part1 = (PivPart *)take((size_t)steps_blocks * sizeof(PivPart));
+    pc->Cf = (double *)take((size_t)k * k * 8);
+    pc->Cinv = (double *)take((size_t)k * k * 8);
+    pc->scal = (double *)take(32);
+    for (void *q : pc->owned)
+        if (!q) {
+            set_error("fgk_precond_build: device allocation failed");
+            return FGK_ERR_OOM;
+        }
+    // Gram partials: chunks of rows for parallelism
+    const int ntile = (k + kGramTile - 1) / kGramTile;
+    const int nz = (int)std::max<int64_t>(1, std::min<int64_t>(64, N / 4096));
+    const int64_t rows_per_z = (N + nz - 1) / nz;
+    double *Gp = (double *)take((size_t)nz * k * k * 8);
+    if (!Gp) {
+        set_error("fgk_precond_build: device allocation failed");
+        return FGK_ERR_OOM;
+    }
+
+    FGK_CUDA(cudaMemsetAsync(pc->L64, 0, (size_t)k * ldN * 8, s));
+    FGK_CUDA(cudaMemsetAsync(pc->L32, 0, (size_t)k * ldN * 4, s));
+    const int init[4] = {k, 0, 0, 0};
+    FGK_CUDA(cudaMemcpyAsync(pc->ints, init, sizeof(init), cudaMemcpyHostToDevice, s));
+    KernArgs ka{p->xq[0], p->xq[1], p->xq[2], p->d, p->two_nu, p->kind, p->s2};
+    k_pc_init<<<steps_blocks, kPcThreads, 0, s>>>(N, p->s2, p->perm[0], pc->dres, part0);
+    FGK_LAUNCH_CHECK();
+    PivPart *bufs[2] = {part0, part1};
+    for (int m = 0; m < k; ++m) {
+        k_pc_step<<<steps_blocks, kPcThreads, 0, s>>>(m, N, ldN, ka, p->perm[0], bufs[m & 1], steps_blocks,
+                                                      bufs[(m + 1) & 1], pc->L64, pc->dres, pc->piv_q, pc->ints,
+                                                      kExhausted * p->s2);
+        FGK_LAUNCH_CHECK();
+    }
+    int hints[4];
+    FGK_CUDA(cudaMemcpyAsync(hints, pc->ints, sizeof(hints), cudaMemcpyDeviceToHost, s));
+    FGK_CUDA(cudaStreamSynchronize(s));
+    const int r = std::min(k, hints[0]);
+    pc->rank = r;
+    k_sum<<<1, 1024, 0, s>>>(pc->dres, N, pc->scal);
+    FGK_LAUNCH_CHECK();
+    {  // L32 as a 2-D tensor for the apply's TMA copies (rank rows of ldN floats)
+        EncodeTiledFn enc = nullptr;
+        FGK_TRY(encode_tiled(&enc));
+        const cuuint64_t dims[2] = {(cuuint64_t)ldN, (cuuint64_t)std::max(r, 1)};
+        const cuuint64_t strides[1] = {(cuuint64_t)ldN * 4};
+        const cuuint32_t box[2] = {(cuuint32_t)kTR, (cuuint32_t)kMC};
+        const cuuint32_t estr[2] = {1, 1};
+        const CUresult cr = enc(&pc->tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, pc->L32, dims, strides, box, estr,
+                                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (cr != CUDA_SUCCESS) {
+            set_error("fgk_precond_build: cuTensorMapEncodeTiled failed (%d)", (int)cr);
+            return FGK_ERR_CUDA;
+        }
+    }
+    if (r > 0) {
+        k_pc_to_f32<<<grid_for((int64_t)r * ldN, 256), 256, 0, s>>>(pc->L64, (int64_t)r * ldN, pc->L32);
+        FGK_LAUNCH_CHECK();
+        k_pc_gram<<<dim3(ntile, ntile, nz), kPcThreads, 0, s>>>(pc->L32, ldN, N, r, rows_per_z, Gp);
+        FGK_LAUNCH_CHECK();
+        k_pc_chol<<<1, kPcThreads, 0, s>>>(Gp, nz, r, pc->sigma2, N, pc->Cf, pc->scal + 1, pc->ints + 1);
+        FGK_LAUNCH_CHECK();
+        k_pc_inverse<<<1, kPcThreads, 0, s>>>(pc->Cf, r, Gp, pc->Cinv);  // Gp (nz * k * k >= k * k) as scratch
+        FGK_LAUNCH_CHECK();
+    }
+    double hs[2] = {0.0, 0.0};
+    FGK_CUDA(cudaMemcpyAsync(hs, pc->scal, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    FGK_CUDA(cudaMemcpyAsync(hints, pc->ints, sizeof(hints), cudaMemcpyDeviceToHost, s));
+    FGK_CUDA(cudaStreamSynchronize(s));
+    pc->trace = hs[0];
+    pc->logdet = r > 0 ? hs[1] : (double)N * std::log(pc->sigma2);
+    if (r > 0 && hints[1]) {
+        set_error("fgk_precond_build: I + L^T L / sigma2 is not positive definite (internal)");
+        return FGK_ERR_INTERNAL;
+    }
+    // the Gram partials are only needed for the factorisation
+    dev_free(Gp, s);
+    pc->owned.pop_back();
+    pc->bytes -= (size_t)nz * k * k * 8;
+    return pc_reserve(pc, 1, s);
+}
+
+}  // namespace fgk
+
+using namespace fgk;
+
+struct fgk_precond_s : public fgk::Precond {};
+
+fgk::Precond *fgk::pc_of(fgk_precond h) { return h; }
+
+extern "C" {
+
+int fgk_precond_build(fgk_handle h, int rank, double sigma2, fgk_stream_t stream, fgk_precond *out) {
+    clear_error();
+    if (out) *out = nullptr;
+    if (!h || !out || rank < 0 || rank > kPcMaxRank || !(sigma2 > 0.0) || !std::isfinite(sigma2)) {
+        set_error("fgk_precond_build: need h, out, 0 <= rank <= %d and a finite sigma2 > 0", kPcMaxRank);
+        return FGK_ERR_INVALID;
+    }
+    fgk_precond_s *pc = new fgk_precond_s();
+    pc->plan = h;
+    pc->k_req = (int)std::min<int64_t>(rank, h->N);
+    pc->sigma2 = sigma2;
+    cudaStream_t s = (cudaStream_t)stream;
+    pc->stream = s;
+    const int rc = pc_build(pc, s);
+    if (rc) {
+        pc_release(pc, s);
+        delete pc;
+        return rc;
+    }
+    *out = pc;
+    return FGK_OK;
+}
+
+int fgk_precond_info(fgk_precond pc, fgk_precond_report *rep, int64_t *pivots) {
+    clear_error();
+    if (!pc || !rep) {
+        set_error("fgk_precond_info: NULL argument");
+        return FGK_ERR_INVALID;
+    }
+    rep->rank_requested = pc->k_req;
+    rep->rank = pc->rank;
+    rep->sigma2 = pc->sigma2;
+    rep->trace_resid = pc->trace;
+    rep->logdet = pc->logdet;
+    rep->device_bytes = pc->bytes;
+    if (pivots && pc->rank > 0) {
+        std::vector<int32_t> q(pc->rank), perm(pc->plan->N);
+        FGK_CUDA(cudaMemcpy(q.data(), pc->piv_q, pc->rank * 4, cudaMemcpyDeviceToHost));
+        FGK_CUDA(cudaMemcpy(perm.data(), pc->plan->perm[0], pc->plan->N * 4, cudaMemcpyDeviceToHost));
+        for (int m = 0; m < pc->rank; ++m) pivots[m] = perm[q[m]];
+    }
+    return FGK_OK;
+}
+
+int fgk_precond_factor(fgk_precond pc, double *L, fgk_stream_t stream) {
+    clear_error();
+    if (!pc || !L) {
+        set_error("fgk_precond_factor: NULL argument");
+        return FGK_ERR_INVALID;
+    }
+    if (pc->rank == 0) return FGK_OK;
+    const int64_t n = pc->plan->N * pc->rank;
+    k_pc_factor_out<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(pc->L64, pc->ldN, pc->rank, pc->plan->N,
+                                                                         pc->plan->perm[0], L);
+    FGK_LAUNCH_CHECK();
+    return FGK_OK;
+}
+
+int fgk_precond_apply(fgk_precond pc, const double *R, int ncols, double *Z, fgk_stream_t stream) {
+    clear_error();
+    if (!pc || !R || !Z || ncols < 1 || ncols > kPcMaxCols) {
+        set_error("fgk_precond_apply: need pc, R, Z and 1 <= ncols <= %d", kPcMaxCols);
+        return FGK_ERR_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const Plan *p = pc->plan;
+    const size_t bytes = (size_t)p->N * ncols * 8;
+    double *Rq = (double *)dev_alloc(bytes, s), *Zq = (double *)dev_alloc(bytes, s);
+    int rc = FGK_OK;
+    if (!Rq || !Zq) {
+        set_error("fgk_precond_apply: device allocation failed");
+        rc = FGK_ERR_OOM;
+    }
+    if (!rc) rc = pc_reserve(pc, ncols, s);
+    if (!rc) rc = to_q_order(p, R, Rq, ncols, 8, s);
+    if (!rc) rc = pc_apply(pc, Rq, ncols, Zq, nullptr, s);
+    if (!rc) rc = pc_check(pc, s);
+    if (!rc) rc = from_q_order(p, Zq, Z, ncols, 8, s);
+    if (Rq) dev_free(Rq, s);
+    if (Zq) dev_free(Zq, s);
+    return rc;
+}
+
+int fgk_precond_destroy(fgk_precond pc) {
+    clear_error();
+    if (!pc) return FGK_OK;
+    pc_release(pc, pc->stream);
+    cudaStreamSynchronize(pc->stream);
+    delete pc;
+    return FGK_OK;
+}
+
+}  // extern "C"

@@ -1,8 +1,8 @@
 // K5-K7: the GP solve (K + sigma^2 I) alpha = y (eq. gp_mean_system) on top of
 // the product, with optional GLS fixed effects.
 //
-// CG (App. A.1, Algorithm 2 with the identity preconditioner and a zero
-// initial guess) runs on a block of columns at once; every column has its own
+// CG (App. A.1, Algorithm 2 with a zero initial guess; the preconditioner is
+// the identity unless one is given, see below) runs on a block of columns at once; every column has its own
 // alpha_j = rho_j / p_j^T A p_j and beta_j = rho'_j / rho_j and stops on its
 // own once ||r_j|| is below its threshold (then its updates are masked).
 // Vectors, inner products and scalars are FP64 and stay on the device; the
@@ -20,6 +20,21 @@
 // iterative refinement with the correction solved in low precision, without
 // restarting the Krylov space at every correction.  In FP64 mode the only
 // replacement is the final confirmation.
+//
+// Preconditioning (App. A.3; Algorithm 2 with s_P = P^{-1}): with a
+// pivoted-Cholesky preconditioner every iteration also forms z = P^{-1} r
+// (Woodbury, three kernels in the captured graph), rho = r^T z and
+// p = z + beta p; the stop test and the replacement triggers stay on the
+// recursive ||r||^2.  Mixed precision then takes the plain refinement form:
+// the FP32 iterations run until the recursive residual has dropped by
+// delta = 1e-3 (or claims convergence), the FP64 true residual replaces it,
+// and every column restarts from p = z.  Keeping p across a replacement, as
+// without a preconditioner, is unstable here: P^{-1} magnifies the gap
+// between the recursive and the true residual outside the span of L by up
+// to 1/sigma^2, so r^T z of the replaced residual no longer matches the kept
+// direction and the next step overshoots (measured: the true residual grew
+// by orders of magnitude); a good preconditioner needs few iterations per
+// refinement step, so the restarts cost little.
 //
 // FP32 breakdowns.  The FP32 product of a direction that lies mostly in the
 // small-eigenvalue subspace of a badly conditioned A can have p^T A p <= 0
@@ -54,7 +69,8 @@ constexpr int kMaxCols = 64;
 // active_next, which the next iteration's first kernel copies over, so no
 // block ever reads a value another block of the same kernel may be writing.
 struct ColState {
-    double rho[kMaxCols];
+    double rho[kMaxCols];  // r^T z (z = r without a preconditioner)
+    double rr[kMaxCols];   // recursive ||r||^2 after the last p-update
     double rho_next[kMaxCols];
     double beta[kMaxCols];
     double thr2[kMaxCols];
@@ -102,7 +118,7 @@ __global__ void k_col_pap(const double *__restrict__ p, const double *__restrict
     block_col_dots<double, double>(p, w, sigma2, p, N, ncols, partial);
 }
 
-// p_j = r_j on the columns flagged in bd (a CG restart)
+// p_j = r_j (or z_j) on the columns flagged in bd (a CG restart)
 __global__ void k_restart_cols(double *__restrict__ p, const double *__restrict__ r, int64_t N, int ncols,
                                const ColState *__restrict__ st) {
     const int64_t n = N * ncols;
@@ -197,24 +213,30 @@ __global__ void k_update_xr(double *__restrict__ x, double *__restrict__ r, cons
 // copy of p for the mixed product and W = s2 p, the diagonal term the next
 // product starts from.
 // The first block records the new state for the next iteration.
+// With a preconditioner r is z = P^{-1} r and beta and rho use the partial
+// sums of r^T z (rz_partial); the stop test always uses ||r||^2.
 template <class W>
 __global__ void k_update_p(double *__restrict__ p, float *__restrict__ p32, W *__restrict__ w,
                            const double *__restrict__ r, double s2, int64_t N, int ncols,
-                           const double *__restrict__ rr_partial, int nblk, ColState *__restrict__ st) {
+                           const double *__restrict__ rr_partial, const double *__restrict__ rz_partial,
+                           int rz_nblk, ColState *__restrict__ st) {
+    const int nblk = gridDim.x;  // rows of rr_partial: one per CTA of k_update_xr (same grid)
     if (st->n_active == 0) return;
     __shared__ double s_beta[kMaxCols];
     __shared__ int s_act[kMaxCols];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int j = warp; j < ncols; j += nw) {
         const double rr = warp_col_sum(rr_partial, nblk, ncols, j, lane);
+        const double rz = rz_partial ? warp_col_sum(rz_partial, rz_nblk, ncols, j, lane) : rr;
         if (lane == 0) {
             const int act = st->active[j];
             const double rho = st->rho[j];
             const int still = act && !st->bd[j] && rr > st->thr2[j];
-            s_beta[j] = act ? (rho > 0.0 ? rr / rho : 0.0) : 0.0;
+            s_beta[j] = act ? (rho > 0.0 ? rz / rho : 0.0) : 0.0;
             s_act[j] = still;
             if (blockIdx.x == 0) {
-                st->rho_next[j] = act ? rr : rho;
+                st->rho_next[j] = act ? rz : rho;
+                if (act) st->rr[j] = rr;
                 st->active_next[j] = still;
                 st->beta[j] = s_beta[j];
                 if (act) st->iters[j] += 1;
@@ -379,8 +401,8 @@ size_t solve_ws_bytes(const Plan *p, int ncols) {
     return 7 * vec + (size_t)kRedBlocks * kMaxCols * kMaxH * 8 + sizeof(ColState) + 4096;
 }
 
-int cg_solve(Plan *p, const double *y, int nrhs, double sigma2, const double *H, int L, double tol, int maxit,
-             int mode, double *alpha, double *beta, fgk_cg_info *info, cudaStream_t user_s) {
+int cg_solve(Plan *p, Precond *pc, const double *y, int nrhs, double sigma2, const double *H, int L, double tol,
+             int maxit, int mode, double *alpha, double *beta, fgk_cg_info *info, cudaStream_t user_s) {
     const int64_t N = p->N;
     const int ncols = nrhs + std::max(L, 0);
     if (ncols > kMaxCols) {
@@ -399,8 +421,16 @@ int cg_solve(Plan *p, const double *y, int nrhs, double sigma2, const double *H,
 
     const size_t vec = (size_t)N * ncols;
     bool mixed = mode == FGK_MIXED;
-    size_t bytes = 5 * vec * 8 + (mixed ? 2 * vec * 4 : 0) + (size_t)kRedBlocks * kMaxCols * (kMaxH + 1) * 8 +
-                   sizeof(ColState) + 4096;
+    const int rz_blocks = pc ? pc_partial_blocks(pc) : kRedBlocks;
+    size_t bytes = (pc ? 6 : 5) * vec * 8 + (mixed ? 2 * vec * 4 : 0) +
+                   (size_t)kRedBlocks * kMaxCols * (kMaxH + 1) * 8 + (size_t)rz_blocks * ncols * 8 +
+                   sizeof(ColState) + 8192;
+    if (pc && pc_reserve(pc, ncols, s) != FGK_OK) {
+        p->stream = saved;
+        cudaStreamDestroy(s);
+        cudaEventDestroy(ev);
+        return FGK_ERR_OOM;
+    }
     char *w = (char *)dev_alloc(bytes, s);
     if (!w) {
         p->stream = saved;
@@ -423,6 +453,8 @@ int cg_solve(Plan *p, const double *y, int nrhs, double sigma2, const double *H,
     float *P32 = mixed ? (float *)carve(vec * 4) : nullptr;
     double *partial = (double *)carve((size_t)kRedBlocks * kMaxCols * kMaxH * 8);
     double *partial2 = (double *)carve((size_t)kRedBlocks * kMaxCols * 8);
+    double *partial3 = (double *)carve((size_t)rz_blocks * ncols * 8);  // r^T z, one row per CTA of the apply
+    double *Zv = pc ? (double *)carve(vec * 8) : nullptr;
     ColState *st = (ColState *)carve(sizeof(ColState));
 
     int rc = FGK_OK;
@@ -435,7 +467,7 @@ int cg_solve(Plan *p, const double *y, int nrhs, double sigma2, const double *H,
     bool converged = false, breakdown = false;
     // mixed mode: replace the recursive residual by the FP64 true residual
     // once it has dropped by this factor since the last replacement
-    double delta = mixed ? env_double("FGK_MIXED_DELTA", 0.5) : 0.0;
+    double delta = mixed ? env_double("FGK_MIXED_DELTA", pc ? 1e-3 : 0.5) : 0.0;
     int restarts = 0;
     std::vector<double> pap(ncols);
     const int check_every = 8;
@@ -451,6 +483,23 @@ int cg_solve(Plan *p, const double *y, int nrhs, double sigma2, const double *H,
         FGK_CUDA(cudaStreamSynchronize(s));
         for (auto &v : out) v = std::sqrt(v);
         return FGK_OK;
+    };
+    // per-column A^T B into out (no square root)
+    auto coldots = [&](const double *A, const double *Bm, std::vector<double> &out) -> int {
+        k_col_dots<<<kRedBlocks, kRedThreads, 0, s>>>(A, Bm, N, ncols, partial);
+        FGK_LAUNCH_CHECK();
+        k_finalize_sums<<<1, kMaxCols, 0, s>>>(partial, kRedBlocks, ncols, dsum);
+        FGK_LAUNCH_CHECK();
+        FGK_CUDA(cudaMemcpyAsync(out.data(), dsum, ncols * 8, cudaMemcpyDeviceToHost, s));
+        FGK_CUDA(cudaStreamSynchronize(s));
+        return FGK_OK;
+    };
+    // z = P^{-1} r and rz = r^T z per column (host), preconditioned solves only
+    std::vector<double> hrz(ncols);
+    auto precondition = [&]() -> int {
+        FGK_TRY(pc_apply(pc, Rv, ncols, Zv, nullptr, s));
+        FGK_TRY(pc_check(pc, s));
+        return coldots(Rv, Zv, hrz);
     };
     // R = B - A X with FP64 scans (replaces the recursive residual)
     auto true_residual = [&]() -> int {
@@ -471,8 +520,9 @@ int cg_solve(Plan *p, const double *y, int nrhs, double sigma2, const double *H,
             k_update_xr<float><<<kRedBlocks, kRedThreads, 0, s>>>(X, Rv, Pv, W32, sigma2, N, ncols, partial,
                                                                  kRedBlocks, partial2, st);
             FGK_LAUNCH_CHECK();
-            k_update_p<float><<<kRedBlocks, kRedThreads, 0, s>>>(Pv, P32, W32, Rv, p->s2, N, ncols, partial2,
-                                                                kRedBlocks, st);
+            if (pc) FGK_TRY(pc_apply(pc, Rv, ncols, Zv, partial3, s));
+            k_update_p<float><<<kRedBlocks, kRedThreads, 0, s>>>(Pv, P32, W32, pc ? Zv : Rv, p->s2, N, ncols,
+                                                                partial2, pc ? partial3 : nullptr, rz_blocks, st);
             FGK_LAUNCH_CHECK();
         } else {
             FGK_TRY(mvm_q_f64(p, Pv, ncols, W64, s, &st->n_active, false));
@@ -481,8 +531,9 @@ int cg_solve(Plan *p, const double *y, int nrhs, double sigma2, const double *H,
             k_update_xr<double><<<kRedBlocks, kRedThreads, 0, s>>>(X, Rv, Pv, W64, sigma2, N, ncols, partial,
                                                                   kRedBlocks, partial2, st);
             FGK_LAUNCH_CHECK();
-            k_update_p<double><<<kRedBlocks, kRedThreads, 0, s>>>(Pv, nullptr, W64, Rv, p->s2, N, ncols,
-                                                                 partial2, kRedBlocks, st);
+            if (pc) FGK_TRY(pc_apply(pc, Rv, ncols, Zv, partial3, s));
+            k_update_p<double><<<kRedBlocks, kRedThreads, 0, s>>>(Pv, nullptr, W64, pc ? Zv : Rv, p->s2, N, ncols,
+                                                                 partial2, pc ? partial3 : nullptr, rz_blocks, st);
             FGK_LAUNCH_CHECK();
         }
         return FGK_OK;
@@ -536,8 +587,13 @@ int cg_solve(Plan *p, const double *y, int nrhs, double sigma2, const double *H,
         if ((rc = colnorms(B, bnorm))) break;
         FGK_CUDA(cudaMemsetAsync(X, 0, vec * 8, s));
         FGK_CUDA(cudaMemcpyAsync(Rv, B, vec * 8, cudaMemcpyDeviceToDevice, s));
-        FGK_CUDA(cudaMemcpyAsync(Pv, B, vec * 8, cudaMemcpyDeviceToDevice, s));
         rnorm = bnorm;
+        if (pc) {  // p = z = P^{-1} b, rho = b^T z
+            if ((rc = precondition())) break;
+            FGK_CUDA(cudaMemcpyAsync(Pv, Zv, vec * 8, cudaMemcpyDeviceToDevice, s));
+        } else {
+            FGK_CUDA(cudaMemcpyAsync(Pv, B, vec * 8, cudaMemcpyDeviceToDevice, s));
+        }
         // warm the products once so their workspace exists before graph capture,
         // then set the product's starting point W = s2 p
         if ((rc = init_p())) break;
@@ -574,8 +630,9 @@ int cg_solve(Plan *p, const double *y, int nrhs, double sigma2, const double *H,
         ColState hs;
         std::memset(&hs, 0, sizeof(hs));
         for (int j = 0; j < ncols; ++j) {
-            hs.rho[j] = hs.rho_next[j] = rnorm[j] * rnorm[j];
-            rho_ref[j] = hs.rho[j];
+            hs.rr[j] = rnorm[j] * rnorm[j];
+            hs.rho[j] = hs.rho_next[j] = pc ? hrz[j] : hs.rr[j];
+            rho_ref[j] = hs.rr[j];
             const double target = 0.5 * tol * bnorm[j];
             hs.thr2[j] = target * target;
             confirmed[j] = rnorm[j] <= tol * bnorm[j];
@@ -621,20 +678,36 @@ int cg_solve(Plan *p, const double *y, int nrhs, double sigma2, const double *H,
             for (int j = 0; j < ncols; ++j) {
                 if (confirmed[j]) continue;
                 if (!snap.active_next[j]) claims = true;
-                if (snap.rho_next[j] <= delta * delta * rho_ref[j]) dropped = true;
+                if (snap.rr[j] <= delta * delta * rho_ref[j]) dropped = true;
             }
             if (!(restart || claims || (dropped && iters_total - last_replacement >= gap))) continue;
             last_replacement = iters_total;
             if ((rc = true_residual())) break;
-            bool drift = false;
-            for (int j = 0; j < ncols; ++j)
-                if (!confirmed[j] && rnorm[j] > 2.0 * std::sqrt(snap.rho_next[j])) drift = true;
+            if (pc && (rc = precondition())) break;
+            // Columns restart from p = z (z = r without a preconditioner) when
+            // their search direction no longer fits the replaced residual: an
+            // FP32 breakdown, a column that had stopped (its p missed the last
+            // update), or a true residual more than twice the recursive one
+            // (the recursion drifted; keeping p would pair a direction scaled
+            // to the recursive residual with rho of the true one).
+            bool drift = false, any_rs = false;
+            for (int j = 0; j < ncols; ++j) {
+                const bool dj = !confirmed[j] && rnorm[j] > 2.0 * std::sqrt(snap.rr[j]);
+                drift = drift || dj;
+                const bool rs = !confirmed[j] && (pc || snap.bd[j] || !snap.active_next[j] || dj) &&
+                                !(rnorm[j] <= tol * bnorm[j]);
+                snap.bd[j] = rs ? 1 : 0;
+                any_rs = any_rs || rs;
+            }
             gap = drift ? 0 : min_gap;
-            if (restart) {
-                k_restart_cols<<<kRedBlocks, kRedThreads, 0, s>>>(Pv, Rv, N, ncols, st);
+            if (any_rs) {
+                FGK_CUDA(cudaMemcpyAsync(st, &snap, sizeof(ColState), cudaMemcpyHostToDevice, s));
+                k_restart_cols<<<kRedBlocks, kRedThreads, 0, s>>>(Pv, pc ? Zv : Rv, N, ncols, st);
                 FGK_LAUNCH_CHECK();
-                std::memset(snap.bd, 0, sizeof(snap.bd));
-                snap.breakdown = 0;
+            }
+            std::memset(snap.bd, 0, sizeof(snap.bd));
+            snap.breakdown = 0;
+            if (restart) {
                 if (++restarts > kMaxRestarts && mixed) {
                     // the FP32 products cannot resolve this system: FP64 from here on
                     mixed = false;
@@ -652,14 +725,16 @@ int cg_solve(Plan *p, const double *y, int nrhs, double sigma2, const double *H,
                 if (!confirmed[j] && rnorm[j] <= tol * bnorm[j]) confirmed[j] = 1;
                 snap.active[j] = snap.active_next[j] = !confirmed[j];
                 if (!confirmed[j]) {
-                    snap.rho[j] = snap.rho_next[j] = rnorm[j] * rnorm[j];
-                    rho_ref[j] = snap.rho[j];
+                    snap.rr[j] = rnorm[j] * rnorm[j];
+                    snap.rho[j] = snap.rho_next[j] = pc ? hrz[j] : snap.rr[j];
+                    rho_ref[j] = snap.rr[j];
                 }
                 snap.n_active += snap.active[j];
             }
             FGK_CUDA(cudaMemcpyAsync(st, &snap, sizeof(ColState), cudaMemcpyHostToDevice, s));
         }
         if (rc) break;
+        if (pc && (rc = pc_check(pc, s))) break;  // a bulk-copy wait of the preconditioner expired
         if (!converged && refinements == 0 && (rc = true_residual())) break;  // report true residuals
         // GLS fixed effects
         double *beta_dev = nullptr;

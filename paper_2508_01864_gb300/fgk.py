@@ -44,6 +44,11 @@ class fgk_cg_info(ctypes.Structure):
                 ("fp64_switch", ctypes.c_int32)]
 
 
+class fgk_precond_report(ctypes.Structure):
+    _fields_ = [("rank_requested", ctypes.c_int32), ("rank", ctypes.c_int32), ("sigma2", ctypes.c_double),
+                ("trace_resid", ctypes.c_double), ("logdet", ctypes.c_double), ("device_bytes", ctypes.c_size_t)]
+
+
 class fgk_plan_info(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64), ("d", ctypes.c_int32), ("two_nu", ctypes.c_int32), ("kind", ctypes.c_int32),
                 ("L", ctypes.c_int32), ("n_levels", ctypes.c_int32), ("outscale2", ctypes.c_double),
@@ -53,7 +58,8 @@ class fgk_plan_info(ctypes.Structure):
 EXPORTS = ["fgk_set_allocator", "fgk_build", "fgk_matvec", "fgk_matvec_q", "fgk_matvec_q_noalloc", "fgk_cg_solve", "fgk_bytes_estimate",
            "fgk_destroy", "fgk_last_error", "fgk_kernel_launches", "fgk_scan_timing", "fgk_get_info",
            "fgk_get_permutation", "fgk_get_level", "fgk_batch_create", "fgk_batch_layout", "fgk_batch_matvec_q",
-           "fgk_batch_cg_solve", "fgk_batch_destroy"]
+           "fgk_batch_cg_solve", "fgk_batch_destroy", "fgk_precond_build", "fgk_precond_info",
+           "fgk_precond_factor", "fgk_precond_apply", "fgk_precond_destroy", "fgk_cg_solve_pc"]
 
 _lock = threading.Lock()
 _lib = None
@@ -110,6 +116,19 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.fgk_batch_cg_solve.restype = i32
         lib.fgk_batch_destroy.argtypes = [vp]
         lib.fgk_batch_destroy.restype = i32
+        lib.fgk_precond_build.argtypes = [vp, i32, dbl, vp, ctypes.POINTER(vp)]
+        lib.fgk_precond_build.restype = i32
+        lib.fgk_precond_info.argtypes = [vp, ctypes.POINTER(fgk_precond_report), ctypes.POINTER(i64)]
+        lib.fgk_precond_info.restype = i32
+        lib.fgk_precond_factor.argtypes = [vp, vp, vp]
+        lib.fgk_precond_factor.restype = i32
+        lib.fgk_precond_apply.argtypes = [vp, vp, i32, vp, vp]
+        lib.fgk_precond_apply.restype = i32
+        lib.fgk_precond_destroy.argtypes = [vp]
+        lib.fgk_precond_destroy.restype = i32
+        lib.fgk_cg_solve_pc.argtypes = [vp, vp, vp, i32, dbl, vp, i32, dbl, i32, i32, vp, vp,
+                                        ctypes.POINTER(fgk_cg_info), vp]
+        lib.fgk_cg_solve_pc.restype = i32
         _lib = lib
         return lib
 
@@ -239,8 +258,10 @@ def fgk_scan_timing(enable: int = -1):
 
 
 def fgk_cg_solve(h: Handle, y: torch.Tensor, sigma2: float, H: torch.Tensor | None = None, L: int = 0,
-                 tol: float = 1e-8, maxit: int = 100000, mode="f64", stream=None, want_beta: bool = True):
-    """Solve (K + sigma2 I) alpha = y, optionally with GLS fixed effects.
+                 tol: float = 1e-8, maxit: int = 100000, mode="f64", stream=None, want_beta: bool = True,
+                 precond=None):
+    """Solve (K + sigma2 I) alpha = y, optionally with GLS fixed effects and
+    a preconditioner from ``fgk_precond_build`` (calls fgk_cg_solve_pc).
 
     Returns (alpha, beta or None, info dict, status) where status is FGK_OK or
     FGK_NOT_CONVERGED; errors raise FgkError."""
@@ -260,16 +281,77 @@ def fgk_cg_solve(h: Handle, y: torch.Tensor, sigma2: float, H: torch.Tensor | No
     res = (ctypes.c_double * ncols)()
     info = fgk_cg_info()
     info.true_resid = ctypes.cast(res, ctypes.POINTER(ctypes.c_double))
-    rc = lib.fgk_cg_solve(h.ptr, y2.data_ptr(), nrhs, float(sigma2), Hp, int(L), float(tol), int(maxit), m,
-                          alpha.data_ptr(), beta.data_ptr() if beta is not None else 0, ctypes.byref(info),
-                          _stream(stream))
-    _check(rc, allow_soft=True)
+    if precond is None:
+        rc = lib.fgk_cg_solve(h.ptr, y2.data_ptr(), nrhs, float(sigma2), Hp, int(L), float(tol), int(maxit), m,
+                              alpha.data_ptr(), beta.data_ptr() if beta is not None else 0, ctypes.byref(info),
+                              _stream(stream))
+    else:
+        rc = lib.fgk_cg_solve_pc(h.ptr, precond.ptr, y2.data_ptr(), nrhs, float(sigma2), Hp, int(L), float(tol),
+                                 int(maxit), m, alpha.data_ptr(), beta.data_ptr() if beta is not None else 0,
+                                 ctypes.byref(info), _stream(stream))
     d = {"iterations": info.iterations, "refinements": info.refinements, "mvm_f32": info.mvm_f32,
          "mvm_f64": info.mvm_f64, "max_true_resid": info.max_true_resid, "true_resid": list(res),
          "restarts": info.restarts, "fp64_switch": info.fp64_switch}
+    try:
+        _check(rc, allow_soft=True)
+    except FgkError as e:
+        e.info = d  # the solve's report, filled on every return
+        raise
     if y.dim() == 1:
         alpha = alpha.squeeze(1)
     return alpha, beta, d, rc
+
+
+@dataclass
+class Precond:
+    ptr: int
+    handle: Handle
+    sigma2: float
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        fgk_precond_destroy(self)
+
+
+def fgk_precond_build(h: Handle, rank: int, sigma2: float, stream=None) -> Precond:
+    """Rank-k pivoted-Cholesky preconditioner P = L L^T + sigma2 I of the plan's K."""
+    out = ctypes.c_void_p()
+    _check(load().fgk_precond_build(h.ptr, int(rank), float(sigma2), _stream(stream), ctypes.byref(out)))
+    return Precond(out.value, h, float(sigma2))
+
+
+def fgk_precond_info(pc: Precond) -> dict:
+    rep = fgk_precond_report()
+    piv = (ctypes.c_int64 * max(1, min(int(pc.handle.N), 1024)))()
+    _check(load().fgk_precond_info(pc.ptr, ctypes.byref(rep), piv))
+    return {"rank_requested": rep.rank_requested, "rank": rep.rank, "sigma2": rep.sigma2,
+            "trace_resid": rep.trace_resid, "logdet": rep.logdet, "device_bytes": rep.device_bytes,
+            "pivots": list(piv)[:rep.rank]}
+
+
+def fgk_precond_factor(pc: Precond, stream=None) -> torch.Tensor:
+    """L (N x k FP64, the caller's point order)."""
+    k = fgk_precond_info(pc)["rank"]
+    L = torch.zeros((pc.handle.N, max(k, 0)), dtype=torch.float64, device="cuda")
+    if k > 0:
+        _check(load().fgk_precond_factor(pc.ptr, L.data_ptr(), _stream(stream)))
+    return L
+
+
+def fgk_precond_apply(pc: Precond, R: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Z = P^{-1} R (Woodbury), R: N x ncols FP64 CUDA tensor in the caller's order."""
+    R2 = _dev_f64_2d(R, "R")
+    Z = torch.empty_like(R2) if out is None else out
+    _check(load().fgk_precond_apply(pc.ptr, R2.data_ptr(), R2.shape[1], Z.data_ptr(), _stream(stream)))
+    return Z.squeeze(1) if R.dim() == 1 else Z
+
+
+def fgk_precond_destroy(pc: Precond) -> None:
+    if pc is not None and pc.ptr:
+        _check(load().fgk_precond_destroy(pc.ptr))
+        pc.ptr = 0
 
 
 def fgk_bytes_estimate(N: int, d: int, nu, kind="l1", nrhs: int = 1) -> int:

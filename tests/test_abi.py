@@ -71,6 +71,16 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert lib.fgk_destroy(None) == 0
     assert lib.fgk_set_allocator(1, None, None) == -1
     assert lib.fgk_set_allocator(None, None, None) == 0
+    # preconditioner: NULL plan, bad rank or sigma2
+    pc = ctypes.c_void_p()
+    assert lib.fgk_precond_build(None, 10, 0.01, None, ctypes.byref(pc)) == -1
+    assert lib.fgk_precond_build(1, -1, 0.01, None, ctypes.byref(pc)) == -1
+    assert lib.fgk_precond_build(1, 10, 0.0, None, ctypes.byref(pc)) == -1
+    assert lib.fgk_precond_build(1, 5000, 0.01, None, ctypes.byref(pc)) == -1
+    assert pc.value is None
+    assert lib.fgk_precond_info(None, None, None) == -1
+    assert lib.fgk_precond_apply(None, 1, 1, 1, None) == -1
+    assert lib.fgk_precond_destroy(None) == 0
 
 
 def test_binding_fails_loudly_without_library(tmp_path):
