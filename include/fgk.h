@@ -293,6 +293,13 @@ uint64_t fgk_kernel_launches(void);
  * waiting for the recorded events. */
 int fgk_scan_timing(int enable, double *total_ms, int64_t *launches);
 
+/* The same CUDA-event timing for any of these kernels (fgk_scan_timing is
+ * kernel FGK_TIMED_SCAN_OUT): the output pass of the level scans, and the
+ * two passes over L of the preconditioner apply (t = L^T R and
+ * Z = R / sigma2 - L c).  FGK_ERR_INVALID for an unknown id. */
+enum { FGK_TIMED_SCAN_OUT = 0, FGK_TIMED_PC_LTR = 1, FGK_TIMED_PC_APPLY = 2 };
+int fgk_kernel_timing(int kernel, int enable, double *total_ms, int64_t *launches);
+
 /* ---- inspection (tests and tools): copies of the cached structure ---- */
 
 typedef struct {

@@ -28,29 +28,31 @@ void add_kernel_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_
 uint64_t kernel_launch_count() { return (uint64_t)g_launches.load(std::memory_order_relaxed); }
 
 static std::mutex g_timing_mu;
-static std::atomic<bool> g_timing_on{false};
-static std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_timing_events;
-static double g_timing_ms = 0.0;
-static int64_t g_timing_n = 0;
+static std::atomic<bool> g_timing_on[kTimedKernels];
+static std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_timing_events[kTimedKernels];
+static double g_timing_ms[kTimedKernels] = {};
+static int64_t g_timing_n[kTimedKernels] = {};
 
-bool scan_timing_enabled() { return g_timing_on.load(std::memory_order_relaxed); }
-void scan_timing_record(cudaEvent_t start, cudaEvent_t stop) {
+bool kernel_timing_enabled(int id) { return g_timing_on[id].load(std::memory_order_relaxed); }
+void kernel_timing_record(int id, cudaEvent_t start, cudaEvent_t stop) {
     std::lock_guard<std::mutex> lk(g_timing_mu);
-    g_timing_events.emplace_back(start, stop);
+    g_timing_events[id].emplace_back(start, stop);
 }
+bool scan_timing_enabled() { return kernel_timing_enabled(kTimedScanOut); }
+void scan_timing_record(cudaEvent_t start, cudaEvent_t stop) { kernel_timing_record(kTimedScanOut, start, stop); }
 // folds recorded event pairs into the totals (synchronises on each pair)
-static int timing_drain() {
+static int timing_drain(int id) {
     std::lock_guard<std::mutex> lk(g_timing_mu);
-    for (auto &e : g_timing_events) {
+    for (auto &e : g_timing_events[id]) {
         FGK_CUDA(cudaEventSynchronize(e.second));
         float ms = 0.f;
         FGK_CUDA(cudaEventElapsedTime(&ms, e.first, e.second));
-        g_timing_ms += ms;
-        ++g_timing_n;
+        g_timing_ms[id] += ms;
+        ++g_timing_n[id];
         cudaEventDestroy(e.first);
         cudaEventDestroy(e.second);
     }
-    g_timing_events.clear();
+    g_timing_events[id].clear();
     return FGK_OK;
 }
 
@@ -392,20 +394,28 @@ int fgk_matvec_q(fgk_handle h, const void *Vq, int nrhs, void *Yq, int precision
 
 uint64_t fgk_kernel_launches(void) { return kernel_launch_count(); }
 
-int fgk_scan_timing(int enable, double *total_ms, int64_t *launches) {
+int fgk_kernel_timing(int kernel, int enable, double *total_ms, int64_t *launches) {
     clear_error();
-    int rc = timing_drain();
+    if (kernel < 0 || kernel >= kTimedKernels) {
+        set_error("fgk_kernel_timing: unknown kernel id %d", kernel);
+        return FGK_ERR_INVALID;
+    }
+    int rc = timing_drain(kernel);
     if (rc != FGK_OK) return rc;
-    if (total_ms) *total_ms = g_timing_ms;
-    if (launches) *launches = g_timing_n;
+    if (total_ms) *total_ms = g_timing_ms[kernel];
+    if (launches) *launches = g_timing_n[kernel];
     if (enable >= 0) {
-        if (enable == 1 && !g_timing_on.load()) {
-            g_timing_ms = 0.0;
-            g_timing_n = 0;
+        if (enable == 1 && !g_timing_on[kernel].load()) {
+            g_timing_ms[kernel] = 0.0;
+            g_timing_n[kernel] = 0;
         }
-        g_timing_on.store(enable == 1);
+        g_timing_on[kernel].store(enable == 1);
     }
     return FGK_OK;
+}
+
+int fgk_scan_timing(int enable, double *total_ms, int64_t *launches) {
+    return fgk_kernel_timing(FGK_TIMED_SCAN_OUT, enable, total_ms, launches);
 }
 
 static int cg_entry(const char *name, fgk_handle h, fgk_precond pc, const double *y, int nrhs, double sigma2,

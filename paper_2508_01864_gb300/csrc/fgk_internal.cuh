@@ -43,9 +43,35 @@ uint64_t kernel_launch_count();
         FGK_CUDA(cudaGetLastError());         \
     } while (0)
 
-// Optional CUDA-event timing of the main scan kernel (tools; off by default).
+// Optional CUDA-event timing of selected kernels (tools; off by default).
+enum : int { kTimedScanOut = FGK_TIMED_SCAN_OUT, kTimedPcLtr = FGK_TIMED_PC_LTR,
+             kTimedPcApply = FGK_TIMED_PC_APPLY, kTimedKernels = 3 };
+bool kernel_timing_enabled(int id);
+void kernel_timing_record(int id, cudaEvent_t start, cudaEvent_t stop);
 bool scan_timing_enabled();
 void scan_timing_record(cudaEvent_t start, cudaEvent_t stop);
+
+// Brackets one launch with events when timing of `id` is on and the stream
+// is not being captured: begin() before the launch, end() after it.
+struct TimedLaunch {
+    int id;
+    cudaStream_t s;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    TimedLaunch(int id_, cudaStream_t s_) : id(id_), s(s_) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (kernel_timing_enabled(id) && cudaStreamIsCapturing(s, &cs) == cudaSuccess &&
+            cs == cudaStreamCaptureStatusNone && cudaEventCreate(&e0) == cudaSuccess &&
+            cudaEventCreate(&e1) == cudaSuccess)
+            cudaEventRecord(e0, s);
+    }
+    void end() {
+        if (e1) {
+            cudaEventRecord(e1, s);
+            kernel_timing_record(id, e0, e1);
+            e0 = e1 = nullptr;
+        }
+    }
+};
 
 // ---------------------------------------------------------------- memory
 void *dev_alloc(size_t bytes, cudaStream_t s);

@@ -13,10 +13,12 @@
 // updates its rows and publishes its own maximum.  A step whose largest
 // residual is at most 1e-12 s2 (numerically exhausted; the paper leaves the
 // case open) records the realised rank and changes nothing.
-// L is FP64 during the build (columns of N entries, q order); the apply uses
-// an FP32 copy, and the Woodbury matrix I + L^T L / sigma^2 is formed from
-// exactly those FP32 values (their products are exact in FP64), so P is the
-// SPD matrix L32 L32^T + sigma^2 I that the apply inverts.
+// L is kept as a float pair per entry (columns of N entries, q order):
+// L = Lhi + Llo to about 48 bits, the sums of the build done in float-pair
+// arithmetic (see below) and the divisions and the residual diagonal in FP64.
+// The apply uses Lhi alone, and the Woodbury matrix I + L^T L / sigma^2 is
+// formed from exactly those FP32 values (float-pair sums of exact products),
+// so P is the SPD matrix Lhi Lhi^T + sigma^2 I that the apply inverts.
 //
 // Apply (Z = P^{-1} R, every CG iteration, inside the captured graph):
 //   t = L^T R          k_pc_ltr (persistent CTAs, per-CTA partials) + k_pc_tsum
@@ -170,9 +172,9 @@ __global__ void k_pc_init(int64_t N, double s2, const int32_t *__restrict__ perm
 // step m of the pivoted Cholesky (see the file comment)
 __global__ void k_pc_step(int m, int64_t N, int64_t ldN, KernArgs ka, const int32_t *__restrict__ perm0,
                           const PivPart *__restrict__ prev, int nprev, PivPart *__restrict__ next,
-                          double *__restrict__ L, double *__restrict__ dres, int32_t *__restrict__ piv_q,
-                          int *__restrict__ rank, double floor) {
-    __shared__ double s_lp[kPcMaxRank];
+                          float *__restrict__ Lhi, float *__restrict__ Llo, double *__restrict__ dres,
+                          int32_t *__restrict__ piv_q, int *__restrict__ rank, double floor) {
+    __shared__ float s_lph[kPcMaxRank], s_lpl[kPcMaxRank];
     __shared__ double s_xp[3];
     PivPart best = piv_none();
     for (int b = threadIdx.x; b < nprev; b += blockDim.x)
@@ -187,7 +189,10 @@ __global__ void k_pc_step(int m, int64_t N, int64_t ldN, KernArgs ka, const int3
     }
     const int64_t piv = best.q;
     if (blockIdx.x == 0 && threadIdx.x == 0) piv_q[m] = (int32_t)piv;
-    for (int t = threadIdx.x; t < m; t += blockDim.x) s_lp[t] = L[(size_t)t * ldN + piv];
+    for (int t = threadIdx.x; t < m; t += blockDim.x) {
+        s_lph[t] = Lhi[(size_t)t * ldN + piv];
+        s_lpl[t] = Llo[(size_t)t * ldN + piv];
+    }
     if (threadIdx.x == 0) {
         s_xp[0] = ka.x0[piv];
         s_xp[1] = ka.d > 1 ? ka.x1[piv] : 0.0;
@@ -198,10 +203,21 @@ __global__ void k_pc_step(int m, int64_t N, int64_t ldN, KernArgs ka, const int3
     PivPart mine = piv_none();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         const double kv = kern_q(ka, i, s_xp);
-        double dot = 0.0;
-        for (int t = 0; t < m; ++t) dot = fma(L[(size_t)t * ldN + i], s_lp[t], dot);
+        // sum_t L_t[i] L_t[pivot] in float pairs: the hi x hi product exactly
+        // (two-product), the cross terms in FP32 (they sit 24 bits lower)
+        F2 acc{0.f, 0.f};
+#pragma unroll 4
+        for (int t = 0; t < m; ++t) {
+            const float ah = Lhi[(size_t)t * ldN + i], al = Llo[(size_t)t * ldN + i];
+            f2_fma(acc, ah, s_lph[t], s_lpl[t]);
+            acc.lo = fmaf(al, s_lph[t], acc.lo);
+        }
+        const double dot = (double)acc.hi + (double)acc.lo;
         const double l = (kv - dot) / sq;
-        L[(size_t)m * ldN + i] = l;
+        float lh, ll;
+        split_f2(l, lh, ll);
+        Lhi[(size_t)m * ldN + i] = lh;
+        Llo[(size_t)m * ldN + i] = ll;
         const double dn = dres[i] - l * l;
         dres[i] = dn;
         const PivPart c{dn, (int64_t)perm0[i], i};
@@ -211,13 +227,9 @@ __global__ void k_pc_step(int m, int64_t N, int64_t ldN, KernArgs ka, const int3
     if (threadIdx.x == 0) next[blockIdx.x] = mine;
 }
 
-__global__ void k_pc_to_f32(const double *__restrict__ a, int64_t n, float *__restrict__ b) {
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
-        b[t] = (float)a[t];
-}
-
 // partial Gram blocks: Gp[z][a][b] = sum over rows of chunk z of L32[a][i] L32[b][i]
-// (products of FP32 values are exact in FP64); tiles (ta <= tb) of 16 x 16
+// (products of FP32 values are exact; float-pair sums per 256 rows, then
+// FP64); tiles (ta <= tb) of 16 x 16
 __global__ void k_pc_gram(const float *__restrict__ L, int64_t ldN, int64_t N, int r, int64_t rows_per_z,
                           double *__restrict__ Gp) {
     __shared__ float sa[kGramTile][kPcThreads + 1];
@@ -239,7 +251,10 @@ __global__ void k_pc_gram(const float *__restrict__ L, int64_t ldN, int64_t N, i
         __syncthreads();
         const int la = threadIdx.x / kGramTile, lb = threadIdx.x % kGramTile;
         const int n = (int)(i1 - c0 < kPcThreads ? i1 - c0 : kPcThreads);
-        for (int k = 0; k < n; ++k) acc = fma((double)sa[la][k], (double)sb[lb][k], acc);
+        F2 f{0.f, 0.f};  // exact float products summed in float pairs
+#pragma unroll 4
+        for (int k = 0; k < n; ++k) f2_fma(f, sa[la][k], sb[lb][k], 0.f);
+        acc += (double)f.hi + (double)f.lo;
         __syncthreads();
     }
     if (a < r && b < r) Gp[((size_t)z * r + a) * r + b] = acc;
@@ -640,14 +655,15 @@ __global__ void __launch_bounds__(kTR) k_pc_apply(const __grid_constant__ CUtens
     }
 }
 
-// L in the caller's point order: out[orig * r + m] = L[m][q]
-__global__ void k_pc_factor_out(const double *__restrict__ L, int64_t ldN, int r, int64_t N,
-                                const int32_t *__restrict__ perm0, double *__restrict__ out) {
+// L in the caller's point order: out[orig * r + m] = Lhi[m][q] + Llo[m][q]
+__global__ void k_pc_factor_out(const float *__restrict__ Lhi, const float *__restrict__ Llo, int64_t ldN, int r,
+                                int64_t N, const int32_t *__restrict__ perm0, double *__restrict__ out) {
     const int64_t n = N * r;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t q = t / r;
         const int m = (int)(t % r);
-        out[(int64_t)perm0[q] * r + m] = L[(size_t)m * ldN + q];
+        const size_t o = (size_t)m * ldN + q;
+        out[(int64_t)perm0[q] * r + m] = (double)Lhi[o] + (double)Llo[o];
     }
 }
 
@@ -658,9 +674,9 @@ struct Precond {
     int k_req = 0, rank = 0;
     double sigma2 = 0.0, logdet = 0.0, trace = 0.0;
     int64_t ldN = 0;
-    double *L64 = nullptr, *dres = nullptr, *Cf = nullptr, *Cinv = nullptr, *t_part = nullptr, *cvec = nullptr,
+    double *dres = nullptr, *Cf = nullptr, *Cinv = nullptr, *t_part = nullptr, *cvec = nullptr,
            *scal = nullptr;
-    float *L32 = nullptr;
+    float *L32 = nullptr, *Llo = nullptr;  // L32: the hi part of L
     int32_t *piv_q = nullptr;
     int *ints = nullptr;  // [0] rank, [1] error flag
     int nb_ltr = 0, chunk = 0, cap_cols = 0;
@@ -800,17 +816,21 @@ int pc_check(const Precond *pc, cudaStream_t s) {
 
 template <int NC>
 static int launch_pc_ltr(const Precond *pc, int r, const double *R, int ncols, int *err, cudaStream_t s) {
+    TimedLaunch tl(kTimedPcLtr, s);
     k_pc_ltr<NC><<<pc->nb_ltr, kTR, ltr_smem(r, NC), s>>>(pc->tmap, r, R, pc->plan->N, ncols, pc->t_part, err);
     FGK_LAUNCH_CHECK();
+    tl.end();
     return FGK_OK;
 }
 
 template <int NC>
 static int launch_pc_apply(const Precond *pc, int r, const double *R, int ncols, double *Z, double *rz_partial,
                            int *err, cudaStream_t s) {
+    TimedLaunch tl(kTimedPcApply, s);
     k_pc_apply<NC><<<pc->nb_ltr, kTR, apply_smem(r, NC), s>>>(pc->tmap, r, R, pc->plan->N, ncols, pc->cvec,
                                                               pc->sigma2, Z, rz_partial, err);
     FGK_LAUNCH_CHECK();
+    tl.end();
     return FGK_OK;
 }
 
@@ -839,7 +859,7 @@ static int pc_build(Precond *pc, cudaStream_t s) {
     FGK_TRY(set_pc_attrs<4>(k));
     FGK_TRY(set_pc_attrs<8>(k));
     pc->ldN = ldN;
-    pc->L64 = (double *)take((size_t)k * ldN * 8);
+    pc->Llo = (float *)take((size_t)k * ldN * 4);
     pc->L32 = (float *)take((size_t)k * ldN * 4);
     pc->dres = (double *)take((size_t)N * 8);
     pc->piv_q = (int32_t *)take((size_t)k * 4);
@@ -864,7 +884,7 @@ static int pc_build(Precond *pc, cudaStream_t s) {
         return FGK_ERR_OOM;
     }
 
-    FGK_CUDA(cudaMemsetAsync(pc->L64, 0, (size_t)k * ldN * 8, s));
+    FGK_CUDA(cudaMemsetAsync(pc->Llo, 0, (size_t)k * ldN * 4, s));
     FGK_CUDA(cudaMemsetAsync(pc->L32, 0, (size_t)k * ldN * 4, s));
     const int init[4] = {k, 0, 0, 0};
     FGK_CUDA(cudaMemcpyAsync(pc->ints, init, sizeof(init), cudaMemcpyHostToDevice, s));
@@ -874,7 +894,8 @@ static int pc_build(Precond *pc, cudaStream_t s) {
     PivPart *bufs[2] = {part0, part1};
     for (int m = 0; m < k; ++m) {
         k_pc_step<<<steps_blocks, kPcThreads, 0, s>>>(m, N, ldN, ka, p->perm[0], bufs[m & 1], steps_blocks,
-                                                      bufs[(m + 1) & 1], pc->L64, pc->dres, pc->piv_q, pc->ints,
+                                                      bufs[(m + 1) & 1], pc->L32, pc->Llo, pc->dres, pc->piv_q,
+                                                      pc->ints,
                                                       kExhausted * p->s2);
         FGK_LAUNCH_CHECK();
     }
@@ -901,8 +922,6 @@ static int pc_build(Precond *pc, cudaStream_t s) {
         }
     }
     if (r > 0) {
-        k_pc_to_f32<<<grid_for((int64_t)r * ldN, 256), 256, 0, s>>>(pc->L64, (int64_t)r * ldN, pc->L32);
-        FGK_LAUNCH_CHECK();
         k_pc_gram<<<dim3(ntile, ntile, nz), kPcThreads, 0, s>>>(pc->L32, ldN, N, r, rows_per_z, Gp);
         FGK_LAUNCH_CHECK();
         k_pc_chol<<<1, kPcThreads, 0, s>>>(Gp, nz, r, pc->sigma2, N, pc->Cf, pc->scal + 1, pc->ints + 1);
@@ -989,7 +1008,8 @@ int fgk_precond_factor(fgk_precond pc, double *L, fgk_stream_t stream) {
     }
     if (pc->rank == 0) return FGK_OK;
     const int64_t n = pc->plan->N * pc->rank;
-    k_pc_factor_out<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(pc->L64, pc->ldN, pc->rank, pc->plan->N,
+    k_pc_factor_out<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(pc->L32, pc->Llo, pc->ldN, pc->rank,
+                                                                         pc->plan->N,
                                                                          pc->plan->perm[0], L);
     FGK_LAUNCH_CHECK();
     return FGK_OK;

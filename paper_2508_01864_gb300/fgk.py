@@ -59,7 +59,8 @@ EXPORTS = ["fgk_set_allocator", "fgk_build", "fgk_matvec", "fgk_matvec_q", "fgk_
            "fgk_destroy", "fgk_last_error", "fgk_kernel_launches", "fgk_scan_timing", "fgk_get_info",
            "fgk_get_permutation", "fgk_get_level", "fgk_batch_create", "fgk_batch_layout", "fgk_batch_matvec_q",
            "fgk_batch_cg_solve", "fgk_batch_destroy", "fgk_precond_build", "fgk_precond_info",
-           "fgk_precond_factor", "fgk_precond_apply", "fgk_precond_destroy", "fgk_cg_solve_pc"]
+           "fgk_precond_factor", "fgk_precond_apply", "fgk_precond_destroy", "fgk_cg_solve_pc",
+           "fgk_kernel_timing"]
 
 _lock = threading.Lock()
 _lib = None
@@ -90,6 +91,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.fgk_kernel_launches.restype = ctypes.c_uint64
         lib.fgk_scan_timing.argtypes = [i32, ctypes.POINTER(dbl), ctypes.POINTER(i64)]
         lib.fgk_scan_timing.restype = i32
+        lib.fgk_kernel_timing.argtypes = [i32, i32, ctypes.POINTER(dbl), ctypes.POINTER(i64)]
+        lib.fgk_kernel_timing.restype = i32
         lib.fgk_cg_solve.argtypes = [vp, vp, i32, dbl, vp, i32, dbl, i32, i32, vp, vp, ctypes.POINTER(fgk_cg_info),
                                      vp]
         lib.fgk_cg_solve.restype = i32
@@ -246,6 +249,17 @@ def fgk_matvec_q_noalloc(h: Handle, Vq: torch.Tensor, out: torch.Tensor, precisi
 
 def fgk_kernel_launches() -> int:
     return int(load().fgk_kernel_launches())
+
+
+FGK_TIMED_SCAN_OUT, FGK_TIMED_PC_LTR, FGK_TIMED_PC_APPLY = 0, 1, 2
+
+
+def fgk_kernel_timing(kernel: int, enable: int = -1):
+    """(total ms, launches) of a timed kernel; enable 1 resets and starts, 0 stops."""
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    _check(load().fgk_kernel_timing(int(kernel), int(enable), ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
 
 
 def fgk_scan_timing(enable: int = -1):
