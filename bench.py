@@ -280,6 +280,28 @@ def run_serving(args, local):
     return 0
 
 
+def run_pcg_probe(args, local):
+    """A short preconditioned mixed solve of the d=2 workload (--pcg-probe
+    RANK, --pcg-maxit iterations): the launch sequence of the benchmark's
+    step, small enough for ncu captures."""
+    import torch
+
+    import workloads
+    from paper_2508_01864_gb300 import fgk
+
+    torch.cuda.set_device(local)
+    p = workloads.c2()
+    h = fgk.fgk_build(torch.as_tensor(p.X, device="cuda"), p.nu, p.ell, kind="product")
+    pc = fgk.fgk_precond_build(h, args.pcg_probe, p.sigma2)
+    y = torch.as_tensor(p.V, device="cuda")
+    _, _, info, rc = fgk.fgk_cg_solve(h, y, p.sigma2, tol=TOL, maxit=args.pcg_maxit, mode="mixed", precond=pc)
+    torch.cuda.synchronize()
+    print(json.dumps({"pcg_probe_rank": args.pcg_probe, "iterations": info["iterations"], "status": rc}), flush=True)
+    fgk.fgk_precond_destroy(pc)
+    fgk.fgk_destroy(h)
+    return 0
+
+
 def run_mvm_only(args, local):
     """W + K FP32 products in the internal order on the d=2 workload with
     --mvm-only points (for profiling the scan kernels at sizes above L2)."""
@@ -336,6 +358,9 @@ def main():
                     help="solve the first K problems of the batched workload (16 rhs each) in one batch")
     ap.add_argument("--f64-sample", type=int, default=4,
                     help="batched mode: problems solved one by one in FP64 for the comparison")
+    ap.add_argument("--pcg-probe", type=int, default=0,
+                    help="run only a short preconditioned solve with this rank (for ncu captures)")
+    ap.add_argument("--pcg-maxit", type=int, default=40)
     ap.add_argument("--mvm-only", type=int, default=0,
                     help="time only the FP32 product on the d=2 workload drawn with this many points")
     args = ap.parse_args()
@@ -344,6 +369,8 @@ def main():
         return run_reference(args, ws, rank)
     if args.mvm_only:
         return run_mvm_only(args, local)
+    if args.pcg_probe:
+        return run_pcg_probe(args, local)
     if args.serving:
         return run_serving(args, local)
     if args.batched:
