@@ -3,11 +3,13 @@
 Requests (a point set, a right-hand side and kernel parameters) arrive over
 time.  The dispatcher admits them in arrival order as soon as a slot is free
 and the device-memory budget has room for the request's estimated footprint
-(``fgk_bytes_estimate``).  Each admitted request runs on a worker thread with
-its own CUDA stream: host->device copies, ``fgk_build`` (its sort and
-dominance structure stay on the device for the request's lifetime),
-``fgk_cg_solve`` (its CG state stays on the device), the device->host copy of
-alpha, ``fgk_destroy``.  The solves of all admitted requests overlap on the
+(``fgk_bytes_estimate`` plus the preconditioner's factor).  Each admitted
+request runs on a worker thread with its own CUDA stream: host->device
+copies, ``fgk_build`` (its sort and dominance structure stay on the device
+for the request's lifetime), the pivoted-Cholesky preconditioner
+(``fgk_precond_build``, rank min(precond_rank, N / 8); 0 turns it off),
+the preconditioned solve (its CG state stays on the device), the
+device->host copy of alpha, ``fgk_destroy``.  The solves of all admitted requests overlap on the
 device; a request leaves as soon as its own solve converges, freeing its slot
 and memory for the next arrival.  Latency is measured from arrival to the
 result being on the host.
@@ -75,7 +77,11 @@ class Stats:
     results: list = field(default_factory=list)
 
 
-def gpu_executor(mode: str = "mixed", maxit: int = 200000):
+def precond_rank_for(N: int, precond_rank: int) -> int:
+    return max(0, min(int(precond_rank), int(N) // 8))
+
+
+def gpu_executor(mode: str = "mixed", maxit: int = 200000, precond_rank: int = 100):
     """The real executor: one request, start to end, on a private stream."""
     import torch
 
@@ -88,22 +94,32 @@ def gpu_executor(mode: str = "mixed", maxit: int = 200000):
             y = torch.as_tensor(np.ascontiguousarray(req.y).reshape(-1, 1)).pin_memory().to("cuda",
                                                                                            non_blocking=True)
             h = fgk.fgk_build(X, req.nu, req.ell, kind=req.kind, stream=stream)
+            pc = None
             try:
+                k = precond_rank_for(req.N, precond_rank)
+                if k > 0 and req.sigma2 > 0:
+                    pc = fgk.fgk_precond_build(h, k, req.sigma2, stream=stream)
                 alpha, _, info, rc = fgk.fgk_cg_solve(h, y, req.sigma2, tol=req.tol, maxit=maxit, mode=mode,
-                                                      stream=stream)
+                                                      stream=stream, precond=pc)
                 a = alpha.cpu().numpy().reshape(-1)
             finally:
+                if pc is not None:
+                    fgk.fgk_precond_destroy(pc)
                 fgk.fgk_destroy(h)
         return a, info, rc
 
     return run
 
 
-def gpu_estimator(nrhs_cols: int = 1):
+def gpu_estimator(nrhs_cols: int = 1, precond_rank: int = 100):
     from . import fgk
 
     def est(req: Request) -> int:
-        return int(fgk.fgk_bytes_estimate(req.N, req.d, req.nu, req.kind, nrhs_cols)) + req.N * (req.d + 3) * 8
+        k = precond_rank_for(req.N, precond_rank)
+        # factor (float pairs), residual diagonal, Gram partials of the build (<= 64 x k x k), apply scratch
+        pc_bytes = req.N * (k + 1) * 8 + 66 * k * k * 8 + 304 * k * 8 + (1 << 20) if k > 0 else 0
+        return (int(fgk.fgk_bytes_estimate(req.N, req.d, req.nu, req.kind, nrhs_cols)) + req.N * (req.d + 3) * 8
+                + pc_bytes)
 
     return est
 
