@@ -7,6 +7,8 @@ Everything here is plain FP64 on the CPU:
 
 * ``mvm_brute``  O1, the definition of K V (C, OpenMP, compensated sums);
 * ``kmat``       the dense matrix K for small N; ``kcols`` selected columns;
+  ``kcross``      the cross-covariance between evaluation points and the data
+  (the vector k_z of the posterior mean, eq. gp_mean);
 * ``mvm_dc``     O2, the paper's ECDF decomposition evaluated literally by a
   re-sorting divide and conquer (C);
 * ``structure``  O3, canonical sort permutations and the dominance-level
@@ -22,6 +24,7 @@ from .core import (  # noqa: F401
     PRODUCT,
     build,
     kcols,
+    kcross,
     kernel,
     kmat,
     max_threads,

@@ -53,6 +53,9 @@ def _load():
         lib.orc_kcols.restype = ctypes.c_int
         lib.orc_kcols.argtypes = [D, ctypes.c_long, ctypes.c_int, ctypes.c_int, D, ctypes.c_double,
                                   ctypes.c_int, Lp, ctypes.c_long, D]
+        lib.orc_kcross.restype = ctypes.c_int
+        lib.orc_kcross.argtypes = [D, ctypes.c_long, D, ctypes.c_long, ctypes.c_int, ctypes.c_int, D,
+                                   ctypes.c_double, ctypes.c_int, D]
         lib.orc_mvm_dc.restype = ctypes.c_int
         lib.orc_mvm_dc.argtypes = [D, ctypes.c_long, ctypes.c_int, ctypes.c_int, D, ctypes.c_double,
                                    ctypes.c_int, D, ctypes.c_int, D]
@@ -153,6 +156,18 @@ def kcols(X, idx, nu, ell, s2: float = 1.0, kind: int = L1) -> np.ndarray:
     if lib.orc_kcols(_dp(X), N, d, _two_nu(nu), _dp(ell), float(s2), int(kind),
                      idx.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), idx.size, _dp(C)) != 0:
         raise ValueError("orc_kcols rejected its arguments")
+    return C
+
+
+def kcross(X, Z, nu, ell, s2: float = 1.0, kind: int = L1) -> np.ndarray:
+    """Dense cross-covariance [K(z_j, x_i)] (M x N), the rows k_z^T of eq. gp_mean."""
+    lib = _load()
+    X, d, ell = _prep(X, ell)
+    Z = np.ascontiguousarray(np.asarray(Z, dtype=np.float64).reshape(-1, d))
+    N, M = X.shape[0], Z.shape[0]
+    C = np.empty((M, N))
+    if lib.orc_kcross(_dp(X), N, _dp(Z), M, d, _two_nu(nu), _dp(ell), float(s2), int(kind), _dp(C)) != 0:
+        raise ValueError("orc_kcross rejected its arguments")
     return C
 
 

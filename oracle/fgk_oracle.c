@@ -18,6 +18,9 @@
  *  orc_kmat        the dense matrix K itself (small N), same definition.
  *  orc_kcols       selected columns K[:, idx] (the pivoted Cholesky of the
  *                  preconditioner needs one column per step), same definition.
+ *  orc_kcross      the cross-covariance [K(z_j, x_i)] between evaluation
+ *                  points Z and the data X (the vector k_z of eq. gp_mean),
+ *                  same definition.
  *  orc_mvm_dc      O2: the paper's own algorithm, written in its order and
  *                  notation: weighted ECDFs with the generalised inequality
  *                  (eq. ECDFdelta), one per orthant delta and weight vector,
@@ -181,6 +184,19 @@ int orc_kcols(const double *X, long N, int d, int two_nu, const double *ell, dou
         for (long c = 0; c < nidx; ++c)
             C[i * nidx + c] = s2 * kern_pair(U + i * d, U + idx[c] * d, d, two_nu, kind);
     free(U);
+    return 0;
+}
+
+int orc_kcross(const double *X, long N, const double *Zp, long M, int d, int two_nu, const double *ell, double s2,
+               int kind, double *C)
+{
+    if (check_args(N, d, two_nu, ell, kind) || M < 1) return -1;
+    double *U = scaled_coords(X, N, d, ell);
+    double *V = scaled_coords(Zp, M, d, ell);
+    for (long j = 0; j < M; ++j)
+        for (long i = 0; i < N; ++i) C[j * N + i] = s2 * kern_pair(V + j * d, U + i * d, d, two_nu, kind);
+    free(U);
+    free(V);
     return 0;
 }
 

@@ -23,6 +23,9 @@ TEST INFRASTRUCTURE ONLY.
                   estimator and Algorithm 1), then alpha = A^{-1}(y - H beta),
                   the weights of eq. gp_mean with m(x) = H beta.
 * ``true_residual``  ||b - A x|| / ||b|| per column, A applied by a callable.
+* ``posterior_mean``  E[f(z) | x, y] = k_z^T alpha + h(z)^T beta (eq. gp_mean,
+                  with alpha = (K + sigma^2 I)^{-1}(y - H beta) as eq. gp_mean_2),
+                  given the cross-covariance rows k_z^T.
 """
 
 from __future__ import annotations
@@ -141,3 +144,11 @@ def true_residual(apply_A, X, B):
     X = np.asarray(X, dtype=np.float64).reshape(B.shape)
     R = B - apply_A(X)
     return np.linalg.norm(R, axis=0) / np.linalg.norm(B, axis=0)
+
+
+def posterior_mean(Kzx, alpha, Hz=None, beta=None):
+    """Kzx: M x N cross-covariance; alpha: N (x nrhs); Hz: M x L, beta: L (x nrhs)."""
+    out = np.asarray(Kzx, dtype=np.float64) @ np.asarray(alpha, dtype=np.float64)
+    if Hz is not None:
+        out = out + np.asarray(Hz, dtype=np.float64) @ np.asarray(beta, dtype=np.float64)
+    return out

@@ -48,3 +48,27 @@ def test_gls_normal_equations(orc):
     alpha, beta = solve.gls(lambda B: np.linalg.solve(A, B), y, H)
     assert np.linalg.norm(H.T @ alpha) < 1e-8 * np.linalg.norm(H.T @ np.linalg.solve(A, y))
     assert np.linalg.norm(A @ alpha - (y - H @ beta)) < 1e-10 * np.linalg.norm(y)
+
+
+@pytest.mark.parametrize("d,nu,kind", [(1, 0.5, 0), (2, 1.5, 1), (3, 2.5, 1), (2, 2.5, 0)])
+def test_posterior_mean_at_the_data_is_y_minus_sigma2_alpha(orc, d, nu, kind):
+    """(K + sigma^2 I) alpha = y, so the posterior mean at the training
+    points, K alpha (eq. gp_mean_2 with z = x_i), equals y - sigma^2 alpha."""
+    p = workloads.small(41 + d, 300, d, nu=nu, ell=[0.2, 0.3, 0.4][:d], nrhs=2)
+    s2 = 0.05
+    K = orc.kmat(p.X, nu, p.ell, kind=kind)
+    alpha = solve.dense_solve(K, s2, p.V)
+    m = solve.posterior_mean(orc.kcross(p.X, p.X, nu, p.ell, kind=kind), alpha)
+    assert np.allclose(m, p.V - s2 * alpha, rtol=1e-9, atol=1e-10)
+
+
+def test_posterior_mean_cross_covariance_is_symmetric_and_matches_the_kernel(orc):
+    p = workloads.small(47, 50, 2, nu=1.5, ell=[0.2, 0.3])
+    Z = np.random.default_rng(3).uniform(-0.2, 1.2, size=(7, 2))
+    C = orc.kcross(p.X, Z, 1.5, p.ell, s2=1.7, kind=1)
+    # K(z, x) = K(x, z): the data as evaluation points of the new points
+    assert np.allclose(C, orc.kcross(Z, p.X, 1.5, p.ell, s2=1.7, kind=1).T, rtol=0, atol=0)
+    # the product kernel of the closed-form 1-D kernels
+    u = np.abs(Z[:, None, :] - p.X[None, :, :]) * np.sqrt(3.0) / p.ell
+    ref = 1.7 * np.prod((1 + u) * np.exp(-u), axis=2)
+    assert np.allclose(C, ref, rtol=1e-13, atol=1e-15)
