@@ -175,6 +175,26 @@ typedef struct {
 int fgk_cg_solve(fgk_handle h, const double *y, int nrhs, double sigma2, const double *H, int L, double tol,
                  int maxit, int mode, double *alpha, double *beta, fgk_cg_info *info, fgk_stream_t stream);
 
+/* The posterior mean at M evaluation points (eq. gp_mean; eq. gp_mean_2 once
+ * alpha is known): out[j] = sum_i K(z_j, x_i) alpha_i + h(z_j)^T beta.
+ *   h          the plan of the data X (kernel, nu, lengthscales, outscale2).
+ *   alpha      device, N x nrhs FP64 row-major, original point order (as
+ *              fgk_cg_solve returns it).
+ *   Z, M       device, M x d FP64 row-major, unscaled coordinates; M >= 1.
+ *   HZ, L      fixed effects at the new points: HZ == NULL && L == 0: none;
+ *              HZ == NULL && L == -1: the default h(z) = [1, z_1..z_d];
+ *              HZ != NULL: device M x L FP64 row-major, 1 <= L <= 8.
+ *   beta       device, L x nrhs FP64 (from fgk_cg_solve), required when L != 0.
+ *   precision  FGK_F64 or FGK_F32: the scans of the product.
+ *   out        device, M x nrhs FP64 (output).
+ * Method: one product over the union of the data and the new points with
+ * weights [alpha; 0], read at the new points -- exact (the definition of
+ * k_z^T alpha), at the cost of building the union's structure (N + M points).
+ * Errors: FGK_ERR_INVALID, FGK_ERR_NONFINITE (alpha or Z), FGK_ERR_OOM.
+ * Synchronises `stream`. */
+int fgk_predict(fgk_handle h, const double *alpha, int nrhs, const double *Z, int64_t M, const double *HZ, int L,
+                const double *beta, int precision, double *out, fgk_stream_t stream);
+
 /* ---- the pivoted-Cholesky preconditioner (App. A.3) ---- */
 
 typedef struct fgk_precond_s *fgk_precond;

@@ -348,7 +348,6 @@ __global__ void k_sum(const double *__restrict__ a, int64_t n, double *__restric
 // returns.
 constexpr int kTR = 256;      // rows per tile (= threads per CTA)
 constexpr int kMC = 32;       // rank indices per chunk
-constexpr int kColsPass = 8;  // right-hand sides per pass over the tiles
 constexpr int kSpinLimit = 1 << 22;
 constexpr int kApplyCtas = 2 * 152;
 
@@ -753,7 +752,6 @@ int pc_apply(const Precond *pc, const double *R, int ncols, double *Z, double *r
         set_error("preconditioner apply: ncols = %d is outside [1, %d] (internal)", ncols, pc->cap_cols);
         return FGK_ERR_INTERNAL;
     }
-    const Plan *p = pc->plan;
     const int r = pc->rank, nb = pc->nb_ltr;
     int *err = pc->ints + 2;
     const int nc = cols_per_pass(ncols);

@@ -60,7 +60,7 @@ EXPORTS = ["fgk_set_allocator", "fgk_build", "fgk_matvec", "fgk_matvec_q", "fgk_
            "fgk_get_permutation", "fgk_get_level", "fgk_batch_create", "fgk_batch_layout", "fgk_batch_matvec_q",
            "fgk_batch_cg_solve", "fgk_batch_destroy", "fgk_precond_build", "fgk_precond_info",
            "fgk_precond_factor", "fgk_precond_apply", "fgk_precond_destroy", "fgk_cg_solve_pc",
-           "fgk_kernel_timing"]
+           "fgk_kernel_timing", "fgk_predict"]
 
 _lock = threading.Lock()
 _lib = None
@@ -132,6 +132,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.fgk_cg_solve_pc.argtypes = [vp, vp, vp, i32, dbl, vp, i32, dbl, i32, i32, vp, vp,
                                         ctypes.POINTER(fgk_cg_info), vp]
         lib.fgk_cg_solve_pc.restype = i32
+        lib.fgk_predict.argtypes = [vp, vp, i32, vp, i64, vp, i32, vp, i32, vp, vp]
+        lib.fgk_predict.restype = i32
         _lib = lib
         return lib
 
@@ -366,6 +368,30 @@ def fgk_precond_destroy(pc: Precond) -> None:
     if pc is not None and pc.ptr:
         _check(load().fgk_precond_destroy(pc.ptr))
         pc.ptr = 0
+
+
+def fgk_predict(h: Handle, alpha: torch.Tensor, Z: torch.Tensor, beta: torch.Tensor | None = None,
+                HZ: torch.Tensor | None = None, L: int = 0, precision="f64", stream=None) -> torch.Tensor:
+    """Posterior mean at the rows of Z (eq. gp_mean): K(Z, X) alpha (+ h(Z) beta)."""
+    a2 = _dev_f64_2d(alpha, "alpha")
+    Z2 = _dev_f64_2d(Z, "Z")
+    if Z2.shape[1] != h.d:
+        raise ValueError("Z must have d columns")
+    prec = {"f64": FGK_F64, "f32": FGK_F32}[precision] if isinstance(precision, str) else int(precision)
+    Hp, bp = 0, 0
+    if HZ is not None:
+        HZ = _dev_f64_2d(HZ, "HZ")
+        L = HZ.shape[1]
+        Hp = HZ.data_ptr()
+    if L != 0:
+        if beta is None:
+            raise ValueError("fixed effects need beta")
+        beta = _dev_f64_2d(beta, "beta")
+        bp = beta.data_ptr()
+    out = torch.empty((Z2.shape[0], a2.shape[1]), dtype=torch.float64, device=a2.device)
+    _check(load().fgk_predict(h.ptr, a2.data_ptr(), a2.shape[1], Z2.data_ptr(), Z2.shape[0], Hp, int(L), bp, prec,
+                              out.data_ptr(), _stream(stream)))
+    return out.squeeze(1) if alpha.dim() == 1 else out
 
 
 def fgk_bytes_estimate(N: int, d: int, nu, kind="l1", nrhs: int = 1) -> int:
