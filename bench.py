@@ -189,7 +189,7 @@ def run_batched(args, local):
     probs = workloads.c4(n_problems=args.batched)
     nrhs = probs[0].V.shape[1]
     t0 = time.perf_counter()
-    eng = batch.BatchEngine(probs, nrhs, kind="product")
+    eng = batch.BatchEngine(probs, nrhs, kind="product", precond_rank=args.batched_rank)
     t_setup = time.perf_counter() - t0
     ys = [torch.as_tensor(p.V, device="cuda") for p in probs]
     sig = [p.sigma2 for p in probs]
@@ -208,6 +208,7 @@ def run_batched(args, local):
     mvm_ms = e0.elapsed_time(e1) / 10
     times = []
     for _ in range(max(args.steps, 1)):
+        eng._free_precs()  # each timed solve builds its preconditioners
         torch.cuda.synchronize()
         e0.record()
         alphas, infos, rc = eng.solve(ys, sig, tol=TOL, maxit=200000)
@@ -234,6 +235,7 @@ def run_batched(args, local):
     out = {"metric": "batched: CG solves/sec at resid<=1e-8 (problems x rhs) and MVM N*nrhs/sec",
            "unit": "solves/s", "value": solves / t_batch, "problems": len(probs), "nrhs": nrhs,
            "rows": rows, "rhs_per_cta": eng.rpc, "autotune_ms": eng.timings, "setup_s": t_setup,
+           "precond_rank": args.batched_rank,
            "batch_solve_s": t_batch, "max_iterations": max(i["iterations"] for i in infos),
            "max_true_resid": max(i["max_true_resid"] for i in infos),
            "mvm_ms": mvm_ms, "mvm_nrhs_per_s": rows * nrhs / (mvm_ms * 1e-3),
@@ -356,6 +358,8 @@ def main():
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--batched", type=int, default=0,
                     help="solve the first K problems of the batched workload (16 rhs each) in one batch")
+    ap.add_argument("--batched-rank", type=int, default=100,
+                    help="batched mode: preconditioner rank per problem (min with N/8; 0: none)")
     ap.add_argument("--f64-sample", type=int, default=4,
                     help="batched mode: problems solved one by one in FP64 for the comparison")
     ap.add_argument("--pcg-probe", type=int, default=0,

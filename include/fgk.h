@@ -285,6 +285,15 @@ int fgk_batch_matvec_q(fgk_batch b, const float *Vq, float *Yq, fgk_stream_t str
 int fgk_batch_cg_solve(fgk_batch b, const double *const *y, const double *sigma2, double tol, int maxit,
                        double *const *alpha, fgk_cg_info *info, fgk_stream_t stream);
 
+/* fgk_batch_cg_solve with one preconditioner per problem (pcs[i] built with
+ * fgk_precond_build on problem i's plan for sigma2[i]): every iteration
+ * applies each active problem's P^{-1} inside the captured graph; the mixed
+ * refinement then replaces at a drop by FGK_MIXED_DELTA (default 1e-3) and
+ * restarts every replaced column from p = P^{-1} r (as fgk_cg_solve_pc).
+ * The preconditioners must outlive the call. */
+int fgk_batch_cg_solve_pc(fgk_batch b, const fgk_precond *pcs, const double *const *y, const double *sigma2,
+                          double tol, int maxit, double *const *alpha, fgk_cg_info *info, fgk_stream_t stream);
+
 int fgk_batch_destroy(fgk_batch b);
 
 /* Upper estimate, in bytes, of the device memory a handle for these sizes

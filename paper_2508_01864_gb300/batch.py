@@ -2,7 +2,10 @@
 
 ``BatchEngine`` builds one plan per problem, groups them into one libfgk batch
 (one launch per phase of the product for the whole batch, the CG iteration a
-captured CUDA graph) and solves all problems and right-hand sides together.
+captured CUDA graph) and solves all problems and right-hand sides together,
+optionally with one pivoted-Cholesky preconditioner per problem (rank
+min(precond_rank, N / 8), built for the sigma^2 of the solve and kept for
+later solves with the same sigma^2).
 
 The autotuner chooses how many right-hand sides one CTA scans (more per CTA
 reuses each tile's loaded structure; fewer gives more CTAs): it times the
@@ -78,7 +81,7 @@ def pick(timings: dict) -> int:
 
 class BatchEngine:
     def __init__(self, problems, nrhs: int, kind: str = "product", autotune: bool = True, reps: int = 5,
-                 stream=None):
+                 stream=None, precond_rank: int = 0):
         import torch
 
         from . import fgk
@@ -86,6 +89,10 @@ class BatchEngine:
         self.fgk = fgk
         self.problems = problems
         self.nrhs = int(nrhs)
+        self.precond_rank = int(precond_rank)
+        self.precs = None
+        self.precs_sigma2 = None
+        self.stream = stream
         self.handles = [fgk.fgk_build(torch.as_tensor(p.X, device="cuda"), p.nu, p.ell, kind=kind, stream=stream)
                         for p in problems]
         variants = [f"d{p.d}nu{p.nu}" for p in problems]
@@ -130,10 +137,30 @@ class BatchEngine:
     def matvec(self, Vq, out=None):
         return self.fgk.fgk_batch_matvec_q(self.batch, Vq, out=out)
 
+    def preconditioners(self, sigma2s):
+        """One rank-min(precond_rank, N/8) preconditioner per problem for these sigma^2."""
+        key = [float(x) for x in sigma2s]
+        if self.precs is not None and self.precs_sigma2 == key:
+            return self.precs
+        self._free_precs()
+        self.precs = [self.fgk.fgk_precond_build(h, max(0, min(self.precond_rank, p.N // 8)), s2, stream=self.stream)
+                      for h, p, s2 in zip(self.handles, self.problems, key)]
+        self.precs_sigma2 = key
+        return self.precs
+
     def solve(self, ys, sigma2s, tol: float = 1e-8, maxit: int = 100000):
-        return self.fgk.fgk_batch_cg_solve(self.batch, ys, sigma2s, tol=tol, maxit=maxit)
+        precs = self.preconditioners(sigma2s) if self.precond_rank > 0 else None
+        return self.fgk.fgk_batch_cg_solve(self.batch, ys, sigma2s, tol=tol, maxit=maxit, precs=precs)
+
+    def _free_precs(self):
+        if self.precs:
+            for q in self.precs:
+                self.fgk.fgk_precond_destroy(q)
+        self.precs = None
+        self.precs_sigma2 = None
 
     def close(self):
+        self._free_precs()
         self.fgk.fgk_batch_destroy(self.batch)
         for h in self.handles:
             self.fgk.fgk_destroy(h)

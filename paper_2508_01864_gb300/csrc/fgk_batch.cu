@@ -17,7 +17,11 @@
 // product + three vector kernels) is captured once as a CUDA graph and
 // replayed.  A problem whose columns have all stopped is skipped by every
 // kernel.  Residual replacements (FP64 products) are taken per problem with
-// the single-plan FP64 product, spaced by the measured cost ratio.
+// the single-plan FP64 product, spaced by the measured cost ratio.  With
+// per-problem pivoted-Cholesky preconditioners (fgk_batch_cg_solve_pc) the
+// iteration also applies each problem's P^{-1} (gated on the problem being
+// active), rho = r^T z and p = z + beta p, and replacements restart every
+// column from p = z (plain refinement with delta = 1e-3, as fgk_cg_solve_pc).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -159,6 +163,7 @@ __global__ void k_batch_diag(const float *__restrict__ V, float *__restrict__ Y,
 // ------------------------------------------------------------------ batched CG
 struct BState {
     double *rho, *rho_next, *thr2;
+    double *rr;  // recursive ||r||^2 after the last p-update (rho is r^T z)
     int *active, *active_next, *iters;
     int *prob_active, *prob_active_next;
     int *bd;  // per column: met p^T A p <= 0 in FP32 (cleared by the host)
@@ -258,11 +263,13 @@ __global__ void k_bupdate_xr(double *__restrict__ x, double *__restrict__ r, con
         partial + (size_t)blockIdx.x * nrhs, red);
 }
 
+// r: the new direction's source (z = P^{-1} r with preconditioners, else r);
+// rz_partial: chunk partials of r^T z (NULL: rho is ||r||^2)
 __global__ void k_bupdate_p(double *__restrict__ p, float *__restrict__ p32, float *__restrict__ w,
                             const double *__restrict__ r, const BatchProb *__restrict__ probs,
                             const Chunk *__restrict__ chunks, const int *__restrict__ prob_c0,
                             const int *__restrict__ prob_nc, int nrhs, const double *__restrict__ rr_partial,
-                            BState st) {
+                            const double *__restrict__ rz_partial, BState st) {
     __shared__ double s_beta[64];
     __shared__ int s_act[64];
     const Chunk c = chunks[blockIdx.x];
@@ -271,15 +278,17 @@ __global__ void k_bupdate_p(double *__restrict__ p, float *__restrict__ p32, flo
     const int c0 = prob_c0[c.prob], nc = prob_nc[c.prob];
     for (int j = warp; j < nrhs; j += nw) {
         const double rr = warp_prob_sum(rr_partial, c0, nc, nrhs, j, lane);
+        const double rz = rz_partial ? warp_prob_sum(rz_partial, c0, nc, nrhs, j, lane) : rr;
         if (lane == 0) {
             const int col = c.prob * nrhs + j;
             const int act = st.active[col];
             const double rho = st.rho[col];
             const int still = act && !st.bd[col] && rr > st.thr2[col];
-            s_beta[j] = act ? (rho > 0.0 ? rr / rho : 0.0) : 0.0;
+            s_beta[j] = act ? (rho > 0.0 ? rz / rho : 0.0) : 0.0;
             s_act[j] = still;
             if (c.first) {
-                st.rho_next[col] = act ? rr : rho;
+                st.rho_next[col] = act ? rz : rho;
+                if (act) st.rr[col] = rr;
                 st.active_next[col] = still;
                 if (act) st.iters[col] += 1;
             }
@@ -344,6 +353,19 @@ __global__ void k_brestart(double *__restrict__ P, const double *__restrict__ R,
     const Chunk c = chunks[blockIdx.x];
     for (int64_t t = (int64_t)c.row0 * nrhs + threadIdx.x; t < (int64_t)c.row1 * nrhs; t += blockDim.x)
         if (bd[c.prob * nrhs + (int)(t % nrhs)]) P[t] = R[t];
+}
+
+// r_j^T z_j per chunk (partials), for active problems (gate: prob_active_next
+// as the p-update of this iteration reads it)
+__global__ void k_chunk_rz(const double *__restrict__ R, const double *__restrict__ Zv,
+                           const Chunk *__restrict__ chunks, int nrhs, const int *__restrict__ prob_active,
+                           double *__restrict__ partial) {
+    __shared__ double red[kRedThreads];
+    const Chunk c = chunks[blockIdx.x];
+    if (prob_active && prob_active[c.prob] == 0) return;
+    chunk_col_sums(
+        c, nrhs, [&](int64_t row, int j) { return R[row * nrhs + j] * Zv[row * nrhs + j]; },
+        partial + (size_t)blockIdx.x * nrhs, red);
 }
 
 // squared column norms per chunk (partials; summed per problem by k_prob_sums)
@@ -576,8 +598,8 @@ int fgk_batch_matvec_q(fgk_batch b, const float *Vq, float *Yq, fgk_stream_t str
     return batch_product(b, Vq, Yq, nullptr, s);
 }
 
-int fgk_batch_cg_solve(fgk_batch b, const double *const *y, const double *sigma2, double tol, int maxit,
-                       double *const *alpha, fgk_cg_info *info, fgk_stream_t stream) {
+static int batch_cg(fgk_batch b, const fgk_precond *pch, const double *const *y, const double *sigma2, double tol,
+                    int maxit, double *const *alpha, fgk_cg_info *info, fgk_stream_t stream) {
     clear_error();
     if (!b || !y || !sigma2 || !alpha || !(tol > 0.0) || maxit < 1) {
         set_error("fgk_batch_cg_solve: bad argument");
@@ -589,6 +611,20 @@ int fgk_batch_cg_solve(fgk_batch b, const double *const *y, const double *sigma2
             set_error("fgk_batch_cg_solve: problem %d has a NULL vector or a bad sigma2", i);
             return FGK_ERR_INVALID;
         }
+    std::vector<Precond *> pcs;
+    if (pch) {
+        for (int i = 0; i < n; ++i) {
+            Precond *pc = pc_of(pch[i]);
+            if (!pc || pc_plan(pc) != b->plans[i] || pc_sigma2(pc) != sigma2[i]) {
+                set_error("fgk_batch_cg_solve_pc: preconditioner %d is NULL or was built for another plan or sigma2",
+                          i);
+                return FGK_ERR_INVALID;
+            }
+            FGK_TRY(pc_reserve(pc, nrhs, (cudaStream_t)stream));
+            pcs.push_back(pc);
+        }
+    }
+    const bool pcon = !pcs.empty();
     cudaStream_t us = (cudaStream_t)stream;
     cudaStream_t s;
     FGK_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
@@ -609,7 +645,10 @@ int fgk_batch_cg_solve(fgk_batch b, const double *const *y, const double *sigma2
     double *pw_part = (double *)take((size_t)b->nchunk * nrhs * 8), *rr_part = (double *)take((size_t)b->nchunk * nrhs * 8);
     double *sig2 = (double *)take(n * 8), *nrm = (double *)take((size_t)C * 8);
     double *nrm_part = (double *)take((size_t)b->nchunk * nrhs * 8);
+    double *Zv = pcon ? (double *)take(vec * 8) : nullptr;
+    double *rz_part = pcon ? (double *)take((size_t)b->nchunk * nrhs * 8) : nullptr;
     BState st;
+    st.rr = (double *)take(C * 8);
     st.rho = (double *)take(C * 8);
     st.rho_next = (double *)take(C * 8);
     st.thr2 = (double *)take(C * 8);
@@ -623,7 +662,7 @@ int fgk_batch_cg_solve(fgk_batch b, const double *const *y, const double *sigma2
     int rc = FGK_OK;
     for (void *q : mine)
         if (!q) rc = FGK_ERR_OOM;
-    std::vector<double> bnorm(C), rnorm(C), rho_ref(C), hrho(C), hthr2(C), hnorm(C);
+    std::vector<double> bnorm(C), rnorm(C), rho_ref(C), hrho(C), hthr2(C), hnorm(C), hrr(C), hrz(C);
     std::vector<int> hact(C), hiters(C, 0), confirmed(C, 0), hpa(n), last_repl(n, 0);
     // gap[i]: min_gap[i] while problem i's last replacement found a true
     // residual within twice the recursive one, else 0 (the FP32 recursion was
@@ -636,7 +675,7 @@ int fgk_batch_cg_solve(fgk_batch b, const double *const *y, const double *sigma2
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     uint64_t graph_nodes = 0;
-    const double delta = env_double_b("FGK_MIXED_DELTA", 0.5);
+    const double delta = env_double_b("FGK_MIXED_DELTA", pcon ? 1e-3 : 0.5);
     const int check_every = 8;
 
     // squared column norms of every problem's slice of A into hnorm (one sync)
@@ -666,9 +705,25 @@ int fgk_batch_cg_solve(fgk_batch b, const double *const *y, const double *sigma2
             for (int j = 0; j < nrhs; ++j) rnorm[i * nrhs + j] = std::sqrt(hnorm[i * nrhs + j]);
         return FGK_OK;
     };
+    // z = P^{-1} r for every problem and r^T z per column into hrz (one sync)
+    auto precondition = [&]() -> int {
+        for (int i = 0; i < n; ++i) {
+            const size_t o = (size_t)b->voff[i] * nrhs;
+            FGK_TRY(pc_apply(pcs[i], Rv + o, nrhs, Zv + o, nullptr, s));
+        }
+        k_chunk_rz<<<b->nchunk, kRedThreads, 0, s>>>(Rv, Zv, b->chunks, nrhs, nullptr, nrm_part);
+        FGK_LAUNCH_CHECK();
+        k_prob_sums<<<grid_for((int64_t)C * 32, 256), 256, 0, s>>>(nrm_part, b->prob_c0, b->prob_nc, n, nrhs, nrm);
+        FGK_LAUNCH_CHECK();
+        FGK_CUDA(cudaMemcpyAsync(hrz.data(), nrm, (size_t)C * 8, cudaMemcpyDeviceToHost, s));
+        FGK_CUDA(cudaStreamSynchronize(s));
+        for (int i = 0; i < n; ++i) FGK_TRY(pc_check(pcs[i], s));
+        return FGK_OK;
+    };
     auto upload_state = [&]() -> int {
         std::vector<int> pa(n, 0);
         for (int c = 0; c < C; ++c) pa[c / nrhs] += hact[c];
+        FGK_CUDA(cudaMemcpyAsync(st.rr, hrr.data(), C * 8, cudaMemcpyHostToDevice, s));
         FGK_CUDA(cudaMemcpyAsync(st.rho, hrho.data(), C * 8, cudaMemcpyHostToDevice, s));
         FGK_CUDA(cudaMemcpyAsync(st.rho_next, hrho.data(), C * 8, cudaMemcpyHostToDevice, s));
         FGK_CUDA(cudaMemcpyAsync(st.thr2, hthr2.data(), C * 8, cudaMemcpyHostToDevice, s));
@@ -697,9 +752,14 @@ int fgk_batch_cg_solve(fgk_batch b, const double *const *y, const double *sigma2
         if ((rc = all_norms(Bv))) break;
         for (int c = 0; c < C; ++c) bnorm[c] = std::sqrt(hnorm[c]);
         rnorm = bnorm;
+        if (pcon) {  // p = z = P^{-1} b, rho = b^T z
+            if ((rc = precondition())) break;
+            FGK_CUDA(cudaMemcpyAsync(Pv, Zv, vec * 8, cudaMemcpyDeviceToDevice, s));
+        }
         for (int c = 0; c < C; ++c) {
-            hrho[c] = rnorm[c] * rnorm[c];
-            rho_ref[c] = hrho[c];
+            hrr[c] = rnorm[c] * rnorm[c];
+            hrho[c] = pcon ? hrz[c] : hrr[c];
+            rho_ref[c] = hrr[c];
             const double t = 0.5 * tol * bnorm[c];
             hthr2[c] = t * t;
             confirmed[c] = rnorm[c] <= tol * bnorm[c];
@@ -751,8 +811,17 @@ int fgk_batch_cg_solve(fgk_batch b, const double *const *y, const double *sigma2
                 k_bupdate_xr<<<b->nchunk, kRedThreads, 0, s>>>(X, Rv, Pv, W32, sig2, b->chunks, b->prob_c0,
                                                                b->prob_nc, nrhs, pw_part, rr_part, st);
                 add_kernel_launches(1);
-                k_bupdate_p<<<b->nchunk, kRedThreads, 0, s>>>(Pv, P32, W32, Rv, b->probs, b->chunks, b->prob_c0,
-                                                              b->prob_nc, nrhs, rr_part, st);
+                if (pcon) {
+                    for (int i = 0; i < n && !crc; ++i) {
+                        const size_t o = (size_t)b->voff[i] * nrhs;
+                        crc = pc_apply(pcs[i], Rv + o, nrhs, Zv + o, nullptr, s, st.prob_active + i);
+                    }
+                    k_chunk_rz<<<b->nchunk, kRedThreads, 0, s>>>(Rv, Zv, b->chunks, nrhs, st.prob_active, rz_part);
+                    add_kernel_launches(1);
+                }
+                k_bupdate_p<<<b->nchunk, kRedThreads, 0, s>>>(Pv, P32, W32, pcon ? Zv : Rv, b->probs, b->chunks,
+                                                              b->prob_c0, b->prob_nc, nrhs, rr_part,
+                                                              pcon ? rz_part : nullptr, st);
                 add_kernel_launches(1);
             }
             cudaError_t ce = cudaStreamEndCapture(s, &graph);
@@ -766,7 +835,7 @@ int fgk_batch_cg_solve(fgk_batch b, const double *const *y, const double *sigma2
             FGK_CUDA(cudaGraphInstantiate(&gexec, graph, 0));
         }
         std::vector<int> snap_act(C), snap_iters(C);
-        std::vector<double> snap_rho(C);
+        std::vector<double> snap_rho(C), snap_rr(C);
         int hbreak = 0;
         while (true) {
             bool all = true;
@@ -781,6 +850,7 @@ int fgk_batch_cg_solve(fgk_batch b, const double *const *y, const double *sigma2
             add_kernel_launches((int64_t)graph_nodes * k);
             FGK_CUDA(cudaMemcpyAsync(snap_act.data(), st.active_next, C * 4, cudaMemcpyDeviceToHost, s));
             FGK_CUDA(cudaMemcpyAsync(snap_rho.data(), st.rho_next, C * 8, cudaMemcpyDeviceToHost, s));
+            FGK_CUDA(cudaMemcpyAsync(snap_rr.data(), st.rr, C * 8, cudaMemcpyDeviceToHost, s));
             FGK_CUDA(cudaMemcpyAsync(snap_iters.data(), st.iters, C * 4, cudaMemcpyDeviceToHost, s));
             FGK_CUDA(cudaMemcpyAsync(&hbreak, st.breakdown, 4, cudaMemcpyDeviceToHost, s));
             FGK_CUDA(cudaStreamSynchronize(s));
@@ -826,19 +896,23 @@ int fgk_batch_cg_solve(fgk_batch b, const double *const *y, const double *sigma2
                     const int c = i * nrhs + j;
                     if (confirmed[c]) continue;
                     if (!snap_act[c]) claims = true;
-                    if (snap_rho[c] <= delta * delta * rho_ref[c]) dropped = true;
+                    if (snap_rr[c] <= delta * delta * rho_ref[c]) dropped = true;
                 }
                 if (broken[i] || claims || (dropped && iters_total - last_repl[i] >= gap[i])) todo.push_back(i);
             }
             if (todo.empty()) continue;
             for (int c = 0; c < C; ++c) {
                 hrho[c] = snap_rho[c];
+                hrr[c] = snap_rr[c];
                 hact[c] = snap_act[c];
             }
             if ((rc = residuals(todo))) break;
-            // restart p = r on the columns whose direction no longer fits the
-            // replaced residual (as fgk_cg_solve): an FP32 breakdown, a column
-            // that had stopped, or a true residual above twice the recursive one
+            if (pcon && (rc = precondition())) break;  // z and r^T z of the replaced residuals
+            // restart p = z (z = r without preconditioners) on the columns whose
+            // direction no longer fits the replaced residual (as fgk_cg_solve):
+            // every replaced column with a preconditioner; without one, an FP32
+            // breakdown, a column that had stopped, or a true residual above
+            // twice the recursive one
             std::vector<int> rs(C, 0);
             bool any_rs = false;
             for (int i : todo) {
@@ -846,9 +920,9 @@ int fgk_batch_cg_solve(fgk_batch b, const double *const *y, const double *sigma2
                 bool drift = false;
                 for (int j = 0; j < nrhs; ++j) {
                     const int c = i * nrhs + j;
-                    const bool dj = !confirmed[c] && rnorm[c] > 2.0 * std::sqrt(snap_rho[c]);
+                    const bool dj = !confirmed[c] && rnorm[c] > 2.0 * std::sqrt(snap_rr[c]);
                     drift = drift || dj;
-                    rs[c] = !confirmed[c] && ((hbreak && hbd[c]) || !snap_act[c] || dj) &&
+                    rs[c] = !confirmed[c] && (pcon || (hbreak && hbd[c]) || !snap_act[c] || dj) &&
                             !(rnorm[c] <= tol * bnorm[c]);
                     any_rs = any_rs || rs[c];
                 }
@@ -856,7 +930,7 @@ int fgk_batch_cg_solve(fgk_batch b, const double *const *y, const double *sigma2
             }
             if (any_rs) {
                 FGK_CUDA(cudaMemcpyAsync(st.bd, rs.data(), (size_t)C * 4, cudaMemcpyHostToDevice, s));
-                k_brestart<<<b->nchunk, 256, 0, s>>>(Pv, Rv, b->chunks, nrhs, st.bd);
+                k_brestart<<<b->nchunk, 256, 0, s>>>(Pv, pcon ? Zv : Rv, b->chunks, nrhs, st.bd);
                 FGK_LAUNCH_CHECK();
                 k_to_f32_diag<<<b->nchunk, 256, 0, s>>>(Pv, P32, W32, b->probs, b->chunks, nrhs);
                 FGK_LAUNCH_CHECK();
@@ -872,8 +946,9 @@ int fgk_batch_cg_solve(fgk_batch b, const double *const *y, const double *sigma2
                     if (!confirmed[c] && rnorm[c] <= tol * bnorm[c]) confirmed[c] = 1;
                     hact[c] = !confirmed[c];
                     if (!confirmed[c]) {
-                        hrho[c] = rnorm[c] * rnorm[c];
-                        rho_ref[c] = hrho[c];
+                        hrr[c] = rnorm[c] * rnorm[c];
+                        hrho[c] = pcon ? hrz[c] : hrr[c];
+                        rho_ref[c] = hrr[c];
                     }
                 }
                 any = true;
@@ -929,6 +1004,20 @@ int fgk_batch_cg_solve(fgk_batch b, const double *const *y, const double *sigma2
         return FGK_NOT_CONVERGED;
     }
     return FGK_OK;
+}
+
+int fgk_batch_cg_solve(fgk_batch b, const double *const *y, const double *sigma2, double tol, int maxit,
+                       double *const *alpha, fgk_cg_info *info, fgk_stream_t stream) {
+    return batch_cg(b, nullptr, y, sigma2, tol, maxit, alpha, info, stream);
+}
+
+int fgk_batch_cg_solve_pc(fgk_batch b, const fgk_precond *pcs, const double *const *y, const double *sigma2,
+                          double tol, int maxit, double *const *alpha, fgk_cg_info *info, fgk_stream_t stream) {
+    if (!pcs) {
+        set_error("fgk_batch_cg_solve_pc: pcs must not be NULL");
+        return FGK_ERR_INVALID;
+    }
+    return batch_cg(b, pcs, y, sigma2, tol, maxit, alpha, info, stream);
 }
 
 }  // extern "C"

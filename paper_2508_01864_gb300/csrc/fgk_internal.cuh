@@ -190,7 +190,8 @@ int from_q_order(const Plan *p, const void *src, void *dst, int nrhs, int elem_b
 struct Precond;
 constexpr int kPcMaxCols = 64;
 constexpr int kRedThreadsPc = 256;
-int pc_apply(const Precond *pc, const double *R, int ncols, double *Z, double *rz_partial, cudaStream_t s);
+int pc_apply(const Precond *pc, const double *R, int ncols, double *Z, double *rz_partial, cudaStream_t s,
+             const int *gate = nullptr);  // gate: device int, 0 = skip (every kernel returns at once)
 int pc_partial_blocks(const Precond *pc);           // CTAs (rows of partials) pc_apply's rz_partial has
 int pc_check(const Precond *pc, cudaStream_t s);    // reads and clears the apply's error word (syncs)
 int pc_reserve(Precond *pc, int ncols, cudaStream_t s);  // apply scratch for ncols (allocates; not in capture)

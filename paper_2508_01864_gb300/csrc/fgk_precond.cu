@@ -439,7 +439,9 @@ __device__ __forceinline__ int tiles_of_cta(int64_t N) {
 template <int NC>
 __global__ void __launch_bounds__(kTR) k_pc_ltr(const __grid_constant__ CUtensorMap map, int r,
                                                  const double *__restrict__ R, int64_t N, int ncols,
-                                                 double *__restrict__ t_part, int *__restrict__ err) {
+                                                 double *__restrict__ t_part, int *__restrict__ err,
+                                                 const int *__restrict__ gate) {
+    if (gate && *gate == 0) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *buf = reinterpret_cast<float *>(smem_raw);
     F2 *Rs = reinterpret_cast<F2 *>(buf + 2 * kMC * kTR);  // kTR x NC
@@ -514,7 +516,9 @@ __global__ void __launch_bounds__(kTR) k_pc_ltr(const __grid_constant__ CUtensor
 }
 
 // t[m][j] = sum over the gridDim partials (one warp per entry)
-__global__ void k_pc_tsum(const double *__restrict__ t_part, int nb, int r, int ncols, double *__restrict__ t) {
+__global__ void k_pc_tsum(const double *__restrict__ t_part, int nb, int r, int ncols, double *__restrict__ t,
+                          const int *__restrict__ gate) {
+    if (gate && *gate == 0) return;
     const int lane = threadIdx.x & 31;
     const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (e >= (int64_t)r * ncols) return;
@@ -527,7 +531,8 @@ __global__ void k_pc_tsum(const double *__restrict__ t_part, int nb, int r, int 
 
 // c[a][j] = sum_b Cinv[a][b] t[b][j] / sigma2^2 (one warp per entry)
 __global__ void k_pc_cmul(const double *__restrict__ t, int r, int ncols, const double *__restrict__ Cinv,
-                          double sigma2, double *__restrict__ c) {
+                          double sigma2, double *__restrict__ c, const int *__restrict__ gate) {
+    if (gate && *gate == 0) return;
     const int lane = threadIdx.x & 31;
     const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (e >= (int64_t)r * ncols) return;
@@ -548,7 +553,8 @@ __global__ void __launch_bounds__(kTR) k_pc_apply(const __grid_constant__ CUtens
                                                    const double *__restrict__ R, int64_t N, int ncols,
                                                    const double *__restrict__ c, double sigma2,
                                                    double *__restrict__ Z, double *__restrict__ rz_partial,
-                                                   int *__restrict__ err) {
+                                                   int *__restrict__ err, const int *__restrict__ gate) {
+    if (gate && *gate == 0) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *buf = reinterpret_cast<float *>(smem_raw);
     uint64_t *bar = reinterpret_cast<uint64_t *>(buf + 2 * kMC * kTR);
@@ -740,14 +746,16 @@ static int set_pc_attrs(int k) {
 }
 
 template <int NC>
-static int launch_pc_ltr(const Precond *pc, int r, const double *R, int ncols, int *err, cudaStream_t s);
+static int launch_pc_ltr(const Precond *pc, int r, const double *R, int ncols, int *err, cudaStream_t s,
+                         const int *gate);
 template <int NC>
 static int launch_pc_apply(const Precond *pc, int r, const double *R, int ncols, double *Z, double *rz_partial,
-                           int *err, cudaStream_t s);
+                           int *err, cudaStream_t s, const int *gate);
 
 int pc_partial_blocks(const Precond *pc) { return pc->nb_ltr; }
 
-int pc_apply(const Precond *pc, const double *R, int ncols, double *Z, double *rz_partial, cudaStream_t s) {
+int pc_apply(const Precond *pc, const double *R, int ncols, double *Z, double *rz_partial, cudaStream_t s,
+             const int *gate) {
     if (ncols < 1 || ncols > pc->cap_cols) {
         set_error("preconditioner apply: ncols = %d is outside [1, %d] (internal)", ncols, pc->cap_cols);
         return FGK_ERR_INTERNAL;
@@ -757,22 +765,22 @@ int pc_apply(const Precond *pc, const double *R, int ncols, double *Z, double *r
     const int nc = cols_per_pass(ncols);
     if (r > 0) {
         switch (nc) {
-            case 1: FGK_TRY(launch_pc_ltr<1>(pc, r, R, ncols, err, s)); break;
-            case 2: FGK_TRY(launch_pc_ltr<2>(pc, r, R, ncols, err, s)); break;
-            case 4: FGK_TRY(launch_pc_ltr<4>(pc, r, R, ncols, err, s)); break;
-            default: FGK_TRY(launch_pc_ltr<8>(pc, r, R, ncols, err, s)); break;
+            case 1: FGK_TRY(launch_pc_ltr<1>(pc, r, R, ncols, err, s, gate)); break;
+            case 2: FGK_TRY(launch_pc_ltr<2>(pc, r, R, ncols, err, s, gate)); break;
+            case 4: FGK_TRY(launch_pc_ltr<4>(pc, r, R, ncols, err, s, gate)); break;
+            default: FGK_TRY(launch_pc_ltr<8>(pc, r, R, ncols, err, s, gate)); break;
         }
         const unsigned nw_blocks = grid_for((int64_t)r * ncols * 32, 256);
-        k_pc_tsum<<<nw_blocks, 256, 0, s>>>(pc->t_part, nb, r, ncols, pc->tvec);
+        k_pc_tsum<<<nw_blocks, 256, 0, s>>>(pc->t_part, nb, r, ncols, pc->tvec, gate);
         FGK_LAUNCH_CHECK();
-        k_pc_cmul<<<nw_blocks, 256, 0, s>>>(pc->tvec, r, ncols, pc->Cinv, pc->sigma2, pc->cvec);
+        k_pc_cmul<<<nw_blocks, 256, 0, s>>>(pc->tvec, r, ncols, pc->Cinv, pc->sigma2, pc->cvec, gate);
         FGK_LAUNCH_CHECK();
     }
     switch (nc) {
-        case 1: return launch_pc_apply<1>(pc, r, R, ncols, Z, rz_partial, err, s);
-        case 2: return launch_pc_apply<2>(pc, r, R, ncols, Z, rz_partial, err, s);
-        case 4: return launch_pc_apply<4>(pc, r, R, ncols, Z, rz_partial, err, s);
-        default: return launch_pc_apply<8>(pc, r, R, ncols, Z, rz_partial, err, s);
+        case 1: return launch_pc_apply<1>(pc, r, R, ncols, Z, rz_partial, err, s, gate);
+        case 2: return launch_pc_apply<2>(pc, r, R, ncols, Z, rz_partial, err, s, gate);
+        case 4: return launch_pc_apply<4>(pc, r, R, ncols, Z, rz_partial, err, s, gate);
+        default: return launch_pc_apply<8>(pc, r, R, ncols, Z, rz_partial, err, s, gate);
     }
 }
 
@@ -813,9 +821,11 @@ int pc_check(const Precond *pc, cudaStream_t s) {
 }
 
 template <int NC>
-static int launch_pc_ltr(const Precond *pc, int r, const double *R, int ncols, int *err, cudaStream_t s) {
+static int launch_pc_ltr(const Precond *pc, int r, const double *R, int ncols, int *err, cudaStream_t s,
+                         const int *gate) {
     TimedLaunch tl(kTimedPcLtr, s);
-    k_pc_ltr<NC><<<pc->nb_ltr, kTR, ltr_smem(r, NC), s>>>(pc->tmap, r, R, pc->plan->N, ncols, pc->t_part, err);
+    k_pc_ltr<NC><<<pc->nb_ltr, kTR, ltr_smem(r, NC), s>>>(pc->tmap, r, R, pc->plan->N, ncols, pc->t_part, err,
+                                                          gate);
     FGK_LAUNCH_CHECK();
     tl.end();
     return FGK_OK;
@@ -823,10 +833,10 @@ static int launch_pc_ltr(const Precond *pc, int r, const double *R, int ncols, i
 
 template <int NC>
 static int launch_pc_apply(const Precond *pc, int r, const double *R, int ncols, double *Z, double *rz_partial,
-                           int *err, cudaStream_t s) {
+                           int *err, cudaStream_t s, const int *gate) {
     TimedLaunch tl(kTimedPcApply, s);
     k_pc_apply<NC><<<pc->nb_ltr, kTR, apply_smem(r, NC), s>>>(pc->tmap, r, R, pc->plan->N, ncols, pc->cvec,
-                                                              pc->sigma2, Z, rz_partial, err);
+                                                              pc->sigma2, Z, rz_partial, err, gate);
     FGK_LAUNCH_CHECK();
     tl.end();
     return FGK_OK;

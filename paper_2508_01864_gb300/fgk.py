@@ -60,7 +60,7 @@ EXPORTS = ["fgk_set_allocator", "fgk_build", "fgk_matvec", "fgk_matvec_q", "fgk_
            "fgk_get_permutation", "fgk_get_level", "fgk_batch_create", "fgk_batch_layout", "fgk_batch_matvec_q",
            "fgk_batch_cg_solve", "fgk_batch_destroy", "fgk_precond_build", "fgk_precond_info",
            "fgk_precond_factor", "fgk_precond_apply", "fgk_precond_destroy", "fgk_cg_solve_pc",
-           "fgk_kernel_timing", "fgk_predict"]
+           "fgk_kernel_timing", "fgk_predict", "fgk_batch_cg_solve_pc"]
 
 _lock = threading.Lock()
 _lib = None
@@ -117,6 +117,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.fgk_batch_cg_solve.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(dbl), dbl, i32, ctypes.POINTER(vp),
                                            ctypes.POINTER(fgk_cg_info), vp]
         lib.fgk_batch_cg_solve.restype = i32
+        lib.fgk_batch_cg_solve_pc.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(dbl), dbl,
+                                              i32, ctypes.POINTER(vp), ctypes.POINTER(fgk_cg_info), vp]
+        lib.fgk_batch_cg_solve_pc.restype = i32
         lib.fgk_batch_destroy.argtypes = [vp]
         lib.fgk_batch_destroy.restype = i32
         lib.fgk_precond_build.argtypes = [vp, i32, dbl, vp, ctypes.POINTER(vp)]
@@ -477,8 +480,10 @@ def fgk_batch_matvec_q(b: Batch, Vq: torch.Tensor, out: torch.Tensor | None = No
     return out
 
 
-def fgk_batch_cg_solve(b: Batch, ys: list, sigma2s, tol: float = 1e-8, maxit: int = 100000, stream=None):
-    """Mixed-precision CG for every problem and column; returns (alphas, infos, status)."""
+def fgk_batch_cg_solve(b: Batch, ys: list, sigma2s, tol: float = 1e-8, maxit: int = 100000, stream=None,
+                       precs: list | None = None):
+    """Mixed-precision CG for every problem and column (preconditioned by
+    ``precs``, one per problem, when given); returns (alphas, infos, status)."""
     lib = load()
     n = len(b.handles)
     ys = [_dev_f64_2d(y, "y") for y in ys]
@@ -490,7 +495,11 @@ def fgk_batch_cg_solve(b: Batch, ys: list, sigma2s, tol: float = 1e-8, maxit: in
     res = [(ctypes.c_double * b.nrhs)() for _ in range(n)]
     for i in range(n):
         infos[i].true_resid = ctypes.cast(res[i], ctypes.POINTER(ctypes.c_double))
-    rc = lib.fgk_batch_cg_solve(b.ptr, yp, sg, float(tol), int(maxit), ap, infos, _stream(stream))
+    if precs is None:
+        rc = lib.fgk_batch_cg_solve(b.ptr, yp, sg, float(tol), int(maxit), ap, infos, _stream(stream))
+    else:
+        pp = (ctypes.c_void_p * n)(*[q.ptr for q in precs])
+        rc = lib.fgk_batch_cg_solve_pc(b.ptr, pp, yp, sg, float(tol), int(maxit), ap, infos, _stream(stream))
     _check(rc, allow_soft=True)
     out = [{"iterations": infos[i].iterations, "refinements": infos[i].refinements, "mvm_f32": infos[i].mvm_f32,
             "mvm_f64": infos[i].mvm_f64, "max_true_resid": infos[i].max_true_resid, "true_resid": list(res[i]),

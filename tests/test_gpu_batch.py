@@ -109,3 +109,35 @@ def test_batch_cg_iterations_track_single_solver(fgk_mod, rpc):
         fgk.fgk_batch_destroy(b)
         for h in handles:
             fgk.fgk_destroy(h)
+
+
+def test_batch_pcg_meets_tolerance_in_fewer_iterations(fgk_mod, orc):
+    """Per-problem pivoted-Cholesky preconditioners (App. A.3) in the batched
+    solve: every problem and column meets the tolerance on the oracle's
+    residual, in fewer iterations than the unpreconditioned batch."""
+    from paper_2508_01864_gb300 import batch as batchmod
+
+    probs = [workloads.small(950 + i, N, d, nu=nu, ell=[0.12, 0.3][:d], nrhs=4)
+             for i, (d, nu, N) in enumerate([(1, 0.5, 1500), (2, 1.5, 3000), (1, 2.5, 2500), (2, 2.5, 2000),
+                                             (2, 0.5, 1200)])]
+    sig = [0.01, 0.02, 0.01, 0.01, 0.05]
+    ys = [to_dev(p.V) for p in probs]
+    plain = batchmod.BatchEngine(probs, 4, kind="product", autotune=False)
+    _, inf0, rc0 = plain.solve(ys, sig, tol=1e-8, maxit=50000)
+    plain.close()
+    eng = batchmod.BatchEngine(probs, 4, kind="product", autotune=False, precond_rank=100)
+    try:
+        alphas, infos, rc = eng.solve(ys, sig, tol=1e-8, maxit=50000)
+        assert rc == 0 and rc0 == 0
+        for p, a, s, info, i0 in zip(probs, alphas, sig, infos, inf0):
+            a = a.cpu().numpy()
+            Ka = orc.mvm_brute(p.X, a, p.nu, p.ell, kind=1)
+            res = np.linalg.norm(p.V - Ka - s * a, axis=0) / np.linalg.norm(p.V, axis=0)
+            assert (res <= 1.05e-8).all(), res
+            assert info["iterations"] < i0["iterations"], (info, i0)
+        # a second solve with the same sigma^2 reuses the preconditioners
+        first = eng.precs
+        eng.solve(ys, sig, tol=1e-8, maxit=50000)
+        assert eng.precs is first
+    finally:
+        eng.close()
