@@ -45,8 +45,6 @@ WORKLOAD = ("d=2 N=200000 nu=3/2 ell=(0.1,0.3) x~U[0,1]^2 product kernel; "
 # version)
 TRAFFIC_BYTES = {
     "k_level_scan<float,P=2,NOFF=1,product,OUT>": 44932608,
-    "k_pc_ltr (t = L^T r)": 161644544 + 147968,
-    "k_pc_apply (z = r/s2 - L c)": 161629696 + 418560,
 }
 FALLBACK_HBM_GBS = 6800.0
 

@@ -51,6 +51,7 @@ namespace {
 constexpr int kPcThreads = 256;
 constexpr int kPcMaxRank = 1024;
 constexpr int kGramTile = 16;
+constexpr size_t kCholSmemMax = 200 * 1024;  // C's packed lower triangle in shared memory up to here
 constexpr double kExhausted = 1e-12;  // stop once the residual diagonal is at most this x s2
 
 struct PivPart {
@@ -92,12 +93,11 @@ __device__ __forceinline__ PivPart block_best(PivPart v) {
     return r;
 }
 
-// unit-lengthscale Matern kernel k(r) = sum_p c_p r^p e^{-r}
-__device__ __forceinline__ double matern(int two_nu, double r) {
-    const double e = exp(-r);
-    if (two_nu == 1) return e;
-    if (two_nu == 3) return (1.0 + r) * e;
-    return (1.0 + r + r * r * (1.0 / 3.0)) * e;
+// unit-lengthscale Matern polynomial part: k(r) = poly(r) e^{-r}
+__device__ __forceinline__ double matern_poly(int two_nu, double r) {
+    if (two_nu == 1) return 1.0;
+    if (two_nu == 3) return 1.0 + r;
+    return 1.0 + r + r * r * (1.0 / 3.0);
 }
 
 struct KernArgs {
@@ -106,18 +106,18 @@ struct KernArgs {
     double s2;
 };
 
+// K(x_i, x_p): both kinds share the exponential e^{-sum_k |u_k|} (L1: of the
+// summed distance; product: the product of the per-dimension factors), so one
+// exp per entry
 __device__ __forceinline__ double kern_q(const KernArgs &k, int64_t i, const double *xp) {
     const double u0 = fabs(k.x0[i] - xp[0]);
-    if (k.d == 1) return k.s2 * matern(k.two_nu, u0);
-    const double u1 = fabs(k.x1[i] - xp[1]);
-    if (k.kind == FGK_L1) {
-        double r = u0 + u1;
-        if (k.d == 3) r += fabs(k.x2[i] - xp[2]);
-        return k.s2 * matern(k.two_nu, r);
-    }
-    double v = matern(k.two_nu, u0) * matern(k.two_nu, u1);
-    if (k.d == 3) v *= matern(k.two_nu, fabs(k.x2[i] - xp[2]));
-    return k.s2 * v;
+    const double u1 = k.d > 1 ? fabs(k.x1[i] - xp[1]) : 0.0;
+    const double u2 = k.d > 2 ? fabs(k.x2[i] - xp[2]) : 0.0;
+    const double e = exp(-(u0 + u1 + u2));
+    if (k.d == 1 || k.kind == FGK_L1) return k.s2 * matern_poly(k.two_nu, u0 + u1 + u2) * e;
+    double v = matern_poly(k.two_nu, u0) * matern_poly(k.two_nu, u1);
+    if (k.d == 3) v *= matern_poly(k.two_nu, u2);
+    return k.s2 * v * e;
 }
 
 // float-pair arithmetic (value = hi + lo): Knuth's two-sum and the
@@ -201,27 +201,42 @@ __global__ void k_pc_step(int m, int64_t N, int64_t ldN, KernArgs ka, const int3
     __syncthreads();
     const double sq = sqrt(best.val);
     PivPart mine = piv_none();
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        const double kv = kern_q(ka, i, s_xp);
+    // two consecutive rows per thread (8-byte vector loads of L; the column
+    // stride ldN is a multiple of 64, so row i0 + 1 < ldN is always inside the
+    // column, and only rows below N are written)
+    for (int64_t i0 = 2 * (blockIdx.x * (int64_t)blockDim.x + threadIdx.x); i0 < N;
+         i0 += 2 * (int64_t)gridDim.x * blockDim.x) {
+        const bool two = i0 + 1 < N;
         // sum_t L_t[i] L_t[pivot] in float pairs: the hi x hi product exactly
         // (two-product), the cross terms in FP32 (they sit 24 bits lower)
-        F2 acc{0.f, 0.f};
+        F2 acc0{0.f, 0.f}, acc1{0.f, 0.f};
 #pragma unroll 4
         for (int t = 0; t < m; ++t) {
-            const float ah = Lhi[(size_t)t * ldN + i], al = Llo[(size_t)t * ldN + i];
-            f2_fma(acc, ah, s_lph[t], s_lpl[t]);
-            acc.lo = fmaf(al, s_lph[t], acc.lo);
+            const float2 ah = *reinterpret_cast<const float2 *>(Lhi + (size_t)t * ldN + i0);
+            const float2 al = *reinterpret_cast<const float2 *>(Llo + (size_t)t * ldN + i0);
+            const float ph = s_lph[t], pl = s_lpl[t];
+            f2_fma(acc0, ah.x, ph, pl);
+            acc0.lo = fmaf(al.x, ph, acc0.lo);
+            f2_fma(acc1, ah.y, ph, pl);
+            acc1.lo = fmaf(al.y, ph, acc1.lo);
         }
-        const double dot = (double)acc.hi + (double)acc.lo;
-        const double l = (kv - dot) / sq;
-        float lh, ll;
-        split_f2(l, lh, ll);
-        Lhi[(size_t)m * ldN + i] = lh;
-        Llo[(size_t)m * ldN + i] = ll;
-        const double dn = dres[i] - l * l;
-        dres[i] = dn;
-        const PivPart c{dn, (int64_t)perm0[i], i};
-        if (piv_better(c, mine)) mine = c;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (h == 1 && !two) break;
+            const int64_t i = i0 + h;
+            const F2 acc = h == 0 ? acc0 : acc1;
+            const double kv = kern_q(ka, i, s_xp);
+            const double dot = (double)acc.hi + (double)acc.lo;
+            const double l = (kv - dot) / sq;
+            float lh, ll;
+            split_f2(l, lh, ll);
+            Lhi[(size_t)m * ldN + i] = lh;
+            Llo[(size_t)m * ldN + i] = ll;
+            const double dn = dres[i] - l * l;
+            dres[i] = dn;
+            const PivPart c{dn, (int64_t)perm0[i], i};
+            if (piv_better(c, mine)) mine = c;
+        }
     }
     mine = block_best(mine);
     if (threadIdx.x == 0) next[blockIdx.x] = mine;
@@ -261,65 +276,96 @@ __global__ void k_pc_gram(const float *__restrict__ L, int64_t ldN, int64_t N, i
 }
 
 // C = I + G / sigma2 (G summed over the z partials, mirrored), its lower
-// Cholesky factor in place (row-major r x r), and log det P by Sylvester:
-// N log sigma2 + 2 sum_j log C_jj.  err = 1 if C is not positive definite.
-__global__ void k_pc_chol(const double *__restrict__ Gp, int nz, int r, double sigma2, int64_t N,
-                          double *__restrict__ C, double *__restrict__ logdet, int *__restrict__ err) {
-    for (int t = threadIdx.x; t < r * r; t += blockDim.x) {
-        const int a = t / r, b = t % r;
-        const int lo = min(a, b), hi = max(a, b);
-        double g = 0.0;
-        for (int z = 0; z < nz; ++z) g += Gp[((size_t)z * r + lo) * r + hi];
-        C[t] = (a == b ? 1.0 : 0.0) + g / sigma2;
-    }
-    __syncthreads();
+// Cholesky factor F (row-major r x r, upper part untouched), and log det P by
+// Sylvester: N log sigma2 + 2 sum_j log F_jj.  err = 1 if C is not positive
+// definite.  One CTA; right-looking: per column j the pivot's square root,
+// the scaled column, then the rank-1 update of the trailing lower triangle
+// (one warp per row).  SMEM: C's lower triangle packed in shared memory
+// (row i at i(i+1)/2) plus the current column; otherwise C in global memory.
+template <bool SMEM>
+__global__ void __launch_bounds__(1024) k_pc_chol(const double *__restrict__ Gp, int nz, int r, double sigma2,
+                                                   int64_t N, double *__restrict__ C, double *__restrict__ logdet,
+                                                   int *__restrict__ err) {
+    extern __shared__ __align__(16) double s_c[];
+    double *col = s_c + (SMEM ? (size_t)r * (r + 1) / 2 : 0);  // r
     __shared__ int s_bad;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    auto at = [&](int i, int l) -> double & { return SMEM ? s_c[(size_t)i * (i + 1) / 2 + l] : C[(size_t)i * r + l]; };
+    for (int i = warp; i < r; i += nw)
+        for (int l = lane; l <= i; l += 32) {
+            double g = 0.0;
+            for (int z = 0; z < nz; ++z) g += Gp[((size_t)z * r + l) * r + i];  // partial tiles hold l <= i
+            at(i, l) = (i == l ? 1.0 : 0.0) + g / sigma2;
+        }
     if (threadIdx.x == 0) s_bad = 0;
     __syncthreads();
     for (int j = 0; j < r; ++j) {
-        if (threadIdx.x == 0) {
-            const double v = C[j * r + j];
-            if (!(v > 0.0)) s_bad = 1;
-            C[j * r + j] = v > 0.0 ? sqrt(v) : 1.0;
+        const double v = at(j, j);  // every thread: no write-back race (read before the barrier below)
+        const bool ok = v > 0.0;
+        const double djj = ok ? sqrt(v) : 1.0;
+        for (int i = j + 1 + threadIdx.x; i < r; i += blockDim.x) {
+            const double x = at(i, j) / djj;
+            at(i, j) = x;
+            col[i] = x;
         }
         __syncthreads();
-        const double djj = C[j * r + j];
-        for (int i = j + 1 + threadIdx.x; i < r; i += blockDim.x) C[i * r + j] /= djj;
-        __syncthreads();
-        const int n = r - j - 1;
-        for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-            const int i = j + 1 + t / n, l = j + 1 + t % n;
-            if (l <= i) C[i * r + l] -= C[i * r + j] * C[l * r + j];
+        if (threadIdx.x == 0) {
+            at(j, j) = djj;
+            if (!ok) s_bad = 1;
+        }
+        for (int i = j + 1 + warp; i < r; i += nw) {
+            const double ci = col[i];
+            for (int l = j + 1 + lane; l <= i; l += 32) at(i, l) -= ci * col[l];
         }
         __syncthreads();
     }
+    if (SMEM)  // the factor out to global memory
+        for (int i = warp; i < r; i += nw)
+            for (int l = lane; l <= i; l += 32) C[(size_t)i * r + l] = s_c[(size_t)i * (i + 1) / 2 + l];
     if (threadIdx.x == 0) {
         double ld = (double)N * log(sigma2);
-        for (int j = 0; j < r; ++j) ld += 2.0 * log(C[j * r + j]);
+        for (int j = 0; j < r; ++j) ld += 2.0 * log(at(j, j));
         *logdet = ld;
         *err = s_bad;
     }
 }
 
-// C^{-1} = F^{-T} F^{-1} from the lower Cholesky factor F (row-major r x r):
-// first F^{-1} column by column (thread c: forward substitution for e_c),
-// then the symmetric product.  Finv and Cinv: r x r row-major.
-__global__ void k_pc_inverse(const double *__restrict__ F, int r, double *__restrict__ Finv,
-                             double *__restrict__ Cinv) {
-    for (int c = threadIdx.x; c < r; c += blockDim.x) {
-        for (int i = 0; i < c; ++i) Finv[i * r + c] = 0.0;
-        for (int i = c; i < r; ++i) {
-            double sacc = i == c ? 1.0 : 0.0;
-            for (int k = c; k < i; ++k) sacc -= F[i * r + k] * Finv[k * r + c];
-            Finv[i * r + c] = sacc / F[i * r + i];
-        }
+// Columns of F^{-1} (F lower, row-major r x r) by forward substitution, one
+// warp per column c: FinvT[c][i] = (F^{-1})[i][c] (zero for i < c).  The
+// dots run across the lanes; the column being solved sits in shared memory.
+__global__ void k_pc_finv(const double *__restrict__ F, int r, double *__restrict__ FinvT) {
+    __shared__ double s_x[4][kPcMaxRank];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int c = blockIdx.x * 4 + w;
+    if (c >= r) return;  // uniform per warp
+    double *x = s_x[w];
+    for (int i = c; i < r; ++i) {
+        double part = 0.0;
+        for (int k = c + lane; k < i; k += 32) part = fma(F[(size_t)i * r + k], x[k], part);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        const double xi = ((i == c ? 1.0 : 0.0) - part) / F[(size_t)i * r + i];
+        if (lane == 0) x[i] = xi;
+        __syncwarp();
     }
-    __syncthreads();
-    for (int t = threadIdx.x; t < r * r; t += blockDim.x) {
-        const int a = t / r, b = t % r;
-        double sacc = 0.0;
-        for (int k = max(a, b); k < r; ++k) sacc += Finv[k * r + a] * Finv[k * r + b];
-        Cinv[t] = sacc;
+    for (int i = lane; i < r; i += 32) FinvT[(size_t)c * r + i] = i < c ? 0.0 : x[i];
+}
+
+// C^{-1} = F^{-T} F^{-1}: Cinv[a][b] = sum_{k >= max(a, b)} Finv[k][a] Finv[k][b],
+// one warp per entry a <= b (mirrored).
+__global__ void k_pc_cinv(const double *__restrict__ FinvT, int r, double *__restrict__ Cinv) {
+    const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (e >= (int64_t)r * r) return;  // uniform per warp
+    const int a = (int)(e / r), b = (int)(e % r);
+    if (a > b) return;
+    double acc = 0.0;
+    for (int k = b + lane; k < r; k += 32) acc = fma(FinvT[(size_t)a * r + k], FinvT[(size_t)b * r + k], acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+        Cinv[(size_t)a * r + b] = acc;
+        Cinv[(size_t)b * r + a] = acc;
     }
 }
 
@@ -349,9 +395,22 @@ __global__ void k_sum(const double *__restrict__ a, int64_t n, double *__restric
 constexpr int kTR = 256;      // rows per tile (= threads per CTA)
 constexpr int kMC = 32;       // rank indices per chunk
 constexpr int kSpinLimit = 1 << 22;
-constexpr int kApplyCtas = 2 * 152;
+constexpr int kPcCtasPerSm = 3;  // persistent CTAs per SM of the passes over L
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory loads by 32-bit shared address (volatile: never moved above
+// the barrier waits that make the data visible)
+__device__ __forceinline__ float lds_f32(uint32_t a) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ F2 lds_f2(uint32_t a) {
+    F2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.hi), "=f"(v.lo) : "r"(a));
+    return v;
+}
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
@@ -388,26 +447,31 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return false;
 }
 
-// The chunk sequence of one CTA within a pass: chunk c is rank chunk
-// c % nchunk of the CTA's tile number c / nchunk.  The buffers and barrier
-// phases follow the CTA's running chunk count g (passes included).
+// The chunk sequence of one CTA within a pass, tile by tile (the apply) or
+// rank block by rank block (t = L^T R).  The buffers and barrier phases
+// follow the CTA's running chunk count g (passes included).
 struct ChunkStream {
     float *buf;     // 2 x kMC x kTR floats
     uint64_t *bar;  // 2 mbarriers
     const CUtensorMap *map;
     int nchunk, ntile_cta;
+    bool rank_major;  // false: chunk c = rank block c % nchunk of tile c / nchunk;
+                      // true:  chunk c = rank block c / ntile_cta of tile c % ntile_cta
 
+    __device__ __forceinline__ int tile_of(int c) const { return rank_major ? c % ntile_cta : c / nchunk; }
+    __device__ __forceinline__ int block_of(int c) const { return rank_major ? c / ntile_cta : c % nchunk; }
     __device__ __forceinline__ int64_t tile_row0(int c) const {
-        return ((int64_t)blockIdx.x + (int64_t)(c / nchunk) * gridDim.x) * kTR;
+        return ((int64_t)blockIdx.x + (int64_t)tile_of(c) * gridDim.x) * kTR;
     }
     __device__ __forceinline__ void issue(int g, int c) const {  // thread 0 only
         const int b = g & 1;
         mbar_expect_tx(bar + b, (uint32_t)(kMC * kTR * 4));
-        tma_load_2d(buf + (size_t)b * kMC * kTR, map, (int)tile_row0(c), (c % nchunk) * kMC, bar + b);
+        tma_load_2d(buf + (size_t)b * kMC * kTR, map, (int)tile_row0(c), block_of(c) * kMC, bar + b);
     }
     // every thread waits for chunk c (the use count of its buffer gives the
-    // parity); false (CTA-uniform) if a wait expired
-    __device__ __forceinline__ bool wait(int c, int *s_bad, int *err) const {
+    // parity); false (CTA-uniform) if a wait expired.  next_issued: chunk
+    // c + 1 is in flight too.
+    __device__ __forceinline__ bool wait(int c, int *s_bad, int *err, bool next_issued) const {
         const uint32_t parity = (uint32_t)((c >> 1) & 1);
         const bool ok = mbar_wait_bounded(bar + (c & 1), parity);
         if (!ok) atomicOr(s_bad, 1);
@@ -415,7 +479,9 @@ struct ChunkStream {
         if (*s_bad) {
             if (threadIdx.x == 0) {
                 atomicOr(err, DEV_TIMEOUT);
-                mbar_wait_bounded(bar + (c & 1), parity);  // let a late copy land before the CTA exits
+                // let late copies land before the CTA exits (bounded again)
+                mbar_wait_bounded(bar + (c & 1), parity);
+                if (next_issued) mbar_wait_bounded(bar + ((c + 1) & 1), (uint32_t)(((c + 1) >> 1) & 1));
             }
             return false;
         }
@@ -430,10 +496,15 @@ __device__ __forceinline__ int tiles_of_cta(int64_t N) {
 }
 
 // t_part[b][m][j] = sum over the rows of CTA b's tiles of L[m][i] R[i][j].
-// R's rows of the current tile sit in shared memory as float pairs; each
-// warp owns the rank indices mm = warp, warp + 8, ... of every chunk, sums
-// over the tile's rows (lanes stride the rows) in float pairs, reduces across
-// the warp with shuffles and adds the result into s_t[m][u] (FP64).
+// The CTA streams its chunks rank block by rank block: rank indices
+// 0..kMC-1 of all its tiles, then the next kMC, and so on (chunk c is rank
+// block c / ntile of the CTA's tile c % ntile).  Warp w owns the rank
+// indices w, w + 8, w + 16, w + 24 of every block; lane l takes rows l,
+// l + 32, ... of each tile and keeps one float-pair running sum per owned
+// rank index and column across all the CTA's tiles, so sums cross lanes
+// (shuffles) only once per rank block, after its last tile.  The rows of R
+// for the next chunk are fetched into registers while the current chunk is
+// summed, then split into float pairs in shared memory.
 // NC: columns per pass (1, 2, 4 or 8); a pass with fewer real columns pads
 // with zero columns.
 template <int NC>
@@ -442,76 +513,121 @@ __global__ void __launch_bounds__(kTR) k_pc_ltr(const __grid_constant__ CUtensor
                                                  double *__restrict__ t_part, int *__restrict__ err,
                                                  const int *__restrict__ gate) {
     if (gate && *gate == 0) return;
+    constexpr int NW = kTR / 32, OWN = kMC / NW, RPL = kTR / 32;  // warps, rank indices per warp, rows per lane
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *buf = reinterpret_cast<float *>(smem_raw);
     F2 *Rs = reinterpret_cast<F2 *>(buf + 2 * kMC * kTR);  // kTR x NC
-    F2 *s_t = Rs + kTR * NC;                               // r x NC running sums (float pairs)
-    uint64_t *bar = reinterpret_cast<uint64_t *>(s_t + (size_t)r * NC);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(Rs + kTR * NC);
     __shared__ int s_bad;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
         mbar_init(bar);
         mbar_init(bar + 1);
         mbar_fence_init();
         s_bad = 0;
     }
+    __syncthreads();  // barriers and s_bad initialised before any thread waits on them
     const int nchunk = (r + kMC - 1) / kMC;
     const int ntile = tiles_of_cta(N);
-    const ChunkStream cs{buf, bar, &map, nchunk, ntile};
+    const ChunkStream cs{buf, bar, &map, nchunk, ntile, true};
     const int total = nchunk * ntile;
     int c_base = 0;  // chunks streamed by earlier passes (barrier phases keep counting)
     for (int j0 = 0; j0 < ncols; j0 += NC) {
         const int nc = min(NC, ncols - j0);
-        for (int t = threadIdx.x; t < r * NC; t += blockDim.x) s_t[t] = F2{0.f, 0.f};
-        __syncthreads();
-        if (total > 0 && threadIdx.x == 0) cs.issue(c_base, 0);
+        F2 acc[OWN][NC];
+#pragma unroll
+        for (int o = 0; o < OWN; ++o)
+#pragma unroll
+            for (int u = 0; u < NC; ++u) acc[o][u] = F2{0.f, 0.f};
+        double rn[NC];  // this thread's row of R for the chunk about to be used
+#pragma unroll
+        for (int u = 0; u < NC; ++u) rn[u] = 0.0;
+        if (total > 0) {
+            const int64_t i = cs.tile_row0(0) + threadIdx.x;
+#pragma unroll
+            for (int u = 0; u < NC; ++u)
+                if (u < nc && i < N) rn[u] = R[i * ncols + j0 + u];
+            if (threadIdx.x == 0) cs.issue(c_base, 0);
+        }
         for (int c = 0; c < total; ++c) {
             const int cc = c_base + c;
             if (threadIdx.x == 0 && c + 1 < total) cs.issue(cc + 1, c + 1);
-            if (c % nchunk == 0) {  // a new tile: its rows of R
-                const int64_t i = cs.tile_row0(c) + threadIdx.x;
 #pragma unroll
-                for (int u = 0; u < NC; ++u) {
-                    float hi = 0.f, lo = 0.f;
-                    if (u < nc && i < N) split_f2(R[i * ncols + j0 + u], hi, lo);
-                    Rs[threadIdx.x * NC + u] = F2{hi, lo};
+            for (int u = 0; u < NC; ++u) {
+                float hi, lo;
+                split_f2(rn[u], hi, lo);
+                Rs[threadIdx.x * NC + u] = F2{hi, lo};
+            }
+            if (c + 1 < total) {
+                const int64_t i = cs.tile_row0(c + 1) + threadIdx.x;
+#pragma unroll
+                for (int u = 0; u < NC; ++u) rn[u] = (u < nc && i < N) ? R[i * ncols + j0 + u] : 0.0;
+            }
+            if (!cs.wait(cc, &s_bad, err, c + 1 < total)) return;  // (its barrier also publishes Rs)
+            const uint32_t la = smem_u32(cs.chunk(cc)) + (uint32_t)(warp * kTR + lane) * 4u;
+            const uint32_t ra = smem_u32(Rs) + (uint32_t)lane * NC * 8u;
+            // (rank indices at or above r read the zeros the copy filled in)
+#pragma unroll
+            for (int k = 0; k < RPL; ++k) {
+                F2 rv[NC];
+#pragma unroll
+                for (int u = 0; u < NC; ++u) rv[u] = lds_f2(ra + (uint32_t)((32 * k * NC + u) * 8));
+#pragma unroll
+                for (int o = 0; o < OWN; ++o) {
+                    const float l = lds_f32(la + (uint32_t)((o * NW * kTR + 32 * k) * 4));
+#pragma unroll
+                    for (int u = 0; u < NC; ++u) f2_fma(acc[o][u], l, rv[u].hi, rv[u].lo);
                 }
             }
-            if (!cs.wait(cc, &s_bad, err)) return;
-            const float *Lc = cs.chunk(cc);
-            const int m0 = (c % nchunk) * kMC, mc = min(kMC, r - m0);
-            for (int mm = warp; mm < mc; mm += nw) {
-                F2 acc[NC];
+            __syncthreads();  // every warp is done with this chunk's buffer and with Rs
+            if (c % ntile == ntile - 1) {
+                // The rank block's last tile: sum each accumulator over the 32
+                // lanes through the buffer just consumed (each warp writes its
+                // lanes' values to its own 4 KB, then every lane adds a slice
+                // and a few shuffles finish), in groups of RG values per lane.
+                const int m0 = (c / ntile) * kMC;
+                constexpr int V = OWN * NC, RG = V < 16 ? V : 16, LPV = 32 / RG, SL = 32 / LPV;
+                const uint32_t wa = smem_u32(cs.chunk(cc)) + (uint32_t)warp * 4096u;
 #pragma unroll
-                for (int u = 0; u < NC; ++u) acc[u] = F2{0.f, 0.f};
+                for (int g0 = 0; g0 < V; g0 += RG) {
 #pragma unroll
-                for (int row = lane; row < kTR; row += 32) {
-                    const float l = Lc[mm * kTR + row];
+                    for (int v = 0; v < RG; ++v) {
+                        const F2 a = acc[(g0 + v) / NC][(g0 + v) % NC];
+                        asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(wa + (uint32_t)((v * 32 + lane) * 8)),
+                                     "f"(a.hi), "f"(a.lo)
+                                     : "memory");
+                    }
+                    __syncwarp();
+                    const int v = lane / LPV, part = lane % LPV;  // value v, lanes part*SL .. part*SL+SL-1
+                    F2 a = F2{0.f, 0.f};
 #pragma unroll
-                    for (int u = 0; u < NC; ++u) f2_fma(acc[u], l, Rs[row * NC + u].hi, Rs[row * NC + u].lo);
-                }
+                    for (int e = 0; e < SL; ++e) a = f2_add(a, lds_f2(wa + (uint32_t)((v * 32 + part * SL + e) * 8)));
 #pragma unroll
-                for (int u = 0; u < NC; ++u) {
-                    F2 a = acc[u];
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
+                    for (int sh = LPV / 2; sh > 0; sh >>= 1) {
                         F2 other;
-                        other.hi = __shfl_xor_sync(0xffffffffu, a.hi, o);
-                        other.lo = __shfl_xor_sync(0xffffffffu, a.lo, o);
+                        other.hi = __shfl_xor_sync(0xffffffffu, a.hi, sh);
+                        other.lo = __shfl_xor_sync(0xffffffffu, a.lo, sh);
                         a = f2_add(a, other);
                     }
-                    if (lane == 0) s_t[(m0 + mm) * NC + u] = f2_add(s_t[(m0 + mm) * NC + u], a);
+                    const int o = (g0 + v) / NC, u = (g0 + v) % NC, m = m0 + warp + o * NW;
+                    if (part == 0 && m < r && u < nc)
+                        t_part[((size_t)blockIdx.x * r + m) * ncols + j0 + u] = (double)a.hi + (double)a.lo;
+                    __syncwarp();
                 }
+#pragma unroll
+                for (int o = 0; o < OWN; ++o)
+#pragma unroll
+                    for (int u = 0; u < NC; ++u) acc[o][u] = F2{0.f, 0.f};
+                // order these generic-proxy writes before the bulk copy that
+                // will refill the buffer, then free it
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncthreads();
             }
-            __syncthreads();  // buffer reuse two chunks later; Rs rewritten at the next tile
         }
         c_base += total;
-        for (int t = threadIdx.x; t < r * nc; t += blockDim.x) {
-            const int m = t / nc, u = t % nc;
-            const F2 v = s_t[m * NC + u];
-            t_part[((size_t)blockIdx.x * r + m) * ncols + j0 + u] = (double)v.hi + (double)v.lo;
-        }
-        __syncthreads();
+        if (ntile == 0)  // a CTA without rows still owns its rows of partials
+            for (int t = threadIdx.x; t < r * nc; t += blockDim.x)
+                t_part[((size_t)blockIdx.x * r + t / nc) * ncols + j0 + t % nc] = 0.0;
     }
 }
 
@@ -568,6 +684,7 @@ __global__ void __launch_bounds__(kTR) k_pc_apply(const __grid_constant__ CUtens
         mbar_fence_init();
         s_bad = 0;
     }
+    __syncthreads();  // barriers and s_bad initialised before any thread waits on them
     const int nchunk = (r + kMC - 1) / kMC;
     const int ntile = tiles_of_cta(N);
     const ChunkStream cs{buf, bar, &map, nchunk, ntile};
@@ -605,16 +722,20 @@ __global__ void __launch_bounds__(kTR) k_pc_apply(const __grid_constant__ CUtens
         for (int c = 0; c < total; ++c) {
             const int cc = c_base + c;
             if (threadIdx.x == 0 && c + 1 < total) cs.issue(cc + 1, c + 1);
-            if (!cs.wait(cc, &s_bad, err)) return;
+            if (!cs.wait(cc, &s_bad, err, c + 1 < total)) return;
             const float *Lc = cs.chunk(cc);
             const int m0 = (c % nchunk) * kMC, mc = min(kMC, r - m0);
             if (mc == kMC) {
+                const uint32_t la = smem_u32(Lc) + threadIdx.x * 4u;
+                const uint32_t ca = smem_u32(cs2 + m0 * NC);
 #pragma unroll 8
                 for (int mm = 0; mm < kMC; ++mm) {
-                    const float l = Lc[mm * kTR + threadIdx.x];
-                    const F2 *cm = cs2 + (m0 + mm) * NC;
+                    const float l = lds_f32(la + (uint32_t)(mm * kTR * 4));
 #pragma unroll
-                    for (int u = 0; u < NC; ++u) f2_fma(acc[u], l, cm[u].hi, cm[u].lo);
+                    for (int u = 0; u < NC; ++u) {
+                        const F2 cm = lds_f2(ca + (uint32_t)((mm * NC + u) * 8));
+                        f2_fma(acc[u], l, cm.hi, cm.lo);
+                    }
                 }
             } else {
                 for (int mm = 0; mm < mc; ++mm) {
@@ -733,7 +854,8 @@ const Plan *pc_plan(const Precond *pc) { return pc->plan; }
 
 static int cols_per_pass(int ncols) { return ncols >= 8 ? 8 : (ncols >= 3 ? (ncols == 3 || ncols == 4 ? 4 : 8) : ncols); }
 static size_t ltr_smem(int r, int nc) {
-    return (size_t)2 * kMC * kTR * 4 + (size_t)kTR * nc * 8 + (size_t)std::max(r, 1) * nc * 8 + 2 * 8;
+    (void)r;
+    return (size_t)2 * kMC * kTR * 4 + (size_t)kTR * nc * 8 + 2 * 8;
 }
 static size_t apply_smem(int r, int nc) { return (size_t)2 * kMC * kTR * 4 + 2 * 8 + (size_t)std::max(r, 1) * nc * 8; }
 
@@ -861,11 +983,21 @@ static int pc_build(Precond *pc, cudaStream_t s) {
     };
     const int steps_blocks = (int)std::min<int64_t>(2 * 152, (N + kPcThreads - 1) / kPcThreads);
     pc->chunk = kTR;
-    pc->nb_ltr = (int)std::min<int64_t>(kApplyCtas, (N + kTR - 1) / kTR);
     FGK_TRY(set_pc_attrs<1>(k));
     FGK_TRY(set_pc_attrs<2>(k));
     FGK_TRY(set_pc_attrs<4>(k));
     FGK_TRY(set_pc_attrs<8>(k));
+    {
+        // persistent CTAs of the two passes over L: as many as are resident
+        // together for one column (at most kPcCtasPerSm per SM)
+        int dev = 0, nsm = 0, occ_a = 0, occ_t = 0;
+        FGK_CUDA(cudaGetDevice(&dev));
+        FGK_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        FGK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, k_pc_apply<1>, kTR, apply_smem(k, 1)));
+        FGK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_t, k_pc_ltr<1>, kTR, ltr_smem(k, 1)));
+        const int per_sm = std::max(1, std::min(kPcCtasPerSm, std::min(occ_a, occ_t)));
+        pc->nb_ltr = (int)std::min<int64_t>((int64_t)per_sm * std::max(nsm, 1), (N + kTR - 1) / kTR);
+    }
     pc->ldN = ldN;
     pc->Llo = (float *)take((size_t)k * ldN * 4);
     pc->L32 = (float *)take((size_t)k * ldN * 4);
@@ -932,9 +1064,22 @@ static int pc_build(Precond *pc, cudaStream_t s) {
     if (r > 0) {
         k_pc_gram<<<dim3(ntile, ntile, nz), kPcThreads, 0, s>>>(pc->L32, ldN, N, r, rows_per_z, Gp);
         FGK_LAUNCH_CHECK();
-        k_pc_chol<<<1, kPcThreads, 0, s>>>(Gp, nz, r, pc->sigma2, N, pc->Cf, pc->scal + 1, pc->ints + 1);
+        const size_t chol_smem = ((size_t)r * (r + 1) / 2 + (size_t)r) * 8;
+        if (chol_smem <= kCholSmemMax) {
+            FGK_CUDA(cudaFuncSetAttribute(k_pc_chol<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)chol_smem));
+            k_pc_chol<true><<<1, 1024, chol_smem, s>>>(Gp, nz, r, pc->sigma2, N, pc->Cf, pc->scal + 1, pc->ints + 1);
+        } else {
+            FGK_CUDA(cudaFuncSetAttribute(k_pc_chol<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)((size_t)r * 8)));
+            k_pc_chol<false><<<1, 1024, (size_t)r * 8, s>>>(Gp, nz, r, pc->sigma2, N, pc->Cf, pc->scal + 1,
+                                                            pc->ints + 1);
+        }
         FGK_LAUNCH_CHECK();
-        k_pc_inverse<<<1, kPcThreads, 0, s>>>(pc->Cf, r, Gp, pc->Cinv);  // Gp (nz * k * k >= k * k) as scratch
+        // Gp (nz * k * k >= k * k doubles) as the scratch of F^{-1}
+        k_pc_finv<<<(r + 3) / 4, 128, 0, s>>>(pc->Cf, r, Gp);
+        FGK_LAUNCH_CHECK();
+        k_pc_cinv<<<grid_for((int64_t)r * r * 32, 256), 256, 0, s>>>(Gp, r, pc->Cinv);
         FGK_LAUNCH_CHECK();
     }
     double hs[2] = {0.0, 0.0};
