@@ -9,6 +9,9 @@ Everything here is plain FP64 on the CPU:
 * ``kmat``       the dense matrix K for small N; ``kcols`` selected columns;
   ``kcross``      the cross-covariance between evaluation points and the data
   (the vector k_z of the posterior mean, eq. gp_mean);
+* ``mvm_dlogell_brute``  the lengthscale-gradient product (dK/d log ell) V
+  from the definition, with ``kernel_dlog`` the closed-form derivatives
+  (App. C.1 gradient formulas);
 * ``mvm_dc``     O2, the paper's ECDF decomposition evaluated literally by a
   re-sorting divide and conquer (C);
 * ``structure``  O3, canonical sort permutations and the dominance-level
@@ -26,10 +29,12 @@ from .core import (  # noqa: F401
     kcols,
     kcross,
     kernel,
+    kernel_dlog,
     kmat,
     max_threads,
     mvm_brute,
     mvm_dc,
     mvm_dc_product32_printed,
+    mvm_dlogell_brute,
     phi,
 )

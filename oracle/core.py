@@ -56,6 +56,12 @@ def _load():
         lib.orc_kcross.restype = ctypes.c_int
         lib.orc_kcross.argtypes = [D, ctypes.c_long, D, ctypes.c_long, ctypes.c_int, ctypes.c_int, D,
                                    ctypes.c_double, ctypes.c_int, D]
+        lib.orc_kernel_dlog.restype = ctypes.c_double
+        lib.orc_kernel_dlog.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double]
+        lib.orc_mvm_dlogell_brute.restype = ctypes.c_int
+        lib.orc_mvm_dlogell_brute.argtypes = [D, ctypes.c_long, ctypes.c_int, ctypes.c_int, D, ctypes.c_double,
+                                              ctypes.c_int, ctypes.c_int, D, ctypes.c_int, Lp, ctypes.c_long, D,
+                                              ctypes.c_int]
         lib.orc_mvm_dc.restype = ctypes.c_int
         lib.orc_mvm_dc.argtypes = [D, ctypes.c_long, ctypes.c_int, ctypes.c_int, D, ctypes.c_double,
                                    ctypes.c_int, D, ctypes.c_int, D]
@@ -132,6 +138,37 @@ def mvm_brute(X, V, nu, ell, s2: float = 1.0, kind: int = L1, rows=None, nthread
                                int(nthreads))
     if rc != 0:
         raise ValueError("orc_mvm_brute rejected its arguments")
+    return Y[:, 0] if vec else Y
+
+
+def kernel_dlog(nu, u, which: int = 0) -> np.ndarray:
+    """which=0: -u k'(u) (= l d/dl of k(|x|/l)); which=1: -k'(u) (App. C.1)."""
+    lib = _load()
+    t = _two_nu(nu)
+    u = np.asarray(u, dtype=np.float64)
+    return np.vectorize(lambda x: lib.orc_kernel_dlog(t, int(which), float(x)), otypes=[np.float64])(u)
+
+
+def mvm_dlogell_brute(X, V, nu, ell, dim: int = -1, s2: float = 1.0, kind: int = L1, rows=None,
+                      nthreads: int = 0) -> np.ndarray:
+    """Y = s2 * (dK/d log ell_dim) V from the definition (dim = -1: all
+    lengthscales scaled together).  ``rows`` selects output rows."""
+    lib = _load()
+    X, d, ell = _prep(X, ell)
+    N = X.shape[0]
+    V = np.asarray(V, dtype=np.float64)
+    vec = V.ndim == 1
+    V = np.ascontiguousarray(V.reshape(N, -1))
+    nrhs = V.shape[1]
+    rp, nr = None, 0
+    if rows is not None:
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        rp, nr = rows.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), rows.size
+    Y = np.empty((N if rows is None else nr, nrhs))
+    rc = lib.orc_mvm_dlogell_brute(_dp(X), N, d, _two_nu(nu), _dp(ell), float(s2), int(kind), int(dim), _dp(V),
+                                   nrhs, rp, nr, _dp(Y), int(nthreads))
+    if rc != 0:
+        raise ValueError("orc_mvm_dlogell_brute rejected its arguments")
     return Y[:, 0] if vec else Y
 
 
