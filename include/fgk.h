@@ -102,6 +102,27 @@ int fgk_build(const double *X, int64_t N, int d, int two_nu, const double *ell, 
  * Asynchronous on `stream`. */
 int fgk_matvec(fgk_handle h, const void *V, int nrhs, void *Y, int precision, fgk_stream_t stream);
 
+/* Y = (dK / d log ell_dim) V: the product with the lengthscale derivative of
+ * K that the trace term of the likelihood gradient needs
+ * (eq. gp_log_likelihood_derivative, tr((K + sigma^2 I)^{-1} dK/dtheta) by
+ * Hutchinson probes, App. A.2), from the gradient formulas of App. C.1.  The
+ * derivative is taken with respect to log ell (ell times the paper's
+ * d/d ell): divide column-wise by ell_dim for d/d ell_dim.
+ *   dim        0 <= dim < d: the lengthscale of coordinate dim; product
+ *              kernel (or d == 1).
+ *              -1: every lengthscale scaled together (ell_k -> t ell_k,
+ *              derivative at t = 1, i.e. the sum of the d per-coordinate
+ *              derivatives); for one isotropic lengthscale this is
+ *              ell dK/d ell, the paper's gradient formulas.  Any kernel.
+ *              The L1 kernel with d > 1 takes only -1 (its per-coordinate
+ *              derivative is not a function of the L1 distance alone):
+ *              other values give FGK_ERR_INVALID.
+ *   V, Y, nrhs, precision as fgk_matvec.  The diagonal of the derivative is
+ *   zero (self-pairs have distance 0).  Allocates a workspace (cudaMallocAsync
+ *   or the installed allocator).  Asynchronous on `stream`. */
+int fgk_matvec_dlogell(fgk_handle h, const void *V, int nrhs, void *Y, int dim, int precision,
+                       fgk_stream_t stream);
+
 /* Y = K V with V and Y in the plan's internal point order: row q holds the
  * point perm_1[q] (fgk_get_permutation(h, 0, ...)), i.e. the points sorted
  * by their first scaled coordinate.  Iterative methods that keep their

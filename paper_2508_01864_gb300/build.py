@@ -26,6 +26,8 @@ SOURCES = [
     "fgk_struct.cu",
     "fgk_scan_f32.cu",
     "fgk_scan_f64.cu",
+    "fgk_dscan_f32.cu",
+    "fgk_dscan_f64.cu",
     "fgk_solve.cu",
     "fgk_noalloc.cu",
     "fgk_batch.cu",

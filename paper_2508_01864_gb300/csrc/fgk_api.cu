@@ -379,6 +379,52 @@ int fgk_matvec(fgk_handle h, const void *V, int nrhs, void *Y, int precision, fg
     return rc;
 }
 
+int fgk_matvec_dlogell(fgk_handle h, const void *V, int nrhs, void *Y, int dim, int precision,
+                       fgk_stream_t stream) {
+    clear_error();
+    if (!h || !V || !Y || nrhs < 1 || (precision != FGK_F64 && precision != FGK_F32)) {
+        set_error("fgk_matvec_dlogell: need h, V, Y, nrhs >= 1 and precision FGK_F64 or FGK_F32");
+        return FGK_ERR_INVALID;
+    }
+    Plan *p = h;
+    if (dim < -1 || dim >= p->d) {
+        set_error("fgk_matvec_dlogell: dim = %d is outside [-1, %d)", dim, p->d);
+        return FGK_ERR_INVALID;
+    }
+    const bool product = p->d > 1 && p->kind == FGK_PRODUCT;
+    if (!product && p->d > 1 && dim >= 0) {
+        set_error("fgk_matvec_dlogell: the L1 kernel's per-coordinate derivative is not supported "
+                  "(pass dim = -1 for all lengthscales together)");
+        return FGK_ERR_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    p->stream = s;
+    const int eb = precision == FGK_F64 ? 8 : 4;
+    const size_t vb = (size_t)p->N * nrhs * eb;
+    char *tmp = (char *)dev_alloc(2 * vb + 256, s);
+    if (!tmp) {
+        set_error("fgk_matvec_dlogell: workspace allocation of %zu bytes failed", 2 * vb);
+        return FGK_ERR_OOM;
+    }
+    void *Vq = tmp;
+    void *Yq = tmp + ((vb + 255) / 256) * 256;
+    int rc = to_q_order(p, V, Vq, nrhs, eb, s);
+    if (rc == FGK_OK && cudaMemsetAsync(Yq, 0, vb, s) != cudaSuccess) {
+        set_error("fgk_matvec_dlogell: cudaMemsetAsync failed");
+        rc = FGK_ERR_CUDA;
+    }
+    // product kernel: one scan per coordinate (summed for dim = -1);
+    // radial (L1 or d = 1): one scan with the derivative's coefficients
+    const int m0 = product ? (dim < 0 ? 0 : dim) : -1;
+    const int m1 = product ? (dim < 0 ? p->d : dim + 1) : 0;
+    for (int m = m0; rc == FGK_OK && m < m1; ++m)
+        rc = precision == FGK_F64 ? dlogell_q_f64(p, m, (const double *)Vq, nrhs, (double *)Yq, s)
+                                  : dlogell_q_f32(p, m, (const float *)Vq, nrhs, (float *)Yq, s);
+    if (rc == FGK_OK) rc = from_q_order(p, Yq, Y, nrhs, eb, s);
+    dev_free(tmp, s);
+    return rc;
+}
+
 int fgk_matvec_q(fgk_handle h, const void *Vq, int nrhs, void *Yq, int precision, fgk_stream_t stream) {
     clear_error();
     if (!h || !Vq || !Yq || nrhs < 1 || (precision != FGK_F64 && precision != FGK_F32)) {

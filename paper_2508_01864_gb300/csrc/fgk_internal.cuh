@@ -174,6 +174,10 @@ int mvm_q_f64(Plan *p, const double *Vq, int nrhs, double *Yq, cudaStream_t s, c
 int mvm_q_f32(Plan *p, const float *Vq, int nrhs, float *Yq, cudaStream_t s, const int *gate,
               bool init_diag = true);
 size_t mvm_ws_bytes(const Plan *p, int nrhs, bool f64);
+// Y_q += s2 (dK/d log ell_dim) V_q in q order (fgk_dscan.cuh); dim in [0, d)
+// for the product kernel, -1 for the radial (L1 or d = 1) derivative
+int dlogell_q_f64(Plan *p, int dim, const double *Vq, int nrhs, double *Yq, cudaStream_t s);
+int dlogell_q_f32(Plan *p, int dim, const float *Vq, int nrhs, float *Yq, cudaStream_t s);
 
 int ensure_ws(Plan *p, size_t bytes, cudaStream_t s);
 

@@ -100,6 +100,11 @@ struct ScanArgs {
     R s2;
     int *err;
     const int *gate;  // NULL, or a device int: 0 = skip the whole product
+    // readout coefficients of the generic-coefficient scans (GEN): the
+    // kernel factor sum_p cf[k][p] r^p e^{-r} of split dimension k (offset
+    // block k), cf[d-1] for the sweep dimension, cf[0] for the L1 kernel's
+    // radial factor
+    R cf[kMaxD][4];
 };
 
 template <class R>
@@ -118,9 +123,18 @@ __device__ __forceinline__ void step_group(R *m, R T, R E) {
         const R ET = E == R(0) ? R(0) : E * T;
         m[1] = E * m[1] + ET * m[0];
         m[0] *= E;
-    } else {
+    } else if constexpr (P == 3) {
         const R ET = E == R(0) ? R(0) : E * T;
         const R ET2 = E == R(0) ? R(0) : ET * T;
+        m[2] = E * m[2] + R(2) * ET * m[1] + ET2 * m[0];
+        m[1] = E * m[1] + ET * m[0];
+        m[0] *= E;
+    } else {
+        static_assert(P == 4, "moment orders up to 3");
+        const R ET = E == R(0) ? R(0) : E * T;
+        const R ET2 = E == R(0) ? R(0) : ET * T;
+        const R ET3 = E == R(0) ? R(0) : ET2 * T;
+        m[3] = E * m[3] + R(3) * ET * m[2] + R(3) * ET2 * m[1] + ET3 * m[0];
         m[2] = E * m[2] + R(2) * ET * m[1] + ET2 * m[0];
         m[1] = E * m[1] + ET * m[0];
         m[0] *= E;
@@ -171,14 +185,60 @@ __device__ __forceinline__ R ucoef_sel(R o, R eo, int e) {
     }
 }
 
+// Generic readout coefficients (GEN scans: the lengthscale derivatives, whose
+// factors have runtime coefficients and one order more).
+__host__ __device__ constexpr int binom_c(int n, int k) {
+    return (k < 0 || k > n) ? 0 : (k == 0 || k == n) ? 1 : binom_c(n - 1, k - 1) + binom_c(n - 1, k);
+}
+template <class R>
+__device__ __forceinline__ R pow_rt(R o, int e) {  // o^e, 0 <= e <= 3
+    return e == 0 ? R(1) : (e == 1 ? o : (e == 2 ? o * o : o * o * o));
+}
+// u_j(o) = e^{-o} sum_{p>=j} cf[p] C(p,j) o^{p-j}, all j < P
+template <class R, int P>
+__device__ __forceinline__ void ucoef_gen(R o, R eo, const R *cf, R *u) {
+    R op[P];
+    op[0] = R(1);
+#pragma unroll
+    for (int q = 1; q < P; ++q) op[q] = op[q - 1] * o;
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+        R acc = R(0);
+#pragma unroll
+        for (int q = j; q < P; ++q) acc += cf[q] * R(binom_c(q, j)) * op[q - j];
+        u[j] = eo * acc;
+    }
+}
+// the same for one run-time j = e
+template <class R, int P>
+__device__ __forceinline__ R ucoef_sel_gen(R o, R eo, int e, const R *cf) {
+    R acc = R(0);
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+        R c = R(0);
+#pragma unroll
+        for (int j = 0; j <= q; ++j)
+            if (j == e) c = cf[q] * R(binom_c(q, j)) * pow_rt<R>(o, q - j);
+        acc += c;
+    }
+    return eo * acc;
+}
+template <class R, int P>
+__device__ __forceinline__ R csum_gen(const R *m, const R *cf) {
+    R acc = R(0);
+#pragma unroll
+    for (int q = 0; q < P; ++q) acc += cf[q] * m[q];
+    return acc;
+}
+
 // Per-entry coefficients of one pass (groups a0 .. a0+GP-1), from the
 // entry's offsets o and e^{-o}:
 //   insertion w: L1   w[q] = e^{-s} s^q (s = sum of offsets), added to M[q];
 //                product w[g] = prod_k o_k^{a_k} e^{-o_k}, added to M[g][0];
 //   readout   u: L1   u[q] = u_q(s); product u[g] = prod_k u_{a_k}(o_k).
 // d = 1 needs neither (v is added to M[0], the query reads sum_q c_q M[q]).
-template <class R, int P, int NOFF, int KIND>
-__device__ __forceinline__ void pass_coef(int a0, const R *o, const R *eo, R *w, R *u) {
+template <class R, int P, int NOFF, int KIND, bool GEN = false>
+__device__ __forceinline__ void pass_coef(int a0, const R *o, const R *eo, R *w, R *u, const R (*cf)[4] = nullptr) {
     using Tr = Traits<P, NOFF, KIND>;
     if constexpr (NOFF == 0) {
         w[0] = R(1);
@@ -192,18 +252,32 @@ __device__ __forceinline__ void pass_coef(int a0, const R *o, const R *eo, R *w,
         w[0] = es;
 #pragma unroll
         for (int q = 1; q < P; ++q) w[q] = w[q - 1] * s;
-        ucoef<R, P>(s, es, u);
+        if constexpr (GEN)
+            ucoef_gen<R, P>(s, es, cf[0], u);
+        else
+            ucoef<R, P>(s, es, u);
     } else {
 #pragma unroll
         for (int g = 0; g < Tr::GP; ++g) {
             const int a = a0 + g;
             const int e0 = NOFF == 1 ? a : a % P;
-            R ww = eo[0] * pow_sel<R, P>(o[0], e0);
-            R uu = ucoef_sel<R, P>(o[0], eo[0], e0);
+            R ww, uu;
+            if constexpr (GEN) {
+                ww = eo[0] * pow_rt<R>(o[0], e0);
+                uu = ucoef_sel_gen<R, P>(o[0], eo[0], e0, cf[0]);
+            } else {
+                ww = eo[0] * pow_sel<R, P>(o[0], e0);
+                uu = ucoef_sel<R, P>(o[0], eo[0], e0);
+            }
             if constexpr (NOFF == 2) {
                 const int e1 = a / P;
-                ww *= eo[1] * pow_sel<R, P>(o[1], e1);
-                uu *= ucoef_sel<R, P>(o[1], eo[1], e1);
+                if constexpr (GEN) {
+                    ww *= eo[1] * pow_rt<R>(o[1], e1);
+                    uu *= ucoef_sel_gen<R, P>(o[1], eo[1], e1, cf[1]);
+                } else {
+                    ww *= eo[1] * pow_sel<R, P>(o[1], e1);
+                    uu *= ucoef_sel<R, P>(o[1], eo[1], e1);
+                }
             }
             w[g] = ww;
             u[g] = uu;
@@ -225,11 +299,14 @@ __device__ __forceinline__ void add_pass(R *M, R v, const R *w) {
     }
 }
 
-template <class R, int P, int NOFF, int KIND>
-__device__ __forceinline__ R read_pass(const R *M, const R *u) {
+template <class R, int P, int NOFF, int KIND, bool GEN = false>
+__device__ __forceinline__ R read_pass(const R *M, const R *u, const R (*cf)[4] = nullptr) {
     using Tr = Traits<P, NOFF, KIND>;
     if constexpr (NOFF == 0) {
-        return csum<R, P>(M);
+        if constexpr (GEN)
+            return csum_gen<R, P>(M, cf[0]);
+        else
+            return csum<R, P>(M);
     } else if constexpr (Tr::NA == 1) {
         R acc = R(0);
 #pragma unroll
@@ -238,7 +315,12 @@ __device__ __forceinline__ R read_pass(const R *M, const R *u) {
     } else {
         R acc = R(0);
 #pragma unroll
-        for (int g = 0; g < Tr::GP; ++g) acc += u[g] * csum<R, P>(M + g * P);
+        for (int g = 0; g < Tr::GP; ++g) {
+            if constexpr (GEN)
+                acc += u[g] * csum_gen<R, P>(M + g * P, cf[NOFF]);
+            else
+                acc += u[g] * csum<R, P>(M + g * P);
+        }
         return acc;
     }
 }
@@ -270,7 +352,7 @@ __device__ __forceinline__ void set_identity(R *x) {
 // carried-in moments, reading queries and inserting sources.  Segments
 // longer than a tile receive their carry from the aggregate pass
 // (MODE == SCAN_AGG writes each tile's totals; k_carry_scan scans them).
-template <class R, int P, int NOFF, int KIND, int MODE>
+template <class R, int P, int NOFF, int KIND, int MODE, bool GEN = false>
 __device__ __forceinline__ void scan_tile(const ScanArgs<R> &A, const WorkItem wi, int r0, int r1) {
     using Tr = Traits<P, NOFF, KIND>;
     constexpr int GM = Tr::GM, CP = Tr::CP, SMM = Tr::SM, AG = Tr::AG, NCH = Tr::NCH;
@@ -400,7 +482,7 @@ __device__ __forceinline__ void scan_tile(const ScanArgs<R> &A, const WorkItem w
                                 oi[k] = NOFF ? o[k][i] : R(0);
                                 eoi[k] = NOFF ? eo[k][i] : R(1);
                             }
-                            pass_coef<R, P, NOFF, KIND>(a0, oi, eoi, w, u);
+                            pass_coef<R, P, NOFF, KIND, GEN>(a0, oi, eoi, w, u, A.cf);
                             add_pass<R, P, NOFF, KIND>(inc[dd] + 1, role == cA ? v[i] : R(0), w);
                             if constexpr (CP == 2) add_pass<R, P, NOFF, KIND>(inc[dd] + 1 + GM, role == cB ? v[i] : R(0), w);
                         }
@@ -523,16 +605,16 @@ __device__ __forceinline__ void scan_tile(const ScanArgs<R> &A, const WorkItem w
                                 oi[k] = NOFF ? o[k][i] : R(0);
                                 eoi[k] = NOFF ? eo[k][i] : R(1);
                             }
-                            pass_coef<R, P, NOFF, KIND>(a0, oi, eoi, w, u);
+                            pass_coef<R, P, NOFF, KIND, GEN>(a0, oi, eoi, w, u, A.cf);
                             if constexpr (CP == 1) {
-                                if (ok) out[i] += read_pass<R, P, NOFF, KIND>(st[dd], u);
+                                if (ok) out[i] += read_pass<R, P, NOFF, KIND, GEN>(st[dd], u, A.cf);
                                 add_pass<R, P, NOFF, KIND>(st[dd], ok ? v[i] : R(0), w);
                             } else {
                                 const bool sa = ok && role == cA, sb = ok && role == cB;
                                 R msel[GM];
 #pragma unroll
                                 for (int m = 0; m < GM; ++m) msel[m] = sa ? st[dd][GM + m] : st[dd][m];
-                                const R rd = read_pass<R, P, NOFF, KIND>(msel, u);
+                                const R rd = read_pass<R, P, NOFF, KIND, GEN>(msel, u, A.cf);
                                 out[i] += (sa || sb) ? rd : R(0);
                                 add_pass<R, P, NOFF, KIND>(st[dd], sa ? v[i] : R(0), w);
                                 add_pass<R, P, NOFF, KIND>(st[dd] + GM, sb ? v[i] : R(0), w);
@@ -550,10 +632,10 @@ __device__ __forceinline__ void scan_tile(const ScanArgs<R> &A, const WorkItem w
     }
 }
 
-template <class R, int P, int NOFF, int KIND, int MODE>
-__global__ void __launch_bounds__(kScanThreads, FGK_SCAN_MINB) k_level_scan(ScanArgs<R> A) {
+template <class R, int P, int NOFF, int KIND, int MODE, bool GEN = false>
+__global__ void __launch_bounds__(kScanThreads, GEN ? 1 : FGK_SCAN_MINB) k_level_scan(ScanArgs<R> A) {
     if (A.gate && *A.gate == 0) return;
-    scan_tile<R, P, NOFF, KIND, MODE>(A, A.items[blockIdx.x], 0, A.nrhs);
+    scan_tile<R, P, NOFF, KIND, MODE, GEN>(A, A.items[blockIdx.x], 0, A.nrhs);
 }
 
 // one warp: exclusive carries of one long segment (tiles a0 .. a0+nt-1 of the
@@ -623,10 +705,13 @@ __global__ void k_diag_init(const R *__restrict__ V, int64_t n, R s2, R *__restr
     Y[i] = s2 * V[i];
 }
 
-template <class R, int P, int NOFF, int KIND>
-int run_levels(Plan *p, const R *Vq, int nrhs, R *Yq, R *ws, cudaStream_t s, const int *gate) {
+template <class R, int P, int NOFF, int KIND, bool GEN = false>
+int run_levels(Plan *p, const R *Vq, int nrhs, R *Yq, R *ws, cudaStream_t s, const int *gate,
+               const double (*cf)[4] = nullptr) {
     using Tr = Traits<P, NOFF, KIND>;
     ScanArgs<R> A;
+    for (int k = 0; k < kMaxD; ++k)
+        for (int q = 0; q < 4; ++q) A.cf[k][q] = cf ? (R)cf[k][q] : R(0);
     A.lv_q = p->lv_q;
     A.lv_dl = std::is_same<R, float>::value ? (const R *)p->lv_dl32 : (const R *)p->lv_dl64;
     A.lv_off = std::is_same<R, float>::value ? (const R *)p->lv_off32 : (const R *)p->lv_off64;
@@ -645,7 +730,7 @@ int run_levels(Plan *p, const R *Vq, int nrhs, R *Yq, R *ws, cudaStream_t s, con
     if (p->n_long > 0) {
         A.items = p->long_items;
         A.agg = agg;
-        k_level_scan<R, P, NOFF, KIND, SCAN_AGG><<<p->n_long, kScanThreads, 0, s>>>(A);
+        k_level_scan<R, P, NOFF, KIND, SCAN_AGG, GEN><<<p->n_long, kScanThreads, 0, s>>>(A);
         FGK_LAUNCH_CHECK();
         const int64_t nthr = (int64_t)p->n_long_segments * 2 * nrhs * Tr::NPT * 32;
         k_carry_scan<R, P, NOFF, KIND><<<grid_for(nthr, 128), 128, 0, s>>>(agg, carry, p->long_seg,
@@ -663,7 +748,7 @@ int run_levels(Plan *p, const R *Vq, int nrhs, R *Yq, R *ws, cudaStream_t s, con
             FGK_CUDA(cudaEventCreate(&e1));
             FGK_CUDA(cudaEventRecord(e0, s));
         }
-        k_level_scan<R, P, NOFF, KIND, SCAN_OUT><<<p->n_items, kScanThreads, 0, s>>>(A);
+        k_level_scan<R, P, NOFF, KIND, SCAN_OUT, GEN><<<p->n_items, kScanThreads, 0, s>>>(A);
         FGK_LAUNCH_CHECK();
         if (e0) {
             FGK_CUDA(cudaEventRecord(e1, s));
@@ -710,5 +795,22 @@ int run_levels_dispatch(Plan *p, const R *Vq, int nrhs, R *Yq, R *ws, cudaStream
     set_error("no scan kernel for P=%d d=%d kind=%d", P, p->d, p->kind);
     return FGK_ERR_INTERNAL;
 }
+
+// Scratch of the generic-coefficient scans: the most passes x aggregate size
+// among them (product, 4 moments, d = 3: 2 channel pairs x 16 offset groups x
+// (1 + 2 x 4)).
+template <class R>
+size_t scan_ws_elems_gen(const Plan *p, int nrhs) {
+    return (size_t)2 * p->n_long * 2 * nrhs * 288 + 64;
+}
+
+// Generic-coefficient scans (the lengthscale derivatives): moments P4 (one
+// more than the kernel's P), readout coefficients cf (see ScanArgs::cf),
+// kind as given (the product kernel with nu = 1/2 is not reduced to L1 here:
+// a derivative factor differs per dimension).  Instantiated in the
+// translation units of the gradient products.
+template <class R>
+int run_levels_gen_dispatch(Plan *p, int P4, int kind, const R *Vq, int nrhs, R *Yq, R *ws, cudaStream_t s,
+                            const double (*cf)[4]);
 
 }  // namespace fgk

@@ -55,7 +55,7 @@ class fgk_plan_info(ctypes.Structure):
                 ("ell", ctypes.c_double * 3), ("device_bytes", ctypes.c_size_t)]
 
 
-EXPORTS = ["fgk_set_allocator", "fgk_build", "fgk_matvec", "fgk_matvec_q", "fgk_matvec_q_noalloc", "fgk_cg_solve", "fgk_bytes_estimate",
+EXPORTS = ["fgk_set_allocator", "fgk_build", "fgk_matvec", "fgk_matvec_dlogell", "fgk_matvec_q", "fgk_matvec_q_noalloc", "fgk_cg_solve", "fgk_bytes_estimate",
            "fgk_destroy", "fgk_last_error", "fgk_kernel_launches", "fgk_scan_timing", "fgk_get_info",
            "fgk_get_permutation", "fgk_get_level", "fgk_batch_create", "fgk_batch_layout", "fgk_batch_matvec_q",
            "fgk_batch_cg_solve", "fgk_batch_destroy", "fgk_precond_build", "fgk_precond_info",
@@ -83,6 +83,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.fgk_build.restype = i32
         lib.fgk_matvec.argtypes = [vp, vp, i32, vp, i32, vp]
         lib.fgk_matvec.restype = i32
+        lib.fgk_matvec_dlogell.argtypes = [vp, vp, i32, vp, i32, i32, vp]
+        lib.fgk_matvec_dlogell.restype = i32
         lib.fgk_matvec_q.argtypes = [vp, vp, i32, vp, i32, vp]
         lib.fgk_matvec_q.restype = i32
         lib.fgk_matvec_q_noalloc.argtypes = [vp, vp, i32, vp, i32, vp]
@@ -221,6 +223,26 @@ def fgk_matvec(h: Handle, V: torch.Tensor, precision="f64", out: torch.Tensor | 
     if out is None:
         out = torch.empty_like(V2)
     _check(lib.fgk_matvec(h.ptr, V2.data_ptr(), V2.shape[1], out.data_ptr(), prec, _stream(stream)))
+    return out.squeeze(1) if squeeze else out
+
+
+def fgk_matvec_dlogell(h: Handle, V: torch.Tensor, dim: int = -1, precision="f64", out: torch.Tensor | None = None,
+                       stream=None):
+    """Y = (dK / d log ell_dim) V (dim = -1: all lengthscales scaled
+    together); see include/fgk.h.  Asynchronous on the stream."""
+    lib = load()
+    prec = {"f64": FGK_F64, "f32": FGK_F32}[precision] if isinstance(precision, str) else int(precision)
+    dt = torch.float64 if prec == FGK_F64 else torch.float32
+    if not V.is_cuda or V.dtype != dt or not V.is_contiguous():
+        raise TypeError(f"V must be a contiguous CUDA {dt} tensor")
+    squeeze = V.dim() == 1
+    V2 = V.unsqueeze(1) if squeeze else V
+    if V2.shape[0] != h.N:
+        raise ValueError("V has the wrong number of rows")
+    if out is None:
+        out = torch.empty_like(V2)
+    _check(lib.fgk_matvec_dlogell(h.ptr, V2.data_ptr(), V2.shape[1], out.data_ptr(), int(dim), prec,
+                                  _stream(stream)))
     return out.squeeze(1) if squeeze else out
 
 
