@@ -23,6 +23,15 @@ TEST INFRASTRUCTURE ONLY.
                   estimator and Algorithm 1), then alpha = A^{-1}(y - H beta),
                   the weights of eq. gp_mean with m(x) = H beta.
 * ``true_residual``  ||b - A x|| / ||b|| per column, A applied by a callable.
+* ``cg_lanczos``  Algorithm 2 again, recording per column the CG
+                  coefficients alpha_k of every step and beta_k of every step
+                  that continued, from which ``lanczos_T`` assembles the
+                  tridiagonal Lanczos matrix: T[k][k] = 1/alpha_k +
+                  beta_{k-1}/alpha_{k-1}, T[k+1][k] = sqrt(beta_k)/alpha_k.
+* ``slq_quadrature``  gamma e_1^T log(T) e_1 (eigen-decomposition of T: the
+                  Gauss quadrature of eq. approximationLogDet, gamma the
+                  squared norm of the Lanczos start vector); ``slq_logdet``
+                  the Hutchinson average over probes plus log det P.
 * ``posterior_mean``  E[f(z) | x, y] = k_z^T alpha + h(z)^T beta (eq. gp_mean,
                   with alpha = (K + sigma^2 I)^{-1}(y - H beta) as eq. gp_mean_2),
                   given the cross-covariance rows k_z^T.
@@ -152,3 +161,78 @@ def posterior_mean(Kzx, alpha, Hz=None, beta=None):
     if Hz is not None:
         out = out + np.asarray(Hz, dtype=np.float64) @ np.asarray(beta, dtype=np.float64)
     return out
+
+
+def cg_lanczos(apply_A, B, tol: float, maxit: int, apply_Pinv=None):
+    """Algorithm 2 with the Lanczos coefficients: returns (X, alphas, betas,
+    gammas) with alphas[j] the alpha of every step of column j, betas[j] the
+    beta of every step after which column j continued, and gammas[j] =
+    b_j^T s_P(b_j), the squared norm of the Lanczos start vector."""
+    B = np.asarray(B, dtype=np.float64)
+    B = B.reshape(B.shape[0], -1)
+    n, m = B.shape
+    s_P = (lambda R: R.copy()) if apply_Pinv is None else (lambda R: np.asarray(apply_Pinv(R)).reshape(n, m))
+    X = np.zeros_like(B)
+    R = B - apply_A(X)
+    Pb = s_P(R)
+    k = np.einsum("ij,ij->j", Pb, R)
+    gammas = k.copy()
+    bnorm = np.linalg.norm(B, axis=0)
+    done = np.linalg.norm(R, axis=0) <= tol * bnorm
+    alphas = [[] for _ in range(m)]
+    betas = [[] for _ in range(m)]
+    for _ in range(maxit):
+        if done.all():
+            break
+        T = apply_A(Pb)
+        pt = np.einsum("ij,ij->j", Pb, T)
+        alpha = np.where(done, 0.0, k / np.where(pt == 0, 1.0, pt))
+        X += alpha * Pb
+        R -= alpha * T
+        for j in range(m):
+            if not done[j]:
+                alphas[j].append(float(alpha[j]))
+        now = np.linalg.norm(R, axis=0) <= tol * bnorm
+        newly = now & ~done
+        Z = s_P(R)
+        k_prev = k
+        k = np.einsum("ij,ij->j", Z, R)
+        beta = k / np.where(k_prev == 0, 1.0, k_prev)
+        for j in range(m):
+            if not done[j] and not newly[j]:
+                betas[j].append(float(beta[j]))
+        done = done | now
+        beta = np.where(done, 0.0, beta)
+        Pb = Z + beta * Pb
+    return X, alphas, betas, gammas
+
+
+def lanczos_T(alphas, betas):
+    """The tridiagonal Lanczos matrix of len(alphas) CG steps (Algorithm 2's
+    entries; the steps' betas between them)."""
+    a = np.asarray(alphas, dtype=np.float64)
+    b = np.asarray(betas, dtype=np.float64)[: max(len(a) - 1, 0)]
+    mm = a.size
+    T = np.zeros((mm, mm))
+    for i in range(mm):
+        T[i, i] = 1.0 / a[i] + (b[i - 1] / a[i - 1] if i > 0 else 0.0)
+        if i + 1 < mm:
+            T[i + 1, i] = T[i, i + 1] = np.sqrt(b[i]) / a[i]
+    return T
+
+
+def slq_quadrature(alphas, betas, gamma: float) -> float:
+    """gamma e_1^T log(T) e_1 = gamma sum_i v_i[0]^2 log(lambda_i) over the
+    eigenpairs of T."""
+    lam, V = np.linalg.eigh(lanczos_T(alphas, betas))
+    return float(gamma * np.sum(V[0, :] ** 2 * np.log(lam)))
+
+
+def slq_logdet(apply_A, B, m: int, tol: float, apply_Pinv=None, logdet_P: float = 0.0):
+    """log det A ~ log det P + mean over the probe columns of B of their
+    quadratures (eq. approximationLogDet with the exact start-vector norms;
+    with a preconditioner the probes are N(0, P) draws).  Returns
+    (estimate, per-probe quadratures, Lanczos steps per probe, solves)."""
+    X, al, be, ga = cg_lanczos(apply_A, B, tol, m, apply_Pinv)
+    quad = np.array([slq_quadrature(al[j], be[j], ga[j]) if al[j] else 0.0 for j in range(len(al))])
+    return logdet_P + float(quad.mean()), quad, np.array([len(a) for a in al]), X
