@@ -273,6 +273,60 @@ int fgk_cg_solve_pc(fgk_handle h, fgk_precond pc, const double *y, int nrhs, dou
                     double tol, int maxit, int mode, double *alpha, double *beta, fgk_cg_info *info,
                     fgk_stream_t stream);
 
+/* ---- log-determinant by stochastic Lanczos quadrature (App. A.2) ---- */
+
+/* Probe vectors distributed as N(0, P) for the preconditioned log-determinant
+ * estimate: B = L_hi E_r + sigma E_n, where L_hi is the FP32 factor the
+ * preconditioner applies (P = L_hi L_hi^T + sigma2 I exactly).  The caller
+ * draws the standard normal numbers:
+ *   E_r  device, k x nprobe FP64 row-major (k: fgk_precond_info's rank),
+ *   E_n  device, N x nprobe FP64 row-major (original point order),
+ *   B    device, N x nprobe FP64 row-major (original point order),
+ *   1 <= nprobe <= 64.  Asynchronous. */
+int fgk_precond_sample(fgk_precond pc, const double *E_r, const double *E_n, int nprobe, double *B,
+                       fgk_stream_t stream);
+
+typedef struct {
+    double logdet;          /* the estimate of log det(K + sigma2 I) */
+    double logdet_precond;  /* log det P added to it (0 without a preconditioner) */
+    int steps_max;          /* the longest Lanczos process of the probes */
+    int solve_status;       /* the CG solve's own return code (FGK_OK or FGK_NOT_CONVERGED) */
+    double max_true_resid;  /* of the solves X */
+} fgk_slq_report;
+
+/* log det(K + sigma2 I) by stochastic Lanczos quadrature: the trace of the
+ * matrix logarithm (eq. approximationLogDet) estimated with the probes B by
+ * Hutchinson's estimator, each quadratic form b^T log(.) b taken from the
+ * tridiagonal Lanczos matrix T_b that CG with a zero initial guess produces
+ * (Algorithm 2: T[k][k] = 1/alpha_k + beta_{k-1}/alpha_{k-1},
+ * T[k+1][k] = sqrt(beta_k)/alpha_k) as gamma_b e_1^T log(T_b) e_1, with
+ * gamma_b = b^T P^{-1} b the squared norm of the Lanczos start vector (the
+ * paper approximates it by N).  With a preconditioner the quadrature is of
+ * P^{-1/2}(K + sigma2 I)P^{-1/2} and log det P (Sylvester, App. A.3) is added;
+ * the probes must then be N(0, P) samples (fgk_precond_sample), else N(0, I).
+ *   pc      NULL (no preconditioner) or built on h for this sigma2.
+ *   B       device, N x nprobe FP64 row-major, original point order;
+ *           1 <= nprobe <= 64.
+ *   m       the most CG (Lanczos) steps per probe; tol the CG stop test
+ *           (relative FP64 true residual, as fgk_cg_solve).  A column's
+ *           Lanczos process ends at its first residual replacement.
+ *   X       device N x nprobe or NULL: the solves (K + sigma2 I)^{-1} B (for
+ *           the Hutchinson trace term of eq. gp_log_likelihood_derivative).
+ *   quad    host nprobe or NULL: gamma_b e_1^T log(T_b) e_1 per probe.
+ *   steps   host nprobe or NULL: Lanczos steps per probe.
+ *   rep     host: the estimate and diagnostics.
+ * The solve runs with FP64 scans.  Synchronises `stream`. */
+int fgk_slq_logdet(fgk_handle h, fgk_precond pc, double sigma2, const double *B, int nprobe, int m, double tol,
+                   double *X, double *quad, int *steps, fgk_slq_report *rep, fgk_stream_t stream);
+
+/* e_1^T log(T) e_1 for the Lanczos matrix T of m CG steps with coefficients
+ * alpha[0..m) and beta[0..m-1) (Algorithm 2's formulas above): the Gauss
+ * quadrature of log with T's eigenvalues as nodes and the squared first
+ * components of its eigenvectors as weights.  Host arrays; no GPU work.
+ * FGK_ERR_INVALID for m < 1, alpha <= 0 or beta < 0; FGK_ERR_BREAKDOWN if a
+ * Ritz value is <= 0. */
+int fgk_lanczos_logquad(const double *alpha, const double *beta, int m, double *out);
+
 /* ---- batches: many problems advanced together (d <= 2) ---- */
 
 typedef struct fgk_batch_s *fgk_batch;

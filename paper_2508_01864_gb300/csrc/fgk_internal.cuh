@@ -203,9 +203,25 @@ Precond *pc_of(fgk_precond h);  // the handle's preconditioner (NULL for NULL)
 double pc_sigma2(const Precond *pc);
 const Plan *pc_plan(const Precond *pc);
 
+double pc_logdet(const Precond *pc);  // log det P (Sylvester)
+int pc_rank(const Precond *pc);
+
+// Lanczos coefficients recorded by a CG solve (Algorithm 2): dev_log holds
+// (alpha, beta) per iteration and column, [(it * ncols + j) * 2 + {0, 1}] for
+// it < cap; after the solve n[j] counts the iterations of column j's single
+// Lanczos process (it ends at the column's first residual replacement) and
+// gamma[j] = b_j^T P^{-1} b_j, the squared norm of its start vector.
+struct LanczosLog {
+    double *dev_log = nullptr;
+    int cap = 0;
+    int n[64] = {};
+    double gamma[64] = {};
+};
+
 // CG / refinement / GLS (fgk_solve.cu); pc may be NULL (s_P = I)
 int cg_solve(Plan *p, Precond *pc, const double *y, int nrhs, double sigma2, const double *H, int L,
-             double tol, int maxit, int mode, double *alpha, double *beta, fgk_cg_info *info, cudaStream_t s);
+             double tol, int maxit, int mode, double *alpha, double *beta, fgk_cg_info *info, cudaStream_t s,
+             LanczosLog *lz = nullptr);
 size_t solve_ws_bytes(const Plan *p, int ncols);
 
 inline int ceil_log2_i64(int64_t n) {

@@ -781,6 +781,21 @@ __global__ void __launch_bounds__(kTR) k_pc_apply(const __grid_constant__ CUtens
     }
 }
 
+// B[orig][j] = sum_m Lhi[m][q] E_r[m][j] + sigma E_n[orig][j] (orig = perm0[q]), FP64
+__global__ void k_pc_sample(const float *__restrict__ Lhi, int64_t ldN, int r, int64_t N,
+                            const int32_t *__restrict__ perm0, const double *__restrict__ Er,
+                            const double *__restrict__ En, int nprobe, double sigma, double *__restrict__ B) {
+    const int64_t n = N * nprobe;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = t / nprobe;
+        const int j = (int)(t % nprobe);
+        double acc = 0.0;
+        for (int m = 0; m < r; ++m) acc = fma((double)Lhi[(size_t)m * ldN + q], Er[(size_t)m * nprobe + j], acc);
+        const int64_t o = (int64_t)perm0[q] * nprobe + j;
+        B[o] = acc + sigma * En[o];
+    }
+}
+
 // L in the caller's point order: out[orig * r + m] = Lhi[m][q] + Llo[m][q]
 __global__ void k_pc_factor_out(const float *__restrict__ Lhi, const float *__restrict__ Llo, int64_t ldN, int r,
                                 int64_t N, const int32_t *__restrict__ perm0, double *__restrict__ out) {
@@ -850,6 +865,8 @@ int pc_reserve(Precond *pc, int ncols, cudaStream_t s) {
 }
 
 double pc_sigma2(const Precond *pc) { return pc->sigma2; }
+double pc_logdet(const Precond *pc) { return pc->logdet; }
+int pc_rank(const Precond *pc) { return pc->rank; }
 const Plan *pc_plan(const Precond *pc) { return pc->plan; }
 
 static int cols_per_pass(int ncols) { return ncols >= 8 ? 8 : (ncols >= 3 ? (ncols == 3 || ncols == 4 ? 4 : 8) : ncols); }
@@ -1164,6 +1181,21 @@ int fgk_precond_factor(fgk_precond pc, double *L, fgk_stream_t stream) {
     k_pc_factor_out<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(pc->L32, pc->Llo, pc->ldN, pc->rank,
                                                                          pc->plan->N,
                                                                          pc->plan->perm[0], L);
+    FGK_LAUNCH_CHECK();
+    return FGK_OK;
+}
+
+int fgk_precond_sample(fgk_precond pc, const double *E_r, const double *E_n, int nprobe, double *B,
+                       fgk_stream_t stream) {
+    clear_error();
+    if (!pc || !E_n || !B || (pc->rank > 0 && !E_r) || nprobe < 1 || nprobe > kPcMaxCols) {
+        set_error("fgk_precond_sample: need pc, E_r (rank > 0), E_n, B and 1 <= nprobe <= %d", kPcMaxCols);
+        return FGK_ERR_INVALID;
+    }
+    const int64_t n = pc->plan->N * nprobe;
+    k_pc_sample<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(pc->L32, pc->ldN, pc->rank, pc->plan->N,
+                                                                    pc->plan->perm[0], E_r, E_n, nprobe,
+                                                                    std::sqrt(pc->sigma2), B);
     FGK_LAUNCH_CHECK();
     return FGK_OK;
 }

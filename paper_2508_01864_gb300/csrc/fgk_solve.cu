@@ -80,6 +80,15 @@ struct ColState {
     int bd[kMaxCols];  // column met p^T A p <= 0 (set by k_update_xr, cleared by the host)
     int n_active;
     int breakdown;
+    // Lanczos coefficients (Algorithm 2): alpha of the last x/r update; when
+    // lz is set, k_update_p logs (alpha, beta) of every iteration of every
+    // column not stopped by the host, lz[(it * ncols + j) * 2 + {0, 1}],
+    // it < lz_cap, and lz_n[j] counts them
+    double alpha[kMaxCols];
+    double *lz;
+    int lz_cap;
+    int lz_n[kMaxCols];
+    int lz_stop[kMaxCols];
 };
 
 constexpr int kMaxRestarts = 4;
@@ -184,6 +193,7 @@ __global__ void k_update_xr(double *__restrict__ x, double *__restrict__ r, cons
                 }
             }
             s_alpha[j] = a;
+            if (blockIdx.x == 0) st->alpha[j] = a;
         }
     }
     __syncthreads();
@@ -239,6 +249,12 @@ __global__ void k_update_p(double *__restrict__ p, float *__restrict__ p32, W *_
                 if (act) st->rr[j] = rr;
                 st->active_next[j] = still;
                 st->beta[j] = s_beta[j];
+                if (act && st->lz && !st->lz_stop[j] && st->lz_n[j] < st->lz_cap && !st->bd[j]) {
+                    const int it = st->lz_n[j];
+                    st->lz[((size_t)it * ncols + j) * 2] = st->alpha[j];
+                    st->lz[((size_t)it * ncols + j) * 2 + 1] = s_beta[j];
+                    st->lz_n[j] = it + 1;
+                }
                 if (act) st->iters[j] += 1;
             }
         }
@@ -402,7 +418,8 @@ size_t solve_ws_bytes(const Plan *p, int ncols) {
 }
 
 int cg_solve(Plan *p, Precond *pc, const double *y, int nrhs, double sigma2, const double *H, int L, double tol,
-             int maxit, int mode, double *alpha, double *beta, fgk_cg_info *info, cudaStream_t user_s) {
+             int maxit, int mode, double *alpha, double *beta, fgk_cg_info *info, cudaStream_t user_s,
+             LanczosLog *lzlog) {
     const int64_t N = p->N;
     const int ncols = nrhs + std::max(L, 0);
     if (ncols > kMaxCols) {
@@ -463,6 +480,7 @@ int cg_solve(Plan *p, Precond *pc, const double *y, int nrhs, double sigma2, con
     uint64_t graph_nodes = 0;
     std::vector<double> bnorm(ncols), rnorm(ncols), rho_ref(ncols);
     std::vector<int> confirmed(ncols, 0);
+    std::vector<int> snap_lz_n(ncols, 0);  // Lanczos coefficients logged per column (last device snapshot)
     int iters_total = 0, refinements = 0, n_f32 = 0, n_f64 = 0;
     bool converged = false, breakdown = false;
     // mixed mode: replace the recursive residual by the FP64 true residual
@@ -639,6 +657,11 @@ int cg_solve(Plan *p, Precond *pc, const double *y, int nrhs, double sigma2, con
             hs.active[j] = hs.active_next[j] = !confirmed[j];
             hs.n_active += hs.active[j];
         }
+        if (lzlog) {  // Lanczos coefficients: the start vector's norm^2 in the P^{-1} metric (rho_0)
+            hs.lz = lzlog->dev_log;
+            hs.lz_cap = lzlog->cap;
+            for (int j = 0; j < ncols; ++j) lzlog->gamma[j] = hs.rho[j];
+        }
         FGK_CUDA(cudaMemcpyAsync(st, &hs, sizeof(hs), cudaMemcpyHostToDevice, s));
         if ((rc = capture())) break;
         ColState snap = hs;
@@ -656,6 +679,7 @@ int cg_solve(Plan *p, Precond *pc, const double *y, int nrhs, double sigma2, con
             add_kernel_launches((int64_t)graph_nodes * k);
             FGK_CUDA(cudaMemcpyAsync(&snap, st, sizeof(ColState), cudaMemcpyDeviceToHost, s));
             FGK_CUDA(cudaStreamSynchronize(s));
+            for (int j = 0; j < ncols; ++j) snap_lz_n[j] = snap.lz_n[j];
             const int after = *std::max_element(snap.iters, snap.iters + ncols);
             iters_total += after - before;
             if (mixed) n_f32 += after - before; else n_f64 += after - before;
@@ -722,6 +746,7 @@ int cg_solve(Plan *p, Precond *pc, const double *y, int nrhs, double sigma2, con
             if ((rc = init_p())) break;  // the residual product overwrote W64 (FP64 mode)
             snap.n_active = 0;
             for (int j = 0; j < ncols; ++j) {
+                snap.lz_stop[j] = 1;  // a replaced residual ends the column's Lanczos process
                 if (!confirmed[j] && rnorm[j] <= tol * bnorm[j]) confirmed[j] = 1;
                 snap.active[j] = snap.active_next[j] = !confirmed[j];
                 if (!confirmed[j]) {
@@ -766,6 +791,8 @@ int cg_solve(Plan *p, Precond *pc, const double *y, int nrhs, double sigma2, con
         FGK_CUDA(cudaStreamSynchronize(s));
     } while (0);
 
+    if (lzlog)
+        for (int j = 0; j < ncols; ++j) lzlog->n[j] = snap_lz_n[j];
     if (gexec) cudaGraphExecDestroy(gexec);
     if (graph) cudaGraphDestroy(graph);
     dev_free((void *)B, s);

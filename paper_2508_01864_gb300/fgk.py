@@ -49,6 +49,11 @@ class fgk_precond_report(ctypes.Structure):
                 ("trace_resid", ctypes.c_double), ("logdet", ctypes.c_double), ("device_bytes", ctypes.c_size_t)]
 
 
+class fgk_slq_report(ctypes.Structure):
+    _fields_ = [("logdet", ctypes.c_double), ("logdet_precond", ctypes.c_double), ("steps_max", ctypes.c_int32),
+                ("solve_status", ctypes.c_int32), ("max_true_resid", ctypes.c_double)]
+
+
 class fgk_plan_info(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64), ("d", ctypes.c_int32), ("two_nu", ctypes.c_int32), ("kind", ctypes.c_int32),
                 ("L", ctypes.c_int32), ("n_levels", ctypes.c_int32), ("outscale2", ctypes.c_double),
@@ -60,7 +65,8 @@ EXPORTS = ["fgk_set_allocator", "fgk_build", "fgk_matvec", "fgk_matvec_dlogell",
            "fgk_get_permutation", "fgk_get_level", "fgk_batch_create", "fgk_batch_layout", "fgk_batch_matvec_q",
            "fgk_batch_cg_solve", "fgk_batch_destroy", "fgk_precond_build", "fgk_precond_info",
            "fgk_precond_factor", "fgk_precond_apply", "fgk_precond_destroy", "fgk_cg_solve_pc",
-           "fgk_kernel_timing", "fgk_predict", "fgk_batch_cg_solve_pc"]
+           "fgk_kernel_timing", "fgk_predict", "fgk_batch_cg_solve_pc", "fgk_precond_sample", "fgk_slq_logdet",
+           "fgk_lanczos_logquad"]
 
 _lock = threading.Lock()
 _lib = None
@@ -132,6 +138,13 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.fgk_precond_factor.restype = i32
         lib.fgk_precond_apply.argtypes = [vp, vp, i32, vp, vp]
         lib.fgk_precond_apply.restype = i32
+        lib.fgk_precond_sample.argtypes = [vp, vp, vp, i32, vp, vp]
+        lib.fgk_precond_sample.restype = i32
+        lib.fgk_slq_logdet.argtypes = [vp, vp, dbl, vp, i32, i32, dbl, vp, ctypes.POINTER(dbl), ctypes.POINTER(i32),
+                                       ctypes.POINTER(fgk_slq_report), vp]
+        lib.fgk_slq_logdet.restype = i32
+        lib.fgk_lanczos_logquad.argtypes = [ctypes.POINTER(dbl), ctypes.POINTER(dbl), i32, ctypes.POINTER(dbl)]
+        lib.fgk_lanczos_logquad.restype = i32
         lib.fgk_precond_destroy.argtypes = [vp]
         lib.fgk_precond_destroy.restype = i32
         lib.fgk_cg_solve_pc.argtypes = [vp, vp, vp, i32, dbl, vp, i32, dbl, i32, i32, vp, vp,
@@ -387,6 +400,47 @@ def fgk_precond_apply(pc: Precond, R: torch.Tensor, out: torch.Tensor | None = N
     Z = torch.empty_like(R2) if out is None else out
     _check(load().fgk_precond_apply(pc.ptr, R2.data_ptr(), R2.shape[1], Z.data_ptr(), _stream(stream)))
     return Z.squeeze(1) if R.dim() == 1 else Z
+
+
+def fgk_precond_sample(pc: Precond, E_r: torch.Tensor, E_n: torch.Tensor, stream=None) -> torch.Tensor:
+    """Probes B = L_hi E_r + sigma E_n ~ N(0, P) from the caller's standard
+    normal draws E_r (k x nprobe) and E_n (N x nprobe), FP64 CUDA tensors."""
+    En = _dev_f64_2d(E_n, "E_n")
+    Er = _dev_f64_2d(E_r, "E_r") if E_r.numel() else E_r
+    B = torch.empty_like(En)
+    _check(load().fgk_precond_sample(pc.ptr, Er.data_ptr() if Er.numel() else None, En.data_ptr(), En.shape[1],
+                                     B.data_ptr(), _stream(stream)))
+    return B
+
+
+def fgk_slq_logdet(h: Handle, B: torch.Tensor, sigma2: float, m: int, tol: float = 1e-8, pc: Precond | None = None,
+                   want_solves: bool = False, stream=None) -> dict:
+    """log det(K + sigma2 I) by stochastic Lanczos quadrature with the probe
+    columns of B (N x nprobe FP64 CUDA tensor, caller's order); see
+    include/fgk.h.  Returns the estimate, log det P, per-probe quadrature
+    values and Lanczos steps, and (want_solves) the solves (K + sigma2 I)^-1 B."""
+    B2 = _dev_f64_2d(B, "B")
+    nprobe = B2.shape[1]
+    X = torch.empty_like(B2) if want_solves else None
+    quad = (ctypes.c_double * nprobe)()
+    steps = (ctypes.c_int32 * nprobe)()
+    rep = fgk_slq_report()
+    _check(load().fgk_slq_logdet(h.ptr, pc.ptr if pc is not None else None, float(sigma2), B2.data_ptr(), nprobe,
+                                 int(m), float(tol), X.data_ptr() if X is not None else None, quad, steps,
+                                 ctypes.byref(rep), _stream(stream)))
+    return {"logdet": rep.logdet, "logdet_precond": rep.logdet_precond, "steps_max": rep.steps_max,
+            "solve_status": rep.solve_status, "max_true_resid": rep.max_true_resid, "quad": list(quad),
+            "steps": list(steps), "X": X}
+
+
+def fgk_lanczos_logquad(alpha, beta) -> float:
+    """e_1^T log(T) e_1 of the Lanczos matrix built from CG coefficients
+    (host computation, no GPU)."""
+    a = (ctypes.c_double * len(alpha))(*[float(x) for x in alpha])
+    b = (ctypes.c_double * max(1, len(beta)))(*([float(x) for x in beta] or [0.0]))
+    out = ctypes.c_double()
+    _check(load().fgk_lanczos_logquad(a, b, len(alpha), ctypes.byref(out)))
+    return out.value
 
 
 def fgk_precond_destroy(pc: Precond) -> None:
