@@ -338,6 +338,74 @@ def run_mvm_only(args, local):
     return 0
 
 
+def run_likelihood(args, local):
+    """The likelihood pieces on the d=2 workload (N = 200000): the gradient
+    products (dK/d log ell_m) V with FP32 and FP64 scans (every lengthscale),
+    and the log-determinant by stochastic Lanczos quadrature with 16 probes and
+    the rank-200 preconditioner, with the Hutchinson trace of the gradient from
+    its solves.  Medians of --steps runs after --warmup."""
+    import torch
+
+    import workloads
+    from paper_2508_01864_gb300 import fgk
+
+    torch.cuda.set_device(local)
+    p = workloads.c2()
+    X = torch.as_tensor(p.X, device="cuda")
+    h = fgk.fgk_build(X, p.nu, p.ell, kind="product")
+    gen = torch.Generator(device="cuda").manual_seed(11)
+    out = {"metric": "likelihood pieces on the d=2 workload", "workload": WORKLOAD.split(";")[0]}
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    for prec, dt in (("f32", torch.float32), ("f64", torch.float64)):
+        V = torch.randn(p.N, 1, dtype=dt, device="cuda", generator=gen)
+        for dim in (0, 1):
+            ms = timed(lambda: fgk.fgk_matvec_dlogell(h, V, dim, prec))
+            out[f"dlogell_{prec}_dim{dim}_ms"] = ms
+            out[f"dlogell_{prec}_dim{dim}_nrhs_per_s"] = p.N / (ms * 1e-3)
+    nprobe, rank = 16, 200
+    pc = fgk.fgk_precond_build(h, rank, p.sigma2)
+    k = fgk.fgk_precond_info(pc)["rank"]
+    Er = torch.randn(k, nprobe, dtype=torch.float64, device="cuda", generator=gen)
+    En = torch.randn(p.N, nprobe, dtype=torch.float64, device="cuda", generator=gen)
+    B = fgk.fgk_precond_sample(pc, Er, En)
+    res = {}
+
+    def slq():
+        res["r"] = fgk.fgk_slq_logdet(h, B, p.sigma2, 2000, tol=1e-8, pc=pc, want_solves=True)
+
+    out["slq_ms"] = timed(slq)
+    r = res["r"]
+    out.update({"slq_nprobe": nprobe, "slq_precond_rank": k, "slq_logdet": r["logdet"],
+                "slq_logdet_precond": r["logdet_precond"], "slq_steps_max": r["steps_max"],
+                "slq_std_error": float(np.std(r["quad"]) / np.sqrt(nprobe)), "slq_max_true_resid": r["max_true_resid"]})
+    # Hutchinson trace tr(A^-1 dK/d log ell_m) with N(0, P) probes: (A^-1 b)^T dK (P^-1 b)
+    Z = fgk.fgk_precond_apply(pc, B)
+    for dim in (0, 1):
+        D = fgk.fgk_matvec_dlogell(h, Z, dim, "f64")
+        sm = (r["X"] * D).sum(0).cpu().numpy()
+        out[f"trace_dim{dim}"] = float(sm.mean())
+        out[f"trace_dim{dim}_std_error"] = float(sm.std() / np.sqrt(nprobe))
+    fgk.fgk_precond_destroy(pc)
+    fgk.fgk_destroy(h)
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -365,12 +433,16 @@ def main():
     ap.add_argument("--pcg-probe", type=int, default=0,
                     help="run only a short preconditioned solve with this rank (for ncu captures)")
     ap.add_argument("--pcg-maxit", type=int, default=40)
+    ap.add_argument("--likelihood", action="store_true",
+                    help="time the gradient products and the log-determinant on the d=2 workload")
     ap.add_argument("--mvm-only", type=int, default=0,
                     help="time only the FP32 product on the d=2 workload drawn with this many points")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
+    if args.likelihood:
+        return run_likelihood(args, local)
     if args.mvm_only:
         return run_mvm_only(args, local)
     if args.pcg_probe:
