@@ -364,6 +364,7 @@ __device__ __forceinline__ void scan_tile(const ScanArgs<R> &A, const WorkItem w
     static_assert((1 << LOG2EPT) == EPT, "EPT must be 4, 8 or 16");
     static_assert(EPT == 8, "vector loads assume 8 entries per thread");
     __shared__ R s_w[ND][NW][AG];
+    __shared__ R s_pre[ND][NW][AG];  // SCAN_OUT: exclusive prefixes of the warp totals
 
     const int64_t N = A.N;
     const int64_t base = (int64_t)wi.tile * kTile;
@@ -549,24 +550,46 @@ __device__ __forceinline__ void scan_tile(const ScanArgs<R> &A, const WorkItem w
 #pragma unroll
                                     for (int m = 0; m < AG; ++m) A.agg[cslot + m] = run[m];
                                 }
-                            } else {
-                                const int GWn = G > 32 ? G / 32 : 1;
-                                const int w0 = is_long ? 0 : (vwarp / GWn) * GWn;
-                                R pre[AG];
+                            } else if (warp == dd) {
+                                // Warp dd: the exclusive prefix of the warp totals (in walk
+                                // order) within each segment's group of warps, by a
+                                // segmented shuffle scan over lanes 0..NW-1, preceded by
+                                // the tile's carry for a long segment.
+                                const int grp = is_long ? NW : (G > 32 ? G / 32 : 1);
+                                R x[AG];
+#pragma unroll
+                                for (int m = 0; m < AG; ++m) x[m] = lane < NW ? s_w[dd][lane][m] : R(0);
+                                for (int dlt = 1; dlt < grp; dlt <<= 1) {
+                                    R prev[AG];
+#pragma unroll
+                                    for (int m = 0; m < AG; ++m) prev[m] = __shfl_up_sync(0xffffffffu, x[m], dlt);
+                                    if ((lane & (grp - 1)) >= dlt) compose_after<R, P, AG>(x, prev);
+                                }
+                                R e[AG];
+#pragma unroll
+                                for (int m = 0; m < AG; ++m) e[m] = __shfl_up_sync(0xffffffffu, x[m], 1);
+                                if ((lane & (grp - 1)) == 0) set_identity<R, AG>(e);
                                 if (is_long) {
+                                    R carry[AG];
 #pragma unroll
-                                    for (int m = 0; m < AG; ++m) pre[m] = A.agg[cslot + m];
-                                } else {
-                                    set_identity<R, AG>(pre);
+                                    for (int m = 0; m < AG; ++m) carry[m] = A.agg[cslot + m];
+                                    compose_after<R, P, AG>(e, carry);
                                 }
-                                for (int w2 = w0; w2 < vwarp; ++w2) {
-                                    R t[AG];
+                                if (lane < NW) {
 #pragma unroll
-                                    for (int m = 0; m < AG; ++m) t[m] = s_w[dd][w2][m];
-                                    compose_after<R, P, AG>(t, pre);
-#pragma unroll
-                                    for (int m = 0; m < AG; ++m) pre[m] = t[m];
+                                    for (int m = 0; m < AG; ++m) s_pre[dd][lane][m] = e[m];
                                 }
+                            }
+                        }
+                        if (MODE == SCAN_OUT) {
+                            __syncthreads();
+#pragma unroll
+                            for (int dd = 0; dd < ND; ++dd) {
+                                const int dir = ND == 2 ? dd : dp;
+                                const int vwarp = dir == 0 ? warp : NW - 1 - warp;
+                                R pre[AG];
+#pragma unroll
+                                for (int m = 0; m < AG; ++m) pre[m] = s_pre[dd][vwarp][m];
                                 compose_after<R, P, AG>(ex[dd], pre);
                             }
                         }
