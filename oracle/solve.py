@@ -32,6 +32,19 @@ TEST INFRASTRUCTURE ONLY.
                   Gauss quadrature of eq. approximationLogDet, gamma the
                   squared norm of the Lanczos start vector); ``slq_logdet``
                   the Hutchinson average over probes plus log det P.
+* ``loglik_exact`` / ``loglik_grad_exact``  the log marginal likelihood
+                  (eq. gp_log_likelihood) and its gradient
+                  (eq. gp_log_likelihood_derivative) from dense matrices:
+                  1/2 a^T dK a - 1/2 tr(A^{-1} dK), a = A^{-1} y.
+* ``loglik_grad_estimate``  the same gradient with the trace term by
+                  Hutchinson probes (App. A.2): mean_i (A^{-1} b_i)^T dK
+                  (P^{-1} b_i), the probes N(0, P) (N(0, I) without P).
+* ``adam_sigma_steps``  the gradient-descent loop of Algorithm 1: Adam
+                  ascent steps on theta = (log ell_k, log varsigma^2) with the
+                  learning rate falling linearly from 0.005 to 0.0005 over
+                  20000 iterations (Sec. 3.1), each followed by the closed-form
+                  update (sigma_j)^2 = y^T (K~ + I)^{-1} y / N with
+                  K~ = K(varsigma_j / sigma_{j-1}, ell_j).
 * ``posterior_mean``  E[f(z) | x, y] = k_z^T alpha + h(z)^T beta (eq. gp_mean,
                   with alpha = (K + sigma^2 I)^{-1}(y - H beta) as eq. gp_mean_2),
                   given the cross-covariance rows k_z^T.
@@ -236,3 +249,69 @@ def slq_logdet(apply_A, B, m: int, tol: float, apply_Pinv=None, logdet_P: float 
     X, al, be, ga = cg_lanczos(apply_A, B, tol, m, apply_Pinv)
     quad = np.array([slq_quadrature(al[j], be[j], ga[j]) if al[j] else 0.0 for j in range(len(al))])
     return logdet_P + float(quad.mean()), quad, np.array([len(a) for a in al]), X
+
+
+def loglik_exact(K, sigma2: float, y) -> float:
+    """eq. gp_log_likelihood: -1/2 y^T A^{-1} y - 1/2 log det A - N/2 log(2 pi), A = K + sigma2 I."""
+    K = np.asarray(K, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64).reshape(-1)
+    A = K + sigma2 * np.eye(K.shape[0])
+    return float(-0.5 * y @ np.linalg.solve(A, y) - 0.5 * np.linalg.slogdet(A)[1]
+                 - 0.5 * y.size * np.log(2 * np.pi))
+
+
+def loglik_grad_exact(K, dKs, sigma2: float, y) -> np.ndarray:
+    """eq. gp_log_likelihood_derivative for each dK in dKs:
+    1/2 a^T dK a - 1/2 tr(A^{-1} dK), a = A^{-1} y."""
+    K = np.asarray(K, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64).reshape(-1)
+    A = K + sigma2 * np.eye(K.shape[0])
+    a = np.linalg.solve(A, y)
+    Ainv = np.linalg.inv(A)
+    return np.array([0.5 * a @ dK @ a - 0.5 * float(np.sum(Ainv * dK.T)) for dK in dKs])
+
+
+def loglik_grad_estimate(apply_Ainv, apply_dKs, y, B, apply_Pinv=None) -> np.ndarray:
+    """The gradient with the trace by Hutchinson probes: for each dK,
+    1/2 a^T dK a - 1/2 mean_i (A^{-1} b_i)^T dK (P^{-1} b_i)."""
+    y = np.asarray(y, dtype=np.float64).reshape(-1, 1)
+    B = np.asarray(B, dtype=np.float64)
+    a = apply_Ainv(y)
+    X = apply_Ainv(B)
+    Z = B if apply_Pinv is None else apply_Pinv(B)
+    out = []
+    for f in apply_dKs:
+        quad = float(a[:, 0] @ f(a)[:, 0])
+        tr = float(np.mean(np.einsum("ij,ij->j", X, f(Z))))
+        out.append(0.5 * quad - 0.5 * tr)
+    return np.array(out)
+
+
+def adam_sigma_steps(grad_fn, quad_fn, n_points: int, theta0, sigma2_0: float, n_steps: int, lr0: float = 0.005,
+                     lr1: float = 0.0005, n_sched: int = 20000, b1: float = 0.9, b2: float = 0.999,
+                     eps: float = 1e-8):
+    """n_steps of Algorithm 1's inner loop.  grad_fn(theta, sigma2, j) is the
+    log-likelihood gradient in theta at (theta, sigma2); quad_fn(theta,
+    sigma2) = y^T (K(theta) + sigma2 I)^{-1} y.  Adam (Kingma and Ba) ascends
+    the log-likelihood; the step size of iteration j (from 0) is
+    lr0 + (lr1 - lr0) min(j / n_sched, 1).  Returns the thetas, sigma2s and
+    gradients of every step."""
+    theta = np.array(theta0, dtype=np.float64)
+    sigma2 = float(sigma2_0)
+    m = np.zeros_like(theta)
+    v = np.zeros_like(theta)
+    thetas, sigmas, grads = [], [], []
+    for j in range(n_steps):
+        g = np.asarray(grad_fn(theta, sigma2, j), dtype=np.float64)
+        m = b1 * m + (1 - b1) * g
+        v = b2 * v + (1 - b2) * g * g
+        mh = m / (1 - b1 ** (j + 1))
+        vh = v / (1 - b2 ** (j + 1))
+        lr = lr0 + (lr1 - lr0) * min(j / n_sched, 1.0)
+        theta = theta + lr * mh / (np.sqrt(vh) + eps)
+        # (K~ + I) = (K(theta) + sigma_{j-1}^2 I) / sigma_{j-1}^2
+        sigma2 = sigma2 * quad_fn(theta, sigma2) / n_points
+        thetas.append(theta.copy())
+        sigmas.append(sigma2)
+        grads.append(g)
+    return np.array(thetas), np.array(sigmas), np.array(grads)
