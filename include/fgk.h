@@ -327,6 +327,39 @@ int fgk_slq_logdet(fgk_handle h, fgk_precond pc, double sigma2, const double *B,
  * Ritz value is <= 0. */
 int fgk_lanczos_logquad(const double *alpha, const double *beta, int m, double *out);
 
+/* ---- the likelihood gradient (eq. gp_log_likelihood_derivative) ---- */
+
+typedef struct {
+    double yAy;            /* y^T (K + sigma2 I)^{-1} y (Algorithm 1's sigma update uses it) */
+    double alpha_sq;       /* alpha^T alpha, alpha = (K + sigma2 I)^{-1} y */
+    double max_true_resid; /* of the solve of [y, B] */
+    int iterations;        /* CG iterations of that solve */
+    int solve_status;      /* its return code (FGK_OK or FGK_NOT_CONVERGED) */
+    int n_grad;            /* entries written to grad */
+} fgk_grad_report;
+
+/* The gradient of the log marginal likelihood log p(y | x, theta)
+ * (eq. gp_log_likelihood_derivative) with respect to the log-parameters:
+ *   d/dtheta = 1/2 a^T dK/dtheta a - 1/2 tr((K + sigma2 I)^{-1} dK/dtheta),
+ *   a = (K + sigma2 I)^{-1} y, the trace by Hutchinson's estimator
+ *   (App. A.2) mean_i ((K + sigma2 I)^{-1} b_i)^T dK/dtheta (P^{-1} b_i) over
+ *   the probe columns b_i of B (N(0, P) draws with a preconditioner,
+ *   fgk_precond_sample; N(0, I) without).
+ *   grad   host: first the lengthscales, d/d log ell_k for k < d with the
+ *          product kernel (d > 1), else one entry for all lengthscales
+ *          scaled together (fgk_matvec_dlogell's dim = -1); then
+ *          d/d log varsigma^2 (the outputscale of the plan) and
+ *          d/d log sigma^2; rep->n_grad entries.
+ *   y      device, N FP64, original point order; B device, N x nprobe FP64
+ *          row-major, 0 <= nprobe <= 63.  nprobe = 0 solves y alone: rep
+ *          holds y^T A^{-1} y and alpha^T alpha, grad only the terms in a
+ *          (the quadratic halves, no trace).
+ *   tol, maxit, mode  of the CG solve of [y, B] (as fgk_cg_solve).
+ *   pc     NULL or built on h for this sigma2.
+ * Allocates a workspace; synchronises `stream`. */
+int fgk_loglik_grad(fgk_handle h, fgk_precond pc, double sigma2, const double *y, const double *B, int nprobe,
+                    double tol, int maxit, int mode, double *grad, fgk_grad_report *rep, fgk_stream_t stream);
+
 /* ---- batches: many problems advanced together (d <= 2) ---- */
 
 typedef struct fgk_batch_s *fgk_batch;

@@ -34,6 +34,7 @@ SOURCES = [
     "fgk_precond.cu",
     "fgk_predict.cu",
     "fgk_slq.cu",
+    "fgk_lik.cu",
 ]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,

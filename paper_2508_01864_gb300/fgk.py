@@ -54,6 +54,11 @@ class fgk_slq_report(ctypes.Structure):
                 ("solve_status", ctypes.c_int32), ("max_true_resid", ctypes.c_double)]
 
 
+class fgk_grad_report(ctypes.Structure):
+    _fields_ = [("yAy", ctypes.c_double), ("alpha_sq", ctypes.c_double), ("max_true_resid", ctypes.c_double),
+                ("iterations", ctypes.c_int32), ("solve_status", ctypes.c_int32), ("n_grad", ctypes.c_int32)]
+
+
 class fgk_plan_info(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64), ("d", ctypes.c_int32), ("two_nu", ctypes.c_int32), ("kind", ctypes.c_int32),
                 ("L", ctypes.c_int32), ("n_levels", ctypes.c_int32), ("outscale2", ctypes.c_double),
@@ -66,7 +71,7 @@ EXPORTS = ["fgk_set_allocator", "fgk_build", "fgk_matvec", "fgk_matvec_dlogell",
            "fgk_batch_cg_solve", "fgk_batch_destroy", "fgk_precond_build", "fgk_precond_info",
            "fgk_precond_factor", "fgk_precond_apply", "fgk_precond_destroy", "fgk_cg_solve_pc",
            "fgk_kernel_timing", "fgk_predict", "fgk_batch_cg_solve_pc", "fgk_precond_sample", "fgk_slq_logdet",
-           "fgk_lanczos_logquad"]
+           "fgk_lanczos_logquad", "fgk_loglik_grad"]
 
 _lock = threading.Lock()
 _lib = None
@@ -145,6 +150,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.fgk_slq_logdet.restype = i32
         lib.fgk_lanczos_logquad.argtypes = [ctypes.POINTER(dbl), ctypes.POINTER(dbl), i32, ctypes.POINTER(dbl)]
         lib.fgk_lanczos_logquad.restype = i32
+        lib.fgk_loglik_grad.argtypes = [vp, vp, dbl, vp, vp, i32, dbl, i32, i32, ctypes.POINTER(dbl),
+                                        ctypes.POINTER(fgk_grad_report), vp]
+        lib.fgk_loglik_grad.restype = i32
         lib.fgk_precond_destroy.argtypes = [vp]
         lib.fgk_precond_destroy.restype = i32
         lib.fgk_cg_solve_pc.argtypes = [vp, vp, vp, i32, dbl, vp, i32, dbl, i32, i32, vp, vp,
@@ -431,6 +439,22 @@ def fgk_slq_logdet(h: Handle, B: torch.Tensor, sigma2: float, m: int, tol: float
     return {"logdet": rep.logdet, "logdet_precond": rep.logdet_precond, "steps_max": rep.steps_max,
             "solve_status": rep.solve_status, "max_true_resid": rep.max_true_resid, "quad": list(quad),
             "steps": list(steps), "X": X}
+
+
+def fgk_loglik_grad(h: Handle, y: torch.Tensor, B: torch.Tensor, sigma2: float, tol: float = 1e-8,
+                    maxit: int = 20000, mode: str = "mixed", pc: Precond | None = None, stream=None) -> dict:
+    """The log-likelihood gradient in (log ell..., log varsigma^2, log sigma^2)
+    with Hutchinson probes B; see include/fgk.h."""
+    y1 = _dev_f64_2d(y, "y")
+    B2 = _dev_f64_2d(B, "B") if B is not None else None
+    g = (ctypes.c_double * 8)()
+    rep = fgk_grad_report()
+    m = FGK_MIXED if mode == "mixed" else FGK_F64
+    _check(load().fgk_loglik_grad(h.ptr, pc.ptr if pc is not None else None, float(sigma2), y1.data_ptr(),
+                                  B2.data_ptr() if B2 is not None else None, B2.shape[1] if B2 is not None else 0,
+                                  float(tol), int(maxit), m, g, ctypes.byref(rep), _stream(stream)))
+    return {"grad": list(g)[: rep.n_grad], "yAy": rep.yAy, "alpha_sq": rep.alpha_sq,
+            "max_true_resid": rep.max_true_resid, "iterations": rep.iterations, "solve_status": rep.solve_status}
 
 
 def fgk_lanczos_logquad(alpha, beta) -> float:
