@@ -516,8 +516,11 @@ __device__ __forceinline__ void scan_tile(const ScanArgs<R> &A, const WorkItem w
                             for (int m = 0; m < AG; ++m) ex[dd][m] = prev[m];
                         }
                     }
-                    // 3. across warps: every thread composes the totals of the
-                    //    earlier warps of its segment (and the tile carry)
+                    // 3. across warps: the warp totals go through shared memory;
+                    //    AGG: one thread composes the tile's total; OUT: one warp
+                    //    per direction scans them (segmented by the segment's
+                    //    warps, after the tile's carry) and every thread composes
+                    //    its warp's exclusive prefix
                     if (G > 32 || MODE == SCAN_AGG) {
 #pragma unroll
                         for (int dd = 0; dd < ND; ++dd) {
