@@ -199,7 +199,7 @@ __global__ void k_pc_step(int m, int64_t N, int64_t ldN, KernArgs ka, const int3
         s_xp[2] = ka.d > 2 ? ka.x2[piv] : 0.0;
     }
     __syncthreads();
-    const double sq = sqrt(best.val);
+    const double isq = 1.0 / sqrt(best.val);  // one division per CTA (GB300's FP64 divide is costly)
     PivPart mine = piv_none();
     // two consecutive rows per thread (8-byte vector loads of L; the column
     // stride ldN is a multiple of 64, so row i0 + 1 < ldN is always inside the
@@ -227,7 +227,7 @@ __global__ void k_pc_step(int m, int64_t N, int64_t ldN, KernArgs ka, const int3
             const F2 acc = h == 0 ? acc0 : acc1;
             const double kv = kern_q(ka, i, s_xp);
             const double dot = (double)acc.hi + (double)acc.lo;
-            const double l = (kv - dot) / sq;
+            const double l = (kv - dot) * isq;
             float lh, ll;
             split_f2(l, lh, ll);
             Lhi[(size_t)m * ldN + i] = lh;
