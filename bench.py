@@ -44,7 +44,9 @@ WORKLOAD = ("d=2 N=200000 nu=3/2 ell=(0.1,0.3) x~U[0,1]^2 product kernel; "
 # the kernels as built (a kernel missing here has no capture of its current
 # version)
 TRAFFIC_BYTES = {
-    "k_level_scan<float,P=2,NOFF=1,product,OUT>": 44933376,
+    "k_level_scan<float,P=2,NOFF=1,product,OUT>": 44934656,
+    "k_pc_ltr (t = L^T r)": 201692416 + 367104,
+    "k_pc_apply (z = r/s2 - L c)": 201672192 + 504320,
 }
 FALLBACK_HBM_GBS = 6800.0
 
