@@ -12,7 +12,8 @@ after ``max_steps``, once the gradient norm is below ``grad_tol``, or once
 theta has moved by less than ``param_tol`` over the last 100 steps (the
 paper's two criteria).  The plan and the preconditioner are built for every
 parameter value; all vector work runs in libfgk, this module holds only the
-scalar Adam and sigma recurrences.
+scalar Adam and sigma recurrences (``adam_sigma_loop``, which takes the two
+evaluations as callables).
 
 The probes are standard normal numbers the caller supplies per step
 (``probes(j)`` returning an N x n array, or (E_r, E_n) pairs with a
@@ -44,47 +45,20 @@ def _lr(j: int, lr0: float, lr1: float, n_sched: int) -> float:
     return lr0 + (lr1 - lr0) * min(j / n_sched, 1.0)
 
 
-def fit_adam_sigma(X: np.ndarray, y: np.ndarray, nu: float, ell0, outscale2_0: float, sigma2_0: float,
-                   probes, max_steps: int, kind: str = "product", precond_rank: int = 0, lr0: float = 0.005,
-                   lr1: float = 0.0005, n_sched: int = 20000, grad_tol: float = 1e-3, param_tol: float = 1e-4,
-                   tol: float = 1e-8, mode: str = "mixed", b1: float = 0.9, b2: float = 0.999,
-                   eps: float = 1e-8) -> FitState:
-    X_dev = torch.as_tensor(np.ascontiguousarray(X, dtype=np.float64), device="cuda")
-    y_dev = torch.as_tensor(np.ascontiguousarray(y, dtype=np.float64), device="cuda")
-    N, d = X_dev.shape[0], X_dev.shape[1] if X_dev.dim() == 2 else 1
-    ell0 = np.broadcast_to(np.asarray(ell0, dtype=np.float64), (d,)).copy()
-    st = FitState(theta=np.concatenate([np.log(ell0), [math.log(outscale2_0)]]), sigma2=float(sigma2_0))
-    per_dim = kind == "product" and d > 1
-    if not per_dim:  # one lengthscale entry in the gradient: all scaled together
-        st.theta = np.concatenate([[math.log(ell0[0])], [math.log(outscale2_0)]])
-        ratio = ell0 / ell0[0]  # the lengthscales keep their ratios
+def adam_sigma_loop(eval_grad, eval_quad, n_points: int, theta0, sigma2_0: float, max_steps: int,
+                    lr0: float = 0.005, lr1: float = 0.0005, n_sched: int = 20000, grad_tol: float = 1e-3,
+                    param_tol: float = 1e-4, b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8) -> FitState:
+    """Algorithm 1's inner loop on host scalars.  eval_grad(theta, sigma2, j)
+    returns (g, info): the log-likelihood gradient in theta at (theta, sigma2)
+    and a dict kept in the history; eval_quad(theta, sigma2) returns
+    y^T (K(theta) + sigma2 I)^{-1} y."""
+    st = FitState(theta=np.array(theta0, dtype=np.float64), sigma2=float(sigma2_0))
     st.m = np.zeros_like(st.theta)
     st.v = np.zeros_like(st.theta)
-
-    def ells(theta):
-        return np.exp(theta[:d]) if per_dim else math.exp(theta[0]) * ratio
-
-    def plan(theta, sigma2):
-        h = fgk.fgk_build(X_dev, nu, ells(theta), outscale2=math.exp(theta[-1]), kind=kind)
-        pc = fgk.fgk_precond_build(h, precond_rank, sigma2) if precond_rank > 0 else None
-        return h, pc
-
     window = []
     for j in range(max_steps):
-        h, pc = plan(st.theta, st.sigma2)
-        try:
-            pr = probes(j)
-            if pc is not None:
-                B = fgk.fgk_precond_sample(pc, torch.as_tensor(pr[0], device="cuda"),
-                                           torch.as_tensor(pr[1], device="cuda"))
-            else:
-                B = torch.as_tensor(np.ascontiguousarray(pr, dtype=np.float64), device="cuda")
-            r = fgk.fgk_loglik_grad(h, y_dev, B, st.sigma2, tol=tol, mode=mode, pc=pc)
-        finally:
-            if pc is not None:
-                fgk.fgk_precond_destroy(pc)
-            fgk.fgk_destroy(h)
-        g = np.array(r["grad"][:-1])  # theta's entries (the nugget follows the closed form)
+        g, info = eval_grad(st.theta, st.sigma2, j)
+        g = np.asarray(g, dtype=np.float64)
         st.m = b1 * st.m + (1 - b1) * g
         st.v = b2 * st.v + (1 - b2) * g * g
         mh = st.m / (1 - b1 ** (j + 1))
@@ -92,18 +66,10 @@ def fit_adam_sigma(X: np.ndarray, y: np.ndarray, nu: float, ell0, outscale2_0: f
         old = st.theta.copy()
         st.theta = st.theta + _lr(j, lr0, lr1, n_sched) * mh / (np.sqrt(vh) + eps)
         # sigma_j^2 = sigma_{j-1}^2 y^T (K(theta_j) + sigma_{j-1}^2 I)^{-1} y / N
-        h, pc = plan(st.theta, st.sigma2)
-        try:
-            q = fgk.fgk_loglik_grad(h, y_dev, None, st.sigma2, tol=tol, mode=mode, pc=pc)["yAy"]
-        finally:
-            if pc is not None:
-                fgk.fgk_precond_destroy(pc)
-            fgk.fgk_destroy(h)
-        st.sigma2 = st.sigma2 * q / N
+        st.sigma2 = st.sigma2 * eval_quad(st.theta, st.sigma2) / n_points
         st.step = j + 1
         gnorm = float(np.linalg.norm(g))
-        st.history.append({"theta": st.theta.copy(), "sigma2": st.sigma2, "grad": g, "grad_norm": gnorm,
-                           "iterations": r["iterations"]})
+        st.history.append({"theta": st.theta.copy(), "sigma2": st.sigma2, "grad": g, "grad_norm": gnorm, **info})
         window.append(old)
         if gnorm < grad_tol:
             break
@@ -112,3 +78,58 @@ def fit_adam_sigma(X: np.ndarray, y: np.ndarray, nu: float, ell0, outscale2_0: f
             if np.linalg.norm(st.theta - window[0]) < param_tol:
                 break
     return st
+
+
+def fit_adam_sigma(X: np.ndarray, y: np.ndarray, nu: float, ell0, outscale2_0: float, sigma2_0: float,
+                   probes, max_steps: int, kind: str = "product", precond_rank: int = 0, lr0: float = 0.005,
+                   lr1: float = 0.0005, n_sched: int = 20000, grad_tol: float = 1e-3, param_tol: float = 1e-4,
+                   tol: float = 1e-8, mode: str = "mixed", b1: float = 0.9, b2: float = 0.999,
+                   eps: float = 1e-8) -> FitState:
+    """``adam_sigma_loop`` with every evaluation on the GPU: a plan (and a
+    preconditioner of ``precond_rank``) for each parameter value,
+    ``fgk_loglik_grad`` with the step's probes for the gradient, and
+    ``fgk_loglik_grad`` without probes for y^T A^{-1} y."""
+    X_dev = torch.as_tensor(np.ascontiguousarray(X, dtype=np.float64), device="cuda")
+    y_dev = torch.as_tensor(np.ascontiguousarray(y, dtype=np.float64), device="cuda")
+    N, d = X_dev.shape[0], X_dev.shape[1] if X_dev.dim() == 2 else 1
+    ell0 = np.broadcast_to(np.asarray(ell0, dtype=np.float64), (d,)).copy()
+    per_dim = kind == "product" and d > 1
+    if per_dim:
+        theta0 = np.concatenate([np.log(ell0), [math.log(outscale2_0)]])
+    else:  # one lengthscale entry in the gradient: all scaled together, keeping their ratios
+        theta0 = np.concatenate([[math.log(ell0[0])], [math.log(outscale2_0)]])
+    ratio = ell0 / ell0[0]
+
+    def ells(theta):
+        return np.exp(theta[:d]) if per_dim else math.exp(theta[0]) * ratio
+
+    def with_plan(theta, sigma2, fn):
+        h = fgk.fgk_build(X_dev, nu, ells(theta), outscale2=math.exp(theta[-1]), kind=kind)
+        pc = fgk.fgk_precond_build(h, precond_rank, sigma2) if precond_rank > 0 else None
+        try:
+            return fn(h, pc)
+        finally:
+            if pc is not None:
+                fgk.fgk_precond_destroy(pc)
+            fgk.fgk_destroy(h)
+
+    def eval_grad(theta, sigma2, j):
+        def run(h, pc):
+            pr = probes(j)
+            if pc is not None:
+                B = fgk.fgk_precond_sample(pc, torch.as_tensor(pr[0], device="cuda"),
+                                           torch.as_tensor(pr[1], device="cuda"))
+            else:
+                B = torch.as_tensor(np.ascontiguousarray(pr, dtype=np.float64), device="cuda")
+            return fgk.fgk_loglik_grad(h, y_dev, B, sigma2, tol=tol, mode=mode, pc=pc)
+
+        r = with_plan(theta, sigma2, run)
+        # theta's entries (the nugget follows the closed form)
+        return np.array(r["grad"][:-1]), {"iterations": r["iterations"]}
+
+    def eval_quad(theta, sigma2):
+        return with_plan(theta, sigma2,
+                         lambda h, pc: fgk.fgk_loglik_grad(h, y_dev, None, sigma2, tol=tol, mode=mode, pc=pc)["yAy"])
+
+    return adam_sigma_loop(eval_grad, eval_quad, N, theta0, sigma2_0, max_steps, lr0=lr0, lr1=lr1, n_sched=n_sched,
+                           grad_tol=grad_tol, param_tol=param_tol, b1=b1, b2=b2, eps=eps)
