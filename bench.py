@@ -113,6 +113,24 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def max_over_ranks(x: float, ws: int, device: str = "cuda") -> float:
+    """The largest x over the ranks of the process group (x itself at one rank)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(ws: int, steps: int, slowest_total_ms: float) -> float:
+    """Whole-job throughput of weak-scaled replicas: every rank does `steps`
+    units, the job lasts as long as the slowest rank."""
+    return ws * steps / (slowest_total_ms / 1e3)
+
+
 def flush_l2(buf):
     buf.add_(1.0)  # writes 256 MiB, twice the 129 MB L2
 
@@ -520,12 +538,8 @@ def main():
     clk = clocks.stop()
     launches = fgk.fgk_kernel_launches() - launches0
     barrier()
-    total_ms = sum(times)
-    if ws > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(times), ws)
+    value = job_rate(ws, args.steps, total_ms)
 
     # ---------------- end to end through the ABI with host buffers
     Xh = torch.as_tensor(p.X).pin_memory()
@@ -546,12 +560,8 @@ def main():
         e2e_times.append(e0.elapsed_time(e1))
         assert rc == 0
         release(h, pc)
-    e2e_ms = sum(e2e_times)
-    if ws > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_val = ws * args.steps / (e2e_ms / 1e3)
+    e2e_ms = max_over_ranks(sum(e2e_times), ws)
+    e2e_val = job_rate(ws, args.steps, e2e_ms)
     h2d = Xh.numel() * 8 + yh.numel() * 8
     d2h = ah.numel() * 8
 
