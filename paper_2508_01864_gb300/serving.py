@@ -72,6 +72,7 @@ class Stats:
     admitted: int = 0
     completed: int = 0
     rejected: int = 0
+    cancelled: int = 0
     peak_bytes: int = 0
     peak_concurrency: int = 0
     results: list = field(default_factory=list)
@@ -140,6 +141,8 @@ class Server:
         self._pool = ThreadPoolExecutor(max_workers=self.slots)
         self._stop = False
         self._futures: dict[int, Future] = {}
+        self._cancelled: set[int] = set()
+        self._admitted: set[int] = set()
         self._dispatcher = threading.Thread(target=self._dispatch, daemon=True)
         self._dispatcher.start()
 
@@ -159,6 +162,22 @@ class Server:
         self._pending.put((req, need))
         return fut
 
+    def cancel(self, rid: int) -> bool:
+        """Withdraw a request that has not been admitted yet: its future
+        resolves at once with the error "cancelled" and it never reaches the
+        device.  A request already admitted runs to completion (its device
+        work is in flight); returns False then, or for an unknown rid."""
+        with self._lock:
+            if rid in self._admitted or rid not in self._futures or rid in self._cancelled:
+                return False
+            self._cancelled.add(rid)
+            fut = self._futures.pop(rid)
+            self.stats.cancelled += 1
+            self._lock.notify_all()  # the dispatcher may be holding it at the head of the queue
+        now = time.perf_counter()
+        fut.set_result(Result(rid, None, {}, -1, now, now, now, error="cancelled"))
+        return True
+
     def close(self, wait: bool = True):
         self._stop = True
         self._pending.put(None)
@@ -173,8 +192,13 @@ class Server:
                 return
             req, need = item
             with self._lock:
-                while self._running >= self.slots or self._used + need > self.budget:
+                while (req.rid not in self._cancelled
+                       and (self._running >= self.slots or self._used + need > self.budget)):
                     self._lock.wait()
+                if req.rid in self._cancelled:
+                    self._cancelled.discard(req.rid)
+                    continue
+                self._admitted.add(req.rid)
                 self._running += 1
                 self._used += need
                 self.stats.admitted += 1
@@ -195,6 +219,7 @@ class Server:
         with self._lock:
             self._used -= need
             self._running -= 1
+            self._admitted.discard(req.rid)
             self.stats.completed += 1
             self.stats.results.append(res)
             fut = self._futures.pop(req.rid, None)

@@ -82,3 +82,63 @@ def test_oversized_request_rejected_and_summary():
     s = serving.summarize(out)
     assert s["completed"] == 4  # 2 rejected/failed (rid 2 oversized, rid 5 raises)
     assert s["p99_s"] >= s["p50_s"] > 0
+
+
+def test_cancelled_requests_never_reach_the_device_and_free_nothing_twice():
+    dev = FakeDevice(per_point=2e-4)
+    srv = serving.Server(budget_bytes=10**9, slots=1, executor=dev.run, estimator=dev.estimate)
+    reqs = make_requests(6, seed=3)
+    for r in reqs:
+        r.rid += 100  # no injected failure (rid 5) here
+    futs = [srv.submit(r) for r in reqs]
+    time.sleep(0.01)  # the first is admitted; the others wait for the single slot
+    assert srv.cancel(reqs[3].rid) and srv.cancel(reqs[5].rid)
+    assert not srv.cancel(reqs[3].rid)  # already cancelled
+    assert not srv.cancel(12345)        # unknown
+    res = [f.result(timeout=30) for f in futs]
+    srv.close()
+    assert [r.error for r in res].count("cancelled") == 2
+    assert res[3].error == "cancelled" and res[5].error == "cancelled"
+    assert reqs[3].rid not in dev.order and reqs[5].rid not in dev.order
+    assert all(r.error is None for i, r in enumerate(res) if i not in (3, 5))
+    assert srv.stats.cancelled == 2 and srv.stats.completed == 4 and srv._used == 0 and srv._running == 0
+
+
+def test_a_running_request_cannot_be_cancelled():
+    gate = threading.Event()
+
+    def slow(req):
+        gate.wait(10)
+        return req.y.copy(), {}, 0
+
+    srv = serving.Server(budget_bytes=10**9, slots=2, executor=slow, estimator=lambda r: 1)
+    r = make_requests(1)[0]
+    fut = srv.submit(r)
+    time.sleep(0.05)
+    assert not srv.cancel(r.rid)
+    gate.set()
+    assert fut.result(timeout=10).error is None
+    srv.close()
+
+
+def test_an_out_of_memory_failure_releases_its_budget():
+    """An executor failing as the library does when its allocator runs dry
+    (FGK_ERR_OOM): the request is reported failed, its bytes return to the
+    budget and later requests are admitted."""
+    from paper_2508_01864_gb300 import fgk
+
+    calls = []
+
+    def oom_once(req):
+        calls.append(req.rid)
+        if req.rid == 0:
+            raise fgk.FgkError(-3, "fgk_cg_solve: workspace allocation failed")
+        return req.y.copy(), {}, 0
+
+    srv = serving.Server(budget_bytes=1000, slots=4, executor=oom_once, estimator=lambda r: 600)
+    reqs = make_requests(4, seed=5)
+    res = [srv.submit(r).result(timeout=30) for r in reqs]
+    srv.close()
+    assert res[0].error is not None and "allocation failed" in res[0].error
+    assert all(r.error is None for r in res[1:])
+    assert calls == [0, 1, 2, 3] and srv._used == 0
