@@ -16,8 +16,9 @@ scalar Adam and sigma recurrences (``adam_sigma_loop``, which takes the two
 evaluations as callables).
 
 The probes are standard normal numbers the caller supplies per step
-(``probes(j)`` returning an N x n array, or (E_r, E_n) pairs with a
-preconditioner, from which ``fgk_precond_sample`` forms N(0, P) probes).
+(``probes(j)`` returning an N x n array, or with a preconditioner an (E_r, E_n)
+pair of precond_rank x n and N x n arrays, from which ``fgk_precond_sample``
+forms N(0, P) probes with the first k rows of E_r, k the factor's rank).
 """
 
 from __future__ import annotations
@@ -116,9 +117,12 @@ def fit_adam_sigma(X: np.ndarray, y: np.ndarray, nu: float, ell0, outscale2_0: f
     def eval_grad(theta, sigma2, j):
         def run(h, pc):
             pr = probes(j)
-            if pc is not None:
-                B = fgk.fgk_precond_sample(pc, torch.as_tensor(pr[0], device="cuda"),
-                                           torch.as_tensor(pr[1], device="cuda"))
+            if pc is not None:  # the factor may have stopped below precond_rank: its first k rows
+                k = fgk.fgk_precond_info(pc)["rank"]
+                Er = np.ascontiguousarray(np.asarray(pr[0], dtype=np.float64)[:k])
+                B = fgk.fgk_precond_sample(pc, torch.as_tensor(Er, device="cuda"),
+                                           torch.as_tensor(np.ascontiguousarray(pr[1], dtype=np.float64),
+                                                           device="cuda"))
             else:
                 B = torch.as_tensor(np.ascontiguousarray(pr, dtype=np.float64), device="cuda")
             return fgk.fgk_loglik_grad(h, y_dev, B, sigma2, tol=tol, mode=mode, pc=pc)

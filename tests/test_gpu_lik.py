@@ -122,3 +122,27 @@ def test_fit_raises_the_exact_likelihood(fgk_mod, orc):
 
     start = ll(np.log([0.6, 0.6, 0.5]), 0.3)
     assert ll(st.theta, st.sigma2) > start + 1.0
+
+
+def test_fit_with_a_preconditioner_raises_the_exact_likelihood(fgk_mod, orc):
+    """The loop with rank-20 preconditioners (N(0, P) probes from the caller's
+    standard normal numbers) on 15 distinct points each repeated 20 times, so
+    the factor stops at rank 15 and only the first 15 rows of each E_r are
+    used: the exact log-likelihood rises (by about 350 with exact gradients)."""
+    from paper_2508_01864_gb300 import fit
+
+    base = workloads.small(93, 15, 2, nu=1.5, ell=[0.2, 0.35])
+    X = np.repeat(base.X, 20, axis=0)
+    N, d, nu, rank = X.shape[0], 2, 1.5, 20
+    rng = np.random.default_rng(4)
+    y = np.repeat(np.sin(5 * base.X[:, 0]) + np.cos(3 * base.X[:, 1]), 20) + 0.1 * rng.standard_normal(N)
+    st = fit.fit_adam_sigma(X, y, nu, [0.6, 0.6], 0.5, 0.3,
+                            lambda j: (rng.standard_normal((rank, 16)), rng.standard_normal((N, 16))),
+                            max_steps=30, precond_rank=rank, lr0=0.05, lr1=0.05, grad_tol=0.0, param_tol=0.0)
+
+    def ll(theta, s2n):
+        K = orc.kmat(X, nu, np.exp(theta[:d]), s2=math.exp(theta[d]), kind=1)
+        return solve.loglik_exact(K, s2n, y)
+
+    assert st.step == 30
+    assert ll(st.theta, st.sigma2) > ll(np.log([0.6, 0.6, 0.5]), 0.3) + 50.0
