@@ -16,9 +16,14 @@
  * product_decomposition), evaluated over a dominance structure whose sorted
  * subsets are computed once per point set and kept on the device (Sec. 2.2.3).
  * On top of the product it solves (K + sigma^2 I) alpha = y by conjugate
- * gradients (App. A.1, Algorithm 2 with the identity preconditioner), with an
- * optional generalised-least-squares fixed-effects mean (Sec. 3.2,
- * Algorithm 1's GLS step).
+ * gradients (App. A.1, Algorithm 2 with the identity or the pivoted-Cholesky
+ * preconditioner of App. A.3), with an optional generalised-least-squares
+ * fixed-effects mean (Sec. 3.2, Algorithm 1's GLS step), and provides the
+ * pieces of the likelihood and its gradient (eqs. gp_log_likelihood and
+ * gp_log_likelihood_derivative): products with the lengthscale derivatives of
+ * K (App. C.1), log det(K + sigma^2 I) by stochastic Lanczos quadrature
+ * (App. A.2), the gradient with Hutchinson probes, and the posterior mean at
+ * new points (eq. gp_mean).
  *
  * Conventions for every entry point:
  *  - Pointers documented "device" must be device memory of the current CUDA
@@ -30,8 +35,10 @@
  *    original point order.
  *  - Work is enqueued on the given stream (NULL = legacy default stream);
  *    calls on one handle must be ordered on one stream (a handle owns one
- *    workspace).  fgk_build and fgk_cg_solve synchronise that stream before
- *    returning; fgk_matvec does not.
+ *    workspace).  fgk_build, the solves (fgk_cg_solve, fgk_cg_solve_pc,
+ *    fgk_slq_logdet, fgk_loglik_grad) and fgk_precond_build synchronise that
+ *    stream before returning; the products (fgk_matvec, fgk_matvec_q,
+ *    fgk_matvec_dlogell) do not.
  *  - Return value: FGK_OK (0) on success, a negative FGK_ERR_* code on
  *    failure (nothing is thrown across the ABI); fgk_last_error() then gives
  *    a message for the calling thread.  FGK_NOT_CONVERGED (1) is a soft
