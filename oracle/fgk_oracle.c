@@ -28,6 +28,8 @@
  *                  gradient product of the trace term of
  *                  eq. gp_log_likelihood_derivative, per lengthscale or for
  *                  all lengthscales scaled together.
+ *  orc_mvm_dc_dlogell_l1  the L1 kernel's lengthscale gradient by the
+ *                  paper's printed ECDF decompositions, on O2's machinery.
  *  orc_mvm_dc      O2: the paper's own algorithm, written in its order and
  *                  notation: weighted ECDFs with the generalised inequality
  *                  (eq. ECDFdelta), one per orthant delta and weight vector,
@@ -571,6 +573,65 @@ int orc_mvm_dc(const double *X, long N, int d, int two_nu, const double *ell, do
  * reading is the binomial expansion of prod_k (1 + a delta_k (z_k - x_k)).
  * Kept beside orc_mvm_dc so the reading can be checked against
  * Proposition 2. */
+/* The L1 kernel's lengthscale gradient by the paper's printed decompositions
+ * (App. C.1: the gradient formulas after eqs. matern_12_decomposition,
+ * matern_32_decomposition, matern_52_decomposition), evaluated with the same
+ * weighted ECDFs F(delta z, delta; delta x, w^(p)) as orc_mvm_dc, one weight
+ * order more (p <= P).  Returned as the derivative with respect to log ell
+ * (ell times the printed d/d ell; every lengthscale scaled together when they
+ * differ per dimension).  In scaled coordinates (z = delta . u_z):
+ *   nu = 1/2:  e^{-z} (z F0 - F1)
+ *   nu = 3/2:  3 e^{-a z} (z^2 F0 - 2 z F1 + F2)
+ *   nu = 5/2:  5/3 e^{-a z} ((a z^3 + z^2) F0 - (2 z + 3 a z^2) F1 + (3 a z + 1) F2 - a F3) */
+int orc_mvm_dc_dlogell_l1(const double *X, long N, int d, int two_nu, const double *ell, double s2,
+                          const double *V, int nrhs, double *Y)
+{
+    if (check_args(N, d, two_nu, ell, ORC_L1) || nrhs < 1) return -1;
+    int P = (two_nu + 1) / 2;
+    int nw = P + 1;
+    double a = sqrt((double)two_nu);
+    double *U = scaled_coords(X, N, d, ell);
+    item_t *it = (item_t *)malloc(sizeof(item_t) * (size_t)(2 * N + 1));
+    double *W = (double *)malloc(sizeof(double) * (size_t)(N + 1) * (size_t)nw);
+    double *F = (double *)malloc(sizeof(double) * (size_t)(N + 1) * (size_t)nw);
+    memset(Y, 0, sizeof(double) * (size_t)N * (size_t)nrhs);
+    int ndelta = 1 << d;
+    for (int c = 0; c < nrhs; ++c) {
+        for (int mask = 0; mask < ndelta; ++mask) {
+            int delta[3];
+            for (int k = 0; k < d; ++k) delta[k] = (mask >> k) & 1 ? -1 : 1;
+            for (long i = 0; i < N; ++i) {
+                double dx = 0.0;
+                for (int k = 0; k < d; ++k) dx += delta[k] * U[i * d + k];
+                for (int q = 0; q < nw; ++q) W[i * nw + q] = V[i * nrhs + c] * pow(dx, q) * exp(a * dx);
+            }
+            memset(F, 0, sizeof(double) * (size_t)N * (size_t)nw);
+            make_keys(U, N, d, delta, it);
+            ecdf_dc(it, 2 * N, 0, d, W, nw, F);
+            for (long j = 0; j < N; ++j) {
+                double z = 0.0;
+                for (int k = 0; k < d; ++k) z += delta[k] * U[j * d + k];
+                const double *Fj = F + j * nw;
+                double acc;
+                if (two_nu == 1)
+                    acc = exp(-z) * (z * Fj[0] - Fj[1]);
+                else if (two_nu == 3)
+                    acc = 3.0 * exp(-a * z) * (z * z * Fj[0] - 2.0 * z * Fj[1] + Fj[2]);
+                else
+                    acc = (5.0 / 3.0) * exp(-a * z) *
+                          ((a * z * z * z + z * z) * Fj[0] - (2.0 * z + 3.0 * a * z * z) * Fj[1] +
+                           (3.0 * a * z + 1.0) * Fj[2] - a * Fj[3]);
+                Y[j * nrhs + c] += s2 * acc;
+            }
+        }
+    }
+    free(U);
+    free(it);
+    free(W);
+    free(F);
+    return 0;
+}
+
 int orc_mvm_dc_product32_printed(const double *X, long N, int d, const double *ell, double s2,
                                  const double *V, double *Y)
 {

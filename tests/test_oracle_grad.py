@@ -96,3 +96,17 @@ def test_gradient_rejects_a_dimension_out_of_range(orc):
     p = workloads.small(6, 10, 2, nu=1.5, ell=[0.1, 0.2])
     with pytest.raises(ValueError):
         orc.mvm_dlogell_brute(p.X, p.V, 1.5, p.ell, dim=2)
+
+
+@pytest.mark.parametrize("nu", NUS)
+@pytest.mark.parametrize("d", [1, 2, 3])
+@pytest.mark.parametrize("pattern", ["uniform", "lattice", "dups"])
+def test_printed_l1_gradient_decomposition_equals_the_definition(orc, nu, d, pattern):
+    """App. C.1's gradient decompositions of the L1 kernels (the ECDF form,
+    evaluated on the literal divide and conquer) against the brute-force
+    derivative."""
+    p = workloads.small(900 + d, 120, d, nu=nu, ell=[0.2, 0.35, 0.15][:d], nrhs=2, pattern=pattern, s2=1.3)
+    got = orc.mvm_dc_dlogell_l1(p.X, p.V, nu, p.ell, s2=p.s2)
+    ref = orc.mvm_dlogell_brute(p.X, p.V, nu, p.ell, dim=-1, s2=p.s2, kind=0)
+    err = np.linalg.norm(got - ref, axis=0) / np.linalg.norm(ref, axis=0)
+    assert (err < 1e-10).all(), err
