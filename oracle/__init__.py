@@ -35,6 +35,7 @@ from .core import (  # noqa: F401
     mvm_brute,
     mvm_dc,
     mvm_dc_dlogell_l1,
+    mvm_dc_dlogell_product,
     mvm_dc_product32_printed,
     mvm_dlogell_brute,
     phi,

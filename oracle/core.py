@@ -65,6 +65,9 @@ def _load():
         lib.orc_mvm_dc_dlogell_l1.restype = ctypes.c_int
         lib.orc_mvm_dc_dlogell_l1.argtypes = [D, ctypes.c_long, ctypes.c_int, ctypes.c_int, D, ctypes.c_double, D,
                                               ctypes.c_int, D]
+        lib.orc_mvm_dc_dlogell_product.restype = ctypes.c_int
+        lib.orc_mvm_dc_dlogell_product.argtypes = [D, ctypes.c_long, ctypes.c_int, ctypes.c_int, D, ctypes.c_double,
+                                                   ctypes.c_int, D, ctypes.c_int, D]
         lib.orc_mvm_dc.restype = ctypes.c_int
         lib.orc_mvm_dc.argtypes = [D, ctypes.c_long, ctypes.c_int, ctypes.c_int, D, ctypes.c_double,
                                    ctypes.c_int, D, ctypes.c_int, D]
@@ -237,6 +240,22 @@ def mvm_dc_dlogell_l1(X, V, nu, ell, s2: float = 1.0) -> np.ndarray:
     Y = np.empty_like(V)
     if lib.orc_mvm_dc_dlogell_l1(_dp(X), N, d, _two_nu(nu), _dp(ell), float(s2), _dp(V), V.shape[1], _dp(Y)) != 0:
         raise ValueError("orc_mvm_dc_dlogell_l1 rejected its arguments")
+    return Y[:, 0] if vec else Y
+
+
+def mvm_dc_dlogell_product(X, V, nu, ell, dim: int = -1, s2: float = 1.0) -> np.ndarray:
+    """The product kernel's log-lengthscale gradient product through
+    Proposition 2's weighted ECDFs with one factor differentiated."""
+    lib = _load()
+    X, d, ell = _prep(X, ell)
+    N = X.shape[0]
+    V = np.asarray(V, dtype=np.float64)
+    vec = V.ndim == 1
+    V = np.ascontiguousarray(V.reshape(N, -1))
+    Y = np.empty_like(V)
+    if lib.orc_mvm_dc_dlogell_product(_dp(X), N, d, _two_nu(nu), _dp(ell), float(s2), int(dim), _dp(V),
+                                      V.shape[1], _dp(Y)) != 0:
+        raise ValueError("orc_mvm_dc_dlogell_product rejected its arguments")
     return Y[:, 0] if vec else Y
 
 

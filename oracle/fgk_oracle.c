@@ -30,6 +30,8 @@
  *                  all lengthscales scaled together.
  *  orc_mvm_dc_dlogell_l1  the L1 kernel's lengthscale gradient by the
  *                  paper's printed ECDF decompositions, on O2's machinery.
+ *  orc_mvm_dc_dlogell_product  the product kernel's lengthscale gradient
+ *                  through Proposition 2 with one factor differentiated.
  *  orc_mvm_dc      O2: the paper's own algorithm, written in its order and
  *                  notation: weighted ECDFs with the generalised inequality
  *                  (eq. ECDFdelta), one per orthant delta and weight vector,
@@ -622,6 +624,110 @@ int orc_mvm_dc_dlogell_l1(const double *X, long N, int d, int two_nu, const doub
                           ((a * z * z * z + z * z) * Fj[0] - (2.0 * z + 3.0 * a * z * z) * Fj[1] +
                            (3.0 * a * z + 1.0) * Fj[2] - a * Fj[3]);
                 Y[j * nrhs + c] += s2 * acc;
+            }
+        }
+    }
+    free(U);
+    free(it);
+    free(W);
+    free(F);
+    return 0;
+}
+
+/* Coefficients f_q of a one-dimensional factor f(u) = sum_q f_q u^q e^{-a u}
+ * (u = |x| / ell, a = sqrt(2 nu)): which = 0 the kernel k (App. C.1), which = 1
+ * its log-lengthscale derivative -u k'(u). */
+static int factor_coefs(int two_nu, int which, double *f)
+{
+    double a = sqrt((double)two_nu);
+    for (int q = 0; q < 4; ++q) f[q] = 0.0;
+    if (which == 0) {
+        f[0] = 1.0;
+        if (two_nu >= 3) f[1] = a;
+        if (two_nu == 5) f[2] = 5.0 / 3.0;
+        return (two_nu + 1) / 2;
+    }
+    if (two_nu == 1) f[1] = 1.0;
+    if (two_nu == 3) f[2] = 3.0;
+    if (two_nu == 5) {
+        f[2] = 5.0 / 3.0;
+        f[3] = 5.0 * a / 3.0;
+    }
+    return (two_nu + 3) / 2;
+}
+
+static double binom_d(int n, int k)
+{
+    double r = 1.0;
+    for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+    return r;
+}
+
+/* The product kernel's lengthscale gradient through Proposition 2: in an
+ * orthant delta every one-dimensional factor f(dz - dx) (dz = delta_k z_k,
+ * dx = delta_k x_k, dz >= dx) splits by the binomial theorem as
+ *   f(dz - dx) = sum_j chi1_j(dz) chi2_j(dx),
+ *   chi1_j(dz) = e^{-a dz} sum_{q >= j} f_q C(q, j) dz^{q-j} (-1)^j,
+ *   chi2_j(dx) = dx^j e^{a dx},
+ * so the sum over sources of prod_k f_k is a sum over index patterns of
+ * weighted ECDFs with weights prod_k chi2 (eq. ECDFdelta), recombined with
+ * prod_k chi1 — eq. product_decomposition with the factor of dimension dim
+ * replaced by -u k'(u) (dim = -1: summed over the dimensions). */
+int orc_mvm_dc_dlogell_product(const double *X, long N, int d, int two_nu, const double *ell, double s2, int dim,
+                               const double *V, int nrhs, double *Y)
+{
+    if (check_args(N, d, two_nu, ell, ORC_PRODUCT) || nrhs < 1 || dim < -1 || dim >= d) return -1;
+    double a = sqrt((double)two_nu);
+    double *U = scaled_coords(X, N, d, ell);
+    item_t *it = (item_t *)malloc(sizeof(item_t) * (size_t)(2 * N + 1));
+    double *W = (double *)malloc(sizeof(double) * (size_t)(N + 1) * 64);
+    double *F = (double *)malloc(sizeof(double) * (size_t)(N + 1) * 64);
+    memset(Y, 0, sizeof(double) * (size_t)N * (size_t)nrhs);
+    int ndelta = 1 << d;
+    for (int m = 0; m < d; ++m) {
+        if (dim >= 0 && m != dim) continue;
+        double f[3][4];
+        int nj[3], nw = 1;
+        for (int k = 0; k < d; ++k) {
+            nj[k] = factor_coefs(two_nu, k == m ? 1 : 0, f[k]);
+            nw *= nj[k];
+        }
+        for (int c = 0; c < nrhs; ++c) {
+            for (int mask = 0; mask < ndelta; ++mask) {
+                int delta[3];
+                for (int k = 0; k < d; ++k) delta[k] = (mask >> k) & 1 ? -1 : 1;
+                for (long i = 0; i < N; ++i)
+                    for (int t = 0; t < nw; ++t) {
+                        double w = V[i * nrhs + c];
+                        int rem = t;
+                        for (int k = 0; k < d; ++k) {
+                            int j = rem % nj[k];
+                            rem /= nj[k];
+                            double dx = delta[k] * U[i * d + k];
+                            w *= pow(dx, j) * exp(a * dx);
+                        }
+                        W[i * nw + t] = w;
+                    }
+                memset(F, 0, sizeof(double) * (size_t)N * (size_t)nw);
+                make_keys(U, N, d, delta, it);
+                ecdf_dc(it, 2 * N, 0, d, W, nw, F);
+                for (long q = 0; q < N; ++q) {
+                    double acc = 0.0;
+                    for (int t = 0; t < nw; ++t) {
+                        double g = F[q * nw + t];
+                        int rem = t;
+                        for (int k = 0; k < d; ++k) {
+                            int j = rem % nj[k];
+                            rem /= nj[k];
+                            double dz = delta[k] * U[q * d + k];
+                            double chi = 0.0;
+                            for (int qq = j; qq < nj[k]; ++qq) chi += f[k][qq] * binom_d(qq, j) * pow(dz, qq - j);
+                            g *= (j % 2 ? -1.0 : 1.0) * chi * exp(-a * dz);
+                        }
+                        acc += g;
+                    }
+                    Y[q * nrhs + c] += s2 * acc;
+                }
             }
         }
     }
