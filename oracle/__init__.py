@@ -34,6 +34,7 @@ from .core import (  # noqa: F401
     max_threads,
     mvm_brute,
     mvm_dc,
+    mvm_dc_cross,
     mvm_dc_dlogell_l1,
     mvm_dc_dlogell_product,
     mvm_dc_product32_printed,

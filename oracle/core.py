@@ -68,6 +68,9 @@ def _load():
         lib.orc_mvm_dc_dlogell_product.restype = ctypes.c_int
         lib.orc_mvm_dc_dlogell_product.argtypes = [D, ctypes.c_long, ctypes.c_int, ctypes.c_int, D, ctypes.c_double,
                                                    ctypes.c_int, D, ctypes.c_int, D]
+        lib.orc_mvm_dc_cross.restype = ctypes.c_int
+        lib.orc_mvm_dc_cross.argtypes = [D, ctypes.c_long, D, ctypes.c_long, ctypes.c_int, ctypes.c_int, D,
+                                         ctypes.c_double, ctypes.c_int, D, ctypes.c_int, D]
         lib.orc_mvm_dc.restype = ctypes.c_int
         lib.orc_mvm_dc.argtypes = [D, ctypes.c_long, ctypes.c_int, ctypes.c_int, D, ctypes.c_double,
                                    ctypes.c_int, D, ctypes.c_int, D]
@@ -225,6 +228,24 @@ def mvm_dc(X, V, nu, ell, s2: float = 1.0, kind: int = L1) -> np.ndarray:
     Y = np.empty_like(V)
     if lib.orc_mvm_dc(_dp(X), N, d, _two_nu(nu), _dp(ell), float(s2), int(kind), _dp(V), V.shape[1], _dp(Y)) != 0:
         raise ValueError("orc_mvm_dc rejected its arguments")
+    return Y[:, 0] if vec else Y
+
+
+def mvm_dc_cross(X, Z, V, nu, ell, s2: float = 1.0, kind: int = L1) -> np.ndarray:
+    """Kernel sums at the new points Z over the data X (the k_z^T V of
+    eq. gp_mean) by the paper's ECDF decomposition (literal, slow)."""
+    lib = _load()
+    X, d, ell = _prep(X, ell)
+    N = X.shape[0]
+    Z = np.ascontiguousarray(np.asarray(Z, dtype=np.float64).reshape(-1, d))
+    M = Z.shape[0]
+    V = np.asarray(V, dtype=np.float64)
+    vec = V.ndim == 1
+    V = np.ascontiguousarray(V.reshape(N, -1))
+    Y = np.empty((M, V.shape[1]))
+    if lib.orc_mvm_dc_cross(_dp(X), N, _dp(Z), M, d, _two_nu(nu), _dp(ell), float(s2), int(kind), _dp(V),
+                            V.shape[1], _dp(Y)) != 0:
+        raise ValueError("orc_mvm_dc_cross rejected its arguments")
     return Y[:, 0] if vec else Y
 
 

@@ -28,6 +28,8 @@
  *                  gradient product of the trace term of
  *                  eq. gp_log_likelihood_derivative, per lengthscale or for
  *                  all lengthscales scaled together.
+ *  orc_mvm_dc_cross  the kernel sums at new points (k_z of eq. gp_mean)
+ *                  by the same decomposition, sources and queries apart.
  *  orc_mvm_dc_dlogell_l1  the L1 kernel's lengthscale gradient by the
  *                  paper's printed ECDF decompositions, on O2's machinery.
  *  orc_mvm_dc_dlogell_product  the product kernel's lengthscale gradient
@@ -432,6 +434,40 @@ static void make_keys(const double *U, long N, int d, const int *delta, item_t *
     free(rank);
 }
 
+/* Keys for sources at the data U (N points) and queries at new points Z
+ * (M points): the dense ranks are taken over the union, with the same
+ * strict source/query offsets as make_keys.  Items 0..N-1 are the sources
+ * (id = data index), N..N+M-1 the queries (id = new-point index). */
+static void make_keys_cross(const double *U, long N, const double *Zs, long M, int d, const int *delta, item_t *it)
+{
+    long T = N + M;
+    vi_t *tmp = (vi_t *)malloc(sizeof(vi_t) * (size_t)T);
+    long *rank = (long *)malloc(sizeof(long) * (size_t)T);
+    for (int k = 0; k < d; ++k) {
+        for (long i = 0; i < T; ++i) {
+            tmp[i].v = delta[k] * (i < N ? U[i * d + k] : Zs[(i - N) * d + k]);
+            tmp[i].i = i;
+        }
+        qsort(tmp, (size_t)T, sizeof(vi_t), cmp_vi);
+        long r = -1;
+        for (long a = 0; a < T; ++a) {
+            if (a == 0 || tmp[a].v != tmp[a - 1].v) ++r;
+            rank[tmp[a].i] = r;
+        }
+        for (long i = 0; i < T; ++i) {
+            long rs = delta[k] > 0 ? 2 * rank[i] : 2 * rank[i] + 1;
+            long rq = delta[k] > 0 ? 2 * rank[i] + 1 : 2 * rank[i];
+            it[i].key[k] = i < N ? rs : rq;
+        }
+    }
+    for (long i = 0; i < T; ++i) {
+        it[i].src = i < N;
+        it[i].id = i < N ? i : i - N;
+    }
+    free(tmp);
+    free(rank);
+}
+
 /* One-dimensional factor pairs phi_{1,p}, phi_{2,p} with k(u - v) equal to
  * sum_p phi_{1,p}(u) phi_{2,p}(v) (Assumption 1), unit lengthscale:
  * eq. k12_decomposition_phi (P=1), eq. k32_decomposition_phi (P=2),
@@ -575,6 +611,95 @@ int orc_mvm_dc(const double *X, long N, int d, int two_nu, const double *ell, do
  * reading is the binomial expansion of prod_k (1 + a delta_k (z_k - x_k)).
  * Kept beside orc_mvm_dc so the reading can be checked against
  * Proposition 2. */
+/* The kernel sums at new points, Y_j = s2 sum_i K(z_j - x_i) V_i (the vector
+ * k_z of eq. gp_mean times V; the kernel sum of eq. kde at any z), by the
+ * same decomposition as orc_mvm_dc: sources at the data, queries at the new
+ * points, one weighted ECDF per orthant and weight vector, recombined with
+ * the printed Matérn formulas (L1) or Proposition 2 (product). */
+int orc_mvm_dc_cross(const double *X, long N, const double *Zp, long M, int d, int two_nu, const double *ell,
+                     double s2, int kind, const double *V, int nrhs, double *Y)
+{
+    if (check_args(N, d, two_nu, ell, kind) || nrhs < 1 || M < 1) return -1;
+    int P = (two_nu + 1) / 2;
+    double a = sqrt((double)two_nu);
+    int nw = 1;
+    if (kind == ORC_L1)
+        nw = P;
+    else
+        for (int k = 0; k < d; ++k) nw *= P;
+    double *U = scaled_coords(X, N, d, ell);
+    double *Zs = scaled_coords(Zp, M, d, ell);
+    item_t *it = (item_t *)malloc(sizeof(item_t) * (size_t)(N + M + 1));
+    double *W = (double *)malloc(sizeof(double) * (size_t)(N + 1) * (size_t)nw);
+    double *F = (double *)malloc(sizeof(double) * (size_t)(M + 1) * (size_t)nw);
+    memset(Y, 0, sizeof(double) * (size_t)M * (size_t)nrhs);
+    int ndelta = 1 << d;
+    for (int c = 0; c < nrhs; ++c) {
+        for (int mask = 0; mask < ndelta; ++mask) {
+            int delta[3];
+            for (int k = 0; k < d; ++k) delta[k] = (mask >> k) & 1 ? -1 : 1;
+            for (long i = 0; i < N; ++i) {
+                double vi = V[i * nrhs + c];
+                if (kind == ORC_L1) {
+                    double dx = 0.0;
+                    for (int k = 0; k < d; ++k) dx += delta[k] * U[i * d + k];
+                    for (int p = 0; p < P; ++p) W[i * nw + p] = vi * pow(dx, p) * exp(a * dx);
+                } else {
+                    for (int t = 0; t < nw; ++t) {
+                        double w = vi;
+                        int rem = t;
+                        for (int k = 0; k < d; ++k) {
+                            int th = rem % P;
+                            rem /= P;
+                            w *= phi2(two_nu, th, delta[k] * U[i * d + k]);
+                        }
+                        W[i * nw + t] = w;
+                    }
+                }
+            }
+            memset(F, 0, sizeof(double) * (size_t)M * (size_t)nw);
+            make_keys_cross(U, N, Zs, M, d, delta, it);
+            ecdf_dc(it, N + M, 0, d, W, nw, F);
+            for (long j = 0; j < M; ++j) {
+                double acc;
+                const double *Fj = F + j * nw;
+                if (kind == ORC_L1) {
+                    double z = 0.0;
+                    for (int k = 0; k < d; ++k) z += delta[k] * Zs[j * d + k];
+                    if (two_nu == 1)
+                        acc = exp(-z) * Fj[0];
+                    else if (two_nu == 3)
+                        acc = exp(-a * z) * ((1.0 + a * z) * Fj[0] - a * Fj[1]);
+                    else {
+                        double c2 = 5.0 / 3.0;
+                        acc = exp(-a * z) *
+                              ((1.0 + a * z + c2 * z * z) * Fj[0] - (a + 2.0 * c2 * z) * Fj[1] + c2 * Fj[2]);
+                    }
+                } else {
+                    acc = 0.0;
+                    for (int t = 0; t < nw; ++t) {
+                        double f = Fj[t];
+                        int rem = t;
+                        for (int k = 0; k < d; ++k) {
+                            int th = rem % P;
+                            rem /= P;
+                            f *= phi1(two_nu, th, delta[k] * Zs[j * d + k]);
+                        }
+                        acc += f;
+                    }
+                }
+                Y[j * nrhs + c] += s2 * acc;
+            }
+        }
+    }
+    free(U);
+    free(Zs);
+    free(it);
+    free(W);
+    free(F);
+    return 0;
+}
+
 /* The L1 kernel's lengthscale gradient by the paper's printed decompositions
  * (App. C.1: the gradient formulas after eqs. matern_12_decomposition,
  * matern_32_decomposition, matern_52_decomposition), evaluated with the same

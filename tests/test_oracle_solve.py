@@ -72,3 +72,19 @@ def test_posterior_mean_cross_covariance_is_symmetric_and_matches_the_kernel(orc
     u = np.abs(Z[:, None, :] - p.X[None, :, :]) * np.sqrt(3.0) / p.ell
     ref = 1.7 * np.prod((1 + u) * np.exp(-u), axis=2)
     assert np.allclose(C, ref, rtol=1e-13, atol=1e-15)
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("nu", [0.5, 1.5, 2.5])
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_kernel_sums_at_new_points_by_the_decomposition(orc, kind, nu, d):
+    """eq. gp_mean's k_z^T V by the ECDF decomposition with sources at the
+    data and queries at new points (some of them on data coordinates, so
+    ties between the two sets occur) against the dense cross-covariance."""
+    p = workloads.small(500 + d, 150, d, nu=nu, ell=[0.3, 0.5, 0.7][:d], nrhs=2, pattern="lattice")
+    rng = np.random.default_rng(d)
+    Z = np.concatenate([rng.uniform(0, 1, size=(40, d)), p.X[:10]])
+    got = orc.mvm_dc_cross(p.X, Z, p.V, nu, p.ell, s2=1.2, kind=kind)
+    ref = orc.kcross(p.X, Z, nu, p.ell, s2=1.2, kind=kind) @ p.V
+    err = np.linalg.norm(got - ref, axis=0) / np.linalg.norm(ref, axis=0)
+    assert (err < 1e-11).all(), err
