@@ -83,6 +83,34 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert lib.fgk_precond_destroy(None) == 0
 
 
+def test_likelihood_entries_reject_invalid_arguments_without_gpu(lib):
+    """The gradient product, the probes, the log-determinant and the
+    likelihood gradient validate their arguments before any CUDA call."""
+    from paper_2508_01864_gb300 import fgk
+
+    # NULL handle / arrays, nrhs < 1, a bad precision
+    assert lib.fgk_matvec_dlogell(None, 1, 1, 1, 0, 0, None) == -1
+    assert b"dlogell" in lib.fgk_last_error()
+    assert lib.fgk_matvec_dlogell(1, 1, 0, 1, 0, 0, None) == -1
+    assert lib.fgk_matvec_dlogell(1, 1, 1, 1, 0, 7, None) == -1
+    assert lib.fgk_precond_sample(None, 1, 1, 1, 1, None) == -1
+    assert b"precond_sample" in lib.fgk_last_error()
+    rep = fgk.fgk_slq_report()
+    for args in [(None, None, 0.1, 1, 4, 10, 1e-8), (1, None, 0.1, None, 4, 10, 1e-8), (1, None, 0.1, 1, 0, 10, 1e-8),
+                 (1, None, 0.1, 1, 65, 10, 1e-8), (1, None, 0.1, 1, 4, 0, 1e-8), (1, None, -1.0, 1, 4, 10, 1e-8),
+                 (1, None, 0.1, 1, 4, 10, 0.0)]:
+        assert lib.fgk_slq_logdet(*args, None, None, None, ctypes.byref(rep), None) == -1, args
+    assert b"slq_logdet" in lib.fgk_last_error()
+    g = (ctypes.c_double * 8)()
+    grep = fgk.fgk_grad_report()
+    for args in [(None, None, 0.1, 1, 1, 4, 1e-8, 10, 2), (1, None, 0.1, None, 1, 4, 1e-8, 10, 2),
+                 (1, None, 0.1, 1, None, 4, 1e-8, 10, 2), (1, None, 0.0, 1, 1, 4, 1e-8, 10, 2),
+                 (1, None, 0.1, 1, 1, 64, 1e-8, 10, 2), (1, None, 0.1, 1, 1, 4, 1e-8, 0, 2),
+                 (1, None, 0.1, 1, 1, 4, 1e-8, 10, 1)]:
+        assert lib.fgk_loglik_grad(*args, g, ctypes.byref(grep), None) == -1, args
+    assert b"loglik_grad" in lib.fgk_last_error()
+
+
 def test_binding_fails_loudly_without_library(tmp_path):
     from paper_2508_01864_gb300 import fgk
 
