@@ -202,6 +202,31 @@ def _dev_f64_2d(t: torch.Tensor, name: str) -> torch.Tensor:
     return t
 
 
+# The library receives bare pointers and cannot see a buffer's size: every
+# row count, column count and output buffer is checked here, before the call,
+# so that a mis-shaped tensor raises instead of being read or written past
+# its end on the device.
+def _rows(t: torch.Tensor, n: int, name: str, what: str = "the plan's points") -> None:
+    if t.shape[0] != n:
+        raise ValueError(f"{name} has {t.shape[0]} rows, {what} are {n}")
+
+
+def _out_for(out, like: torch.Tensor, name: str = "out") -> torch.Tensor:
+    """The caller's output buffer for a result shaped like ``like`` (2-D):
+    same device and dtype, contiguous, the same shape (or a vector when the
+    result has one column); returned as a view of like's shape.  A new
+    tensor when ``out`` is None."""
+    if out is None:
+        return torch.empty_like(like)
+    if (not isinstance(out, torch.Tensor) or out.device != like.device or out.dtype != like.dtype
+            or not out.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous {like.dtype} tensor on {like.device}")
+    vec = out.dim() == 1 and like.shape[1] == 1 and out.shape[0] == like.shape[0]
+    if tuple(out.shape) != tuple(like.shape) and not vec:
+        raise ValueError(f"{name} has shape {tuple(out.shape)}, the result {tuple(like.shape)}")
+    return out.view(like.shape)
+
+
 @dataclass
 class Handle:
     ptr: int
@@ -239,10 +264,8 @@ def fgk_matvec(h: Handle, V: torch.Tensor, precision="f64", out: torch.Tensor | 
         raise TypeError(f"V must be a contiguous CUDA {dt} tensor")
     squeeze = V.dim() == 1
     V2 = V.unsqueeze(1) if squeeze else V
-    if V2.shape[0] != h.N:
-        raise ValueError("V has the wrong number of rows")
-    if out is None:
-        out = torch.empty_like(V2)
+    _rows(V2, h.N, "V")
+    out = _out_for(out, V2)
     _check(lib.fgk_matvec(h.ptr, V2.data_ptr(), V2.shape[1], out.data_ptr(), prec, _stream(stream)))
     return out.squeeze(1) if squeeze else out
 
@@ -258,10 +281,8 @@ def fgk_matvec_dlogell(h: Handle, V: torch.Tensor, dim: int = -1, precision="f64
         raise TypeError(f"V must be a contiguous CUDA {dt} tensor")
     squeeze = V.dim() == 1
     V2 = V.unsqueeze(1) if squeeze else V
-    if V2.shape[0] != h.N:
-        raise ValueError("V has the wrong number of rows")
-    if out is None:
-        out = torch.empty_like(V2)
+    _rows(V2, h.N, "V")
+    out = _out_for(out, V2)
     _check(lib.fgk_matvec_dlogell(h.ptr, V2.data_ptr(), V2.shape[1], out.data_ptr(), int(dim), prec,
                                   _stream(stream)))
     return out.squeeze(1) if squeeze else out
@@ -275,8 +296,8 @@ def fgk_matvec_q(h: Handle, Vq: torch.Tensor, precision="f32", out: torch.Tensor
     if not Vq.is_cuda or Vq.dtype != dt or not Vq.is_contiguous():
         raise TypeError(f"Vq must be a contiguous CUDA {dt} tensor")
     V2 = Vq.unsqueeze(1) if Vq.dim() == 1 else Vq
-    if out is None:
-        out = torch.empty_like(V2)
+    _rows(V2, h.N, "Vq")
+    out = _out_for(out, V2)
     _check(lib.fgk_matvec_q(h.ptr, V2.data_ptr(), V2.shape[1], out.data_ptr(), prec, _stream(stream)))
     return out
 
@@ -287,11 +308,14 @@ def fgk_matvec_q_noalloc(h: Handle, Vq: torch.Tensor, out: torch.Tensor, precisi
     lib = load()
     prec = {"f64": FGK_F64, "f32": FGK_F32}[precision] if isinstance(precision, str) else int(precision)
     dt = torch.float64 if prec == FGK_F64 else torch.float32
-    for t, n in ((Vq, "Vq"), (out, "out")):
-        if not t.is_cuda or t.dtype != dt or not t.is_contiguous():
-            raise TypeError(f"{n} must be a contiguous CUDA {dt} tensor")
+    if not Vq.is_cuda or Vq.dtype != dt or not Vq.is_contiguous():
+        raise TypeError(f"Vq must be a contiguous CUDA {dt} tensor")
+    if out is None:
+        raise TypeError("out is required (this call allocates nothing)")
     V2 = Vq.unsqueeze(1) if Vq.dim() == 1 else Vq
-    _check(lib.fgk_matvec_q_noalloc(h.ptr, V2.data_ptr(), V2.shape[1], out.data_ptr(), prec, _stream(stream)))
+    _rows(V2, h.N, "Vq")
+    out2 = _out_for(out, V2)
+    _check(lib.fgk_matvec_q_noalloc(h.ptr, V2.data_ptr(), V2.shape[1], out2.data_ptr(), prec, _stream(stream)))
     return out
 
 
@@ -329,11 +353,13 @@ def fgk_cg_solve(h: Handle, y: torch.Tensor, sigma2: float, H: torch.Tensor | No
     FGK_NOT_CONVERGED; errors raise FgkError."""
     lib = load()
     y2 = _dev_f64_2d(y, "y")
+    _rows(y2, h.N, "y")
     nrhs = y2.shape[1]
     m = {"f64": FGK_F64, "mixed": FGK_MIXED}[mode] if isinstance(mode, str) else int(mode)
     Hp = 0
     if H is not None:
         H = _dev_f64_2d(H, "H")
+        _rows(H, h.N, "H")
         L = H.shape[1]
         Hp = H.data_ptr()
     Leff = L if L >= 0 else 1 + h.d
@@ -369,6 +395,7 @@ class Precond:
     ptr: int
     handle: Handle
     sigma2: float
+    rank: int = 0  # the realised rank k (the factor's columns)
 
     def __enter__(self):
         return self
@@ -380,8 +407,14 @@ class Precond:
 def fgk_precond_build(h: Handle, rank: int, sigma2: float, stream=None) -> Precond:
     """Rank-k pivoted-Cholesky preconditioner P = L L^T + sigma2 I of the plan's K."""
     out = ctypes.c_void_p()
-    _check(load().fgk_precond_build(h.ptr, int(rank), float(sigma2), _stream(stream), ctypes.byref(out)))
-    return Precond(out.value, h, float(sigma2))
+    lib = load()
+    _check(lib.fgk_precond_build(h.ptr, int(rank), float(sigma2), _stream(stream), ctypes.byref(out)))
+    rep = fgk_precond_report()
+    rc = lib.fgk_precond_info(out.value, ctypes.byref(rep), None)
+    if rc != FGK_OK:
+        lib.fgk_precond_destroy(out.value)
+        _check(rc)
+    return Precond(out.value, h, float(sigma2), int(rep.rank))
 
 
 def fgk_precond_info(pc: Precond) -> dict:
@@ -405,7 +438,8 @@ def fgk_precond_factor(pc: Precond, stream=None) -> torch.Tensor:
 def fgk_precond_apply(pc: Precond, R: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     """Z = P^{-1} R (Woodbury), R: N x ncols FP64 CUDA tensor in the caller's order."""
     R2 = _dev_f64_2d(R, "R")
-    Z = torch.empty_like(R2) if out is None else out
+    _rows(R2, pc.handle.N, "R")
+    Z = _out_for(out, R2)
     _check(load().fgk_precond_apply(pc.ptr, R2.data_ptr(), R2.shape[1], Z.data_ptr(), _stream(stream)))
     return Z.squeeze(1) if R.dim() == 1 else Z
 
@@ -414,9 +448,16 @@ def fgk_precond_sample(pc: Precond, E_r: torch.Tensor, E_n: torch.Tensor, stream
     """Probes B = L_hi E_r + sigma E_n ~ N(0, P) from the caller's standard
     normal draws E_r (k x nprobe) and E_n (N x nprobe), FP64 CUDA tensors."""
     En = _dev_f64_2d(E_n, "E_n")
-    Er = _dev_f64_2d(E_r, "E_r") if E_r.numel() else E_r
+    _rows(En, pc.handle.N, "E_n")
+    if pc.rank > 0:
+        Er = _dev_f64_2d(E_r, "E_r")
+        _rows(Er, pc.rank, "E_r", "the preconditioner's rank")
+        if Er.shape[1] != En.shape[1]:
+            raise ValueError(f"E_r has {Er.shape[1]} columns, E_n {En.shape[1]}")
+    else:
+        Er = E_r
     B = torch.empty_like(En)
-    _check(load().fgk_precond_sample(pc.ptr, Er.data_ptr() if Er.numel() else None, En.data_ptr(), En.shape[1],
+    _check(load().fgk_precond_sample(pc.ptr, Er.data_ptr() if pc.rank > 0 else None, En.data_ptr(), En.shape[1],
                                      B.data_ptr(), _stream(stream)))
     return B
 
@@ -428,6 +469,7 @@ def fgk_slq_logdet(h: Handle, B: torch.Tensor, sigma2: float, m: int, tol: float
     include/fgk.h.  Returns the estimate, log det P, per-probe quadrature
     values and Lanczos steps, and (want_solves) the solves (K + sigma2 I)^-1 B."""
     B2 = _dev_f64_2d(B, "B")
+    _rows(B2, h.N, "B")
     nprobe = B2.shape[1]
     X = torch.empty_like(B2) if want_solves else None
     quad = (ctypes.c_double * nprobe)()
@@ -446,7 +488,12 @@ def fgk_loglik_grad(h: Handle, y: torch.Tensor, B: torch.Tensor, sigma2: float, 
     """The log-likelihood gradient in (log ell..., log varsigma^2, log sigma^2)
     with Hutchinson probes B; see include/fgk.h."""
     y1 = _dev_f64_2d(y, "y")
+    _rows(y1, h.N, "y")
+    if y1.shape[1] != 1:
+        raise ValueError("y must be one column")
     B2 = _dev_f64_2d(B, "B") if B is not None else None
+    if B2 is not None:
+        _rows(B2, h.N, "B")
     g = (ctypes.c_double * 8)()
     rep = fgk_grad_report()
     m = FGK_MIXED if mode == "mixed" else FGK_F64
@@ -477,6 +524,7 @@ def fgk_predict(h: Handle, alpha: torch.Tensor, Z: torch.Tensor, beta: torch.Ten
                 HZ: torch.Tensor | None = None, L: int = 0, precision="f64", stream=None) -> torch.Tensor:
     """Posterior mean at the rows of Z (eq. gp_mean): K(Z, X) alpha (+ h(Z) beta)."""
     a2 = _dev_f64_2d(alpha, "alpha")
+    _rows(a2, h.N, "alpha")
     Z2 = _dev_f64_2d(Z, "Z")
     if Z2.shape[1] != h.d:
         raise ValueError("Z must have d columns")
@@ -484,12 +532,16 @@ def fgk_predict(h: Handle, alpha: torch.Tensor, Z: torch.Tensor, beta: torch.Ten
     Hp, bp = 0, 0
     if HZ is not None:
         HZ = _dev_f64_2d(HZ, "HZ")
+        _rows(HZ, Z2.shape[0], "HZ", "the rows of Z")
         L = HZ.shape[1]
         Hp = HZ.data_ptr()
     if L != 0:
         if beta is None:
             raise ValueError("fixed effects need beta")
         beta = _dev_f64_2d(beta, "beta")
+        Leff = L if L > 0 else 1 + h.d
+        if tuple(beta.shape) != (Leff, a2.shape[1]):
+            raise ValueError(f"beta has shape {tuple(beta.shape)}, expected {(Leff, a2.shape[1])}")
         bp = beta.data_ptr()
     out = torch.empty((Z2.shape[0], a2.shape[1]), dtype=torch.float64, device=a2.device)
     _check(load().fgk_predict(h.ptr, a2.data_ptr(), a2.shape[1], Z2.data_ptr(), Z2.shape[0], Hp, int(L), bp, prec,
@@ -574,8 +626,7 @@ def fgk_batch_matvec_q(b: Batch, Vq: torch.Tensor, out: torch.Tensor | None = No
     lib = load()
     if not Vq.is_cuda or Vq.dtype != torch.float32 or not Vq.is_contiguous() or Vq.shape != (b.rows[-1], b.nrhs):
         raise TypeError("Vq must be a contiguous CUDA float32 tensor of shape (total rows, nrhs)")
-    if out is None:
-        out = torch.empty_like(Vq)
+    out = _out_for(out, Vq)
     _check(lib.fgk_batch_matvec_q(b.ptr, Vq.data_ptr(), out.data_ptr(), _stream(stream)))
     return out
 
@@ -586,7 +637,13 @@ def fgk_batch_cg_solve(b: Batch, ys: list, sigma2s, tol: float = 1e-8, maxit: in
     ``precs``, one per problem, when given); returns (alphas, infos, status)."""
     lib = load()
     n = len(b.handles)
+    if len(ys) != n or len(sigma2s) != n or (precs is not None and len(precs) != n):
+        raise ValueError(f"the batch has {n} problems: give one y, one sigma2 (and one preconditioner) each")
     ys = [_dev_f64_2d(y, "y") for y in ys]
+    for y, hh in zip(ys, b.handles):
+        _rows(y, hh.N, "y")
+        if y.shape[1] != b.nrhs:
+            raise ValueError(f"y has {y.shape[1]} columns, the batch {b.nrhs}")
     alphas = [torch.empty_like(y) for y in ys]
     yp = (ctypes.c_void_p * n)(*[y.data_ptr() for y in ys])
     ap = (ctypes.c_void_p * n)(*[a.data_ptr() for a in alphas])
