@@ -191,7 +191,23 @@ def cpu_baseline(p, iters, seconds):
             "sample": (f"{done} output rows of the FP64 brute-force product in {dt:.1f} s, scaled to a full product "
                        f"({t_mvm:.1f} s) x {iters} CG iterations (the GPU solve's count; the preconditioner's "
                        f"CPU cost, under 0.1% of that, is left out)"),
-            "mvm_nrhs_per_s": p.N / t_mvm}
+            "mvm_nrhs_per_s": p.N / t_mvm, "paper_dc": paper_dc_timing(p, iters)}
+
+
+def paper_dc_timing(p, iters):
+    """The oracle's literal divide and conquer (the paper's algorithm, one
+    thread, sorts redone at every node) on one full product of the same
+    workload: context for the GPU product, not the baseline above."""
+    import oracle
+
+    try:
+        t0 = time.perf_counter()
+        oracle.mvm_dc(p.X, p.V[:, 0], p.nu, p.ell, kind=oracle.PRODUCT)
+        t = time.perf_counter() - t0
+    except Exception as e:  # context only: never lose the benchmark line for it
+        return {"error": f"{type(e).__name__}: {e}"}
+    return {"mvm_s": t, "mvm_nrhs_per_s": p.N / t, "solves_per_s": 1.0 / (t * iters), "threads": 1,
+            "note": f"one full FP64 product by the literal divide and conquer, x {iters} CG iterations"}
 
 
 def run_batched(args, local):

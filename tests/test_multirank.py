@@ -1,7 +1,8 @@
 """The benchmark's multi-rank path on the CPU: two gloo ranks of weak-scaled
 replicas agree on the slowest rank's time (max over ranks, no data-path
 collective besides it) and report the whole-job rate from it; the
-reference arm runs on rank 0 only.  No GPU."""
+reference arm runs on rank 0 only; the CPU context timing of the paper's
+divide and conquer reports one full product.  No GPU."""
 
 import os
 import socket
@@ -68,3 +69,15 @@ def test_reference_arm_runs_on_rank_zero_only():
         ref_iters, warmup, steps, ref_seconds = 1, 0, 1, 0.0
 
     assert bench.run_reference(A(), 2, 1) == 0  # rank 1: no work, exit code 0
+
+
+def test_paper_dc_timing_reports_one_full_product():
+    sys.path.insert(0, ROOT)
+    import bench
+    import workloads
+
+    p = workloads.c2(N=3000)
+    r = bench.paper_dc_timing(p, 100)
+    assert set(r) >= {"mvm_s", "mvm_nrhs_per_s", "solves_per_s", "threads"} and r["threads"] == 1
+    assert r["solves_per_s"] == pytest.approx(1.0 / (100 * r["mvm_s"]))
+    assert r["mvm_nrhs_per_s"] == pytest.approx(3000 / r["mvm_s"])
