@@ -289,7 +289,9 @@ int fgk_cg_solve_pc(fgk_handle h, fgk_precond pc, const double *y, int nrhs, dou
  *   E_r  device, k x nprobe FP64 row-major (k: fgk_precond_info's rank),
  *   E_n  device, N x nprobe FP64 row-major (original point order),
  *   B    device, N x nprobe FP64 row-major (original point order),
- *   1 <= nprobe <= 64.  Asynchronous. */
+ *   1 <= nprobe <= 64.  Asynchronous.  Errors: FGK_ERR_INVALID (a NULL
+ * argument, E_r NULL with k > 0 (it may be NULL at k = 0), nprobe outside
+ * the range). */
 int fgk_precond_sample(fgk_precond pc, const double *E_r, const double *E_n, int nprobe, double *B,
                        fgk_stream_t stream);
 
@@ -322,7 +324,14 @@ typedef struct {
  *   quad    host nprobe or NULL: gamma_b e_1^T log(T_b) e_1 per probe.
  *   steps   host nprobe or NULL: Lanczos steps per probe.
  *   rep     host: the estimate and diagnostics.
- * The solve runs with FP64 scans.  Synchronises `stream`. */
+ * The solve runs with FP64 scans.  Allocates a workspace of 16 m nprobe
+ * bytes (the coefficient log), plus 8 N nprobe when X is NULL.  Synchronises
+ * `stream`.  A probe whose solve stops at m steps is not an error (its
+ * partial Lanczos process is used; rep->solve_status is FGK_NOT_CONVERGED).
+ * Errors: FGK_ERR_INVALID (arguments, or pc built on another plan or for
+ * another sigma2), FGK_ERR_OOM, FGK_ERR_NONFINITE (B), FGK_ERR_BREAKDOWN (a
+ * Ritz value <= 0: the system is not positive definite), or any other error
+ * of the CG solve. */
 int fgk_slq_logdet(fgk_handle h, fgk_precond pc, double sigma2, const double *B, int nprobe, int m, double tol,
                    double *X, double *quad, int *steps, fgk_slq_report *rep, fgk_stream_t stream);
 
@@ -363,7 +372,12 @@ typedef struct {
  *          (the quadratic halves, no trace).
  *   tol, maxit, mode  of the CG solve of [y, B] (as fgk_cg_solve).
  *   pc     NULL or built on h for this sigma2.
- * Allocates a workspace; synchronises `stream`. */
+ * Allocates a workspace of about 8 N (4 nprobe + 3) bytes; synchronises
+ * `stream`.  A solve that stops at maxit is not an error (rep->solve_status
+ * is FGK_NOT_CONVERGED and the gradient uses its iterate).  Errors:
+ * FGK_ERR_INVALID (arguments, or pc built on another plan or for another
+ * sigma2), FGK_ERR_OOM, FGK_ERR_NONFINITE (y or B), FGK_ERR_BREAKDOWN, or any
+ * other error of the solve, the preconditioner or the gradient products. */
 int fgk_loglik_grad(fgk_handle h, fgk_precond pc, double sigma2, const double *y, const double *B, int nprobe,
                     double tol, int maxit, int mode, double *grad, fgk_grad_report *rep, fgk_stream_t stream);
 
