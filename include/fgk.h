@@ -43,6 +43,14 @@
  *    failure (nothing is thrown across the ABI); fgk_last_error() then gives
  *    a message for the calling thread.  FGK_NOT_CONVERGED (1) is a soft
  *    result of fgk_cg_solve.
+ *  - Error codes, where an entry lists none of its own: FGK_ERR_INVALID for
+ *    a NULL handle or required pointer or a count outside its documented
+ *    range (checked before any device work is enqueued); FGK_ERR_OOM when a
+ *    device allocation fails; FGK_ERR_CUDA when a CUDA call or a kernel
+ *    launch fails; FGK_ERR_TIMEOUT when a bounded device-side wait expires;
+ *    FGK_ERR_INTERNAL when a device-side consistency check fails.  The sizes
+ *    of caller buffers cannot be checked: they must match the documented
+ *    shapes.  An asynchronous call reports what it sees at enqueue time.
  */
 #ifndef FGK_H
 #define FGK_H
