@@ -98,9 +98,11 @@ def _prep(X, ell):
 
 
 def _two_nu(nu) -> int:
+    """2 nu for nu = 1/2 .. 9/2 (the closed forms of App. C.1); the
+    decomposition entries (O2) reject nu > 5/2 themselves."""
     t = int(round(2 * float(nu)))
-    if t not in (1, 3, 5):
-        raise ValueError(f"nu must be 1/2, 3/2 or 5/2, got {nu}")
+    if t not in (1, 3, 5, 7, 9) or abs(2 * float(nu) - t) > 1e-12:
+        raise ValueError(f"nu must be 1/2, 3/2, 5/2, 7/2 or 9/2, got {nu}")
     return t
 
 

@@ -9,7 +9,11 @@
  * Everything is FP64 and deliberately plain:
  *
  *  orc_kernel      closed-form half-integer Matérn kernels, eqs. matern_1_2,
- *                  matern_3_2, matern_5_2 (App. C.1), unit lengthscale.
+ *                  matern_3_2, matern_5_2, matern_7_2, matern_9_2 (App. C.1),
+ *                  unit lengthscale.  The definition-based entries below
+ *                  (O1, K, columns, cross-covariance, gradient products)
+ *                  take nu = 1/2 .. 9/2; the decompositions (O2 and its
+ *                  relatives) are printed for nu <= 5/2 and take only those.
  *  orc_mvm_brute   O1: the definition of the product, eqs. covariance_matrix
  *                  and Ky (Sec. 2), with the L1 kernel (eq. L1_kernel) or the
  *                  product kernel (eq. product_kernel), scaled as in
@@ -66,7 +70,7 @@
 #define ORC_PRODUCT 1
 
 /* ---------------------------------------------------------------------- */
-/* Closed-form kernels (App. C.1, eqs. matern_1_2, matern_3_2, matern_5_2)  */
+/* Closed-form kernels (App. C.1, eqs. matern_1_2 .. matern_9_2)           */
 /* ---------------------------------------------------------------------- */
 
 double orc_kernel(int two_nu, double u)
@@ -82,6 +86,14 @@ double orc_kernel(int two_nu, double u)
     case 5: {
         double s = sqrt(5.0) * u;
         return (1.0 + s + (5.0 / 3.0) * u * u) * exp(-s);
+    }
+    case 7: { /* eq. matern_7_2 */
+        double s = sqrt(7.0) * u;
+        return (1.0 + s + (14.0 / 5.0) * u * u + (7.0 * sqrt(7.0) / 15.0) * u * u * u) * exp(-s);
+    }
+    case 9: { /* eq. matern_9_2 */
+        double u2 = u * u;
+        return (1.0 + 3.0 * u + (27.0 / 7.0) * u2 + (18.0 / 7.0) * u2 * u + (27.0 / 35.0) * u2 * u2) * exp(-3.0 * u);
     }
     default:
         return NAN;
@@ -102,14 +114,23 @@ static double kern_pair(const double *ua, const double *ub, int d, int two_nu, i
     return p;
 }
 
+/* The definition (O1 and the dense forms) takes nu = 1/2 .. 9/2; the
+ * paper's decompositions (O2) are printed for nu <= 5/2 only, and those
+ * entry points check that separately (check_dc). */
 static int check_args(long N, int d, int two_nu, const double *ell, int kind)
 {
     if (N < 0 || d < 1 || d > 3) return -1;
-    if (two_nu != 1 && two_nu != 3 && two_nu != 5) return -1;
+    if (two_nu != 1 && two_nu != 3 && two_nu != 5 && two_nu != 7 && two_nu != 9) return -1;
     if (kind != ORC_L1 && kind != ORC_PRODUCT) return -1;
     for (int k = 0; k < d; ++k)
         if (!(ell[k] > 0.0) || !isfinite(ell[k])) return -1;
     return 0;
+}
+
+static int check_dc(long N, int d, int two_nu, const double *ell, int kind)
+{
+    if (two_nu != 1 && two_nu != 3 && two_nu != 5) return -1;
+    return check_args(N, d, two_nu, ell, kind);
 }
 
 static double *scaled_coords(const double *X, long N, int d, const double *ell)
@@ -220,7 +241,8 @@ int orc_kcross(const double *X, long N, const double *Zp, long M, int d, int two
 /* which = 0: -u k'(u), the derivative of k(|x|/l) with respect to log l
  *            (u = |x| / l): nu=1/2: u e^{-u}; nu=3/2: 3 u^2 e^{-sqrt3 u};
  *            nu=5/2: (5/3)(u^2 + sqrt5 u^3) e^{-sqrt5 u}.
- * which = 1: -k'(u): e^{-u}; 3 u e^{-sqrt3 u}; (5/3)(u + sqrt5 u^2) e^{-sqrt5 u}. */
+ * which = 1: -k'(u): e^{-u}; 3 u e^{-sqrt3 u}; (5/3)(u + sqrt5 u^2) e^{-sqrt5 u};
+ *            nu=7/2, 9/2 from eqs. dmatern72_dl, dmatern92_dl. */
 double orc_kernel_dlog(int two_nu, int which, double u)
 {
     u = fabs(u);
@@ -234,6 +256,13 @@ double orc_kernel_dlog(int two_nu, int which, double u)
         break;
     case 5:
         m = (5.0 / 3.0) * (u + sqrt(5.0) * u * u) * exp(-sqrt(5.0) * u);
+        break;
+    case 7:
+        m = ((7.0 / 5.0) * u + (7.0 * sqrt(7.0) / 5.0) * u * u + (49.0 / 15.0) * u * u * u) * exp(-sqrt(7.0) * u);
+        break;
+    case 9:
+        m = ((9.0 / 7.0) * u + (27.0 / 7.0) * u * u + (162.0 / 35.0) * u * u * u + (81.0 / 35.0) * u * u * u * u) *
+            exp(-3.0 * u);
         break;
     default:
         return NAN;
@@ -517,7 +546,7 @@ int orc_phi(int two_nu, int which, int p, double x, double *out)
 int orc_mvm_dc(const double *X, long N, int d, int two_nu, const double *ell, double s2, int kind,
                const double *V, int nrhs, double *Y)
 {
-    if (check_args(N, d, two_nu, ell, kind) || nrhs < 1) return -1;
+    if (check_dc(N, d, two_nu, ell, kind) || nrhs < 1) return -1;
     int P = (two_nu + 1) / 2;
     double a = sqrt((double)two_nu);
     int nw = 1;
@@ -619,7 +648,7 @@ int orc_mvm_dc(const double *X, long N, int d, int two_nu, const double *ell, do
 int orc_mvm_dc_cross(const double *X, long N, const double *Zp, long M, int d, int two_nu, const double *ell,
                      double s2, int kind, const double *V, int nrhs, double *Y)
 {
-    if (check_args(N, d, two_nu, ell, kind) || nrhs < 1 || M < 1) return -1;
+    if (check_dc(N, d, two_nu, ell, kind) || nrhs < 1 || M < 1) return -1;
     int P = (two_nu + 1) / 2;
     double a = sqrt((double)two_nu);
     int nw = 1;
@@ -713,7 +742,7 @@ int orc_mvm_dc_cross(const double *X, long N, const double *Zp, long M, int d, i
 int orc_mvm_dc_dlogell_l1(const double *X, long N, int d, int two_nu, const double *ell, double s2,
                           const double *V, int nrhs, double *Y)
 {
-    if (check_args(N, d, two_nu, ell, ORC_L1) || nrhs < 1) return -1;
+    if (check_dc(N, d, two_nu, ell, ORC_L1) || nrhs < 1) return -1;
     int P = (two_nu + 1) / 2;
     int nw = P + 1;
     double a = sqrt((double)two_nu);
@@ -801,7 +830,7 @@ static double binom_d(int n, int k)
 int orc_mvm_dc_dlogell_product(const double *X, long N, int d, int two_nu, const double *ell, double s2, int dim,
                                const double *V, int nrhs, double *Y)
 {
-    if (check_args(N, d, two_nu, ell, ORC_PRODUCT) || nrhs < 1 || dim < -1 || dim >= d) return -1;
+    if (check_dc(N, d, two_nu, ell, ORC_PRODUCT) || nrhs < 1 || dim < -1 || dim >= d) return -1;
     double a = sqrt((double)two_nu);
     double *U = scaled_coords(X, N, d, ell);
     item_t *it = (item_t *)malloc(sizeof(item_t) * (size_t)(2 * N + 1));

@@ -12,6 +12,7 @@ from scipy import special
 import workloads
 
 NUS = (0.5, 1.5, 2.5)
+NUS_ALL = NUS + (3.5, 4.5)  # eqs. dmatern72_dl, dmatern92_dl
 
 
 def bessel_k(nu, u):
@@ -24,7 +25,7 @@ def bessel_k(nu, u):
     return out
 
 
-@pytest.mark.parametrize("nu", NUS)
+@pytest.mark.parametrize("nu", NUS_ALL)
 def test_kernel_dlog_is_the_log_lengthscale_derivative_of_the_bessel_form(orc, nu):
     u = np.linspace(0.0, 6.0, 61)
     h = 1e-5
@@ -49,7 +50,7 @@ def _fd_product(orc, X, V, nu, ell, dim, kind, h=1e-5):
 
 
 @pytest.mark.parametrize("kind", [0, 1])
-@pytest.mark.parametrize("nu", NUS)
+@pytest.mark.parametrize("nu", NUS_ALL)
 @pytest.mark.parametrize("d", [1, 2, 3])
 def test_gradient_product_matches_finite_differences(orc, kind, nu, d):
     p = workloads.small(700 + d, 150, d, nu=nu, ell=[0.2, 0.35, 0.15][:d], nrhs=2)

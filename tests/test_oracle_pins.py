@@ -14,6 +14,9 @@ import workloads
 from oracle import structure
 
 NUS = (0.5, 1.5, 2.5)
+# the closed forms of eqs. matern_7_2 and matern_9_2: the definition-based
+# entries take them (the decompositions O2 and phi stop at 5/2)
+NUS_ALL = NUS + (3.5, 4.5)
 
 
 def matern_bessel(nu, u):
@@ -72,7 +75,7 @@ def relerr(a, b):
 # kernel values
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("nu", NUS)
+@pytest.mark.parametrize("nu", NUS_ALL)
 def test_kernel_closed_form_vs_bessel(orc, nu):
     u = np.concatenate([[0.0], np.geomspace(1e-4, 25.0, 200)])
     got = orc.kernel(nu, u)
@@ -81,13 +84,13 @@ def test_kernel_closed_form_vs_bessel(orc, nu):
     assert orc.kernel(nu, 0.0) == 1.0
 
 
-@pytest.mark.parametrize("nu", NUS)
+@pytest.mark.parametrize("nu", NUS_ALL)
 def test_kernel_closed_form_vs_general_formula(orc, nu):
     u = np.linspace(0, 12, 97)
     assert np.allclose(orc.kernel(nu, u), matern_general(int(nu - 0.5), u), rtol=1e-14, atol=1e-300)
 
 
-@pytest.mark.parametrize("nu", NUS)
+@pytest.mark.parametrize("nu", NUS_ALL)
 def test_kernel_closed_form_vs_state_space(orc, nu):
     tau = np.linspace(0, 4, 17)
     assert np.allclose(orc.kernel(nu, tau), matern_state_space(nu, tau), rtol=1e-10, atol=1e-14)
@@ -110,7 +113,7 @@ def test_phi_factorisation(orc, nu):
 # --------------------------------------------------------------------------
 
 @pytest.mark.parametrize("d", [1, 2, 3])
-@pytest.mark.parametrize("nu", NUS)
+@pytest.mark.parametrize("nu", NUS_ALL)
 @pytest.mark.parametrize("kind", [0, 1])
 def test_brute_vs_scipy_dense(orc, d, nu, kind):
     p = workloads.small(100 + d, 150, d, nu=nu, ell=[0.2, 0.35, 0.5][:d], nrhs=3, s2=1.7)
@@ -151,7 +154,7 @@ def test_ou_closed_form_inverse(orc):
     assert relerr(got, v[perm]) < 1e-11
 
 
-@pytest.mark.parametrize("nu", NUS)
+@pytest.mark.parametrize("nu", NUS_ALL)
 def test_kronecker_tensor_grid(orc, nu):
     """Product kernel on a tensor grid: K = K1 (x) K2 (eq. product_kernel);
     at nu = 1/2 the L1 kernel is the same matrix (eq. matern_l1_12)."""
@@ -171,7 +174,7 @@ def test_kronecker_tensor_grid(orc, nu):
 
 
 @pytest.mark.parametrize("kind", [0, 1])
-@pytest.mark.parametrize("nu", NUS)
+@pytest.mark.parametrize("nu", NUS_ALL)
 def test_lengthscale_limits(orc, kind, nu):
     rng = np.random.default_rng(6)
     X = rng.uniform(0, 1, (60, 2))
@@ -210,6 +213,37 @@ def test_positive_definiteness(orc, d, nu):
         assert lam_l1 > 0
     else:
         assert lam_l1 < 0
+
+
+@pytest.mark.parametrize("d", [2, 3])
+@pytest.mark.parametrize("nu", (3.5, 4.5))
+def test_positive_definiteness_of_the_smoother_kernels(orc, d, nu):
+    """Props. 3-4 at nu = 7/2, 9/2 (lengthscale 0.15, where the smallest
+    eigenvalue of the product kernel stays far above eigvalsh's rounding):
+    the product kernel is PD, the L1 kernel indefinite."""
+    rng = np.random.default_rng(20 + d)
+    X = rng.uniform(0, 1, (300, d))
+    ell = np.full(d, 0.15)
+    w = np.linalg.eigvalsh(orc.kmat(X, nu, ell, kind=1))
+    assert w[0] > 1e3 * X.shape[0] * np.finfo(float).eps * w[-1]
+    assert np.linalg.eigvalsh(orc.kmat(X, nu, ell, kind=0))[0] < -1e-2
+
+
+def test_decompositions_stop_at_five_halves(orc):
+    """The paper prints the decompositions (O2, the phi pairs) for nu <= 5/2
+    only: those entries refuse nu = 7/2, while the definition accepts it."""
+    p = workloads.small(5, 20, 2, nu=1.5)
+    assert np.isfinite(orc.mvm_brute(p.X, p.V, 3.5, p.ell, kind=1)).all()
+    for call in (lambda: orc.mvm_dc(p.X, p.V, 3.5, p.ell, kind=1),
+                 lambda: orc.mvm_dc(p.X, p.V, 4.5, p.ell, kind=0),
+                 lambda: orc.mvm_dc_dlogell_l1(p.X, p.V, 3.5, p.ell),
+                 lambda: orc.mvm_dc_dlogell_product(p.X, p.V, 3.5, p.ell),
+                 lambda: orc.mvm_dc_cross(p.X, p.X[:3], p.V, 3.5, p.ell),
+                 lambda: orc.phi(3.5, 1, 0, 0.5)):
+        with pytest.raises(ValueError):
+            call()
+    with pytest.raises(ValueError):
+        orc.kernel(3.0, 0.5)  # not a half-integer
 
 
 # --------------------------------------------------------------------------
