@@ -148,10 +148,14 @@ class Server:
 
     # ------------------------------------------------------------ client side
     def submit(self, req: Request) -> Future:
+        """Queue a request; its future resolves with a Result.  Raises
+        RuntimeError once the server is closed (nothing would run it)."""
         fut: Future = Future()
         need = self.estimator(req)
         req.arrival = time.perf_counter()
         with self._lock:
+            if self._stop:
+                raise RuntimeError("the server is closed")
             self.stats.submitted += 1
             if need > self.budget:
                 self.stats.rejected += 1
@@ -159,7 +163,8 @@ class Server:
                                       error=f"needs {need} bytes, more than the {self.budget}-byte budget"))
                 return fut
             self._futures[req.rid] = fut
-        self._pending.put((req, need))
+            # queued under the lock, so that it cannot land behind close()'s end marker
+            self._pending.put((req, need))
         return fut
 
     def cancel(self, rid: int) -> bool:
@@ -179,8 +184,11 @@ class Server:
         return True
 
     def close(self, wait: bool = True):
-        self._stop = True
-        self._pending.put(None)
+        """Stop taking requests; those already queued are still admitted and
+        run, then the dispatcher and the workers end."""
+        with self._lock:
+            self._stop = True
+            self._pending.put(None)
         self._dispatcher.join()
         self._pool.shutdown(wait=wait)
 

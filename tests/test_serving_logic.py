@@ -142,3 +142,47 @@ def test_an_out_of_memory_failure_releases_its_budget():
     assert res[0].error is not None and "allocation failed" in res[0].error
     assert all(r.error is None for r in res[1:])
     assert calls == [0, 1, 2, 3] and srv._used == 0
+
+
+def test_close_runs_what_was_queued_and_refuses_what_comes_after():
+    dev = FakeDevice(per_point=1e-5)
+    srv = serving.Server(budget_bytes=10**9, slots=2, executor=dev.run, estimator=dev.estimate)
+    reqs = [r for r in make_requests(8, seed=3) if r.rid != 5]
+    futs = [srv.submit(r) for r in reqs]
+    srv.close()
+    assert all(f.done() and f.result(timeout=0).error is None for f in futs)
+    try:
+        srv.submit(make_requests(1, seed=4)[0])
+        raise AssertionError("a closed server took a request")
+    except RuntimeError as e:
+        assert "closed" in str(e)
+
+
+def test_submissions_racing_close_either_run_or_are_refused():
+    """Four threads submit while the server closes: every request that was
+    taken resolves (none is left behind the end marker), the rest raise."""
+    dev = FakeDevice(per_point=0.0)
+    srv = serving.Server(budget_bytes=10**9, slots=3, executor=dev.run, estimator=dev.estimate)
+    reqs = [r for r in make_requests(400, seed=5) if r.rid != 5]
+    taken, refused, lock = [], [], threading.Lock()
+
+    def client(part):
+        for r in part:
+            try:
+                f = srv.submit(r)
+                with lock:
+                    taken.append(f)
+            except RuntimeError:
+                with lock:
+                    refused.append(r.rid)
+
+    threads = [threading.Thread(target=client, args=(reqs[i::4],)) for i in range(4)]
+    for t in threads:
+        t.start()
+    time.sleep(0.002)
+    srv.close()
+    for t in threads:
+        t.join(timeout=30)
+    assert len(taken) + len(refused) == len(reqs)
+    assert all(f.result(timeout=30).error is None for f in taken)
+    assert srv.stats.completed == len(taken)
