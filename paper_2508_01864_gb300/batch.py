@@ -93,8 +93,21 @@ class BatchEngine:
         self.precs = None
         self.precs_sigma2 = None
         self.stream = stream
-        self.handles = [fgk.fgk_build(torch.as_tensor(p.X, device="cuda"), p.nu, p.ell, kind=kind, stream=stream)
-                        for p in problems]
+        self.batch = None
+        self.handles = []
+        try:
+            for p in problems:
+                self.handles.append(fgk.fgk_build(torch.as_tensor(p.X, device="cuda"), p.nu, p.ell, kind=kind,
+                                                  stream=stream))
+            self._setup(problems, autotune, reps, stream)
+        except BaseException:
+            self.close()  # a failed build, tuning or batch: free what was made
+            raise
+
+    def _setup(self, problems, autotune, reps, stream):
+        import torch
+
+        fgk = self.fgk
         variants = [f"d{p.d}nu{p.nu}" for p in problems]
         rows = sum(p.N for p in problems)
         gpu = torch.cuda.get_device_name()
@@ -119,17 +132,19 @@ class BatchEngine:
         Y = torch.empty_like(V)
         for rpc in candidates(self.nrhs):
             b = fgk.fgk_batch_create(self.handles, self.nrhs, rpc, stream=stream)
-            fgk.fgk_batch_matvec_q(b, V, out=Y)
-            torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record()
-            for _ in range(reps):
+            try:
                 fgk.fgk_batch_matvec_q(b, V, out=Y)
-            e1.record()
-            torch.cuda.synchronize()
-            self.timings[str(rpc)] = e0.elapsed_time(e1) / reps
-            fgk.fgk_batch_destroy(b)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(reps):
+                    fgk.fgk_batch_matvec_q(b, V, out=Y)
+                e1.record()
+                torch.cuda.synchronize()
+                self.timings[str(rpc)] = e0.elapsed_time(e1) / reps
+            finally:
+                fgk.fgk_batch_destroy(b)
         best = pick({int(k): v for k, v in self.timings.items()})
         store_cache({self.key: {"rhs_per_cta": best, "timings_ms": self.timings}})
         return best
@@ -143,8 +158,16 @@ class BatchEngine:
         if self.precs is not None and self.precs_sigma2 == key:
             return self.precs
         self._free_precs()
-        self.precs = [self.fgk.fgk_precond_build(h, max(0, min(self.precond_rank, p.N // 8)), s2, stream=self.stream)
-                      for h, p, s2 in zip(self.handles, self.problems, key)]
+        precs = []
+        try:
+            for h, p, s2 in zip(self.handles, self.problems, key):
+                precs.append(self.fgk.fgk_precond_build(h, max(0, min(self.precond_rank, p.N // 8)), s2,
+                                                        stream=self.stream))
+        except BaseException:
+            for q in precs:
+                self.fgk.fgk_precond_destroy(q)
+            raise
+        self.precs = precs
         self.precs_sigma2 = key
         return self.precs
 
@@ -160,8 +183,10 @@ class BatchEngine:
         self.precs_sigma2 = None
 
     def close(self):
+        """Free the preconditioners, the batch and the plans (idempotent)."""
         self._free_precs()
         self.fgk.fgk_batch_destroy(self.batch)
+        self.batch = None
         for h in self.handles:
             self.fgk.fgk_destroy(h)
         self.handles = []
