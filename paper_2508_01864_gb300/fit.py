@@ -106,8 +106,10 @@ def fit_adam_sigma(X: np.ndarray, y: np.ndarray, nu: float, ell0, outscale2_0: f
 
     def with_plan(theta, sigma2, fn):
         h = fgk.fgk_build(X_dev, nu, ells(theta), outscale2=math.exp(theta[-1]), kind=kind)
-        pc = fgk.fgk_precond_build(h, precond_rank, sigma2) if precond_rank > 0 else None
+        pc = None
         try:
+            if precond_rank > 0:
+                pc = fgk.fgk_precond_build(h, precond_rank, sigma2)
             return fn(h, pc)
         finally:
             if pc is not None:
@@ -118,7 +120,7 @@ def fit_adam_sigma(X: np.ndarray, y: np.ndarray, nu: float, ell0, outscale2_0: f
         def run(h, pc):
             pr = probes(j)
             if pc is not None:  # the factor may have stopped below precond_rank: its first k rows
-                k = fgk.fgk_precond_info(pc)["rank"]
+                k = pc.rank
                 Er = np.ascontiguousarray(np.asarray(pr[0], dtype=np.float64)[:k])
                 B = fgk.fgk_precond_sample(pc, torch.as_tensor(Er, device="cuda"),
                                            torch.as_tensor(np.ascontiguousarray(pr[1], dtype=np.float64),
