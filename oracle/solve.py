@@ -45,6 +45,11 @@ TEST INFRASTRUCTURE ONLY.
                   20000 iterations (Sec. 3.1), each followed by the closed-form
                   update (sigma_j)^2 = y^T (K~ + I)^{-1} y / N with
                   K~ = K(varsigma_j / sigma_{j-1}, ell_j).
+* ``algorithm1_outer``  Algorithm 1 around its gradient descents: the OLS
+                  start, then GLS estimates of beta at the current
+                  parameters, their running average subtracted from y before
+                  the next descent, until successive GLS estimates differ by
+                  at most eps_beta.
 * ``posterior_mean``  E[f(z) | x, y] = k_z^T alpha + h(z)^T beta (eq. gp_mean,
                   with alpha = (K + sigma^2 I)^{-1}(y - H beta) as eq. gp_mean_2),
                   given the cross-covariance rows k_z^T.
@@ -315,3 +320,37 @@ def adam_sigma_steps(grad_fn, quad_fn, n_points: int, theta0, sigma2_0: float, n
         sigmas.append(sigma2)
         grads.append(g)
     return np.array(thetas), np.array(sigmas), np.array(grads)
+
+
+def algorithm1_outer(descend, beta_gls, H, y, theta0, sigma2_0: float, eps_beta: float, max_rep: int):
+    """Algorithm 1 with its gradient descents supplied: descend(y_c, theta,
+    sigma2) runs one descent (Adam steps on theta with the sigma update) on
+    the centred data y_c from (theta, sigma2) and returns the final
+    (theta, sigma2); beta_gls(theta, sigma2) returns
+    (H^T (K + sigma^2 I)^{-1} H)^{-1} H^T (K + sigma^2 I)^{-1} y for the
+    parameters theta (K = K(varsigma, ell)).  In the algorithm's order:
+    beta_OLS = (H^T H)^{-1} H^T y and a descent on y - H beta_OLS; then, for
+    i = 1, 2, ..., beta_GLS at the current parameters, beta_AVG = (i-1)/i
+    beta_AVG + beta_GLS / i, a descent on y - H beta_AVG, and the change
+    ||beta_GLS - beta_old|| (beta_old starting at beta_OLS), until the change
+    is at most eps_beta or max_rep repetitions.  Returns the final beta_GLS,
+    theta, sigma2 and per repetition (beta_GLS, beta_AVG, change, theta,
+    sigma2)."""
+    H = np.asarray(H, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    beta_ols = np.linalg.solve(H.T @ H, H.T @ y)
+    theta, sigma2 = descend(y - H @ beta_ols, np.array(theta0, dtype=np.float64), float(sigma2_0))
+    beta_avg = np.zeros(H.shape[1])
+    beta_old = beta_ols
+    reps = []
+    beta = beta_ols
+    for i in range(1, max_rep + 1):
+        beta = np.asarray(beta_gls(theta, sigma2), dtype=np.float64)
+        beta_avg = (i - 1) / i * beta_avg + beta / i
+        theta, sigma2 = descend(y - H @ beta_avg, theta, sigma2)
+        change = float(np.linalg.norm(beta - beta_old))
+        beta_old = beta
+        reps.append((beta.copy(), beta_avg.copy(), change, np.array(theta, dtype=np.float64), float(sigma2)))
+        if change <= eps_beta:
+            break
+    return beta, theta, sigma2, reps
