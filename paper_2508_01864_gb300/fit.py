@@ -139,3 +139,100 @@ def fit_adam_sigma(X: np.ndarray, y: np.ndarray, nu: float, ell0, outscale2_0: f
 
     return adam_sigma_loop(eval_grad, eval_quad, N, theta0, sigma2_0, max_steps, lr0=lr0, lr1=lr1, n_sched=n_sched,
                            grad_tol=grad_tol, param_tol=param_tol, b1=b1, b2=b2, eps=eps)
+
+
+# ------------------------------------------------------------ Algorithm 1, outer loop
+@dataclass
+class GlsFit:
+    beta: np.ndarray        # the last GLS estimate of the fixed effects
+    beta_avg: np.ndarray    # the running average subtracted from y before the last descent
+    theta: np.ndarray
+    sigma2: float
+    reps: int               # GLS repetitions
+    history: list = field(default_factory=list)
+
+
+def gls_outer_loop(descend, beta_gls, H, y, theta0, sigma2_0: float, eps_beta: float = 1e-3,
+                   max_rep: int = 20) -> GlsFit:
+    """Algorithm 1 around its gradient descents, on host values.
+    descend(y_c, theta, sigma2) runs one descent on the centred data y_c and
+    returns (theta, sigma2, info); beta_gls(theta, sigma2) returns the GLS
+    estimate (H^T A^{-1} H)^{-1} H^T A^{-1} y, A = K(theta) + sigma2 I.
+
+    The first descent runs on y - H beta_OLS (beta_OLS from the normal
+    equations of H, an L x L system).  Each repetition r = 1, 2, ... takes
+    beta_GLS at the current parameters, folds it into the running mean of
+    all GLS estimates so far, descends on y minus H times that mean, and
+    stops once beta_GLS has moved by at most eps_beta since the previous
+    repetition (the first is compared with beta_OLS), or after max_rep."""
+    H = np.asarray(H, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64).reshape(-1)
+    prev = np.linalg.solve(H.T @ H, H.T @ y)
+    theta, sigma2, info = descend(y - H @ prev, np.array(theta0, dtype=np.float64), float(sigma2_0))
+    fit = GlsFit(beta=prev.copy(), beta_avg=np.zeros(H.shape[1]), theta=np.asarray(theta, dtype=np.float64),
+                 sigma2=float(sigma2), reps=0)
+    fit.history.append({"beta_ols": prev.copy(), "theta": fit.theta.copy(), "sigma2": fit.sigma2, **info})
+    total = np.zeros(H.shape[1])
+    for r in range(1, max_rep + 1):
+        b = np.asarray(beta_gls(fit.theta, fit.sigma2), dtype=np.float64).reshape(-1)
+        total += b
+        mean = total / r
+        theta, sigma2, info = descend(y - H @ mean, fit.theta, fit.sigma2)
+        moved = float(np.linalg.norm(b - prev))
+        prev = b
+        fit.beta, fit.beta_avg, fit.reps = b.copy(), mean, r
+        fit.theta, fit.sigma2 = np.asarray(theta, dtype=np.float64), float(sigma2)
+        fit.history.append({"beta_gls": b.copy(), "beta_avg": mean.copy(), "change": moved,
+                            "theta": fit.theta.copy(), "sigma2": fit.sigma2, **info})
+        if moved <= eps_beta:
+            break
+    return fit
+
+
+def fit_gls(X: np.ndarray, y: np.ndarray, H: np.ndarray, nu: float, ell0, outscale2_0: float, sigma2_0: float,
+            probes, steps_per_descent: int, eps_beta: float = 1e-3, max_rep: int = 20, kind: str = "product",
+            precond_rank: int = 0, tol: float = 1e-8, mode: str = "mixed", **adam) -> GlsFit:
+    """Algorithm 1 on the GPU: ``gls_outer_loop`` whose descents are
+    ``fit_adam_sigma`` runs (each restarting Adam and its rate schedule, at
+    most ``steps_per_descent`` steps; ``adam`` passes lr0, lr1, n_sched,
+    grad_tol, param_tol, b1, b2, eps) and whose GLS estimates come from
+    ``fgk_cg_solve`` with the covariates H (N x L, e.g. [1, x_1 .. x_d]) at
+    the current parameters.  theta is (log ell_1 .. log ell_d, log
+    varsigma^2) for the product kernel with d > 1, else (log ell, log
+    varsigma^2) with the lengthscales scaled together."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    d = X.shape[1]
+    ell0 = np.broadcast_to(np.asarray(ell0, dtype=np.float64), (d,)).copy()
+    per_dim = kind == "product" and d > 1
+    ratio = ell0 / ell0[0]
+    theta0 = np.concatenate([np.log(ell0) if per_dim else [math.log(ell0[0])], [math.log(outscale2_0)]])
+
+    def params(theta):
+        ell = np.exp(theta[:d]) if per_dim else math.exp(theta[0]) * ratio
+        return ell, math.exp(theta[-1])
+
+    def descend(yc, theta, sigma2):
+        ell, s2 = params(theta)
+        st = fit_adam_sigma(X, yc, nu, ell, s2, sigma2, probes, steps_per_descent, kind=kind,
+                            precond_rank=precond_rank, tol=tol, mode=mode, **adam)
+        return st.theta, st.sigma2, {"steps": st.step}
+
+    X_dev = torch.as_tensor(X, device="cuda")
+    y_dev = torch.as_tensor(np.ascontiguousarray(y, dtype=np.float64).reshape(-1), device="cuda")
+    H_dev = torch.as_tensor(np.ascontiguousarray(H, dtype=np.float64), device="cuda")
+
+    def beta_gls(theta, sigma2):
+        ell, s2 = params(theta)
+        h = fgk.fgk_build(X_dev, nu, ell, outscale2=s2, kind=kind)
+        pc = None
+        try:
+            if precond_rank > 0:
+                pc = fgk.fgk_precond_build(h, precond_rank, sigma2)
+            _, beta, _, _ = fgk.fgk_cg_solve(h, y_dev, sigma2, H=H_dev, tol=tol, mode=mode, precond=pc)
+            return beta.cpu().numpy().reshape(-1)
+        finally:
+            if pc is not None:
+                fgk.fgk_precond_destroy(pc)
+            fgk.fgk_destroy(h)
+
+    return gls_outer_loop(descend, beta_gls, H, y, theta0, sigma2_0, eps_beta, max_rep)
