@@ -557,6 +557,25 @@ def main():
     total_ms = max_over_ranks(sum(times), ws)
     value = job_rate(ws, args.steps, total_ms)
 
+    # ---------------- one more step, outside the timed region, split into its phases
+    # (each library call synchronises the stream, so events between the calls bound them)
+    try:
+        flush_l2(flush)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        h = fgk.fgk_build(X, p.nu, p.ell, kind="product")
+        ev[1].record(stream)
+        pc = fgk.fgk_precond_build(h, rank_pc, p.sigma2) if rank_pc > 0 else None
+        ev[2].record(stream)
+        _, _, info_ph, _ = fgk.fgk_cg_solve(h, y, p.sigma2, tol=TOL, maxit=100000, mode=args.mode, precond=pc)
+        ev[3].record(stream)
+        ev[3].synchronize()
+        release(h, pc)
+        phases = {"build_ms": ev[0].elapsed_time(ev[1]), "precond_ms": ev[1].elapsed_time(ev[2]),
+                  "solve_ms": ev[2].elapsed_time(ev[3]), "iterations": info_ph["iterations"]}
+    except Exception as e:  # a breakdown is context: never lose the benchmark line for it
+        phases = {"error": f"{type(e).__name__}: {e}"}
+
     # ---------------- end to end through the ABI with host buffers
     Xh = torch.as_tensor(p.X).pin_memory()
     yh = torch.as_tensor(y_host).pin_memory()
@@ -686,6 +705,7 @@ def main():
                "true_resid": infos[-1]["max_true_resid"]},
         "precond": pc_info,
         "unpreconditioned_step_ms": plain_ms,
+        "phases_ms": phases,
     }
     print(json.dumps(line), flush=True)
     if ws > 1:
