@@ -23,6 +23,7 @@ CASES = [  # seed, N, d, nu, ell, kind
     (12, 400, 2, 1.5, [0.1, 0.3], oracle.PRODUCT),
     (13, 250, 3, 2.5, [0.3, 0.2, 0.4], oracle.PRODUCT),
     (14, 350, 2, 2.5, [0.25, 0.15], oracle.L1),
+    (15, 300, 2, 3.5, [0.2, 0.3], oracle.PRODUCT),
 ]
 ROWS = [0, 7, 42, 123, 249]
 DISTANCES = [0.0, 0.1, 0.5, 1.0, 2.5]
@@ -31,7 +32,7 @@ DISTANCES = [0.0, 0.1, 0.5, 1.0, 2.5]
 def lines():
     out = ["# kernel <2nu> <u> <k(u)>: closed forms of App. C.1 at u = |x| / ell",
            "# mvm <seed> <N> <d> <nu> <ell...> <kind> <row> <Y[row]>: O1, s2 = 1, V = the seeded N(0,1) column"]
-    for nu in (0.5, 1.5, 2.5):
+    for nu in (0.5, 1.5, 2.5, 3.5, 4.5):
         for u in DISTANCES:
             out.append(f"kernel {int(2 * nu)} {u!r} {float(oracle.kernel(nu, u))!r}")
     for seed, N, d, nu, ell, kind in CASES:

@@ -19,14 +19,14 @@ def _records(tag):
 
 def test_kernel_values(orc):
     recs = _records("kernel")
-    assert len(recs) == 15
+    assert len(recs) == 25
     for _, two_nu, u, k in recs:
         assert float(orc.kernel(int(two_nu) / 2, float(u))) == pytest.approx(float(k), rel=1e-15, abs=0)
 
 
 def test_product_values(orc):
     recs = _records("mvm")
-    assert len(recs) == 20
+    assert len(recs) == 25
     for rec in recs:
         seed, N, d, nu = int(rec[1]), int(rec[2]), int(rec[3]), float(rec[4])
         ell = [float(e) for e in rec[5:5 + d]]
