@@ -81,3 +81,17 @@ def test_paper_dc_timing_reports_one_full_product():
     assert set(r) >= {"mvm_s", "mvm_nrhs_per_s", "solves_per_s", "threads"} and r["threads"] == 1
     assert r["solves_per_s"] == pytest.approx(1.0 / (100 * r["mvm_s"]))
     assert r["mvm_nrhs_per_s"] == pytest.approx(3000 / r["mvm_s"])
+
+
+def test_cpu_baseline_reports_the_contract_fields():
+    sys.path.insert(0, ROOT)
+    import bench
+    import workloads
+
+    p = workloads.c2(N=3000)
+    cb = bench.cpu_baseline(p, 50, 0.2)
+    assert cb["kind"] == "oracle" and cb["unit"] == bench.UNIT and cb["cores"] >= 1
+    assert cb["value"] > 0 and "output rows" in cb["sample"]
+    # the rate is one full product per iteration: value = mvm rate / (N x iterations)
+    assert cb["value"] == pytest.approx(cb["mvm_nrhs_per_s"] / (p.N * 50), rel=1e-12)
+    assert cb["paper_dc"]["threads"] == 1 and cb["paper_dc"]["solves_per_s"] > 0
