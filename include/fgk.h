@@ -279,7 +279,9 @@ int fgk_precond_destroy(fgk_precond pc);
 
 /* fgk_cg_solve preconditioned by pc (Algorithm 2 with s_P = P^{-1}): every
  * argument as fgk_cg_solve; pc == NULL is fgk_cg_solve.  pc must come from
- * the same plan and be built for the same sigma2 (else FGK_ERR_INVALID).  The
+ * the same plan and be built for the same sigma2 (else FGK_ERR_INVALID), and
+ * the columns solved together, nrhs plus the L fixed-effect columns, must
+ * number at most 64 (else FGK_ERR_INVALID, before any device work).  The
  * stop test stays on the unpreconditioned true residual ||b - A x|| / ||b||;
  * in mixed mode the FP32 iterations run until the recursive residual has
  * dropped by FGK_MIXED_DELTA (default 1e-3 here), then the FP64 true
