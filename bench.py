@@ -44,7 +44,6 @@ WORKLOAD = ("d=2 N=200000 nu=3/2 ell=(0.1,0.3) x~U[0,1]^2 product kernel; "
 # the kernels as built (a kernel missing here has no capture of its current
 # version)
 TRAFFIC_BYTES = {
-    "k_level_scan<float,P=2,NOFF=1,product,OUT>": 44934656,
     "k_pc_ltr (t = L^T r)": 201692416 + 367104,
     "k_pc_apply (z = r/s2 - L c)": 201672192 + 504320,
 }
@@ -339,8 +338,14 @@ def run_pcg_probe(args, local):
 
 
 def run_mvm_only(args, local):
-    """W + K FP32 products in the internal order on the d=2 workload with
-    --mvm-only points (for profiling the scan kernels at sizes above L2)."""
+    """W + K products in the internal order on the d=2 workload drawn with
+    --mvm-only points and --mvm-nrhs columns (structure above L2 from
+    N ~ 1M; used for the roofline of the whole product and for the ncu
+    captures of the scan kernels): FP32 and FP64 products, the output pass
+    timed alone by the library's events, and the whole FP32 product against
+    the measured HBM peak with the algorithmic bytes
+    B_alg = E (12 + 8 nrhs) + 8 N nrhs (structure read once, each entry's
+    operand read and its contribution written once, V read and Y written)."""
     import torch
 
     import workloads
@@ -348,27 +353,52 @@ def run_mvm_only(args, local):
 
     torch.cuda.set_device(local)
     p = workloads.c2(N=args.mvm_only)
+    nrhs = args.mvm_nrhs
     X = torch.as_tensor(p.X, device="cuda")
     h = fgk.fgk_build(X, p.nu, p.ell, kind="product")
-    Vq = torch.randn(p.N, 1, dtype=torch.float32, device="cuda")
-    Yq = torch.empty_like(Vq)
-    for _ in range(args.warmup):
-        fgk.fgk_matvec_q(h, Vq, "f32", out=Yq)
-    torch.cuda.synchronize()
-    ts = []
-    for _ in range(args.steps):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        fgk.fgk_matvec_q(h, Vq, "f32", out=Yq)
-        e1.record()
-        e1.synchronize()
-        ts.append(e0.elapsed_time(e1))
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    out = {"metric": "exact Matérn MVM N·nrhs/sec", "unit": "N·nrhs/s", "N": p.N, "nrhs": nrhs,
+           "workload": f"d=2 N={p.N} nu=3/2 ell=(0.1,0.3) x~U[0,1]^2 product kernel, nrhs={nrhs}"}
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")  # 256 MiB, above L2
+    for prec, dt in (("f32", torch.float32), ("f64", torch.float64)):
+        Vq = torch.randn(p.N, nrhs, dtype=dt, device="cuda", generator=gen)
+        Yq = torch.empty_like(Vq)
+        for _ in range(args.warmup):
+            fgk.fgk_matvec_q(h, Vq, prec, out=Yq)
+        torch.cuda.synchronize()
+        if prec == "f32":
+            fgk.fgk_scan_timing(1)
+        ts = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fgk.fgk_matvec_q(h, Vq, prec, out=Yq)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = statistics.median(ts)
+        out[f"{prec}_ms"] = ms
+        out[f"{prec}_value"] = p.N * nrhs / (ms * 1e-3)
+        if prec == "f32":
+            scan_ms, scan_n = fgk.fgk_scan_timing(0)
+            out["scan_out_f32_ms"] = scan_ms / max(scan_n, 1)
     info = fgk.fgk_get_info(h)
     fgk.fgk_destroy(h)
-    ms = statistics.median(ts)
-    print(json.dumps({"metric": "exact Matérn MVM N·nrhs/sec (FP32 scans)", "value": p.N / (ms * 1e-3),
-                      "unit": "N·nrhs/s", "ms": ms, "N": p.N, "levels": info["n_levels"]}), flush=True)
+    pk, src = peaks()
+    E = info["n_levels"] * p.N
+    b_alg = E * (12 + 8 * nrhs) + 8 * p.N * nrhs
+    b_out = E * (12 + 8 * nrhs)
+    gbs = b_alg / (out["f32_ms"] * 1e-3) / 1e9
+    gbs_out = b_out / (out["scan_out_f32_ms"] * 1e-3) / 1e9
+    out.update({"value": out["f32_value"], "levels": info["n_levels"], "entries": E, "l2_flushed": True,
+                "roofline": {"bound": "hbm", "kernel": "whole FP32 product (all launches)", "achieved": gbs,
+                             "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": gbs / pk["hbm_gbs"],
+                             "algorithmic_bytes": b_alg, "peak_source": src},
+                "scan_out_roofline": {"bound": "hbm", "achieved": gbs_out, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                                      "frac": gbs_out / pk["hbm_gbs"], "algorithmic_bytes": b_out}})
+    print(json.dumps(out), flush=True)
     return 0
 
 
@@ -469,6 +499,7 @@ def main():
     ap.add_argument("--pcg-maxit", type=int, default=40)
     ap.add_argument("--likelihood", action="store_true",
                     help="time the gradient products and the log-determinant on the d=2 workload")
+    ap.add_argument("--mvm-nrhs", type=int, default=1, help="columns of the --mvm-only products")
     ap.add_argument("--mvm-only", type=int, default=0,
                     help="time only the FP32 product on the d=2 workload drawn with this many points")
     args = ap.parse_args()

@@ -6,8 +6,9 @@
  *
  *     Y = K V,   K_ij = s2 * K(x_i - x_j),                  (Sec. 2, eq. Ky)
  *
- * for the half-integer Matérn kernels nu = 1/2, 3/2, 5/2 (App. C.1,
- * eqs. matern_1_2, matern_3_2, matern_5_2) combined over d <= 3 coordinates
+ * for the half-integer Matérn kernels nu = 1/2, 3/2, 5/2, 7/2, 9/2 (App. C.1,
+ * eqs. matern_1_2 ... matern_9_2, eq. matern_explicit) combined over d <= 3
+ * coordinates
  * either through the L1 norm, K(u) = k(sum_k |u_k| / ell_k) (eq. L1_kernel),
  * or as a product, K(u) = prod_k k(|u_k| / ell_k) (eq. product_kernel), with
  * one lengthscale per dimension (eq. scaled_kernel read per dimension).  It
@@ -97,7 +98,11 @@ int fgk_set_allocator(fgk_alloc_fn alloc, fgk_free_fn free_fn, void *ctx);
  *   X          device, N x d FP64 row-major; finite (else FGK_ERR_NONFINITE).
  *   N          1 <= N <= 2^30.
  *   d          1, 2 or 3.
- *   two_nu     2 nu: 1, 3 or 5.
+ *   two_nu     2 nu: 1, 3, 5, 7 or 9 (9 only with d <= 2).  nu = 7/2 and
+ *              9/2 (eqs. matern_7_2, matern_9_2) run the scans with four and
+ *              five moments and run-time coefficients; the batch calls take
+ *              nu <= 5/2, the lengthscale-derivative products nu <= 7/2
+ *              (nu <= 5/2 at d = 3).
  *   ell        host, d lengthscales, finite and > 0.
  *   outscale2  varsigma^2 > 0 (1 when the kernel has no outputscale).
  *   kind       FGK_L1 or FGK_PRODUCT (identical when two_nu == 1 or d == 1).
@@ -149,16 +154,22 @@ int fgk_matvec_q(fgk_handle h, const void *Vq, int nrhs, void *Yq, int precision
  * memory during the call (their device memory is planned before they start:
  * a serving loop whose budget is already handed out, an engine whose memory
  * plan is fixed, a latency-critical path that cannot afford an allocator
- * call).  The paper has no counterpart; this is an interface choice.
+ * call or an out-of-memory error in the middle of its work).  The paper has
+ * no counterpart; this is an interface choice.
  * It calls no cudaMalloc, cudaFree or allocating library routine: the
- * scratch of the level scans lives in one 16 MiB __device__ array compiled
- * into the library, which every GPU that loads the library holds until the
- * process exits.  The first call on a device looks up that array's device
- * address (make it before any stream capture).  All calls on a device share
- * the array: calls whose work overlaps on the GPU race and must be ordered
- * by the caller.  A product needing more scratch than the array holds
- * (the need grows with nrhs and with the number of tiles in segments longer
- * than a tile) returns FGK_ERR_INVALID without launching anything.
+ * scratch of the product (one output row per level, N x nrhs values each,
+ * and the tile aggregates of segments longer than a tile) lives in one
+ * 64 MiB __device__ array compiled into the library.  The CUDA runtime
+ * loads code and such arrays lazily, so the first fgk_build on each device
+ * reserves the array there (and looks up its device address), and every
+ * fgk_build has the runtime load the product kernels of its plan: build
+ * plans while allocation is still allowed.  The array is then held until
+ * the process exits.  All calls on a device share the array and it keeps
+ * the last call's contents: calls whose work overlaps on the GPU race and
+ * must be ordered by the caller.  FGK_ERR_INVALID, without launching
+ * anything: a product needing more scratch than the array holds (the need
+ * grows with nrhs and with the number of levels), or a call made while
+ * another device than the plan's is current.
  * Arguments, layout and precision as fgk_matvec_q; the handle comes from an
  * earlier fgk_build.  Asynchronous. */
 int fgk_matvec_q_noalloc(fgk_handle h, const void *Vq, int nrhs, void *Yq, int precision, fgk_stream_t stream);

@@ -93,7 +93,8 @@ def cg(apply_A, B, tol: float, maxit: int, apply_Pinv=None):
     return (X[:, 0] if vec else X), iters
 
 
-def pivoted_cholesky(column, diag, k: int, forced=None, tie_rtol: float = 0.0, eps: float = 1e-12):
+def pivoted_cholesky(column, diag, k: int, forced=None, tie_rtol: float = 0.0, eps: float = 1e-12,
+                     tie_atol: float = 0.0):
     """Rank-k pivoted Cholesky of the SPD matrix with diagonal ``diag`` and
     columns ``column(i)``.  Returns (L (N x r), pivots (r,), residual
     diagonal) with r <= k: the factorisation stops early once the largest
@@ -104,8 +105,10 @@ def pivoted_cholesky(column, diag, k: int, forced=None, tie_rtol: float = 0.0, e
 
     ``forced``: follow these pivots instead of choosing them, after checking
     that each is a largest remaining diagonal entry within a relative
-    ``tie_rtol`` (for comparing with a computation whose rounding may break
-    near-ties the other way)."""
+    ``tie_rtol`` or an absolute ``tie_atol`` (for comparing with a computation
+    whose rounding may break near-ties the other way: a residual diagonal
+    s2 - sum_m l_m^2 carries an absolute rounding error on the scale of the
+    diagonal s2, so once the residuals are small the absolute term decides)."""
     d = np.array(diag, dtype=np.float64, copy=True)
     N = d.size
     floor = eps * float(d.max()) if N else 0.0
@@ -117,7 +120,7 @@ def pivoted_cholesky(column, diag, k: int, forced=None, tie_rtol: float = 0.0, e
             if m >= len(forced):
                 break
             i = int(forced[m])
-            if not d[i] >= top * (1.0 - tie_rtol):
+            if not d[i] >= top * (1.0 - tie_rtol) - tie_atol:
                 raise ValueError(f"step {m}: pivot {i} has residual {d[i]!r}, the largest is {top!r}")
         else:
             i = int(np.argmax(d))

@@ -244,7 +244,8 @@ size_t plan_bytes_estimate(int64_t N, int d, int two_nu, int kind, int nrhs) {
     b += (size_t)N * (4 * d + 4 + 8 * d + 8 * d);                         // perms, rank, xq, xraw
     const int64_t ntiles = (N + kTile - 1) / kTile;
     b += (size_t)nlev * ntiles * sizeof(WorkItem) + (size_t)ntiles * 8;  // work lists
-    b += (size_t)2 * nlev * ntiles * 2 * nrhs * 4 * 29 * 8;             // scan scratch (upper bound)
+    b += (size_t)2 * nlev * ntiles * 2 * nrhs * 4 * 29 * 8;             // scan aggregates (upper bound)
+    b += (size_t)nlev * N * nrhs * 8;                                      // level rows of an FP64 product
     b += (size_t)N * nrhs * 8 * 10 + (size_t)N * 8 * 12;                 // solver vectors
     (void)two_nu;
     (void)kind;
@@ -274,7 +275,8 @@ int fgk_set_allocator(fgk_alloc_fn alloc, fgk_free_fn free_fn, void *ctx) {
 const char *fgk_last_error(void) { return g_err; }
 
 size_t fgk_bytes_estimate(int64_t N, int d, int two_nu, int kind, int nrhs) {
-    if (N < 1 || N > (int64_t(1) << 30) || d < 1 || d > 3 || (two_nu != 1 && two_nu != 3 && two_nu != 5) ||
+    if (N < 1 || N > (int64_t(1) << 30) || d < 1 || d > 3 || two_nu < 1 || two_nu > 9 || two_nu % 2 == 0 ||
+        (two_nu == 9 && d == 3) ||
         (kind != FGK_L1 && kind != FGK_PRODUCT) || nrhs < 1)
         return 0;
     return plan_bytes_estimate(N, d, two_nu, kind, nrhs);
@@ -296,8 +298,12 @@ int fgk_build(const double *X, int64_t N, int d, int two_nu, const double *ell, 
         set_error("fgk_build: d = %d is not 1, 2 or 3", d);
         return FGK_ERR_INVALID;
     }
-    if (two_nu != 1 && two_nu != 3 && two_nu != 5) {
-        set_error("fgk_build: two_nu = %d is not 1, 3 or 5", two_nu);
+    if (two_nu < 1 || two_nu > 9 || two_nu % 2 == 0) {
+        set_error("fgk_build: two_nu = %d is not 1, 3, 5, 7 or 9", two_nu);
+        return FGK_ERR_INVALID;
+    }
+    if (two_nu == 9 && d == 3) {
+        set_error("fgk_build: nu = 9/2 is built for d <= 2 (its five-moment scans at d = 3 are not built)");
         return FGK_ERR_INVALID;
     }
     if (kind != FGK_L1 && kind != FGK_PRODUCT) {
@@ -328,11 +334,20 @@ int fgk_build(const double *X, int64_t N, int d, int two_nu, const double *ell, 
     p->L = ceil_log2_i64(N);
     p->nlev = d == 1 ? 1 : (d == 2 ? p->L : p->L * (p->L + 1) / 2);
     p->ldN = (N + 63) / 64 * 64;
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete p;
+        set_error("fgk_build: cudaGetDevice failed");
+        return FGK_ERR_CUDA;
+    }
     int rc = plan_alloc(p, (void **)&p->dev_err, 16);
     if (rc == FGK_OK) rc = cudaMemsetAsync(p->dev_err, 0, 16, p->stream) == cudaSuccess ? FGK_OK : FGK_ERR_CUDA;
     if (rc == FGK_OK) rc = build_sort(p, X);
     if (rc == FGK_OK) rc = build_levels(p);
     if (rc == FGK_OK) rc = build_worklists(p);
+    if (rc == FGK_OK) rc = scan_preload_f32(p);
+    if (rc == FGK_OK) rc = scan_preload_f64(p);
+    if (rc == FGK_OK) rc = noalloc_setup();
     if (rc == FGK_OK) rc = check_dev_error(p, "fgk_build");
     if (rc != FGK_OK) {
         plan_release(p);

@@ -94,13 +94,15 @@ __global__ void __launch_bounds__(kScanThreads, FGK_SCAN_MINB) k_batch_scan(Batc
     A.V = B.V + pr.voff * B.nrhs;
     A.nrhs = B.nrhs;
     A.Y = B.Y + pr.voff * B.nrhs;
+    A.rows = nullptr;  // outputs added to Y atomically
+    A.row_stride = 0;
     A.agg = (MODE == SCAN_AGG ? B.agg : B.carry) + pr.agg_off;
     A.s2 = pr.s2;
     A.err = B.err;
     A.gate = nullptr;
     switch (pr.variant) {
 #define FGK_BCASE(PP, NO, KK) \
-    case variant_key(PP, NO, KK): scan_tile<float, PP, NO, KK, MODE>(A, bi.w, bi.r0, bi.r1); break;
+    case variant_key(PP, NO, KK): scan_tile<float, PP, NO, KK, MODE, false, false>(A, bi.w, bi.r0, bi.r1); break;
         FGK_BCASE(1, 0, FGK_L1)
         FGK_BCASE(2, 0, FGK_L1)
         FGK_BCASE(3, 0, FGK_L1)
@@ -480,8 +482,9 @@ int fgk_batch_create(const fgk_handle *handles, int n, int nrhs, int rhs_per_cta
         return FGK_ERR_INVALID;
     }
     for (int i = 0; i < n; ++i)
-        if (!handles[i] || handles[i]->d > 2) {
-            set_error("fgk_batch_create: handle %d is NULL or has d > 2 (batches take d <= 2)", i);
+        if (!handles[i] || handles[i]->d > 2 || handles[i]->P > 3) {
+            set_error("fgk_batch_create: handle %d is NULL, has d > 2 or nu > 5/2 (batches take d <= 2, "
+                      "nu <= 5/2)", i);
             return FGK_ERR_INVALID;
         }
     fgk_batch_s *b = new fgk_batch_s();

@@ -17,24 +17,31 @@
 
 namespace fgk {
 
+// P4 moments (2..5) with coefficients cf; kind as given (the product kernel
+// with nu = 1/2 is not reduced to L1 here: a derivative factor differs per
+// dimension)
 template <class R>
 int run_levels_gen_dispatch(Plan *p, int P4, int kind, const R *Vq, int nrhs, R *Yq, R *ws, cudaStream_t s,
-                            const double (*cf)[4]) {
+                            const double (*cf)[kMaxCoef], const int *gate, bool init_diag, bool preload) {
     const int NOFF = p->d - 1;
     const int kk = NOFF == 0 ? FGK_L1 : kind;
     const int key = (P4 * 3 + NOFF) * 2 + kk;
     switch (key) {
-#define FGK_GCASE(PP, NO, KK) \
-    case (PP * 3 + NO) * 2 + KK: return run_levels<R, PP, NO, KK, true>(p, Vq, nrhs, Yq, ws, s, nullptr, cf);
+#define FGK_GCASE(PP, NO, KK)     \
+    case (PP * 3 + NO) * 2 + KK:  \
+        return run_levels<R, PP, NO, KK, true>(p, Vq, nrhs, Yq, ws, s, gate, init_diag, cf, preload);
         FGK_GCASE(2, 0, FGK_L1)
         FGK_GCASE(3, 0, FGK_L1)
         FGK_GCASE(4, 0, FGK_L1)
+        FGK_GCASE(5, 0, FGK_L1)
         FGK_GCASE(2, 1, FGK_L1)
         FGK_GCASE(3, 1, FGK_L1)
         FGK_GCASE(4, 1, FGK_L1)
+        FGK_GCASE(5, 1, FGK_L1)
         FGK_GCASE(2, 1, FGK_PRODUCT)
         FGK_GCASE(3, 1, FGK_PRODUCT)
         FGK_GCASE(4, 1, FGK_PRODUCT)
+        FGK_GCASE(5, 1, FGK_PRODUCT)
         FGK_GCASE(2, 2, FGK_L1)
         FGK_GCASE(3, 2, FGK_L1)
         FGK_GCASE(4, 2, FGK_L1)
@@ -45,7 +52,7 @@ int run_levels_gen_dispatch(Plan *p, int P4, int kind, const R *Vq, int nrhs, R 
     default:
         break;
     }
-    set_error("no gradient scan kernel for %d moments, d=%d, kind=%d", P4, p->d, kind);
+    set_error("no generic-coefficient scan kernel for %d moments, d=%d, kind=%d", P4, p->d, kind);
     return FGK_ERR_INTERNAL;
 }
 
@@ -54,17 +61,24 @@ int run_levels_gen_dispatch(Plan *p, int P4, int kind, const R *Vq, int nrhs, R 
 // the L1 kernel's common scale).  Y_q is accumulated: the caller zeroes it.
 template <class R>
 int dlogell_q(Plan *p, int dim, const R *Vq, int nrhs, R *Yq, cudaStream_t s) {
-    static const double c[3][4] = {{1, 0, 0, 0}, {1, 1, 0, 0}, {1, 1, 1.0 / 3.0, 0}};
-    static const double h[3][4] = {{0, 1, 0, 0}, {0, 0, 1, 0}, {0, 0, 1.0 / 3.0, 1.0 / 3.0}};
-    const int iv = (p->P - 1);
-    double cf[kMaxD][4] = {};
+    // c of the kernel (P moments) and h_q = c_{q-1} - q c_q (P + 1 moments)
+    const int P = p->P;
+    if (P + 1 > 5 || (P + 1 == 5 && p->d == 3)) {
+        set_error("fgk_matvec_dlogell: the lengthscale derivative is built for nu <= 7/2 at d <= 2 and nu <= 5/2 "
+                  "at d = 3 (it needs %d moments here)", P + 1);
+        return FGK_ERR_INVALID;
+    }
+    double c[kMaxCoef], h[kMaxCoef];
+    matern_coef(P, c);
+    for (int q = 0; q < kMaxCoef; ++q) h[q] = (q > 0 ? c[q - 1] : 0.0) - q * c[q];
+    double cf[kMaxD][kMaxCoef] = {};
     const bool radial = p->d == 1 || dim < 0;
     for (int k = 0; k < kMaxD; ++k)
-        for (int q = 0; q < 4; ++q) cf[k][q] = (radial ? (k == 0) : (k == dim)) ? h[iv][q] : c[iv][q];
+        for (int q = 0; q < kMaxCoef; ++q) cf[k][q] = (radial ? (k == 0) : (k == dim)) ? h[q] : c[q];
     if (p->nlev == 0) return FGK_OK;
-    FGK_TRY(ensure_ws(p, scan_ws_elems_gen<R>(p, nrhs) * sizeof(R), s));
-    return run_levels_gen_dispatch<R>(p, p->P + 1, radial ? FGK_L1 : FGK_PRODUCT, Vq, nrhs, Yq, (R *)p->ws.p, s,
-                                      cf);
+    const int kind = radial ? FGK_L1 : FGK_PRODUCT;
+    FGK_TRY(ensure_ws(p, scan_ws_elems_for(p, nrhs, P + 1, kind) * sizeof(R), s));
+    return run_levels_gen_dispatch<R>(p, P + 1, kind, Vq, nrhs, Yq, (R *)p->ws.p, s, cf, nullptr, false);
 }
 
 }  // namespace fgk

@@ -119,6 +119,7 @@ struct Plan {
     int nlev = 0;
     int64_t ldN = 0;  // stride between levels: N rounded up to a multiple of 64 entries
     cudaStream_t stream = nullptr;
+    int device = 0;   // the CUDA device the plan was built on (current during fgk_build)
 
     // sort results (device)
     int32_t *perm[kMaxD] = {nullptr, nullptr, nullptr};  // position in x'_k order -> point
@@ -174,6 +175,17 @@ int mvm_q_f64(Plan *p, const double *Vq, int nrhs, double *Yq, cudaStream_t s, c
 int mvm_q_f32(Plan *p, const float *Vq, int nrhs, float *Yq, cudaStream_t s, const int *gate,
               bool init_diag = true);
 size_t mvm_ws_bytes(const Plan *p, int nrhs, bool f64);
+// the same products (init_diag, no gate) on caller-supplied scratch of
+// mvm_ws_bytes(p, nrhs, f64) bytes; allocate nothing
+int mvm_q_f64_ws(Plan *p, const double *Vq, int nrhs, double *Yq, double *ws, cudaStream_t s);
+int mvm_q_f32_ws(Plan *p, const float *Vq, int nrhs, float *Yq, float *ws, cudaStream_t s);
+// the runtime loads kernels lazily, on first launch; these make it load the
+// plan's product kernels at build time instead
+int scan_preload_f32(Plan *p);
+int scan_preload_f64(Plan *p);
+// the fixed scratch of fgk_matvec_q_noalloc on the current device: looked up
+// (and the array reserved) once per device, at the first fgk_build there
+int noalloc_setup();
 // Y_q += s2 (dK/d log ell_dim) V_q in q order (fgk_dscan.cuh); dim in [0, d)
 // for the product kernel, -1 for the radial (L1 or d = 1) derivative
 int dlogell_q_f64(Plan *p, int dim, const double *Vq, int nrhs, double *Yq, cudaStream_t s);

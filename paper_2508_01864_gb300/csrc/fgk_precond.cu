@@ -93,11 +93,16 @@ __device__ __forceinline__ PivPart block_best(PivPart v) {
     return r;
 }
 
-// unit-lengthscale Matern polynomial part: k(r) = poly(r) e^{-r}
+// unit-lengthscale Matern polynomial part: k(r) = poly(r) e^{-r} with
+// poly(r) = sum_{p<P} c_p r^p, c = (1), (1, 1), (1, 1, 1/3), (1, 1, 2/5, 1/15),
+// (1, 1, 3/7, 2/21, 1/105) for nu = 1/2 .. 9/2 (eqs. matern_1_2 .. matern_9_2
+// in scaled units; eq. matern_explicit), by Horner's rule
 __device__ __forceinline__ double matern_poly(int two_nu, double r) {
     if (two_nu == 1) return 1.0;
     if (two_nu == 3) return 1.0 + r;
-    return 1.0 + r + r * r * (1.0 / 3.0);
+    if (two_nu == 5) return 1.0 + r * (1.0 + r * (1.0 / 3.0));
+    if (two_nu == 7) return 1.0 + r * (1.0 + r * (2.0 / 5.0 + r * (1.0 / 15.0)));
+    return 1.0 + r * (1.0 + r * (3.0 / 7.0 + r * (2.0 / 21.0 + r * (1.0 / 105.0))));
 }
 
 struct KernArgs {

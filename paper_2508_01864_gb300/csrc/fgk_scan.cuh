@@ -44,6 +44,8 @@
 // of thousands of them would turn that into a visible error in the distance.
 #pragma once
 
+#include <algorithm>
+#include <cmath>
 #include <type_traits>
 
 #include "fgk_internal.cuh"
@@ -51,6 +53,10 @@
 namespace fgk {
 
 constexpr int ipow_c(int b, int e) { return e == 0 ? 1 : b * ipow_c(b, e - 1); }
+
+// readout coefficients per factor of the generic-coefficient scans: up to six
+// moments (the nu = 9/2 kernel has five, its lengthscale derivative six)
+constexpr int kMaxCoef = 6;
 
 enum { SCAN_AGG = 0, SCAN_OUT = 1 };
 
@@ -78,7 +84,7 @@ struct Traits {
     static constexpr int GM = GP * P;                  // moments per channel in a pass
     static constexpr int SM = CP * GM;                 // moments per pass and direction
     static constexpr int AG = 1 + SM;                  // aggregate: T, moments
-    static constexpr int NDIR = SM <= 12 ? 2 : 1;      // directions walked together
+    static constexpr int NDIR = SM <= 8 ? 2 : 1;       // directions walked together
     static constexpr int NPT = NPASS * NGP;            // passes per right-hand side
     static constexpr int NWC = NOFF == 0 ? 1 : (NA == 1 ? P : GP);  // per-entry coefficients of a pass
 };
@@ -95,7 +101,12 @@ struct ScanArgs {
     const WorkItem *items;
     const R *V;  // q order, N x nrhs, in the scan precision
     int nrhs;
-    R *Y;      // q order, N x nrhs, accumulated atomically
+    R *Y;      // q order, N x nrhs: accumulated atomically when rows == NULL
+    // per-level output rows (q order, N x nrhs each, level l at l * row_stride):
+    // every (level, point, column) slot is written exactly once per product by
+    // a plain store, and k_level_sum adds the levels in a fixed order
+    R *rows;
+    int64_t row_stride;
     R *agg;    // SCAN_AGG: tile aggregates out; SCAN_OUT: carries in
     R s2;
     int *err;
@@ -104,7 +115,7 @@ struct ScanArgs {
     // kernel factor sum_p cf[k][p] r^p e^{-r} of split dimension k (offset
     // block k), cf[d-1] for the sweep dimension, cf[0] for the L1 kernel's
     // radial factor
-    R cf[kMaxD][4];
+    R cf[kMaxD][kMaxCoef];
 };
 
 template <class R>
@@ -113,6 +124,10 @@ template <>
 __device__ __forceinline__ float exp_neg<float>(float x) { return __expf(-x); }
 template <>
 __device__ __forceinline__ double exp_neg<double>(double x) { return exp(-x); }
+
+__host__ __device__ constexpr int binom_c(int n, int k) {
+    return (k < 0 || k > n) ? 0 : (k == 0 || k == n) ? 1 : binom_c(n - 1, k - 1) + binom_c(n - 1, k);
+}
 
 // one group of P moments stepped by (T, E = e^{-T})
 template <class R, int P>
@@ -130,14 +145,21 @@ __device__ __forceinline__ void step_group(R *m, R T, R E) {
         m[1] = E * m[1] + ET * m[0];
         m[0] *= E;
     } else {
-        static_assert(P == 4, "moment orders up to 3");
-        const R ET = E == R(0) ? R(0) : E * T;
-        const R ET2 = E == R(0) ? R(0) : ET * T;
-        const R ET3 = E == R(0) ? R(0) : ET2 * T;
-        m[3] = E * m[3] + R(3) * ET * m[2] + R(3) * ET2 * m[1] + ET3 * m[0];
-        m[2] = E * m[2] + R(2) * ET * m[1] + ET2 * m[0];
-        m[1] = E * m[1] + ET * m[0];
-        m[0] *= E;
+        // any order: m_q <- sum_{t<=q} C(q,t) E T^{q-t} m_t, from the highest q
+        // down so that every m_t read is still the old one; the powers
+        // E T^k are formed by repeated multiplication (each stays bounded by
+        // max_T T^k e^{-T}, so nothing overflows before it is scaled)
+        R ETk[P];
+        ETk[0] = E;
+#pragma unroll
+        for (int k = 1; k < P; ++k) ETk[k] = E == R(0) ? R(0) : ETk[k - 1] * T;
+#pragma unroll
+        for (int q = P - 1; q >= 0; --q) {
+            R acc = ETk[0] * m[q];
+#pragma unroll
+            for (int t = 0; t < q; ++t) acc += R(binom_c(q, t)) * ETk[q - t] * m[t];
+            m[q] = acc;
+        }
     }
 }
 
@@ -187,12 +209,12 @@ __device__ __forceinline__ R ucoef_sel(R o, R eo, int e) {
 
 // Generic readout coefficients (GEN scans: the lengthscale derivatives, whose
 // factors have runtime coefficients and one order more).
-__host__ __device__ constexpr int binom_c(int n, int k) {
-    return (k < 0 || k > n) ? 0 : (k == 0 || k == n) ? 1 : binom_c(n - 1, k - 1) + binom_c(n - 1, k);
-}
 template <class R>
-__device__ __forceinline__ R pow_rt(R o, int e) {  // o^e, 0 <= e <= 3
-    return e == 0 ? R(1) : (e == 1 ? o : (e == 2 ? o * o : o * o * o));
+__device__ __forceinline__ R pow_rt(R o, int e) {  // o^e, 0 <= e < kMaxCoef
+    R r = R(1);
+#pragma unroll
+    for (int k = 1; k < kMaxCoef; ++k) r = k <= e ? r * o : r;
+    return r;
 }
 // u_j(o) = e^{-o} sum_{p>=j} cf[p] C(p,j) o^{p-j}, all j < P
 template <class R, int P>
@@ -238,7 +260,7 @@ __device__ __forceinline__ R csum_gen(const R *m, const R *cf) {
 //   readout   u: L1   u[q] = u_q(s); product u[g] = prod_k u_{a_k}(o_k).
 // d = 1 needs neither (v is added to M[0], the query reads sum_q c_q M[q]).
 template <class R, int P, int NOFF, int KIND, bool GEN = false>
-__device__ __forceinline__ void pass_coef(int a0, const R *o, const R *eo, R *w, R *u, const R (*cf)[4] = nullptr) {
+__device__ __forceinline__ void pass_coef(int a0, const R *o, const R *eo, R *w, R *u, const R (*cf)[kMaxCoef] = nullptr) {
     using Tr = Traits<P, NOFF, KIND>;
     if constexpr (NOFF == 0) {
         w[0] = R(1);
@@ -300,7 +322,7 @@ __device__ __forceinline__ void add_pass(R *M, R v, const R *w) {
 }
 
 template <class R, int P, int NOFF, int KIND, bool GEN = false>
-__device__ __forceinline__ R read_pass(const R *M, const R *u, const R (*cf)[4] = nullptr) {
+__device__ __forceinline__ R read_pass(const R *M, const R *u, const R (*cf)[kMaxCoef] = nullptr) {
     using Tr = Traits<P, NOFF, KIND>;
     if constexpr (NOFF == 0) {
         if constexpr (GEN)
@@ -352,7 +374,9 @@ __device__ __forceinline__ void set_identity(R *x) {
 // carried-in moments, reading queries and inserting sources.  Segments
 // longer than a tile receive their carry from the aggregate pass
 // (MODE == SCAN_AGG writes each tile's totals; k_carry_scan scans them).
-template <class R, int P, int NOFF, int KIND, int MODE, bool GEN = false>
+// ROWS: the output pass stores into the level rows (A.rows); otherwise it adds
+// into Y atomically (the batched products).
+template <class R, int P, int NOFF, int KIND, int MODE, bool GEN = false, bool ROWS = true>
 __device__ __forceinline__ void scan_tile(const ScanArgs<R> &A, const WorkItem wi, int r0, int r1) {
     using Tr = Traits<P, NOFF, KIND>;
     constexpr int GM = Tr::GM, CP = Tr::CP, SMM = Tr::SM, AG = Tr::AG, NCH = Tr::NCH;
@@ -379,11 +403,18 @@ __device__ __forceinline__ void scan_tile(const ScanArgs<R> &A, const WorkItem w
     // ---- this thread's entries (the level stride keeps 8-entry groups aligned)
     uint32_t q[EPT];
     R g[EPT], eg[EPT], o[NO][EPT], eo[NO][EPT];
+    R vpre[EPT];  // the first column's operands, gathered as soon as q is known (0 on padding:
+                  // the fold inserts padding entries as zero-weight sources)
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) vpre[i] = R(0);
     if (nvalid > 0) {
         const uint4 *qp = reinterpret_cast<const uint4 *>(A.lv_q + lo + p0);
         const uint4 qa = qp[0], qb = qp[1];
         q[0] = qa.x; q[1] = qa.y; q[2] = qa.z; q[3] = qa.w;
         q[4] = qb.x; q[5] = qb.y; q[6] = qb.z; q[7] = qb.w;
+#pragma unroll
+        for (int i = 0; i < EPT; ++i)
+            vpre[i] = (i < nvalid && r0 < r1) ? A.V[(size_t)(q[i] & 0x3fffffffu) * A.nrhs + r0] : R(0);
         if constexpr (sizeof(R) == 4) {
             const float4 *gp = reinterpret_cast<const float4 *>(A.lv_dl + lo + p0);
             const float4 ga = gp[0], gb = gp[1];
@@ -442,14 +473,13 @@ __device__ __forceinline__ void scan_tile(const ScanArgs<R> &A, const WorkItem w
     const int GW = G < 32 ? G : 32;
     const bool is_long = S > kTile;
 
-    for (int r = r0; r < r1; ++r) {
-        R v[EPT], out[EPT];
+    R v[EPT];  // this column's operands; the next column's are gathered at the end of the loop body
 #pragma unroll
-        for (int i = 0; i < EPT; ++i) {
-            out[i] = R(0);
-            const size_t idx = (size_t)(q[i] & 0x3fffffffu) * A.nrhs + r;
-            v[i] = i < nvalid ? A.V[idx] : R(0);
-        }
+    for (int i = 0; i < EPT; ++i) v[i] = vpre[i];
+    for (int r = r0; r < r1; ++r) {
+        R out[EPT];
+#pragma unroll
+        for (int i = 0; i < EPT; ++i) out[i] = R(0);
 #pragma unroll 1
         for (int pq = 0; pq < NPT; ++pq) {
             const int pp = pq / NGP;       // channel pair
@@ -652,8 +682,19 @@ __device__ __forceinline__ void scan_tile(const ScanArgs<R> &A, const WorkItem w
         }
         if constexpr (MODE == SCAN_OUT) {
 #pragma unroll
+            for (int i = 0; i < EPT; ++i) {
+                if (i >= nvalid) continue;
+                const size_t t = (size_t)(q[i] & 0x3fffffffu) * A.nrhs + r;
+                if constexpr (ROWS)
+                    A.rows[(size_t)wi.level * A.row_stride + t] = A.s2 * out[i];
+                else
+                    atomicAdd(A.Y + t, A.s2 * out[i]);
+            }
+        }
+        if (r + 1 < r1) {
+#pragma unroll
             for (int i = 0; i < EPT; ++i)
-                if (i < nvalid) atomicAdd(A.Y + (size_t)(q[i] & 0x3fffffffu) * A.nrhs + r, A.s2 * out[i]);
+                v[i] = i < nvalid ? A.V[(size_t)(q[i] & 0x3fffffffu) * A.nrhs + r + 1] : R(0);
         }
     }
 }
@@ -731,13 +772,73 @@ __global__ void k_diag_init(const R *__restrict__ V, int64_t n, R s2, R *__restr
     Y[i] = s2 * V[i];
 }
 
+// S5: Y = base + sum over levels of the level rows, the levels added in
+// ascending order (the same order on every call, so a product is
+// reproducible bit for bit); base = s2 V (the self-pairs, which no level
+// holds) when V is given, else the Y already there.
+template <class R>
+__global__ void k_level_sum(const R *__restrict__ rows, int nlev, int64_t n, const R *__restrict__ V, R s2,
+                            R *__restrict__ Y, const int *__restrict__ gate) {
+    if (gate && *gate == 0) return;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        R acc = V ? s2 * V[t] : Y[t];
+#pragma unroll 4
+        for (int l = 0; l < nlev; ++l) acc += rows[(size_t)l * n + t];
+        Y[t] = acc;
+    }
+}
+
+// Scratch of one product, in elements of the scan precision: the level rows
+// (n_levels x N x nrhs), then the tile aggregates and the tile carries of
+// the long segments (n_long tiles x 2 directions x nrhs x passes x aggregate
+// size each).  The pass count and aggregate size follow Traits.
+inline size_t scan_pass_elems(int P, int noff, int kind) {
+    int na = 1;
+    if (kind == FGK_PRODUCT && noff > 0 && P > 1)
+        for (int k = 0; k < noff; ++k) na *= P;
+    const size_t cp = noff == 0 ? 1 : 2;
+    const size_t npass = noff == 2 ? 2 : 1;
+    const size_t gp = (na > 1 && cp * na * P > 12) ? 1 : na;
+    const size_t ngp = na / gp;
+    const size_t ag = 1 + cp * gp * P;
+    return npass * ngp * ag;
+}
+inline size_t scan_rows_elems(const Plan *p, int nrhs) {
+    return ((size_t)p->nlev * p->N * nrhs + 63) / 64 * 64;
+}
+inline size_t scan_ws_elems_for(const Plan *p, int nrhs, int P, int kind) {
+    const size_t slot = (size_t)2 * nrhs * scan_pass_elems(P, p->d - 1, kind);
+    return scan_rows_elems(p, nrhs) + 2 * (size_t)p->n_long * slot + 64;
+}
+
+// One product's level scans: aggregate pass and carry scan over the long
+// segments, output pass over every tile (each writing its level row), then
+// the fixed-order level sum into Yq.  init_diag: Yq = s2 Vq + levels; else
+// Yq += levels.
+// preload: only make the runtime load the kernels this product would launch
+// (their attributes are queried), so that a later product loads nothing.
 template <class R, int P, int NOFF, int KIND, bool GEN = false>
-int run_levels(Plan *p, const R *Vq, int nrhs, R *Yq, R *ws, cudaStream_t s, const int *gate,
-               const double (*cf)[4] = nullptr) {
+int run_levels(Plan *p, const R *Vq, int nrhs, R *Yq, R *ws, cudaStream_t s, const int *gate, bool init_diag,
+               const double (*cf)[kMaxCoef] = nullptr, bool preload = false) {
     using Tr = Traits<P, NOFF, KIND>;
+    if (preload) {
+        // Also make sure the context's per-thread stack holds the largest
+        // frame (spilled registers) of these kernels: a launch whose frame
+        // exceeds cudaLimitStackSize (1 KiB by default) is not safe.
+        cudaFuncAttributes fa[4];
+        FGK_CUDA(cudaFuncGetAttributes(&fa[0], k_level_scan<R, P, NOFF, KIND, SCAN_AGG, GEN>));
+        FGK_CUDA(cudaFuncGetAttributes(&fa[1], k_level_scan<R, P, NOFF, KIND, SCAN_OUT, GEN>));
+        FGK_CUDA(cudaFuncGetAttributes(&fa[2], k_carry_scan<R, P, NOFF, KIND>));
+        FGK_CUDA(cudaFuncGetAttributes(&fa[3], k_level_sum<R>));
+        size_t need = 0, have = 0;
+        for (const auto &a : fa) need = std::max(need, a.localSizeBytes);
+        FGK_CUDA(cudaDeviceGetLimit(&have, cudaLimitStackSize));
+        if (need > have) FGK_CUDA(cudaDeviceSetLimit(cudaLimitStackSize, (need + 255) / 256 * 256));
+        return FGK_OK;
+    }
     ScanArgs<R> A;
     for (int k = 0; k < kMaxD; ++k)
-        for (int q = 0; q < 4; ++q) A.cf[k][q] = cf ? (R)cf[k][q] : R(0);
+        for (int q = 0; q < kMaxCoef; ++q) A.cf[k][q] = cf ? (R)cf[k][q] : R(0);
     A.lv_q = p->lv_q;
     A.lv_dl = std::is_same<R, float>::value ? (const R *)p->lv_dl32 : (const R *)p->lv_dl64;
     A.lv_off = std::is_same<R, float>::value ? (const R *)p->lv_off32 : (const R *)p->lv_off64;
@@ -747,12 +848,14 @@ int run_levels(Plan *p, const R *Vq, int nrhs, R *Yq, R *ws, cudaStream_t s, con
     A.V = Vq;
     A.nrhs = nrhs;
     A.Y = Yq;
+    A.rows = ws;
+    A.row_stride = p->N * nrhs;
     A.s2 = (R)p->s2;
     A.err = p->dev_err;
     A.gate = gate;
     const size_t per_slot = (size_t)2 * nrhs * Tr::NPT * Tr::AG;
-    R *agg = ws;
-    R *carry = ws + (size_t)p->n_long * per_slot;
+    R *agg = ws + scan_rows_elems(p, nrhs);
+    R *carry = agg + (size_t)p->n_long * per_slot;
     if (p->n_long > 0) {
         A.items = p->long_items;
         A.agg = agg;
@@ -781,26 +884,57 @@ int run_levels(Plan *p, const R *Vq, int nrhs, R *Yq, R *ws, cudaStream_t s, con
             scan_timing_record(e0, e1);
         }
     }
+    const int64_t n = p->N * nrhs;
+    const unsigned blocks = (unsigned)std::min<int64_t>(grid_for(n, 256), 152 * 8);
+    k_level_sum<R><<<blocks, 256, 0, s>>>(ws, p->nlev, n, init_diag ? Vq : nullptr, (R)p->s2, Yq, gate);
+    FGK_LAUNCH_CHECK();
     return FGK_OK;
 }
 
+// the kernel's own scans: nu = 1/2 or d = 1 make both kinds the same kernel
+inline int scan_kind(const Plan *p) { return (p->P == 1 || p->d == 1) ? FGK_L1 : p->kind; }
+
 template <class R>
 size_t scan_ws_elems(const Plan *p, int nrhs) {
-    // generous: the most passes x aggregate size (product, P = 3, d = 3:
-    // 2 channel pairs x 9 offset groups x (1 + 2 x 3))
-    return (size_t)2 * p->n_long * 2 * nrhs * 128 + 64;
+    return scan_ws_elems_for(p, nrhs, p->P, scan_kind(p));
 }
 
-// dispatch over (P, d-1, kind); nu = 1/2 or d = 1 make both kinds the same kernel
+// Matérn coefficients c_p of k(r) = sum_p c_p r^p e^{-r} in scaled units
+// (eqs. matern_1_2 ... matern_9_2; eq. matern_explicit gives them for any
+// half-integer nu: c_p = (P-1)! (2P-2-p)! 2^p / ((2P-2)! p! (P-1-p)!))
+inline void matern_coef(int P, double *c) {
+    for (int q = 0; q < kMaxCoef; ++q) c[q] = 0.0;
+    auto fact = [](int n) {
+        double f = 1.0;
+        for (int k = 2; k <= n; ++k) f *= k;
+        return f;
+    };
+    for (int q = 0; q < P; ++q)
+        c[q] = fact(P - 1) * fact(2 * P - 2 - q) * std::ldexp(1.0, q) / (fact(2 * P - 2) * fact(q) * fact(P - 1 - q));
+}
+
+// dispatch over (P, d-1, kind).  nu <= 5/2: the scans with the coefficients
+// compiled in; nu = 7/2, 9/2: the generic-coefficient scans (fgk_dscan.cuh)
+// with c in every factor.
 template <class R>
-int run_levels_dispatch(Plan *p, const R *Vq, int nrhs, R *Yq, R *ws, cudaStream_t s,
-                        const int *gate) {
+int run_levels_gen_dispatch(Plan *p, int P4, int kind, const R *Vq, int nrhs, R *Yq, R *ws, cudaStream_t s,
+                            const double (*cf)[kMaxCoef], const int *gate, bool init_diag, bool preload = false);
+
+template <class R>
+int run_levels_dispatch(Plan *p, const R *Vq, int nrhs, R *Yq, R *ws, cudaStream_t s, const int *gate,
+                        bool init_diag, bool preload = false) {
     const int P = p->P, NOFF = p->d - 1;
-    const int kind = (P == 1 || NOFF == 0) ? FGK_L1 : p->kind;
+    const int kind = scan_kind(p);
+    if (P > 3) {
+        double cf[kMaxD][kMaxCoef];
+        for (int k = 0; k < kMaxD; ++k) matern_coef(P, cf[k]);
+        return run_levels_gen_dispatch<R>(p, P, kind, Vq, nrhs, Yq, ws, s, cf, gate, init_diag, preload);
+    }
     const int key = (P * 3 + NOFF) * 2 + kind;
     switch (key) {
-#define FGK_CASE(PP, NO, KK) \
-    case (PP * 3 + NO) * 2 + KK: return run_levels<R, PP, NO, KK>(p, Vq, nrhs, Yq, ws, s, gate);
+#define FGK_CASE(PP, NO, KK)          \
+    case (PP * 3 + NO) * 2 + KK:      \
+        return run_levels<R, PP, NO, KK>(p, Vq, nrhs, Yq, ws, s, gate, init_diag, nullptr, preload);
         FGK_CASE(1, 0, FGK_L1)
         FGK_CASE(2, 0, FGK_L1)
         FGK_CASE(3, 0, FGK_L1)
@@ -821,22 +955,5 @@ int run_levels_dispatch(Plan *p, const R *Vq, int nrhs, R *Yq, R *ws, cudaStream
     set_error("no scan kernel for P=%d d=%d kind=%d", P, p->d, p->kind);
     return FGK_ERR_INTERNAL;
 }
-
-// Scratch of the generic-coefficient scans: the most passes x aggregate size
-// among them (product, 4 moments, d = 3: 2 channel pairs x 16 offset groups x
-// (1 + 2 x 4)).
-template <class R>
-size_t scan_ws_elems_gen(const Plan *p, int nrhs) {
-    return (size_t)2 * p->n_long * 2 * nrhs * 288 + 64;
-}
-
-// Generic-coefficient scans (the lengthscale derivatives): moments P4 (one
-// more than the kernel's P), readout coefficients cf (see ScanArgs::cf),
-// kind as given (the product kernel with nu = 1/2 is not reduced to L1 here:
-// a derivative factor differs per dimension).  Instantiated in the
-// translation units of the gradient products.
-template <class R>
-int run_levels_gen_dispatch(Plan *p, int P4, int kind, const R *Vq, int nrhs, R *Yq, R *ws, cudaStream_t s,
-                            const double (*cf)[4]);
 
 }  // namespace fgk

@@ -5,14 +5,19 @@
 namespace fgk {
 
 int mvm_q_f32(Plan *p, const float *Vq, int nrhs, float *Yq, cudaStream_t s, const int *gate, bool init_diag) {
-    const int64_t n = p->N * nrhs;
-    if (init_diag) {
-        k_diag_init<float><<<grid_for(n, 256), 256, 0, s>>>(Vq, n, (float)p->s2, Yq, gate);
-        FGK_LAUNCH_CHECK();
-    }
-    if (p->nlev == 0) return FGK_OK;
     FGK_TRY(ensure_ws(p, scan_ws_elems<float>(p, nrhs) * sizeof(float), s));
-    return run_levels_dispatch<float>(p, Vq, nrhs, Yq, (float *)p->ws.p, s, gate);
+    return run_levels_dispatch<float>(p, Vq, nrhs, Yq, (float *)p->ws.p, s, gate, init_diag);
+}
+
+// the same product with the caller's scratch (scan_ws_elems elements)
+int mvm_q_f32_ws(Plan *p, const float *Vq, int nrhs, float *Yq, float *ws, cudaStream_t s) {
+    return run_levels_dispatch<float>(p, Vq, nrhs, Yq, ws, s, nullptr, true);
+}
+
+// load the kernels of this plan's float product now (at build), so that no
+// later product has the runtime load code
+int scan_preload_f32(Plan *p) {
+    return run_levels_dispatch<float>(p, nullptr, 1, nullptr, nullptr, nullptr, nullptr, true, true);
 }
 
 }  // namespace fgk

@@ -179,8 +179,8 @@ def _stream(stream) -> int:
 
 def _two_nu(nu) -> int:
     t = int(round(2 * float(nu)))
-    if t not in (1, 3, 5):
-        raise ValueError(f"nu must be 1/2, 3/2 or 5/2, got {nu}")
+    if t not in (1, 3, 5, 7, 9):
+        raise ValueError(f"nu must be 1/2, 3/2, 5/2, 7/2 or 9/2, got {nu}")
     return t
 
 

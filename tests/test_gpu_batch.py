@@ -69,7 +69,7 @@ def test_batch_cg_meets_tolerance(fgk_mod, orc):
             a = a.cpu().numpy()
             Ka = orc.mvm_brute(p.X, a, p.nu, p.ell, kind=1)
             res = np.linalg.norm(p.V - Ka - s * a, axis=0) / np.linalg.norm(p.V, axis=0)
-            assert (res <= 1.05e-8).all(), res
+            assert (res <= 1e-8).all(), res
             assert info["max_true_resid"] <= 1e-8 and info["iterations"] > 0
     finally:
         fgk.fgk_batch_destroy(b)
@@ -133,7 +133,7 @@ def test_batch_pcg_meets_tolerance_in_fewer_iterations(fgk_mod, orc):
             a = a.cpu().numpy()
             Ka = orc.mvm_brute(p.X, a, p.nu, p.ell, kind=1)
             res = np.linalg.norm(p.V - Ka - s * a, axis=0) / np.linalg.norm(p.V, axis=0)
-            assert (res <= 1.05e-8).all(), res
+            assert (res <= 1e-8).all(), res
             assert info["iterations"] < i0["iterations"], (info, i0)
         # a second solve with the same sigma^2 reuses the preconditioners
         first = eng.precs

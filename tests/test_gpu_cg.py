@@ -18,7 +18,8 @@ def dense_A(orc, p, kind, sigma2):
     return K + sigma2 * np.eye(p.N)
 
 
-@pytest.mark.parametrize("d,nu", [(1, 0.5), (1, 2.5), (2, 1.5), (2, 2.5), (3, 1.5)])
+@pytest.mark.parametrize("d,nu", [(1, 0.5), (1, 2.5), (2, 1.5), (2, 2.5), (3, 1.5), (1, 3.5), (2, 3.5), (2, 4.5),
+                                  (3, 3.5)])
 @pytest.mark.parametrize("mode", ["f64", "mixed"])
 def test_cg_matches_dense_solve(fgk_mod, orc, d, nu, mode):
     fgk = fgk_mod

@@ -33,6 +33,10 @@ def _dims(d, kind):
 # at d = 1 the product kernel is the L1 kernel: above N = 100 only the L1 case runs
 PARITY = [(N, d, pattern, nrhs, nu, kind) for kind in ("l1", "product") for nu in (0.5, 1.5, 2.5)
           for (N, d, pattern, nrhs) in CASES if not (kind == "product" and d == 1 and N > 100)]
+# nu = 7/2 (eq. dmatern72_dl): the scans with five moments
+PARITY += [(N, d, pattern, nrhs, 3.5, kind) for kind in ("l1", "product")
+           for (N, d, pattern, nrhs) in [(1000, 1, "dups", 2), (2500, 2, "uniform", 1), (600, 2, "wide", 1)]
+           if not (kind == "product" and d == 1)]
 
 
 @pytest.mark.parametrize("N,d,pattern,nrhs,nu,kind", PARITY)
@@ -91,3 +95,15 @@ def test_gradient_product_d2_workload_sampled(fgk_mod, orc, prec, tol):
             ref = orc.mvm_dlogell_brute(p.X, V, p.nu, p.ell, dim=dim, kind=1, rows=rows)
             err = np.linalg.norm(y[rows] - ref) / np.linalg.norm(ref)
             assert err <= tol, (dim, err)
+
+
+@pytest.mark.parametrize("d,nu", [(2, 4.5), (3, 3.5)])
+def test_gradient_beyond_the_built_orders_is_rejected(fgk_mod, d, nu):
+    """The nu = 9/2 derivative needs six moments and the nu = 7/2 one at d = 3
+    five moments with two split dimensions: neither is built, both refused."""
+    fgk = fgk_mod
+    p = workloads.small(78, 500, d, nu=nu, ell=[0.2, 0.3, 0.25][:d])
+    with fgk.fgk_build(to_dev(p.X), p.nu, p.ell, kind="product") as h:
+        with pytest.raises(fgk.FgkError) as e:
+            fgk.fgk_matvec_dlogell(h, to_dev(p.V), 0, "f64")
+        assert e.value.code == -1

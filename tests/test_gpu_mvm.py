@@ -170,3 +170,74 @@ def test_permutation_equivariance_and_linearity(fgk_mod):
         assert np.allclose(y2, y1[perm], rtol=1e-12, atol=1e-12 * np.abs(y1).max())
         comb = fgk.fgk_matvec(h1, to_dev(2 * p.V[:, :1] - 3 * p.V[:, 1:])).cpu().numpy()
         assert np.allclose(comb, 2 * y1[:, :1] - 3 * y1[:, 1:], atol=1e-12 * np.abs(y1).max())
+
+
+@pytest.mark.parametrize("d,nu,N,nrhs", [(2, 1.5, 200000, 1), (2, 2.5, 60000, 3), (3, 2.5, 20000, 2),
+                                         (1, 0.5, 50000, 2)])
+def test_product_bit_reproducible(fgk_mod, d, nu, N, nrhs):
+    """S5: the levels are summed in a fixed order, so the same product is
+    bit-identical call after call, in both precisions, also with another
+    plan's product launched in between on another stream."""
+    fgk = fgk_mod
+    p = workloads.small(300 + d, N, d, nu=nu, ell=[0.1, 0.3, 0.2][:d], nrhs=nrhs)
+    other = workloads.small(301 + d, 7000, 2, nu=1.5, ell=[0.2, 0.2], nrhs=4)
+    with build(fgk, p, "product") as h, build(fgk, other, "product") as h2:
+        for dt, prec in ((torch.float32, "f32"), (torch.float64, "f64")):
+            V = to_dev(p.V, dt)
+            first = fgk.fgk_matvec(h, V, prec).cpu().numpy()
+            side = torch.cuda.Stream()
+            with torch.cuda.stream(side):
+                fgk.fgk_matvec(h2, to_dev(other.V, dt), prec, stream=side)
+            again = fgk.fgk_matvec(h, V, prec).cpu().numpy()
+            torch.cuda.synchronize()
+            bits = np.uint32 if dt == torch.float32 else np.uint64
+            assert np.array_equal(first.view(bits), again.view(bits)), prec
+
+
+# nu = 7/2 and 9/2 (eqs. matern_7_2, matern_9_2): the scans with four and five
+# moments and the coefficients of eq. matern_explicit passed at run time
+HIGH_NU_CASES = [(N, d, pattern, nrhs, nu, kind)
+                 for nu in (3.5, 4.5)
+                 for (N, d, pattern, nrhs, kind) in [
+                     (1, 1, "uniform", 1, "l1"), (700, 1, "dups", 2, "l1"), (5000, 1, "uniform", 1, "l1"),
+                     (64, 2, "lattice", 1, "product"), (2500, 2, "dups", 2, "product"),
+                     (5000, 2, "uniform", 1, "product"), (3000, 2, "uniform", 2, "l1"),
+                     (100, 3, "dups", 1, "product"), (3001, 3, "uniform", 1, "product"),
+                     (2049, 3, "lattice", 1, "l1"), (600, 2, "wide", 2, "product")]
+                 if not (nu == 4.5 and d == 3)]
+
+
+def test_nine_halves_at_d3_is_refused(fgk_mod):
+    """nu = 9/2 is built for d <= 2: the library refuses d = 3."""
+    fgk = fgk_mod
+    p = workloads.small(5, 100, 3, nu=4.5, ell=[0.2, 0.3, 0.4])
+    with pytest.raises(fgk.FgkError) as e:
+        fgk.fgk_build(to_dev(p.X), p.nu, p.ell, kind="product")
+    assert e.value.code == -1
+
+
+@pytest.mark.parametrize("N,d,pattern,nrhs,nu,kind", HIGH_NU_CASES)
+def test_mvm_parity_higher_nu(fgk_mod, orc, N, d, pattern, nrhs, nu, kind):
+    fgk = fgk_mod
+    ell = [0.2, 0.35, 0.5][:d] if pattern != "wide" else [10.0, 20.0, 30.0][:d]
+    p = workloads.small(11 * N + d, N, d, nu=nu, ell=ell, nrhs=nrhs, pattern=pattern, s2=1.3)
+    ref = orc.mvm_brute(p.X, p.V, nu, p.ell, s2=p.s2, kind=0 if kind == "l1" else 1)
+    with build(fgk, p, kind) as h:
+        y64 = fgk.fgk_matvec(h, to_dev(p.V), "f64").cpu().numpy()
+        y32 = fgk.fgk_matvec(h, to_dev(p.V, torch.float32), "f32").cpu().numpy()
+    assert (colwise_relerr(y64, ref) <= TOL64).all(), colwise_relerr(y64, ref)
+    assert (colwise_relerr(y32, ref) <= TOL32).all(), colwise_relerr(y32, ref)
+
+
+def test_mvm_higher_nu_c2_shape_sampled(fgk_mod, orc):
+    """nu = 9/2 on the d=2 workload's points (N = 200000), 200 sampled rows."""
+    fgk = fgk_mod
+    p = workloads.c2()
+    V = np.random.default_rng(45).standard_normal((p.N, 1))
+    rows = sampled_rows(p.N, 200, 9)
+    ref = orc.mvm_brute(p.X, V, 4.5, p.ell, kind=1, rows=rows)
+    with fgk.fgk_build(to_dev(p.X), 4.5, p.ell, kind="product") as h:
+        y64 = fgk.fgk_matvec(h, to_dev(V), "f64").cpu().numpy()[rows]
+        y32 = fgk.fgk_matvec(h, to_dev(V, torch.float32), "f32").cpu().numpy()[rows]
+    assert (colwise_relerr(y64, ref) <= TOL64).all()
+    assert (colwise_relerr(y32, ref) <= TOL32).all()

@@ -25,13 +25,17 @@ CASES = [  # d, nu, kind, N, pattern
     (3, 1.5, "l1", 1000, "uniform"),
     (2, 1.5, "product", 1600, "lattice"),
     (2, 0.5, "product", 900, "dups"),
+    (2, 3.5, "product", 1500, "uniform"),
+    (1, 4.5, "l1", 1200, "uniform"),
+    (3, 3.5, "product", 800, "uniform"),
 ]
 
 
 def oracle_factor(orc, p, kind, rank, forced):
     kk = 0 if kind == "l1" else 1
     col = lambda i: orc.kcols(p.X, [i], p.nu, p.ell, s2=p.s2, kind=kk)[:, 0]  # noqa: E731
-    return osolve.pivoted_cholesky(col, np.full(p.N, p.s2), rank, forced=forced, tie_rtol=1e-9)
+    return osolve.pivoted_cholesky(col, np.full(p.N, p.s2), rank, forced=forced, tie_rtol=1e-9,
+                                   tie_atol=1e-12 * p.s2)
 
 
 @pytest.mark.parametrize("d,nu,kind,N,pattern", CASES)
@@ -49,7 +53,9 @@ def test_factor_pivots_trace_logdet(fgk_mod, orc, d, nu, kind, N, pattern):
     Lo, pivo, dres = oracle_factor(orc, p, kind, rank, forced=piv)
     assert info["rank"] == Lo.shape[1] == len(piv)
     assert np.abs(L - Lo).max() <= 1e-9 * np.sqrt(p.s2)
-    if pattern == "uniform":  # generic positions: the same pivots without forcing
+    if pattern == "uniform" and nu <= 2.5:  # generic positions: the same pivots without forcing
+        # (the smoother kernels leave near-ties between residual diagonals, which
+        # two roundings may order differently; the forced comparison above covers them)
         _, free, _ = oracle_factor(orc, p, kind, rank, forced=None)
         assert np.array_equal(free, piv)
     assert abs(info["trace_resid"] - dres.sum()) <= 1e-9 * p.N * p.s2
@@ -85,7 +91,7 @@ def test_rank_exhaustion_and_rank_zero(fgk_mod, orc):
             assert fgk.fgk_precond_info(pc0)["rank"] == 0
 
 
-@pytest.mark.parametrize("d,nu", [(1, 2.5), (2, 1.5), (2, 2.5), (3, 1.5)])
+@pytest.mark.parametrize("d,nu", [(1, 2.5), (2, 1.5), (2, 2.5), (3, 1.5), (2, 3.5), (2, 4.5)])
 @pytest.mark.parametrize("mode", ["f64", "mixed"])
 def test_pcg_matches_dense_solve(fgk_mod, orc, d, nu, mode):
     fgk = fgk_mod
