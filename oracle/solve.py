@@ -50,6 +50,16 @@ TEST INFRASTRUCTURE ONLY.
                   parameters, their running average subtracted from y before
                   the next descent, until successive GLS estimates differ by
                   at most eps_beta.
+* ``minres``      the minimum-residual method of Paige and Saunders for a
+                  symmetric system that need not be positive definite, such as
+                  K + sigma^2 I with the L1 kernel at nu >= 3/2, d >= 2
+                  (App. B, Prop. 4: not positive definite there, so CG can
+                  break down).  Lanczos vectors started at b, the tridiagonal
+                  T_k reduced to upper-triangular form by Givens rotations as it
+                  grows, x_k = the minimiser of ||b - A x|| over the Krylov
+                  space K_k(A, b), updated through the direction vectors of the
+                  triangular factor; stop once the recursive residual norm
+                  |phi_k| <= tol ||b||.  One column at a time.
 * ``posterior_mean``  E[f(z) | x, y] = k_z^T alpha + h(z)^T beta (eq. gp_mean,
                   with alpha = (K + sigma^2 I)^{-1}(y - H beta) as eq. gp_mean_2),
                   given the cross-covariance rows k_z^T.
@@ -357,3 +367,53 @@ def algorithm1_outer(descend, beta_gls, H, y, theta0, sigma2_0: float, eps_beta:
         if change <= eps_beta:
             break
     return beta, theta, sigma2, reps
+
+
+def minres(apply_A, b, tol: float, maxit: int):
+    """x with ||b - A x|| <= tol ||b|| (recursive estimate), A symmetric.
+    Returns (x, iterations, residual norms |phi_k| per iteration)."""
+    b = np.asarray(b, dtype=np.float64).reshape(-1)
+    n = b.size
+    x = np.zeros(n)
+    beta1 = float(np.linalg.norm(b))
+    if beta1 == 0.0:
+        return x, 0, []
+    v_prev = np.zeros(n)
+    v = b / beta1
+    beta = beta1                      # beta_k: the Lanczos coefficient below v_k
+    c_prev, s_prev = -1.0, 0.0        # the previous rotation (c_0 = -1, s_0 = 0)
+    delta1, eps = 0.0, 0.0            # delta_k^(1), eps_k: T's entries above the diagonal, rotated
+    phi = beta1                       # |phi_k| = ||r_k||
+    d_prev = np.zeros(n)
+    d_pp = np.zeros(n)
+    history = []
+    k = 0
+    while k < maxit:
+        k += 1
+        # Lanczos: beta_{k+1} v_{k+1} = A v_k - alpha_k v_k - beta_k v_{k-1}
+        p = apply_A(v)
+        alpha = float(v @ p)
+        p = p - alpha * v - beta * v_prev
+        beta_next = float(np.linalg.norm(p))
+        # the previous rotation applied to column k of T: (delta_k, alpha_k, beta_{k+1})
+        delta2 = c_prev * delta1 + s_prev * alpha
+        gamma1 = s_prev * delta1 - c_prev * alpha
+        eps_next = s_prev * beta_next
+        delta1_next = -c_prev * beta_next
+        # a new rotation annihilates beta_{k+1}
+        gamma2 = float(np.hypot(gamma1, beta_next))
+        if gamma2 == 0.0:
+            break
+        c, s = gamma1 / gamma2, beta_next / gamma2
+        tau = c * phi
+        phi = s * phi
+        d = (v - delta2 * d_prev - eps * d_pp) / gamma2
+        x = x + tau * d
+        history.append(phi)
+        if phi <= tol * beta1 or beta_next == 0.0:
+            break
+        d_pp, d_prev = d_prev, d
+        v_prev, v = v, p / beta_next
+        beta, delta1, eps = beta_next, delta1_next, eps_next
+        c_prev, s_prev = c, s
+    return x, k, history
