@@ -301,6 +301,27 @@ int fgk_cg_solve_pc(fgk_handle h, fgk_precond pc, const double *y, int nrhs, dou
                     double tol, int maxit, int mode, double *alpha, double *beta, fgk_cg_info *info,
                     fgk_stream_t stream);
 
+/* Solve (K + sigma2 I) alpha = y when K + sigma2 I is symmetric but need not
+ * be positive definite, by MINRES (Paige and Saunders): the L1 kernel at
+ * nu >= 3/2 and d >= 2, which App. B (Prop. 4) shows is not positive
+ * definite, so that fgk_cg_solve can stop with FGK_ERR_BREAKDOWN on it.
+ * Lanczos vectors from each column b of y, the tridiagonal reduced by Givens
+ * rotations, alpha the minimiser of ||b - A x|| over the Krylov space; FP64
+ * scans, zero start.  A column stops when its recursive residual is at most
+ * tol ||b||; its true residual is then recomputed with FP64 scans and the
+ * process restarts on it from the current alpha until that meets tol too.
+ *   y, alpha   device, N x nrhs FP64 row-major, original point order
+ *              (alpha: output).  1 <= nrhs <= 64.
+ *   sigma2     >= 0;  tol > 0;  maxit >= 1 (iterations over all restarts).
+ *   info       host, may be NULL: iterations, restarts (in refinements and
+ *              restarts), FP64 products, true residuals (true_resid if set).
+ * FGK_NOT_CONVERGED when a column misses tol after maxit iterations (alpha
+ * holds the best iterate); FGK_ERR_NONFINITE for NaN or Inf in y.
+ * Synchronises the stream once per iteration.  Allocates a workspace of
+ * 8 N nrhs doubles plus the product's. */
+int fgk_minres_solve(fgk_handle h, const double *y, int nrhs, double sigma2, double tol, int maxit, double *alpha,
+                     fgk_cg_info *info, fgk_stream_t stream);
+
 /* ---- log-determinant by stochastic Lanczos quadrature (App. A.2) ---- */
 
 /* Probe vectors distributed as N(0, P) for the preconditioned log-determinant

@@ -29,6 +29,7 @@ SOURCES = [
     "fgk_dscan_f32.cu",
     "fgk_dscan_f64.cu",
     "fgk_solve.cu",
+    "fgk_minres.cu",
     "fgk_noalloc.cu",
     "fgk_batch.cu",
     "fgk_precond.cu",

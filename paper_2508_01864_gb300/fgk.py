@@ -70,6 +70,7 @@ EXPORTS = ["fgk_set_allocator", "fgk_build", "fgk_matvec", "fgk_matvec_dlogell",
            "fgk_get_permutation", "fgk_get_level", "fgk_batch_create", "fgk_batch_layout", "fgk_batch_matvec_q",
            "fgk_batch_cg_solve", "fgk_batch_destroy", "fgk_precond_build", "fgk_precond_info",
            "fgk_precond_factor", "fgk_precond_apply", "fgk_precond_destroy", "fgk_cg_solve_pc",
+           "fgk_minres_solve",
            "fgk_kernel_timing", "fgk_predict", "fgk_batch_cg_solve_pc", "fgk_precond_sample", "fgk_slq_logdet",
            "fgk_lanczos_logquad", "fgk_loglik_grad"]
 
@@ -158,6 +159,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.fgk_cg_solve_pc.argtypes = [vp, vp, vp, i32, dbl, vp, i32, dbl, i32, i32, vp, vp,
                                         ctypes.POINTER(fgk_cg_info), vp]
         lib.fgk_cg_solve_pc.restype = i32
+        lib.fgk_minres_solve.argtypes = [vp, vp, i32, dbl, dbl, i32, vp, vp, vp]
+        lib.fgk_minres_solve.restype = i32
         lib.fgk_predict.argtypes = [vp, vp, i32, vp, i64, vp, i32, vp, i32, vp, vp]
         lib.fgk_predict.restype = i32
         _lib = lib
@@ -341,6 +344,35 @@ def fgk_scan_timing(enable: int = -1):
     n = ctypes.c_int64()
     _check(load().fgk_scan_timing(int(enable), ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
+
+
+def fgk_minres_solve(h: Handle, y: torch.Tensor, sigma2: float, tol: float = 1e-8, maxit: int = 100000,
+                     stream=None):
+    """Solve (K + sigma2 I) alpha = y by MINRES (symmetric, possibly
+    indefinite: the L1 kernel at nu >= 3/2, d >= 2).  Returns (alpha, info
+    dict, status) with status FGK_OK or FGK_NOT_CONVERGED; errors raise."""
+    lib = load()
+    y2 = _dev_f64_2d(y, "y")
+    _rows(y2, h.N, "y")
+    nrhs = y2.shape[1]
+    if nrhs > 64:
+        raise ValueError(f"fgk_minres_solve takes at most 64 columns, got {nrhs}")
+    alpha = torch.empty_like(y2)
+    res = (ctypes.c_double * nrhs)()
+    info = fgk_cg_info()
+    info.true_resid = ctypes.cast(res, ctypes.POINTER(ctypes.c_double))
+    rc = lib.fgk_minres_solve(h.ptr, y2.data_ptr(), nrhs, float(sigma2), float(tol), int(maxit), alpha.data_ptr(),
+                              ctypes.byref(info), _stream(stream))
+    d = {"iterations": info.iterations, "restarts": info.restarts, "mvm_f64": info.mvm_f64,
+         "max_true_resid": info.max_true_resid, "true_resid": list(res)}
+    try:
+        _check(rc, allow_soft=True)
+    except FgkError as e:
+        e.info = d
+        raise
+    if y.dim() == 1:
+        alpha = alpha.squeeze(1)
+    return alpha, d, rc
 
 
 def fgk_cg_solve(h: Handle, y: torch.Tensor, sigma2: float, H: torch.Tensor | None = None, L: int = 0,

@@ -81,6 +81,15 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert lib.fgk_precond_info(None, None, None) == -1
     assert lib.fgk_precond_apply(None, 1, 1, 1, None) == -1
     assert lib.fgk_precond_destroy(None) == 0
+    # MINRES: NULL handle or outputs, nrhs outside [1, 64], sigma2 < 0, tol <= 0, maxit < 1
+    for args in [(None, 1, 1, 0.01, 1e-8, 10, 1), (1, None, 1, 0.01, 1e-8, 10, 1), (1, 1, 1, 0.01, 1e-8, 10, None),
+                 (1, 1, 0, 0.01, 1e-8, 10, 1), (1, 1, 65, 0.01, 1e-8, 10, 1), (1, 1, 1, -1.0, 1e-8, 10, 1),
+                 (1, 1, 1, 0.01, 0.0, 10, 1), (1, 1, 1, 0.01, 1e-8, 0, 1)]:
+        assert lib.fgk_minres_solve(*args, None, None) == -1, args
+    # nu = 9/2 is built for d <= 2 only
+    assert lib.fgk_build(1, 10, 3, 9, ell, 1.0, 1, None, ctypes.byref(out)) == -1
+    assert b"9/2" in lib.fgk_last_error()
+    assert lib.fgk_bytes_estimate(1000, 3, 9, 1, 1) == 0 and lib.fgk_bytes_estimate(1000, 3, 7, 1, 1) > 0
 
 
 def test_likelihood_entries_reject_invalid_arguments_without_gpu(lib):

@@ -52,7 +52,12 @@ def test_factor_pivots_trace_logdet(fgk_mod, orc, d, nu, kind, N, pattern):
     piv = np.array(info["pivots"])
     Lo, pivo, dres = oracle_factor(orc, p, kind, rank, forced=piv)
     assert info["rank"] == Lo.shape[1] == len(piv)
-    assert np.abs(L - Lo).max() <= 1e-9 * np.sqrt(p.s2)
+    # each column divides by the square root of its pivot's residual d_m, so
+    # the rounding of the residuals (absolute, on the scale of s2) grows by
+    # sqrt(s2 / d_m) once they are small (the smoother kernels exhaust fast)
+    d_min = min(Lo[piv[m], m] ** 2 for m in range(len(piv)))
+    tol_L = 1e-9 * np.sqrt(p.s2) * max(1.0, np.sqrt(1e-4 * p.s2 / d_min))
+    assert np.abs(L - Lo).max() <= tol_L
     if pattern == "uniform" and nu <= 2.5:  # generic positions: the same pivots without forcing
         # (the smoother kernels leave near-ties between residual diagonals, which
         # two roundings may order differently; the forced comparison above covers them)
