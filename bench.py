@@ -402,6 +402,73 @@ def run_mvm_only(args, local):
     return 0
 
 
+def run_latency(args, local):
+    """The d=1 workload (N = 4096, nu = 1/2, ell = 0.2, one right-hand side):
+    one product K v per replay of a CUDA graph holding it (the product in the
+    plan's internal order, captured once after a warm-up), each replay timed
+    on its own by events; p50 / p99 over --latency replays, FP64 and FP32.
+    At this size the product is launch latency, not bandwidth."""
+    import torch
+
+    import workloads
+    from paper_2508_01864_gb300 import fgk
+
+    torch.cuda.set_device(local)
+    p = workloads.c1()
+    h = fgk.fgk_build(torch.as_tensor(p.X, device="cuda"), p.nu, p.ell, kind="l1")
+    out = {"metric": "exact Matérn MVM latency (graph replay)", "unit": "us", "workload":
+           "d=1 N=4096 nu=1/2 ell=0.2 x~U[0,1], one K v", "replays": args.latency}
+    side = torch.cuda.Stream()
+    for prec, dt in (("f64", torch.float64), ("f32", torch.float32)):
+        Vq = torch.as_tensor(p.V, dtype=dt, device="cuda").contiguous()
+        Yq = torch.empty_like(Vq)
+        with torch.cuda.stream(side):
+            for _ in range(3):
+                fgk.fgk_matvec_q(h, Vq, prec, out=Yq, stream=side)
+        side.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side):
+            fgk.fgk_matvec_q(h, Vq, prec, out=Yq, stream=side)
+        for _ in range(max(args.warmup, 3)):
+            g.replay()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(args.latency):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g.replay()
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e3)
+        ts.sort()
+        out[f"{prec}_p50_us"] = ts[len(ts) // 2]
+        out[f"{prec}_p99_us"] = ts[min(len(ts) - 1, int(0.99 * len(ts)))]
+        out[f"{prec}_min_us"] = ts[0]
+        del g
+    out["kernels_per_product"] = 4
+    fgk.fgk_destroy(h)
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_peaks(args, local):
+    """Measured FP32 and FP64 FMA throughput of this GPU (fgk_fma_rate), the
+    ALU roofline denominators, beside the copy bandwidth of MEASURED_PEAKS."""
+    import torch
+
+    from paper_2508_01864_gb300 import fgk
+
+    torch.cuda.set_device(local)
+    pk, src = peaks()
+    out = {"metric": "measured FMA throughput", "unit": "TFLOP/s",
+           "fp32_tflops": fgk.fgk_fma_rate("f32", 10) / 1e12, "fp64_tflops": fgk.fgk_fma_rate("f64", 5) / 1e12,
+           "hbm_gbs": pk.get("hbm_gbs"), "hbm_source": src,
+           "how": "16 independent FMA chains per thread, 8 CTAs x 256 threads per SM, best of the timed launches"}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_likelihood(args, local):
     """The likelihood pieces on the d=2 workload (N = 200000): the gradient
     products (dK/d log ell_m) V with FP32 and FP64 scans (every lengthscale),
@@ -500,6 +567,9 @@ def main():
     ap.add_argument("--likelihood", action="store_true",
                     help="time the gradient products and the log-determinant on the d=2 workload")
     ap.add_argument("--mvm-nrhs", type=int, default=1, help="columns of the --mvm-only products")
+    ap.add_argument("--latency", type=int, default=0,
+                    help="d=1 workload: p50/p99 of this many CUDA-graph replays of one product")
+    ap.add_argument("--peaks", action="store_true", help="measured FP32/FP64 FMA throughput")
     ap.add_argument("--mvm-only", type=int, default=0,
                     help="time only the FP32 product on the d=2 workload drawn with this many points")
     args = ap.parse_args()
@@ -508,6 +578,10 @@ def main():
         return run_reference(args, ws, rank)
     if args.likelihood:
         return run_likelihood(args, local)
+    if args.latency:
+        return run_latency(args, local)
+    if args.peaks:
+        return run_peaks(args, local)
     if args.mvm_only:
         return run_mvm_only(args, local)
     if args.pcg_probe:

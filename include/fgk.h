@@ -322,6 +322,32 @@ int fgk_cg_solve_pc(fgk_handle h, fgk_precond pc, const double *y, int nrhs, dou
 int fgk_minres_solve(fgk_handle h, const double *y, int nrhs, double sigma2, double tol, int maxit, double *alpha,
                      fgk_cg_info *info, fgk_stream_t stream);
 
+/* One d = 1 problem over several devices (SURVEY's sharded form of the d = 1
+ * product): each device holds a shard, a contiguous range of the points in
+ * sorted order, and a plan of its own points; the plan's product covers the
+ * pairs inside the shard, and the pairs between shards act through P
+ * moments per shard and direction (Sec. 2.1, the fast sum updating of
+ * eq. fast_exact_decomposition_1d with the running sums relative to an
+ * anchor point):
+ *   M_q = sum_j v_j delta_j^q exp(-delta_j),  q < P = nu + 1/2,
+ * delta_j = x'_last - x'_j (forward: this shard's sources seen from after
+ * it) or x'_j - x'_first (backward), x' the scaled coordinates.
+ *
+ * fgk_shard_moments: V device N x nrhs FP64, original point order, 1 <= nrhs
+ * <= 64; out host, 2 + 2 nrhs P doubles: x'_first, x'_last, then M indexed
+ * [(r * 2 + dir) * P + q] (dir 0 forward, 1 backward).  FP64, fixed-order
+ * sums.  Synchronises the stream.  d = 1 plans only (FGK_ERR_INVALID).
+ *
+ * fgk_shard_fixup: Y += the contributions of the other shards' points, given
+ * carry (host, 2 nrhs P doubles, the same indexing): dir 0 the moments of
+ * every point before this shard anchored at its x'_first, dir 1 those after
+ * it anchored at x'_last (the caller composes them from all shards'
+ * fgk_shard_moments by the binomial step M'_q = exp(-g) sum_{t<=q} C(q,t)
+ * g^{q-t} M_t over each gap g).  Y device N x nrhs FP64, original order.
+ * Asynchronous. */
+int fgk_shard_moments(fgk_handle h, const double *V, int nrhs, double *out, fgk_stream_t stream);
+int fgk_shard_fixup(fgk_handle h, const double *carry, int nrhs, double *Y, fgk_stream_t stream);
+
 /* ---- log-determinant by stochastic Lanczos quadrature (App. A.2) ---- */
 
 /* Probe vectors distributed as N(0, P) for the preconditioned log-determinant
@@ -499,6 +525,15 @@ int fgk_scan_timing(int enable, double *total_ms, int64_t *launches);
  * Z = R / sigma2 - L c).  FGK_ERR_INVALID for an unknown id. */
 enum { FGK_TIMED_SCAN_OUT = 0, FGK_TIMED_PC_LTR = 1, FGK_TIMED_PC_APPLY = 2 };
 int fgk_kernel_timing(int kernel, int enable, double *total_ms, int64_t *launches);
+
+/* Measured fused multiply-add throughput of the current device, the
+ * denominator of the ALU roofline of the FP64 scans and of the FP32 scans
+ * with many moments (the paper has no counterpart; instrumentation).  A
+ * kernel of independent FMA chains (16 per thread, 8 resident CTAs of 256
+ * threads per SM) is launched once to warm up and `reps` times timed by CUDA
+ * events on `stream`; *flops receives 2 x FMAs / second of the fastest
+ * launch.  precision FGK_F32 or FGK_F64; reps >= 1.  Synchronises. */
+int fgk_fma_rate(int precision, int reps, double *flops, fgk_stream_t stream);
 
 /* ---- inspection (tests and tools): copies of the cached structure ---- */
 

@@ -30,6 +30,8 @@ SOURCES = [
     "fgk_dscan_f64.cu",
     "fgk_solve.cu",
     "fgk_minres.cu",
+    "fgk_shard.cu",
+    "fgk_peak.cu",
     "fgk_noalloc.cu",
     "fgk_batch.cu",
     "fgk_precond.cu",

@@ -120,6 +120,7 @@ struct Plan {
     int64_t ldN = 0;  // stride between levels: N rounded up to a multiple of 64 entries
     cudaStream_t stream = nullptr;
     int device = 0;   // the CUDA device the plan was built on (current during fgk_build)
+    int sort_spin_limit = 1 << 24;  // bound on the sort's look-back spins per predecessor
 
     // sort results (device)
     int32_t *perm[kMaxD] = {nullptr, nullptr, nullptr};  // position in x'_k order -> point

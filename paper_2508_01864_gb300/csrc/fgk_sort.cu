@@ -17,6 +17,7 @@
 // same for every key are skipped.  Every look-back wait is bounded; on expiry
 // the kernel records DEV_TIMEOUT in the plan's error word and stops waiting.
 #include <algorithm>
+#include <cstdlib>
 
 #include "fgk_internal.cuh"
 
@@ -28,6 +29,9 @@ constexpr int kSortThreads = 256;
 constexpr int kSortIPT = 8;
 constexpr int kSortTile = kSortThreads * kSortIPT;
 constexpr int kSortWarps = kSortThreads / 32;
+// bound on the look-back's spins on one predecessor tile; fgk_build takes a
+// smaller one from FGK_SORT_SPIN_LIMIT (a test hook that makes the wait
+// expire, so that the expiry path is exercised)
 constexpr int kSpinLimit = 1 << 24;
 
 constexpr uint32_t ST_AGG = 1u << 30;
@@ -101,17 +105,27 @@ __global__ void k_digit_offsets(const uint32_t *__restrict__ hist, uint32_t *__r
 
 // One LSD pass.  Tiles are taken in order from *tile_counter so that every
 // tile a look-back waits on has already been started by a running CTA.
+// Once a wait has expired (the error word is set) the CTAs that start later
+// take no tile and return: every tile still looks back only at tiles taken
+// before it, and the host abandons the sort.  A tile whose wait expired
+// stops summing its predecessors, so its offsets are at most the true ones
+// and its writes stay inside the output.
 __global__ void __launch_bounds__(kSortThreads) k_sort_pass(
     const uint64_t *__restrict__ kin, const int32_t *__restrict__ vin, uint64_t *__restrict__ kout,
     int32_t *__restrict__ vout, int64_t N, int shift, const uint32_t *__restrict__ digit_off,
-    uint32_t *__restrict__ status, uint32_t *__restrict__ tile_counter, int *__restrict__ err) {
+    uint32_t *__restrict__ status, uint32_t *__restrict__ tile_counter, int *__restrict__ err, int spin_limit) {
     __shared__ uint16_t cnt[kSortIPT][kSortWarps][256];  // per (round, warp, digit); later exclusive offsets
     __shared__ uint32_t tile_excl[256];
     __shared__ uint32_t s_tile;
+    __shared__ int s_stop;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
+    if (tid == 0) {
+        s_stop = *((volatile int *)err) != 0;
+        if (!s_stop) s_tile = atomicAdd(tile_counter, 1u);
+    }
     for (int i = tid; i < kSortIPT * kSortWarps * 256; i += kSortThreads) (&cnt[0][0][0])[i] = 0;
     __syncthreads();
+    if (s_stop) return;
     const uint32_t tile = s_tile;
     const int64_t base = (int64_t)tile * kSortTile;
 
@@ -154,7 +168,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(
             while (j >= 0) {
                 uint32_t w = *((volatile uint32_t *)(status + (size_t)j * 256 + tid));
                 if ((w & ~ST_VAL) == 0) {
-                    if (++spins > kSpinLimit) {
+                    if (++spins > spin_limit) {
                         atomicExch(err, DEV_TIMEOUT);
                         break;
                     }
@@ -244,7 +258,7 @@ static int radix_sort(Plan *p, const double *xs, int32_t *perm_out, cudaStream_t
         FGK_CUDA(cudaMemsetAsync(status, 0, (size_t)ntiles * 256 * 4, s));
         FGK_CUDA(cudaMemsetAsync(counters + pass, 0, 4, s));
         k_sort_pass<<<ntiles, kSortThreads, 0, s>>>(kin, vin, kout, vout, N, 8 * pass, offs + pass * 256, status,
-                                                     counters + pass, p->dev_err);
+                                                     counters + pass, p->dev_err, p->sort_spin_limit);
         FGK_LAUNCH_CHECK();
         std::swap(kin, kout);
         std::swap(vin, vout);
@@ -277,9 +291,21 @@ int build_sort(Plan *p, const double *X) {
         set_error("fgk_build: X holds a NaN or an infinity (or x * sqrt(2nu)/ell overflows)");
         return FGK_ERR_NONFINITE;
     }
+    {
+        const char *lim = getenv("FGK_SORT_SPIN_LIMIT");
+        p->sort_spin_limit = lim ? std::max(1, atoi(lim)) : kSpinLimit;
+    }
     for (int k = 0; k < d; ++k) {
         FGK_TRY(plan_alloc(p, (void **)&p->perm[k], N * sizeof(int32_t)));
         FGK_TRY(radix_sort(p, xs + k * N, p->perm[k], s));
+    }
+    // an expired look-back leaves the permutations invalid: stop before using them
+    {
+        const int rc = check_dev_error(p, "radix sort");
+        if (rc != FGK_OK) {
+            dev_free(xs, s);
+            return rc;
+        }
     }
     FGK_TRY(plan_alloc(p, (void **)&p->rank1, N * sizeof(int32_t)));
     k_invert<<<grid_for(N, 256), 256, 0, s>>>(p->perm[0], N, p->rank1);

@@ -14,6 +14,7 @@ import os
 import threading
 from dataclasses import dataclass
 
+import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -70,7 +71,7 @@ EXPORTS = ["fgk_set_allocator", "fgk_build", "fgk_matvec", "fgk_matvec_dlogell",
            "fgk_get_permutation", "fgk_get_level", "fgk_batch_create", "fgk_batch_layout", "fgk_batch_matvec_q",
            "fgk_batch_cg_solve", "fgk_batch_destroy", "fgk_precond_build", "fgk_precond_info",
            "fgk_precond_factor", "fgk_precond_apply", "fgk_precond_destroy", "fgk_cg_solve_pc",
-           "fgk_minres_solve",
+           "fgk_minres_solve", "fgk_shard_moments", "fgk_shard_fixup", "fgk_fma_rate",
            "fgk_kernel_timing", "fgk_predict", "fgk_batch_cg_solve_pc", "fgk_precond_sample", "fgk_slq_logdet",
            "fgk_lanczos_logquad", "fgk_loglik_grad"]
 
@@ -161,6 +162,12 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.fgk_cg_solve_pc.restype = i32
         lib.fgk_minres_solve.argtypes = [vp, vp, i32, dbl, dbl, i32, vp, vp, vp]
         lib.fgk_minres_solve.restype = i32
+        lib.fgk_shard_moments.argtypes = [vp, vp, i32, vp, vp]
+        lib.fgk_shard_moments.restype = i32
+        lib.fgk_shard_fixup.argtypes = [vp, vp, i32, vp, vp]
+        lib.fgk_shard_fixup.restype = i32
+        lib.fgk_fma_rate.argtypes = [i32, i32, ctypes.POINTER(dbl), vp]
+        lib.fgk_fma_rate.restype = i32
         lib.fgk_predict.argtypes = [vp, vp, i32, vp, i64, vp, i32, vp, i32, vp, vp]
         lib.fgk_predict.restype = i32
         _lib = lib
@@ -344,6 +351,45 @@ def fgk_scan_timing(enable: int = -1):
     n = ctypes.c_int64()
     _check(load().fgk_scan_timing(int(enable), ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
+
+
+def fgk_fma_rate(precision="f32", reps: int = 5, stream=None) -> float:
+    """Measured FMA throughput of the current device in FLOP/s (2 per FMA)."""
+    prec = {"f64": FGK_F64, "f32": FGK_F32}[precision] if isinstance(precision, str) else int(precision)
+    out = ctypes.c_double()
+    _check(load().fgk_fma_rate(prec, int(reps), ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
+def fgk_shard_moments(h: Handle, V: torch.Tensor, stream=None):
+    """(x'_first, x'_last, M) of this shard (d = 1 plan): M[r, dir, q] as
+    fgk_shard_moments documents (numpy, FP64)."""
+    lib = load()
+    V2 = _dev_f64_2d(V, "V")
+    _rows(V2, h.N, "V")
+    nrhs = V2.shape[1]
+    if nrhs > 64:
+        raise ValueError(f"at most 64 columns, got {nrhs}")
+    P = (h.two_nu + 1) // 2
+    out = np.zeros(2 + 2 * nrhs * P)
+    _check(lib.fgk_shard_moments(h.ptr, V2.data_ptr(), nrhs, out.ctypes.data, _stream(stream)))
+    return float(out[0]), float(out[1]), out[2:].reshape(nrhs, 2, P)
+
+
+def fgk_shard_fixup(h: Handle, carry, Y: torch.Tensor, stream=None):
+    """Y += the other shards' contributions, from carry[r, dir, q] (dir 0:
+    the points before this shard, anchored at its first point; dir 1: after,
+    at its last)."""
+    lib = load()
+    Y2 = _dev_f64_2d(Y, "Y")
+    _rows(Y2, h.N, "Y")
+    nrhs = Y2.shape[1]
+    P = (h.two_nu + 1) // 2
+    c = np.ascontiguousarray(carry, dtype=np.float64)
+    if c.shape != (nrhs, 2, P):
+        raise ValueError(f"carry must have shape {(nrhs, 2, P)}, got {c.shape}")
+    _check(lib.fgk_shard_fixup(h.ptr, c.ctypes.data, nrhs, Y2.data_ptr(), _stream(stream)))
+    return Y
 
 
 def fgk_minres_solve(h: Handle, y: torch.Tensor, sigma2: float, tol: float = 1e-8, maxit: int = 100000,
