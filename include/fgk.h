@@ -262,13 +262,17 @@ typedef struct {
  * pivot is the point with the largest remaining diagonal of K - L L^T (ties:
  * the smallest original point index), and L gains the column of K at the
  * pivot minus what the earlier columns explain, divided by the square root of
- * that diagonal entry.  The factor is computed in FP64 and applied from an
- * FP32 copy; the Woodbury matrix I + L^T L / sigma2 is formed from the FP32
- * values, so P is exactly (FP32 L)(FP32 L)^T + sigma2 I.
+ * that diagonal entry.  The factor is stored in FP32 and each new column is
+ * rounded to FP32 before the later columns and the residual diagonal use it,
+ * so the factor is the exact pivoted-Cholesky recurrence of its own stored
+ * columns (the next columns take up each rounding); its sums are float pairs
+ * of exact products (about 48 bits), the divisions and the residual diagonal
+ * FP64.  The Woodbury matrix I + L^T L / sigma2 is formed from the stored
+ * values, so P is exactly L L^T + sigma2 I for the stored L.
  *   h       a built plan; it must outlive the preconditioner.
  *   rank    0 <= rank <= 1024 (the paper uses 100); rank 0 gives P = sigma2 I.
  *   sigma2  > 0, the noise variance of the systems it will precondition.
- * Device memory: about N x rank x 12 bytes plus O(rank^2).  Synchronises
+ * Device memory: about N x rank x 4 bytes plus O(rank^2).  Synchronises
  * `stream`.  Errors: FGK_ERR_INVALID (arguments), FGK_ERR_OOM. */
 int fgk_precond_build(fgk_handle h, int rank, double sigma2, fgk_stream_t stream, fgk_precond *out);
 

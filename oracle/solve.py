@@ -103,8 +103,13 @@ def cg(apply_A, B, tol: float, maxit: int, apply_Pinv=None):
     return (X[:, 0] if vec else X), iters
 
 
+def f32_store(l):
+    """A factor column as stored in FP32 (round to nearest)."""
+    return np.asarray(l, dtype=np.float64).astype(np.float32).astype(np.float64)
+
+
 def pivoted_cholesky(column, diag, k: int, forced=None, tie_rtol: float = 0.0, eps: float = 1e-12,
-                     tie_atol: float = 0.0):
+                     tie_atol: float = 0.0, store=None):
     """Rank-k pivoted Cholesky of the SPD matrix with diagonal ``diag`` and
     columns ``column(i)``.  Returns (L (N x r), pivots (r,), residual
     diagonal) with r <= k: the factorisation stops early once the largest
@@ -118,7 +123,12 @@ def pivoted_cholesky(column, diag, k: int, forced=None, tie_rtol: float = 0.0, e
     ``tie_rtol`` or an absolute ``tie_atol`` (for comparing with a computation
     whose rounding may break near-ties the other way: a residual diagonal
     s2 - sum_m l_m^2 carries an absolute rounding error on the scale of the
-    diagonal s2, so once the residuals are small the absolute term decides)."""
+    diagonal s2, so once the residuals are small the absolute term decides).
+
+    ``store``: the rounding applied to each new column before it is kept
+    (a factor stored in fewer bits, e.g. ``f32_store``); the later columns and
+    the residual diagonal then use the stored values, so the factor is the
+    exact pivoted Cholesky recurrence of its own stored columns."""
     d = np.array(diag, dtype=np.float64, copy=True)
     N = d.size
     floor = eps * float(d.max()) if N else 0.0
@@ -138,6 +148,8 @@ def pivoted_cholesky(column, diag, k: int, forced=None, tie_rtol: float = 0.0, e
             break
         c = np.asarray(column(i), dtype=np.float64).reshape(N)
         l = (c - L[:, :m] @ L[i, :m]) / np.sqrt(d[i])
+        if store is not None:
+            l = store(l)
         L[:, m] = l
         d = d - l * l
         piv.append(i)

@@ -13,12 +13,16 @@
 // updates its rows and publishes its own maximum.  A step whose largest
 // residual is at most 1e-12 s2 (numerically exhausted; the paper leaves the
 // case open) records the realised rank and changes nothing.
-// L is kept as a float pair per entry (columns of N entries, q order):
-// L = Lhi + Llo to about 48 bits, the sums of the build done in float-pair
-// arithmetic (see below) and the divisions and the residual diagonal in FP64.
-// The apply uses Lhi alone, and the Woodbury matrix I + L^T L / sigma^2 is
-// formed from exactly those FP32 values (float-pair sums of exact products),
-// so P is the SPD matrix Lhi Lhi^T + sigma^2 I that the apply inverts.
+// L is stored in FP32 (columns of N entries, q order), and each new column
+// is rounded to FP32 before anything else uses it: the later columns and the
+// residual diagonal are those of the stored factor, so the factor is the
+// exact pivoted-Cholesky recurrence of its own stored columns (the rounding of
+// a column, ~2^-24 of it, is taken up by the next ones, far below the
+// residual the rank leaves).  The sums of the build are float pairs of exact
+// products (two-product, two-sum), the divisions and the residual diagonal
+// FP64.  The apply and the Woodbury matrix I + L^T L / sigma^2 use the same
+// FP32 values, so P is exactly the SPD matrix L L^T + sigma^2 I the apply
+// inverts.
 //
 // Apply (Z = P^{-1} R, every CG iteration, inside the captured graph):
 //   t = L^T R          k_pc_ltr (persistent CTAs, per-CTA partials) + k_pc_tsum
@@ -177,9 +181,9 @@ __global__ void k_pc_init(int64_t N, double s2, const int32_t *__restrict__ perm
 // step m of the pivoted Cholesky (see the file comment)
 __global__ void k_pc_step(int m, int64_t N, int64_t ldN, KernArgs ka, const int32_t *__restrict__ perm0,
                           const PivPart *__restrict__ prev, int nprev, PivPart *__restrict__ next,
-                          float *__restrict__ Lhi, float *__restrict__ Llo, double *__restrict__ dres,
-                          int32_t *__restrict__ piv_q, int *__restrict__ rank, double floor) {
-    __shared__ float s_lph[kPcMaxRank], s_lpl[kPcMaxRank];
+                          float *__restrict__ L, double *__restrict__ dres, int32_t *__restrict__ piv_q,
+                          int *__restrict__ rank, double floor) {
+    __shared__ float s_lp[kPcMaxRank];
     __shared__ double s_xp[3];
     PivPart best = piv_none();
     for (int b = threadIdx.x; b < nprev; b += blockDim.x)
@@ -194,10 +198,7 @@ __global__ void k_pc_step(int m, int64_t N, int64_t ldN, KernArgs ka, const int3
     }
     const int64_t piv = best.q;
     if (blockIdx.x == 0 && threadIdx.x == 0) piv_q[m] = (int32_t)piv;
-    for (int t = threadIdx.x; t < m; t += blockDim.x) {
-        s_lph[t] = Lhi[(size_t)t * ldN + piv];
-        s_lpl[t] = Llo[(size_t)t * ldN + piv];
-    }
+    for (int t = threadIdx.x; t < m; t += blockDim.x) s_lp[t] = L[(size_t)t * ldN + piv];
     if (threadIdx.x == 0) {
         s_xp[0] = ka.x0[piv];
         s_xp[1] = ka.d > 1 ? ka.x1[piv] : 0.0;
@@ -212,18 +213,15 @@ __global__ void k_pc_step(int m, int64_t N, int64_t ldN, KernArgs ka, const int3
     for (int64_t i0 = 2 * (blockIdx.x * (int64_t)blockDim.x + threadIdx.x); i0 < N;
          i0 += 2 * (int64_t)gridDim.x * blockDim.x) {
         const bool two = i0 + 1 < N;
-        // sum_t L_t[i] L_t[pivot] in float pairs: the hi x hi product exactly
-        // (two-product), the cross terms in FP32 (they sit 24 bits lower)
+        // sum_t L_t[i] L_t[pivot]: each product of two FP32 values made exact
+        // by the two-product, the running sum a float pair
         F2 acc0{0.f, 0.f}, acc1{0.f, 0.f};
-#pragma unroll 4
+#pragma unroll 8
         for (int t = 0; t < m; ++t) {
-            const float2 ah = *reinterpret_cast<const float2 *>(Lhi + (size_t)t * ldN + i0);
-            const float2 al = *reinterpret_cast<const float2 *>(Llo + (size_t)t * ldN + i0);
-            const float ph = s_lph[t], pl = s_lpl[t];
-            f2_fma(acc0, ah.x, ph, pl);
-            acc0.lo = fmaf(al.x, ph, acc0.lo);
-            f2_fma(acc1, ah.y, ph, pl);
-            acc1.lo = fmaf(al.y, ph, acc1.lo);
+            const float2 a = *reinterpret_cast<const float2 *>(L + (size_t)t * ldN + i0);
+            const float ph = s_lp[t];
+            f2_fma(acc0, a.x, ph, 0.f);
+            f2_fma(acc1, a.y, ph, 0.f);
         }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -232,11 +230,9 @@ __global__ void k_pc_step(int m, int64_t N, int64_t ldN, KernArgs ka, const int3
             const F2 acc = h == 0 ? acc0 : acc1;
             const double kv = kern_q(ka, i, s_xp);
             const double dot = (double)acc.hi + (double)acc.lo;
-            const double l = (kv - dot) * isq;
-            float lh, ll;
-            split_f2(l, lh, ll);
-            Lhi[(size_t)m * ldN + i] = lh;
-            Llo[(size_t)m * ldN + i] = ll;
+            const float lf = (float)((kv - dot) * isq);
+            L[(size_t)m * ldN + i] = lf;
+            const double l = (double)lf;  // the stored value from here on
             const double dn = dres[i] - l * l;
             dres[i] = dn;
             const PivPart c{dn, (int64_t)perm0[i], i};
@@ -786,8 +782,8 @@ __global__ void __launch_bounds__(kTR) k_pc_apply(const __grid_constant__ CUtens
     }
 }
 
-// B[orig][j] = sum_m Lhi[m][q] E_r[m][j] + sigma E_n[orig][j] (orig = perm0[q]), FP64
-__global__ void k_pc_sample(const float *__restrict__ Lhi, int64_t ldN, int r, int64_t N,
+// B[orig][j] = sum_m L[m][q] E_r[m][j] + sigma E_n[orig][j] (orig = perm0[q]), FP64
+__global__ void k_pc_sample(const float *__restrict__ L, int64_t ldN, int r, int64_t N,
                             const int32_t *__restrict__ perm0, const double *__restrict__ Er,
                             const double *__restrict__ En, int nprobe, double sigma, double *__restrict__ B) {
     const int64_t n = N * nprobe;
@@ -795,21 +791,21 @@ __global__ void k_pc_sample(const float *__restrict__ Lhi, int64_t ldN, int r, i
         const int64_t q = t / nprobe;
         const int j = (int)(t % nprobe);
         double acc = 0.0;
-        for (int m = 0; m < r; ++m) acc = fma((double)Lhi[(size_t)m * ldN + q], Er[(size_t)m * nprobe + j], acc);
+        for (int m = 0; m < r; ++m) acc = fma((double)L[(size_t)m * ldN + q], Er[(size_t)m * nprobe + j], acc);
         const int64_t o = (int64_t)perm0[q] * nprobe + j;
         B[o] = acc + sigma * En[o];
     }
 }
 
-// L in the caller's point order: out[orig * r + m] = Lhi[m][q] + Llo[m][q]
-__global__ void k_pc_factor_out(const float *__restrict__ Lhi, const float *__restrict__ Llo, int64_t ldN, int r,
-                                int64_t N, const int32_t *__restrict__ perm0, double *__restrict__ out) {
+// L in the caller's point order: out[orig * r + m] = L[m][q]
+__global__ void k_pc_factor_out(const float *__restrict__ L, int64_t ldN, int r, int64_t N,
+                                const int32_t *__restrict__ perm0, double *__restrict__ out) {
     const int64_t n = N * r;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t q = t / r;
         const int m = (int)(t % r);
         const size_t o = (size_t)m * ldN + q;
-        out[(int64_t)perm0[q] * r + m] = (double)Lhi[o] + (double)Llo[o];
+        out[(int64_t)perm0[q] * r + m] = (double)L[o];
     }
 }
 
@@ -822,7 +818,7 @@ struct Precond {
     int64_t ldN = 0;
     double *dres = nullptr, *Cf = nullptr, *Cinv = nullptr, *t_part = nullptr, *cvec = nullptr,
            *scal = nullptr;
-    float *L32 = nullptr, *Llo = nullptr;  // L32: the hi part of L
+    float *L32 = nullptr;  // the factor, k columns of ldN (q order)
     int32_t *piv_q = nullptr;
     int *ints = nullptr;  // [0] rank, [1] error flag
     int nb_ltr = 0, chunk = 0, cap_cols = 0;
@@ -1021,7 +1017,6 @@ static int pc_build(Precond *pc, cudaStream_t s) {
         pc->nb_ltr = (int)std::min<int64_t>((int64_t)per_sm * std::max(nsm, 1), (N + kTR - 1) / kTR);
     }
     pc->ldN = ldN;
-    pc->Llo = (float *)take((size_t)k * ldN * 4);
     pc->L32 = (float *)take((size_t)k * ldN * 4);
     pc->dres = (double *)take((size_t)N * 8);
     pc->piv_q = (int32_t *)take((size_t)k * 4);
@@ -1046,7 +1041,6 @@ static int pc_build(Precond *pc, cudaStream_t s) {
         return FGK_ERR_OOM;
     }
 
-    FGK_CUDA(cudaMemsetAsync(pc->Llo, 0, (size_t)k * ldN * 4, s));
     FGK_CUDA(cudaMemsetAsync(pc->L32, 0, (size_t)k * ldN * 4, s));
     const int init[4] = {k, 0, 0, 0};
     FGK_CUDA(cudaMemcpyAsync(pc->ints, init, sizeof(init), cudaMemcpyHostToDevice, s));
@@ -1056,8 +1050,7 @@ static int pc_build(Precond *pc, cudaStream_t s) {
     PivPart *bufs[2] = {part0, part1};
     for (int m = 0; m < k; ++m) {
         k_pc_step<<<steps_blocks, kPcThreads, 0, s>>>(m, N, ldN, ka, p->perm[0], bufs[m & 1], steps_blocks,
-                                                      bufs[(m + 1) & 1], pc->L32, pc->Llo, pc->dres, pc->piv_q,
-                                                      pc->ints,
+                                                      bufs[(m + 1) & 1], pc->L32, pc->dres, pc->piv_q, pc->ints,
                                                       kExhausted * p->s2);
         FGK_LAUNCH_CHECK();
     }
@@ -1183,8 +1176,7 @@ int fgk_precond_factor(fgk_precond pc, double *L, fgk_stream_t stream) {
     }
     if (pc->rank == 0) return FGK_OK;
     const int64_t n = pc->plan->N * pc->rank;
-    k_pc_factor_out<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(pc->L32, pc->Llo, pc->ldN, pc->rank,
-                                                                         pc->plan->N,
+    k_pc_factor_out<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(pc->L32, pc->ldN, pc->rank, pc->plan->N,
                                                                          pc->plan->perm[0], L);
     FGK_LAUNCH_CHECK();
     return FGK_OK;

@@ -775,16 +775,36 @@ __global__ void k_diag_init(const R *__restrict__ V, int64_t n, R s2, R *__restr
 // S5: Y = base + sum over levels of the level rows, the levels added in
 // ascending order (the same order on every call, so a product is
 // reproducible bit for bit); base = s2 V (the self-pairs, which no level
-// holds) when V is given, else the Y already there.
+// holds) when V is given, else the Y already there.  Rows are stride apart
+// (a multiple of 16 bytes), so each thread reads 16 bytes of every level at
+// once: the independent loads of all levels are in flight together.
 template <class R>
-__global__ void k_level_sum(const R *__restrict__ rows, int nlev, int64_t n, const R *__restrict__ V, R s2,
-                            R *__restrict__ Y, const int *__restrict__ gate) {
+__global__ void k_level_sum(const R *__restrict__ rows, int nlev, int64_t n, int64_t stride,
+                            const R *__restrict__ V, R s2, R *__restrict__ Y, const int *__restrict__ gate) {
     if (gate && *gate == 0) return;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-        R acc = V ? s2 * V[t] : Y[t];
-#pragma unroll 4
-        for (int l = 0; l < nlev; ++l) acc += rows[(size_t)l * n + t];
-        Y[t] = acc;
+    constexpr int W = 16 / sizeof(R);  // elements per 16-byte load
+    using Vec = typename std::conditional<sizeof(R) == 4, float4, double2>::type;
+    const int64_t nv = n / W;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nv; t += (int64_t)gridDim.x * blockDim.x) {
+        R acc[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) acc[w] = V ? s2 * V[t * W + w] : Y[t * W + w];
+#pragma unroll 6
+        for (int l = 0; l < nlev; ++l) {
+            const Vec x = reinterpret_cast<const Vec *>(rows + (size_t)l * stride)[t];
+            const R *xv = reinterpret_cast<const R *>(&x);
+#pragma unroll
+            for (int w = 0; w < W; ++w) acc[w] += xv[w];
+        }
+#pragma unroll
+        for (int w = 0; w < W; ++w) Y[t * W + w] = acc[w];
+    }
+    // the tail past the last full vector
+    for (int64_t e = nv * W + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        R acc = V ? s2 * V[e] : Y[e];
+        for (int l = 0; l < nlev; ++l) acc += rows[(size_t)l * stride + e];
+        Y[e] = acc;
     }
 }
 
@@ -803,8 +823,10 @@ inline size_t scan_pass_elems(int P, int noff, int kind) {
     const size_t ag = 1 + cp * gp * P;
     return npass * ngp * ag;
 }
+// level rows: stride = N nrhs rounded up to 16 bytes' worth of elements
+inline size_t scan_row_stride(const Plan *p, int nrhs) { return ((size_t)p->N * nrhs + 3) / 4 * 4; }
 inline size_t scan_rows_elems(const Plan *p, int nrhs) {
-    return ((size_t)p->nlev * p->N * nrhs + 63) / 64 * 64;
+    return ((size_t)p->nlev * scan_row_stride(p, nrhs) + 63) / 64 * 64;
 }
 inline size_t scan_ws_elems_for(const Plan *p, int nrhs, int P, int kind) {
     const size_t slot = (size_t)2 * nrhs * scan_pass_elems(P, p->d - 1, kind);
@@ -849,7 +871,7 @@ int run_levels(Plan *p, const R *Vq, int nrhs, R *Yq, R *ws, cudaStream_t s, con
     A.nrhs = nrhs;
     A.Y = Yq;
     A.rows = ws;
-    A.row_stride = p->N * nrhs;
+    A.row_stride = (int64_t)scan_row_stride(p, nrhs);
     A.s2 = (R)p->s2;
     A.err = p->dev_err;
     A.gate = gate;
@@ -885,8 +907,9 @@ int run_levels(Plan *p, const R *Vq, int nrhs, R *Yq, R *ws, cudaStream_t s, con
         }
     }
     const int64_t n = p->N * nrhs;
-    const unsigned blocks = (unsigned)std::min<int64_t>(grid_for(n, 256), 152 * 8);
-    k_level_sum<R><<<blocks, 256, 0, s>>>(ws, p->nlev, n, init_diag ? Vq : nullptr, (R)p->s2, Yq, gate);
+    const unsigned blocks = (unsigned)std::min<int64_t>(grid_for(n / (16 / sizeof(R)) + 1, 256), 152 * 8);
+    k_level_sum<R><<<blocks, 256, 0, s>>>(ws, p->nlev, n, (int64_t)scan_row_stride(p, nrhs),
+                                          init_diag ? Vq : nullptr, (R)p->s2, Yq, gate);
     FGK_LAUNCH_CHECK();
     return FGK_OK;
 }

@@ -69,10 +69,12 @@ def test_preconditioned_gradient_matches_the_oracle(fgk_mod, orc):
         Bg = fgk.fgk_precond_sample(pc, to_dev(Er), to_dev(En))
         got = fgk.fgk_loglik_grad(h, to_dev(y), Bg, s2n, tol=1e-11, mode="f64", pc=pc)
     K = orc.kmat(p.X, p.nu, p.ell, s2=p.s2, kind=1)
-    L, _, _ = solve.pivoted_cholesky(lambda i: K[:, i], np.diag(K), k, forced=info["pivots"], tie_rtol=1e-9)
+    # (the library stores its factor in FP32, the recurrence run on the stored columns)
+    L, _, _ = solve.pivoted_cholesky(lambda i: K[:, i], np.diag(K), k, forced=info["pivots"], tie_rtol=1e-9,
+                                     tie_atol=1e-12 * K[0, 0], store=solve.f32_store)
     B = L @ Er + math.sqrt(s2n) * En
     ref, _ = _oracle_grad(orc, p, y, "product", s2n, p.ell, p.s2, B, lambda R: solve.woodbury_apply(L, s2n, R))
-    # the library's probes and P use the FP32 factor: agreement to its rounding
+    # the library's probes and P use its FP32-stored factor, which the oracle's reproduces
     np.testing.assert_allclose(got["grad"], ref, rtol=1e-5, atol=1e-6 * np.abs(ref).max())
 
 

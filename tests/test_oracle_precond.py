@@ -113,3 +113,29 @@ def test_forced_pivots_are_checked(orc):
     bad[3] = piv[0]  # an exhausted pivot is never a largest residual
     with pytest.raises(ValueError):
         solve.pivoted_cholesky(col, np.diag(K), 10, forced=bad)
+
+
+def test_factor_stored_in_fp32(orc):
+    """store = f32_store: every stored entry is an FP32 value; the
+    recurrence runs on the stored columns, so the residual diagonal is
+    exactly diag(K - L L^T) of the stored factor (each pivot the largest of
+    it), and the next columns take up each rounding: the residual trace at
+    the same rank equals the unrounded factor's to 1e-6."""
+    p = workloads.small(66, 500, 2, nu=1.5, ell=[0.15, 0.3], s2=1.7)
+    K = orc.kmat(p.X, p.nu, p.ell, s2=1.7, kind=1)
+    col = lambda i: K[:, i]  # noqa: E731
+    L, piv, dres = solve.pivoted_cholesky(col, np.diag(K), 80, store=solve.f32_store)
+    Lx, _, dx = solve.pivoted_cholesky(col, np.diag(K), 80)
+    assert np.array_equal(L.astype(np.float32).astype(np.float64), L)
+    assert np.allclose(dres, np.diag(K - L @ L.T), rtol=0, atol=1e-13)
+    for m in range(L.shape[1]):
+        rdiag = np.diag(K) - (L[:, :m] ** 2).sum(axis=1)
+        assert rdiag[piv[m]] >= rdiag.max() * (1 - 1e-12)
+    assert abs(dres.sum() - dx.sum()) <= 1e-6 * dx.sum()
+    # a matrix of exact rank 12 (12 points, each twice): the rounding of the
+    # stored columns leaves a residual that a few more columns take up
+    base = workloads.small(31, 12, 2, nu=1.5, ell=[0.3, 0.3])
+    X2 = np.concatenate([base.X, base.X])
+    K2 = orc.kmat(X2, 1.5, np.array([0.3, 0.3]), kind=1)
+    L2, _, d2 = solve.pivoted_cholesky(lambda i: K2[:, i], np.diag(K2), 40, store=solve.f32_store)
+    assert 12 <= L2.shape[1] < 24 and d2.max() <= 1e-12
