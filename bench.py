@@ -40,10 +40,17 @@ TOL = 1e-8
 WORKLOAD = ("d=2 N=200000 nu=3/2 ell=(0.1,0.3) x~U[0,1]^2 product kernel; "
             "CG (K+0.01I)alpha=y to FP64 true resid 1e-8; step = build + preconditioner + solve")
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# per-iteration kernels on this workload, from the committed ncu captures of
-# the kernels as built (a kernel missing here has no capture of its current
-# version)
-TRAFFIC_BYTES = {}
+# per-iteration kernels on this workload, by preconditioner rank, from the
+# committed ncu captures of the kernels as built
+# (profiles/pc_apply_and_scan_traffic_d2_N200k_rank350.txt; a kernel or rank
+# missing here has no capture of its current version)
+TRAFFIC_BYTES = {
+    350: {
+        "k_level_scan<float,P=2,NOFF=1,product,OUT>": 44142464 + 12672,
+        "k_pc_ltr (t = L^T r)": 281732864 + 808576,
+        "k_pc_apply (z = r/s2 - L c)": 281718400 + 702592,
+    },
+}
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -209,7 +216,9 @@ def paper_dc_timing(p, iters):
 def run_batched(args, local):
     """The batched workload: K problems (N log-uniform 1k-100k, d in {1,2},
     nu mixed, 16 N(0,1) right-hand sides each) solved in one batch (mixed
-    precision), against the plain per-problem FP64 solve on a sample."""
+    precision, rank --batched-rank preconditioners), against the same solves
+    one problem at a time: plain FP64, FP64 preconditioned, mixed
+    preconditioned, on every problem."""
     import torch
 
     import workloads
@@ -247,20 +256,34 @@ def run_batched(args, local):
         times.append(e0.elapsed_time(e1) / 1e3)
         assert rc == 0, infos
     t_batch = statistics.median(times)
-    # the plain per-problem FP64 GPU solve on a sample, extrapolated by size
-    sample = list(range(min(args.f64_sample, len(probs))))
-    t_f64 = 0.0
-    for i in sample:
-        p = probs[i]
+    # The same 64 x 16 solves one problem at a time on the same GPU, every
+    # problem (no sample, no extrapolation), three ways: the plain FP64 solve
+    # (no preconditioner: the baseline the batched form is set against), the
+    # FP64 solve with the same rank preconditioner, and the mixed solve with
+    # it; plans are built before timing (as the batch's are, in its setup) and
+    # preconditioner builds are timed (as the batch's are, inside its solve).
+    per = {"f64_plain": 0.0, "f64_precond": 0.0, "mixed_precond": 0.0}
+    iters = {k: 0 for k in per}
+    worst = {k: 0.0 for k in per}
+    for i, p in enumerate(probs):
         h = fgk.fgk_build(torch.as_tensor(p.X, device="cuda"), p.nu, p.ell, kind="product")
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        a, _, info, rc = fgk.fgk_cg_solve(h, ys[i], p.sigma2, tol=TOL, maxit=200000, mode="f64")
-        torch.cuda.synchronize()
-        t_f64 += time.perf_counter() - t1
+        k = min(args.batched_rank, p.N)
+        for key, mode, rk in (("f64_plain", "f64", 0), ("f64_precond", "f64", k), ("mixed_precond", "mixed", k)):
+            if args.f64_plain_max and key == "f64_plain" and i >= args.f64_plain_max:
+                continue
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            pc = fgk.fgk_precond_build(h, rk, p.sigma2) if rk > 0 else None
+            a, _, info, rc = fgk.fgk_cg_solve(h, ys[i], p.sigma2, tol=TOL, maxit=200000, mode=mode, precond=pc)
+            torch.cuda.synchronize()
+            per[key] += time.perf_counter() - t1
+            if pc is not None:
+                fgk.fgk_precond_destroy(pc)
+            assert rc == 0, (key, i, info)
+            iters[key] = max(iters[key], info["iterations"])
+            worst[key] = max(worst[key], info["max_true_resid"])
         fgk.fgk_destroy(h)
-    frac = sum(probs[i].N for i in sample) / rows
-    t_f64_all = t_f64 / frac if frac > 0 else float("nan")
+    n_plain = len(probs) if not args.f64_plain_max else min(args.f64_plain_max, len(probs))
     solves = len(probs) * nrhs
     out = {"metric": "batched: CG solves/sec at resid<=1e-8 (problems x rhs) and MVM N*nrhs/sec",
            "unit": "solves/s", "value": solves / t_batch, "problems": len(probs), "nrhs": nrhs,
@@ -269,8 +292,10 @@ def run_batched(args, local):
            "batch_solve_s": t_batch, "max_iterations": max(i["iterations"] for i in infos),
            "max_true_resid": max(i["max_true_resid"] for i in infos),
            "mvm_ms": mvm_ms, "mvm_nrhs_per_s": rows * nrhs / (mvm_ms * 1e-3),
-           "f64_per_problem": {"sample_problems": len(sample), "sample_s": t_f64,
-                               "extrapolated_s": t_f64_all, "solves_per_s": solves / t_f64_all},
+           "per_problem": {key: {"problems": (n_plain if key == "f64_plain" else len(probs)), "seconds": per[key],
+                                 "solves_per_s": (n_plain if key == "f64_plain" else len(probs)) * nrhs / per[key],
+                                 "max_iterations": iters[key], "max_true_resid": worst[key]}
+                           for key in per},
            "workload": "first %d problems of the seeded batched workload (N log-uniform 1k-100k, d in {1,2}, "
                        "nu in {1/2,3/2,5/2}, ell log-uniform 0.05-0.5, 16 N(0,1) rhs, sigma^2=0.01, product kernel)"
                        % len(probs)}
@@ -556,8 +581,8 @@ def main():
                     help="solve the first K problems of the batched workload (16 rhs each) in one batch")
     ap.add_argument("--batched-rank", type=int, default=100,
                     help="batched mode: preconditioner rank per problem (min with N/8; 0: none)")
-    ap.add_argument("--f64-sample", type=int, default=4,
-                    help="batched mode: problems solved one by one in FP64 for the comparison")
+    ap.add_argument("--f64-plain-max", type=int, default=0,
+                    help="--batched: solve only the first this-many problems with the plain FP64 solve (0: all)")
     ap.add_argument("--pcg-probe", type=int, default=0,
                     help="run only a short preconditioned solve with this rank (for ncu captures)")
     ap.add_argument("--pcg-maxit", type=int, default=40)
@@ -780,7 +805,7 @@ def main():
     dom = max(kernels, key=lambda k: kernels[k]["avg_launch_ms"])
     kd = kernels[dom]
     roofline = {"bound": "hbm", "achieved": kd["achieved_gbs"], "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": kd["frac"], "traffic": TRAFFIC_BYTES.get(dom), "kernel": dom,
+                "frac": kd["frac"], "traffic": TRAFFIC_BYTES.get(args.precond_rank, {}).get(dom), "kernel": dom,
                 "peak_source": f"{src} (hbm_gbs, copy burst)", "avg_launch_ms": kd["avg_launch_ms"],
                 "algorithmic_bytes_per_launch": kd["algorithmic_bytes_per_launch"], "per_iteration_kernels": kernels}
 

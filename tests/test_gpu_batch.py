@@ -141,3 +141,33 @@ def test_batch_pcg_meets_tolerance_in_fewer_iterations(fgk_mod, orc):
         assert eng.precs is first
     finally:
         eng.close()
+
+
+def test_full_batched_workload(fgk_mod, orc):
+    """The batched workload at its full size: 64 problems (N log-uniform 1k-100k,
+    d in {1, 2}, nu in {1/2, 3/2, 5/2}), 16 right-hand sides each, solved in one
+    batch with rank-100 preconditioners to 1e-8.  For every problem the
+    residual y - (K + sigma^2 I) alpha on 40 sampled rows, with K alpha from the
+    brute-force oracle, has norm at most 1e-8 ||y|| per column (a subset of the
+    rows cannot carry more than the whole residual), and the library's own
+    FP64 true residual is at most 1e-8."""
+    from paper_2508_01864_gb300 import batch as batchmod
+
+    probs = workloads.c4()
+    assert len(probs) == 64 and probs[0].V.shape[1] == 16
+    ys = [to_dev(p.V) for p in probs]
+    sig = [p.sigma2 for p in probs]
+    eng = batchmod.BatchEngine(probs, 16, kind="product", precond_rank=100)
+    try:
+        alphas, infos, rc = eng.solve(ys, sig, tol=1e-8, maxit=200000)
+        assert rc == 0
+        rng = np.random.default_rng(64)
+        for p, a, s, info in zip(probs, alphas, sig, infos):
+            assert info["max_true_resid"] <= 1e-8, info
+            a = a.cpu().numpy()
+            rows = np.sort(rng.choice(p.N, size=min(40, p.N), replace=False))
+            Ka = orc.mvm_brute(p.X, a, p.nu, p.ell, kind=1, rows=rows)
+            r = p.V[rows] - Ka - s * a[rows]
+            assert (np.linalg.norm(r, axis=0) <= 1e-8 * np.linalg.norm(p.V, axis=0)).all(), p.name
+    finally:
+        eng.close()
