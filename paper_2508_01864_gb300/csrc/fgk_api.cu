@@ -155,10 +155,12 @@ int build_worklists(Plan *p) {
     const int ntiles = (int)((N + kTile - 1) / kTile);
     std::vector<WorkItem> items, longs;
     std::vector<int32_t> segs;
+    std::vector<uint32_t> map_long, map_short;
     int slot = 0;
     for (int lev = 0; lev < p->nlev; ++lev) {
         const int log2S = p->lev_log2S[lev];
         const int64_t S = int64_t(1) << log2S;
+        (S <= kTile ? map_short : map_long).push_back((uint32_t)lev | ((uint32_t)log2S << 16));
         if (S <= kTile) {
             for (int t = 0; t < ntiles; ++t) items.push_back(WorkItem{lev, t, -1, 0, 0, log2S});
         } else {
@@ -182,6 +184,20 @@ int build_worklists(Plan *p) {
     p->n_long = (int)longs.size();
     p->n_long_segments = (int)(segs.size() / 2);
     p->long_seg_host = segs;
+    p->ntiles = ntiles;
+    // the kernels find their work item from the block index: level rows of
+    // ntiles blocks each, in the order of the list (long levels first)
+    std::vector<uint32_t> map = map_long;
+    map.insert(map.end(), map_short.begin(), map_short.end());
+    if (p->nlev > 0xffff) {
+        set_error("fgk_build: %d levels exceed the level map", p->nlev);
+        return FGK_ERR_INVALID;
+    }
+    if (!map.empty()) {
+        FGK_TRY(plan_alloc(p, (void **)&p->lv_map, sizeof(uint32_t) * map.size()));
+        FGK_CUDA(cudaMemcpyAsync(p->lv_map, map.data(), sizeof(uint32_t) * map.size(), cudaMemcpyHostToDevice,
+                                 p->stream));
+    }
     if (p->n_items) {
         FGK_TRY(plan_alloc(p, (void **)&p->items, sizeof(WorkItem) * all.size()));
         FGK_CUDA(cudaMemcpyAsync(p->items, all.data(), sizeof(WorkItem) * all.size(), cudaMemcpyHostToDevice,

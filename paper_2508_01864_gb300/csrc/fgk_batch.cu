@@ -91,6 +91,9 @@ __global__ void __launch_bounds__(kScanThreads, FGK_SCAN_MINB) k_batch_scan(Batc
     A.ldN = pr.ldN;
     A.nlev = pr.nlev;
     A.items = nullptr;
+    A.lv_map = nullptr;  // the work item comes from the batch list
+    A.ntiles = 0;
+    A.n_long = 0;
     A.V = B.V + pr.voff * B.nrhs;
     A.nrhs = B.nrhs;
     A.Y = B.Y + pr.voff * B.nrhs;

@@ -141,6 +141,8 @@ struct Plan {
     WorkItem *items = nullptr;     // all items
     WorkItem *long_items = nullptr;
     int n_items = 0, n_long = 0;
+    int ntiles = 0;                // tiles per level
+    uint32_t *lv_map = nullptr;    // per block row of the lists: level | log2S << 16 (long levels first)
     int n_long_segments = 0;
     std::vector<int32_t> long_seg_host;  // [first agg, n tiles] per long segment
     int32_t *long_seg = nullptr;

@@ -99,6 +99,13 @@ struct ScanArgs {
     int64_t ldN;
     int nlev;
     const WorkItem *items;
+    // the work item of block k, without a load per block: k / ntiles indexes
+    // lv_map (level | log2S << 16, the long-segment levels first), the tile is
+    // k mod ntiles, and the first n_long blocks are the long-segment tiles with
+    // aggregate slot k
+    const uint32_t *lv_map;
+    int ntiles;
+    int n_long;
     const R *V;  // q order, N x nrhs, in the scan precision
     int nrhs;
     R *Y;      // q order, N x nrhs: accumulated atomically when rows == NULL
@@ -168,6 +175,50 @@ __device__ __forceinline__ void step_all(R *M, R T, R E) {
 #pragma unroll
     for (int a = 0; a < MOM / P; ++a) step_group<R, P>(M + a * P, T, E);
 }
+
+// One group of P moments kept relative to an anchor behind the current
+// position (m~ = e^{+X} m, X the distance from the anchor): a step by G
+// shifts only the polynomial part, m~_q <- sum_{t<=q} C(q,t) G^{q-t} m~_t.
+template <class R, int P>
+__device__ __forceinline__ void astep_group(R *m, R G) {
+    if constexpr (P == 2) {
+        m[1] = fma(G, m[0], m[1]);
+    } else if constexpr (P == 3) {
+        const R gm0 = G * m[0];
+        m[2] = fma(G, fma(R(2), m[1], gm0), m[2]);
+        m[1] += gm0;
+    } else if constexpr (P > 3) {
+        R Gk[P];
+        Gk[0] = R(1);
+#pragma unroll
+        for (int k = 1; k < P; ++k) Gk[k] = Gk[k - 1] * G;
+#pragma unroll
+        for (int q = P - 1; q >= 1; --q) {
+            R acc = m[q];
+#pragma unroll
+            for (int t = 0; t < q; ++t) acc += R(binom_c(q, t)) * Gk[q - t] * m[t];
+            m[q] = acc;
+        }
+    }
+}
+
+template <class R, int P, int MOM>
+__device__ __forceinline__ void astep_all(R *M, R G) {
+#pragma unroll
+    for (int a = 0; a < MOM / P; ++a) astep_group<R, P>(M + a * P, G);
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ double rcp_approx(double x) { return 1.0 / x; }
+
+// a thread's anchored walk is used when the gaps between its entries sum to
+// at most this (scaled units): e^{+X} <= e^{30} ~ 1e13 keeps every anchored
+// moment far from the FP32 range limit
+constexpr float kAnchorSpan = 30.0f;
 
 // coefficients u_j(o) = e^{-o} sum_{p>=j} c_p C(p,j) o^{p-j}
 template <class R, int P>
@@ -376,8 +427,26 @@ __device__ __forceinline__ void set_identity(R *x) {
 // (MODE == SCAN_AGG writes each tile's totals; k_carry_scan scans them).
 // ROWS: the output pass stores into the level rows (A.rows); otherwise it adds
 // into Y atomically (the batched products).
+//
+// Anchored fold and walk (FP32).  Within one thread's entries the moments
+// may be kept relative to the thread's first entry in walk order instead of
+// the current one, m~ = e^{+X} M with X the distance walked since that entry:
+// a step by a gap G then only shifts the polynomial part (astep_group, no
+// decay), a source enters scaled by e^{+X}, a query's read is scaled by
+// e^{-X}, and the fold's total is scaled back by e^{-X} once.  e^{-X} is the
+// running product of the entries' decays e^{-g} (the factors the plain walk
+// multiplies by), e^{+X} its reciprocal.  A warp takes this form when each of
+// its threads' gaps sum to at most kAnchorSpan; the step into the first entry
+// is always the plain one.
+// The arithmetic of one tile, from this thread's entries (q, gaps, offsets,
+// the first column's operands, and for lane 31 the gap into the entry after
+// its last one) already in registers; entries past the level's end carry
+// q = 0, zero gaps and offsets and zero operands.
 template <class R, int P, int NOFF, int KIND, int MODE, bool GEN = false, bool ROWS = true>
-__device__ __forceinline__ void scan_tile(const ScanArgs<R> &A, const WorkItem wi, int r0, int r1) {
+__device__ __forceinline__ void scan_compute(const ScanArgs<R> &A, const WorkItem wi, int r0, int r1,
+                                             const uint32_t (&q)[kScanEPT], const R (&g)[kScanEPT],
+                                             const R (&o)[NOFF > 0 ? NOFF : 1][kScanEPT],
+                                             const R (&vpre)[kScanEPT], R gn31) {
     using Tr = Traits<P, NOFF, KIND>;
     constexpr int GM = Tr::GM, CP = Tr::CP, SMM = Tr::SM, AG = Tr::AG, NCH = Tr::NCH;
     constexpr int NGP = Tr::NGP, NPT = Tr::NPT, NWC = Tr::NWC;
@@ -385,10 +454,12 @@ __device__ __forceinline__ void scan_tile(const ScanArgs<R> &A, const WorkItem w
     constexpr int EPT = kScanEPT, NT = kScanThreads, NW = NT / 32;
     constexpr int LOG2EPT = (EPT == 8) ? 3 : (EPT == 4 ? 2 : (EPT == 16 ? 4 : 0));
     constexpr int NO = NOFF > 0 ? NOFF : 1;
+    constexpr bool ANCH = std::is_same<R, float>::value && !GEN && NOFF < 2;
     static_assert((1 << LOG2EPT) == EPT, "EPT must be 4, 8 or 16");
     static_assert(EPT == 8, "vector loads assume 8 entries per thread");
     __shared__ R s_w[ND][NW][AG];
     __shared__ R s_pre[ND][NW][AG];  // SCAN_OUT: exclusive prefixes of the warp totals
+    __shared__ R s_car[2][AG];       // SCAN_OUT, long segments: the tile's carries (both directions)
 
     const int64_t N = A.N;
     const int64_t base = (int64_t)wi.tile * kTile;
@@ -400,61 +471,9 @@ __device__ __forceinline__ void scan_tile(const ScanArgs<R> &A, const WorkItem w
     const int64_t p0 = base + j0;
     const int nvalid = (int)(N - p0 < 0 ? 0 : (N - p0 > EPT ? EPT : N - p0));
 
-    // ---- this thread's entries (the level stride keeps 8-entry groups aligned)
-    uint32_t q[EPT];
-    R g[EPT], eg[EPT], o[NO][EPT], eo[NO][EPT];
-    R vpre[EPT];  // the first column's operands, gathered as soon as q is known (0 on padding:
-                  // the fold inserts padding entries as zero-weight sources)
-#pragma unroll
-    for (int i = 0; i < EPT; ++i) vpre[i] = R(0);
-    if (nvalid > 0) {
-        const uint4 *qp = reinterpret_cast<const uint4 *>(A.lv_q + lo + p0);
-        const uint4 qa = qp[0], qb = qp[1];
-        q[0] = qa.x; q[1] = qa.y; q[2] = qa.z; q[3] = qa.w;
-        q[4] = qb.x; q[5] = qb.y; q[6] = qb.z; q[7] = qb.w;
-#pragma unroll
-        for (int i = 0; i < EPT; ++i)
-            vpre[i] = (i < nvalid && r0 < r1) ? A.V[(size_t)(q[i] & 0x3fffffffu) * A.nrhs + r0] : R(0);
-        if constexpr (sizeof(R) == 4) {
-            const float4 *gp = reinterpret_cast<const float4 *>(A.lv_dl + lo + p0);
-            const float4 ga = gp[0], gb = gp[1];
-            g[0] = ga.x; g[1] = ga.y; g[2] = ga.z; g[3] = ga.w;
-            g[4] = gb.x; g[5] = gb.y; g[6] = gb.z; g[7] = gb.w;
-#pragma unroll
-            for (int k = 0; k < NOFF; ++k) {
-                const float4 *op = reinterpret_cast<const float4 *>(A.lv_off + ((size_t)k * A.nlev) * A.ldN + lo + p0);
-                const float4 oa = op[0], ob = op[1];
-                o[k][0] = oa.x; o[k][1] = oa.y; o[k][2] = oa.z; o[k][3] = oa.w;
-                o[k][4] = ob.x; o[k][5] = ob.y; o[k][6] = ob.z; o[k][7] = ob.w;
-            }
-        } else {
-            const double2 *gp = reinterpret_cast<const double2 *>(A.lv_dl + lo + p0);
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const double2 x = gp[h];
-                g[2 * h] = x.x;
-                g[2 * h + 1] = x.y;
-            }
-#pragma unroll
-            for (int k = 0; k < NOFF; ++k) {
-                const double2 *op = reinterpret_cast<const double2 *>(A.lv_off + ((size_t)k * A.nlev) * A.ldN + lo + p0);
-#pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const double2 x = op[h];
-                    o[k][2 * h] = x.x;
-                    o[k][2 * h + 1] = x.y;
-                }
-            }
-        }
-    }
+    R eg[EPT], eo[NO][EPT];
 #pragma unroll
     for (int i = 0; i < EPT; ++i) {
-        if (i >= nvalid) {  // padding: identity steps, no role
-            q[i] = 0;
-            g[i] = R(0);
-#pragma unroll
-            for (int k = 0; k < NOFF; ++k) o[k][i] = R(0);
-        }
         eg[i] = exp_neg<R>(g[i]);
 #pragma unroll
         for (int k = 0; k < NOFF; ++k) eo[k][i] = exp_neg<R>(o[k][i]);
@@ -463,10 +482,15 @@ __device__ __forceinline__ void scan_tile(const ScanArgs<R> &A, const WorkItem w
     R gn = __shfl_down_sync(0xffffffffu, g[0], 1);
     R egn = __shfl_down_sync(0xffffffffu, eg[0], 1);
     if (lane == 31) {
-        const int64_t pn = p0 + EPT;
-        gn = pn < N ? A.lv_dl[lo + pn] : R(0);
+        gn = gn31;
         egn = exp_neg<R>(gn);
     }
+    // the gaps between this thread's entries (the same in both walk directions)
+    R span = R(0);
+#pragma unroll
+    for (int i = 1; i < EPT; ++i) span += g[i];
+    bool fast = false;
+    if constexpr (ANCH) fast = __all_sync(0xffffffffu, span <= R(kAnchorSpan));
 
     const bool multi = log2S < LOG2EPT;  // whole segments inside one thread
     const int G = multi ? 1 : (int)((S >> LOG2EPT) < (int64_t)NT ? (S >> LOG2EPT) : (int64_t)NT);
@@ -486,6 +510,15 @@ __device__ __forceinline__ void scan_tile(const ScanArgs<R> &A, const WorkItem w
             const int a0 = NGP == 1 ? 0 : (pq % NGP) * Tr::GP;  // first offset-power group of the pass
             const int cA = pp;
             const int cB = NOFF == 0 ? 0 : (cA ^ (NCH - 1));
+            // a long tile's carries (both directions), read now and parked in shared
+            // memory before the first barrier below, so the load is hidden by the fold
+            R cpf = R(0);
+            if constexpr (MODE == SCAN_OUT) {
+                if (is_long && tid < 2 * AG) {
+                    const int cdir = tid / AG;
+                    cpf = A.agg[((((size_t)wi.agg * 2 + cdir) * A.nrhs + r) * NPT + pq) * AG + (tid - cdir * AG)];
+                }
+            }
 #pragma unroll
             for (int dp = 0; dp < NDP; ++dp) {
                 R ex[ND][AG];
@@ -496,27 +529,60 @@ __device__ __forceinline__ void scan_tile(const ScanArgs<R> &A, const WorkItem w
                     R inc[ND][AG];
 #pragma unroll
                     for (int dd = 0; dd < ND; ++dd) set_identity<R, AG>(inc[dd]);
+                    auto fold = [&](auto anch) {
+                        constexpr bool AN = decltype(anch)::value;
+                        R Rr[ND];
 #pragma unroll
-                    for (int ii = 0; ii < EPT; ++ii) {
+                        for (int dd = 0; dd < ND; ++dd) Rr[dd] = R(1);
 #pragma unroll
-                        for (int dd = 0; dd < ND; ++dd) {
-                            const int dir = ND == 2 ? dd : dp;
-                            const int i = dir == 0 ? ii : EPT - 1 - ii;
-                            const R gg = dir == 0 ? g[i] : (i < EPT - 1 ? g[i + 1] : gn);
-                            const R ee = dir == 0 ? eg[i] : (i < EPT - 1 ? eg[i + 1] : egn);
-                            step_all<R, P, SMM>(inc[dd] + 1, gg, ee);
-                            inc[dd][0] += gg;
-                            const int role = NOFF == 0 ? 0 : (int)(q[i] >> (32 - NOFF));
-                            R oi[NO], eoi[NO], w[NWC], u[NWC];
+                        for (int ii = 0; ii < EPT; ++ii) {
 #pragma unroll
-                            for (int k = 0; k < NO; ++k) {
-                                oi[k] = NOFF ? o[k][i] : R(0);
-                                eoi[k] = NOFF ? eo[k][i] : R(1);
+                            for (int dd = 0; dd < ND; ++dd) {
+                                const int dir = ND == 2 ? dd : dp;
+                                const int i = dir == 0 ? ii : EPT - 1 - ii;
+                                const R gg = dir == 0 ? g[i] : (i < EPT - 1 ? g[i + 1] : gn);
+                                const R ee = dir == 0 ? eg[i] : (i < EPT - 1 ? eg[i + 1] : egn);
+                                R vi = v[i];
+                                if constexpr (AN) {
+                                    // the first entry starts from the identity: nothing to step
+                                    if (ii > 0) {
+                                        astep_all<R, P, SMM>(inc[dd] + 1, gg);
+                                        Rr[dd] *= ee;
+                                        vi *= rcp_approx(Rr[dd]);
+                                    }
+                                } else {
+                                    step_all<R, P, SMM>(inc[dd] + 1, gg, ee);
+                                    inc[dd][0] += gg;
+                                }
+                                const int role = NOFF == 0 ? 0 : (int)(q[i] >> (32 - NOFF));
+                                R oi[NO], eoi[NO], w[NWC], u[NWC];
+#pragma unroll
+                                for (int k = 0; k < NO; ++k) {
+                                    oi[k] = NOFF ? o[k][i] : R(0);
+                                    eoi[k] = NOFF ? eo[k][i] : R(1);
+                                }
+                                pass_coef<R, P, NOFF, KIND, GEN>(a0, oi, eoi, w, u, A.cf);
+                                add_pass<R, P, NOFF, KIND>(inc[dd] + 1, role == cA ? vi : R(0), w);
+                                if constexpr (CP == 2) add_pass<R, P, NOFF, KIND>(inc[dd] + 1 + GM, role == cB ? vi : R(0), w);
                             }
-                            pass_coef<R, P, NOFF, KIND, GEN>(a0, oi, eoi, w, u, A.cf);
-                            add_pass<R, P, NOFF, KIND>(inc[dd] + 1, role == cA ? v[i] : R(0), w);
-                            if constexpr (CP == 2) add_pass<R, P, NOFF, KIND>(inc[dd] + 1 + GM, role == cB ? v[i] : R(0), w);
                         }
+                        if constexpr (AN) {
+#pragma unroll
+                            for (int dd = 0; dd < ND; ++dd) {
+                                const int dir = ND == 2 ? dd : dp;
+#pragma unroll
+                                for (int m = 0; m < SMM; ++m) inc[dd][1 + m] *= Rr[dd];
+                                inc[dd][0] = (dir == 0 ? g[0] : gn) + span;
+                            }
+                        }
+                    };
+                    if constexpr (ANCH) {
+                        if (fast)
+                            fold(std::true_type{});
+                        else
+                            fold(std::false_type{});
+                    } else {
+                        fold(std::false_type{});
                     }
                     // 2. inclusive scan over the threads of each segment (virtual lanes)
                     for (int dlt = 1; dlt < GW; dlt <<= 1) {
@@ -562,14 +628,17 @@ __device__ __forceinline__ void scan_tile(const ScanArgs<R> &A, const WorkItem w
                                 for (int m = 0; m < AG; ++m) s_w[dd][vwarp][m] = inc[dd][m];
                             }
                         }
+                        if (MODE == SCAN_OUT && dp == 0 && is_long && tid < 2 * AG) {
+                            const int cdir = tid / AG;
+                            s_car[cdir][tid - cdir * AG] = cpf;
+                        }
                         __syncthreads();
 #pragma unroll
                         for (int dd = 0; dd < ND; ++dd) {
                             const int dir = ND == 2 ? dd : dp;
-                            const int vwarp = dir == 0 ? warp : NW - 1 - warp;
-                            const size_t cslot = ((((size_t)wi.agg * 2 + dir) * A.nrhs + r) * NPT + pq) * AG;
                             if (MODE == SCAN_AGG) {
                                 if (tid == dd * 32) {  // the tile's total
+                                    const size_t cslot = ((((size_t)wi.agg * 2 + dir) * A.nrhs + r) * NPT + pq) * AG;
                                     R run[AG];
                                     set_identity<R, AG>(run);
                                     for (int w2 = 0; w2 < NW; ++w2) {
@@ -605,7 +674,7 @@ __device__ __forceinline__ void scan_tile(const ScanArgs<R> &A, const WorkItem w
                                 if (is_long) {
                                     R carry[AG];
 #pragma unroll
-                                    for (int m = 0; m < AG; ++m) carry[m] = A.agg[cslot + m];
+                                    for (int m = 0; m < AG; ++m) carry[m] = s_car[dir][m];
                                     compose_after<R, P, AG>(e, carry);
                                 }
                                 if (lane < NW) {
@@ -636,46 +705,70 @@ __device__ __forceinline__ void scan_tile(const ScanArgs<R> &A, const WorkItem w
                     for (int dd = 0; dd < ND; ++dd)
 #pragma unroll
                         for (int m = 0; m < SMM; ++m) st[dd][m] = ex[dd][1 + m];
+                    auto walk = [&](auto anch) {
+                        constexpr bool AN = decltype(anch)::value;
+                        R Rr[ND];
 #pragma unroll
-                    for (int ii = 0; ii < EPT; ++ii) {
+                        for (int dd = 0; dd < ND; ++dd) Rr[dd] = R(1);
 #pragma unroll
-                        for (int dd = 0; dd < ND; ++dd) {
-                            const int dir = ND == 2 ? dd : dp;
-                            const int i = dir == 0 ? ii : EPT - 1 - ii;
-                            if (multi) {
-                                const int jj = j0 + i;
-                                const bool seg_start = dir == 0 ? (jj & (S - 1)) == 0 : ((jj + 1) & (S - 1)) == 0;
-                                if (seg_start) {
+                        for (int ii = 0; ii < EPT; ++ii) {
 #pragma unroll
-                                    for (int m = 0; m < SMM; ++m) st[dd][m] = R(0);
+                            for (int dd = 0; dd < ND; ++dd) {
+                                const int dir = ND == 2 ? dd : dp;
+                                const int i = dir == 0 ? ii : EPT - 1 - ii;
+                                if (multi) {
+                                    const int jj = j0 + i;
+                                    const bool seg_start = dir == 0 ? (jj & (S - 1)) == 0 : ((jj + 1) & (S - 1)) == 0;
+                                    if (seg_start) {
+#pragma unroll
+                                        for (int m = 0; m < SMM; ++m) st[dd][m] = R(0);
+                                    }
+                                }
+                                const R gg = dir == 0 ? g[i] : (i < EPT - 1 ? g[i + 1] : gn);
+                                const R ee = dir == 0 ? eg[i] : (i < EPT - 1 ? eg[i + 1] : egn);
+                                R vi = v[i];
+                                if (AN && ii > 0) {
+                                    astep_all<R, P, SMM>(st[dd], gg);
+                                    Rr[dd] *= ee;
+                                    vi *= rcp_approx(Rr[dd]);
+                                } else {
+                                    step_all<R, P, SMM>(st[dd], gg, ee);
+                                }
+                                const int role = NOFF == 0 ? 0 : (int)(q[i] >> (32 - NOFF));
+                                R oi[NO], eoi[NO], w[NWC], u[NWC];
+#pragma unroll
+                                for (int k = 0; k < NO; ++k) {
+                                    oi[k] = NOFF ? o[k][i] : R(0);
+                                    eoi[k] = NOFF ? eo[k][i] : R(1);
+                                }
+                                pass_coef<R, P, NOFF, KIND, GEN>(a0, oi, eoi, w, u, A.cf);
+                                // padding entries read into slots that are never stored and
+                                // insert zero
+                                if constexpr (CP == 1) {
+                                    const R rd = read_pass<R, P, NOFF, KIND, GEN>(st[dd], u, A.cf);
+                                    out[i] = AN ? fma(Rr[dd], rd, out[i]) : out[i] + rd;
+                                    add_pass<R, P, NOFF, KIND>(st[dd], vi, w);
+                                } else {
+                                    const bool sa = role == cA, sb = role == cB;
+                                    R msel[GM];
+#pragma unroll
+                                    for (int m = 0; m < GM; ++m) msel[m] = sa ? st[dd][GM + m] : st[dd][m];
+                                    R rd = read_pass<R, P, NOFF, KIND, GEN>(msel, u, A.cf);
+                                    if constexpr (NOFF == 2) rd = (sa || sb) ? rd : R(0);
+                                    out[i] = AN ? fma(Rr[dd], rd, out[i]) : out[i] + rd;
+                                    add_pass<R, P, NOFF, KIND>(st[dd], sa ? vi : R(0), w);
+                                    add_pass<R, P, NOFF, KIND>(st[dd] + GM, sb ? vi : R(0), w);
                                 }
                             }
-                            const R gg = dir == 0 ? g[i] : (i < EPT - 1 ? g[i + 1] : gn);
-                            const R ee = dir == 0 ? eg[i] : (i < EPT - 1 ? eg[i + 1] : egn);
-                            step_all<R, P, SMM>(st[dd], gg, ee);
-                            const bool ok = i < nvalid;
-                            const int role = NOFF == 0 ? 0 : (int)(q[i] >> (32 - NOFF));
-                            R oi[NO], eoi[NO], w[NWC], u[NWC];
-#pragma unroll
-                            for (int k = 0; k < NO; ++k) {
-                                oi[k] = NOFF ? o[k][i] : R(0);
-                                eoi[k] = NOFF ? eo[k][i] : R(1);
-                            }
-                            pass_coef<R, P, NOFF, KIND, GEN>(a0, oi, eoi, w, u, A.cf);
-                            if constexpr (CP == 1) {
-                                if (ok) out[i] += read_pass<R, P, NOFF, KIND, GEN>(st[dd], u, A.cf);
-                                add_pass<R, P, NOFF, KIND>(st[dd], ok ? v[i] : R(0), w);
-                            } else {
-                                const bool sa = ok && role == cA, sb = ok && role == cB;
-                                R msel[GM];
-#pragma unroll
-                                for (int m = 0; m < GM; ++m) msel[m] = sa ? st[dd][GM + m] : st[dd][m];
-                                const R rd = read_pass<R, P, NOFF, KIND, GEN>(msel, u, A.cf);
-                                out[i] += (sa || sb) ? rd : R(0);
-                                add_pass<R, P, NOFF, KIND>(st[dd], sa ? v[i] : R(0), w);
-                                add_pass<R, P, NOFF, KIND>(st[dd] + GM, sb ? v[i] : R(0), w);
-                            }
                         }
+                    };
+                    if constexpr (ANCH) {
+                        if (fast)
+                            walk(std::true_type{});
+                        else
+                            walk(std::false_type{});
+                    } else {
+                        walk(std::false_type{});
                     }
                 }
             }
@@ -699,10 +792,115 @@ __device__ __forceinline__ void scan_tile(const ScanArgs<R> &A, const WorkItem w
     }
 }
 
+template <class R, int P, int NOFF, int KIND, int MODE, bool GEN = false, bool ROWS = true>
+__device__ __forceinline__ void scan_tile(const ScanArgs<R> &A, const WorkItem wi, int r0, int r1) {
+    using Tr = Traits<P, NOFF, KIND>;
+    constexpr int GM = Tr::GM, CP = Tr::CP, SMM = Tr::SM, AG = Tr::AG, NCH = Tr::NCH;
+    constexpr int NGP = Tr::NGP, NPT = Tr::NPT, NWC = Tr::NWC;
+    constexpr int ND = Tr::NDIR, NDP = 2 / ND;  // directions per walk, direction passes
+    constexpr int EPT = kScanEPT, NT = kScanThreads, NW = NT / 32;
+    constexpr int LOG2EPT = (EPT == 8) ? 3 : (EPT == 4 ? 2 : (EPT == 16 ? 4 : 0));
+    constexpr int NO = NOFF > 0 ? NOFF : 1;
+    constexpr bool ANCH = std::is_same<R, float>::value && !GEN && NOFF < 2;
+    static_assert((1 << LOG2EPT) == EPT, "EPT must be 4, 8 or 16");
+    static_assert(EPT == 8, "vector loads assume 8 entries per thread");
+
+    const int64_t N = A.N;
+    const int64_t base = (int64_t)wi.tile * kTile;
+    const int log2S = wi.log2S;
+    const int64_t S = int64_t(1) << log2S;
+    const size_t lo = (size_t)wi.level * A.ldN;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int j0 = tid * EPT;
+    const int64_t p0 = base + j0;
+    const int nvalid = (int)(N - p0 < 0 ? 0 : (N - p0 > EPT ? EPT : N - p0));
+
+    // ---- this thread's entries (the level stride keeps 8-entry groups aligned)
+    uint32_t q[EPT];
+    R g[EPT], o[NO][EPT];
+    R vpre[EPT];  // the first column's operands (0 on padding: the fold inserts padding entries as
+                  // zero-weight sources)
+    if (nvalid > 0) {
+        const uint4 *qp = reinterpret_cast<const uint4 *>(A.lv_q + lo + p0);
+        const uint4 qa = qp[0], qb = qp[1];
+        q[0] = qa.x; q[1] = qa.y; q[2] = qa.z; q[3] = qa.w;
+        q[4] = qb.x; q[5] = qb.y; q[6] = qb.z; q[7] = qb.w;
+        if constexpr (sizeof(R) == 4) {
+            const float4 *gp = reinterpret_cast<const float4 *>(A.lv_dl + lo + p0);
+            const float4 ga = gp[0], gb = gp[1];
+            g[0] = ga.x; g[1] = ga.y; g[2] = ga.z; g[3] = ga.w;
+            g[4] = gb.x; g[5] = gb.y; g[6] = gb.z; g[7] = gb.w;
+#pragma unroll
+            for (int k = 0; k < NOFF; ++k) {
+                const float4 *op = reinterpret_cast<const float4 *>(A.lv_off + ((size_t)k * A.nlev) * A.ldN + lo + p0);
+                const float4 oa = op[0], ob = op[1];
+                o[k][0] = oa.x; o[k][1] = oa.y; o[k][2] = oa.z; o[k][3] = oa.w;
+                o[k][4] = ob.x; o[k][5] = ob.y; o[k][6] = ob.z; o[k][7] = ob.w;
+            }
+        } else {
+            const double2 *gp = reinterpret_cast<const double2 *>(A.lv_dl + lo + p0);
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const double2 x = gp[h];
+                g[2 * h] = x.x;
+                g[2 * h + 1] = x.y;
+            }
+#pragma unroll
+            for (int k = 0; k < NOFF; ++k) {
+                const double2 *op = reinterpret_cast<const double2 *>(A.lv_off + ((size_t)k * A.nlev) * A.ldN + lo + p0);
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const double2 x = op[h];
+                    o[k][2 * h] = x.x;
+                    o[k][2 * h + 1] = x.y;
+                }
+            }
+        }
+    }
+    // the gate word is read while the entries are in flight and tested below
+    const int gate_on = A.gate ? *A.gate : 1;
+    if (nvalid < EPT) {  // past the level's end: identity steps, no role, no weight
+#pragma unroll
+        for (int i = 0; i < EPT; ++i) {
+            if (i >= nvalid) {
+                q[i] = 0;
+                g[i] = R(0);
+#pragma unroll
+                for (int k = 0; k < NOFF; ++k) o[k][i] = R(0);
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < EPT; ++i)
+        vpre[i] = (i < nvalid && r0 < r1) ? A.V[(size_t)(q[i] & 0x3fffffffu) * A.nrhs + r0] : R(0);
+    R gn31 = R(0);
+    if (lane == 31) {
+        const int64_t pn = p0 + EPT;
+        gn31 = pn < N ? A.lv_dl[lo + pn] : R(0);
+    }
+    if (!gate_on) return;  // uniform over the CTA
+    scan_compute<R, P, NOFF, KIND, MODE, GEN, ROWS>(A, wi, r0, r1, q, g, o, vpre, gn31);
+}
+
+// the work item of list position k (block rows of ntiles tiles per level, the
+// long-segment levels first; their tiles own aggregate slot k)
+template <class R>
+__device__ __forceinline__ WorkItem item_of(const ScanArgs<R> &A, int k) {
+    const int slot = k / A.ntiles;
+    const uint32_t lm = __ldg(A.lv_map + slot);
+    WorkItem wi;
+    wi.level = (int)(lm & 0xffffu);
+    wi.log2S = (int)(lm >> 16);
+    wi.tile = k - slot * A.ntiles;
+    wi.agg = k < A.n_long ? k : -1;
+    wi.seg_tile0 = 0;
+    wi.seg_ntiles = 0;
+    return wi;
+}
+
 template <class R, int P, int NOFF, int KIND, int MODE, bool GEN = false>
 __global__ void __launch_bounds__(kScanThreads, GEN ? 1 : FGK_SCAN_MINB) k_level_scan(ScanArgs<R> A) {
-    if (A.gate && *A.gate == 0) return;
-    scan_tile<R, P, NOFF, KIND, MODE, GEN>(A, A.items[blockIdx.x], 0, A.nrhs);
+    scan_tile<R, P, NOFF, KIND, MODE, GEN>(A, item_of(A, blockIdx.x), 0, A.nrhs);
 }
 
 // one warp: exclusive carries of one long segment (tiles a0 .. a0+nt-1 of the
@@ -839,6 +1037,13 @@ inline size_t scan_ws_elems_for(const Plan *p, int nrhs, int P, int kind) {
 // Yq += levels.
 // preload: only make the runtime load the kernels this product would launch
 // (their attributes are queried), so that a later product loads nothing.
+template <class R, int P, int NOFF, int KIND, int MODE, bool GEN>
+int launch_scan(const ScanArgs<R> &A, int nitems, cudaStream_t s) {
+    k_level_scan<R, P, NOFF, KIND, MODE, GEN><<<nitems, kScanThreads, 0, s>>>(A);
+    FGK_LAUNCH_CHECK();
+    return FGK_OK;
+}
+
 template <class R, int P, int NOFF, int KIND, bool GEN = false>
 int run_levels(Plan *p, const R *Vq, int nrhs, R *Yq, R *ws, cudaStream_t s, const int *gate, bool init_diag,
                const double (*cf)[kMaxCoef] = nullptr, bool preload = false) {
@@ -875,14 +1080,16 @@ int run_levels(Plan *p, const R *Vq, int nrhs, R *Yq, R *ws, cudaStream_t s, con
     A.s2 = (R)p->s2;
     A.err = p->dev_err;
     A.gate = gate;
+    A.lv_map = p->lv_map;
+    A.ntiles = p->ntiles;
+    A.n_long = p->n_long;
     const size_t per_slot = (size_t)2 * nrhs * Tr::NPT * Tr::AG;
     R *agg = ws + scan_rows_elems(p, nrhs);
     R *carry = agg + (size_t)p->n_long * per_slot;
     if (p->n_long > 0) {
         A.items = p->long_items;
         A.agg = agg;
-        k_level_scan<R, P, NOFF, KIND, SCAN_AGG, GEN><<<p->n_long, kScanThreads, 0, s>>>(A);
-        FGK_LAUNCH_CHECK();
+        FGK_TRY((launch_scan<R, P, NOFF, KIND, SCAN_AGG, GEN>(A, p->n_long, s)));
         const int64_t nthr = (int64_t)p->n_long_segments * 2 * nrhs * Tr::NPT * 32;
         k_carry_scan<R, P, NOFF, KIND><<<grid_for(nthr, 128), 128, 0, s>>>(agg, carry, p->long_seg,
                                                                            p->n_long_segments, nrhs, gate);
@@ -899,8 +1106,7 @@ int run_levels(Plan *p, const R *Vq, int nrhs, R *Yq, R *ws, cudaStream_t s, con
             FGK_CUDA(cudaEventCreate(&e1));
             FGK_CUDA(cudaEventRecord(e0, s));
         }
-        k_level_scan<R, P, NOFF, KIND, SCAN_OUT, GEN><<<p->n_items, kScanThreads, 0, s>>>(A);
-        FGK_LAUNCH_CHECK();
+        FGK_TRY((launch_scan<R, P, NOFF, KIND, SCAN_OUT, GEN>(A, p->n_items, s)));
         if (e0) {
             FGK_CUDA(cudaEventRecord(e1, s));
             scan_timing_record(e0, e1);
