@@ -307,7 +307,8 @@ def run_batched(args, local):
 def run_serving(args, local):
     """Continuous-batching replay of the serving stream's first K requests:
     first as a burst (all arriving at once) to measure the sustained capacity,
-    then with Poisson arrivals at 0.8x that capacity for the latencies."""
+    then with Poisson arrivals at 0.8x that capacity for the latencies, then at
+    1.5x (an overload: the queue grows and admission holds requests back)."""
     import torch
 
     import workloads
@@ -323,16 +324,19 @@ def run_serving(args, local):
     srv = serving.Server(budget_bytes=150e9, slots=args.slots)
     burst = serving.replay(srv, requests, np.zeros(len(requests)), rate=1.0)
     srv.close()
-    sb = serving.summarize(burst)
+    sb = serving.summarize(burst, requests)
     out["burst"] = sb
     cap = sb.get("solves_per_s", 0.0)
     if cap > 0:
-        srv = serving.Server(budget_bytes=150e9, slots=args.slots)
-        steady = serving.replay(srv, requests, gaps[:len(requests)], rate=0.8 * cap)
-        srv.close()
-        out["steady_0.8x"] = serving.summarize(steady)
+        for name, f in (("steady_0.8x", 0.8), ("overload_1.5x", 1.5)):
+            srv = serving.Server(budget_bytes=150e9, slots=args.slots)
+            res = serving.replay(srv, requests, gaps[:len(requests)], rate=f * cap)
+            srv.close()
+            out[name] = serving.summarize(res, requests)
+            out[name]["arrival_rate_per_s"] = f * cap
+            out[name]["peak_concurrency"] = srv.stats.peak_concurrency
+            out[name]["peak_bytes"] = srv.stats.peak_bytes
         out["value"] = out["steady_0.8x"].get("solves_per_s")
-        out["peak_concurrency"] = srv.stats.peak_concurrency
     print(json.dumps(out), flush=True)
     return 0
 

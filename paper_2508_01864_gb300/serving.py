@@ -117,8 +117,8 @@ def gpu_estimator(nrhs_cols: int = 1, precond_rank: int = 100):
 
     def est(req: Request) -> int:
         k = precond_rank_for(req.N, precond_rank)
-        # factor (float pairs), residual diagonal, Gram partials of the build (<= 64 x k x k), apply scratch
-        pc_bytes = req.N * (k + 1) * 8 + 66 * k * k * 8 + 304 * k * 8 + (1 << 20) if k > 0 else 0
+        # factor (FP32), residual diagonal, Gram partials of the build (<= 64 x k x k), apply scratch
+        pc_bytes = req.N * k * 4 + req.N * 8 + 66 * k * k * 8 + 304 * k * 8 + (1 << 20) if k > 0 else 0
         return (int(fgk.fgk_bytes_estimate(req.N, req.d, req.nu, req.kind, nrhs_cols)) + req.N * (req.d + 3) * 8
                 + pc_bytes)
 
@@ -250,15 +250,40 @@ def replay(server: Server, requests: list[Request], gaps: np.ndarray, rate: floa
     return [f.result() for f in futs]
 
 
-def summarize(results: list[Result]) -> dict:
+def summarize(results: list[Result], requests: list[Request] | None = None) -> dict:
+    """Latency percentiles (arrival to result on the host), the time spent
+    queued (arrival to admission) and solving (admission to result), the
+    throughput over the replay's span; with the requests, the same per
+    variant (d, nu) and the variants of the requests at or above the p99."""
     ok = [r for r in results if r.error is None and r.status in (0, 1)]
     if not ok:
         return {"completed": 0}
     lat = np.array([r.latency for r in ok])
+    wait = np.array([r.admitted - r.arrival for r in ok])
+    serve = np.array([r.finished - r.admitted for r in ok])
     span = max(r.finished for r in ok) - min(r.arrival for r in ok)
-    return {"completed": len(ok), "failed": len(results) - len(ok),
-            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-            "mean_s": float(lat.mean()), "makespan_s": float(span), "solves_per_s": len(ok) / span}
+    out = {"completed": len(ok), "failed": len(results) - len(ok),
+           "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+           "mean_s": float(lat.mean()), "queued_p50_s": float(np.percentile(wait, 50)),
+           "queued_p99_s": float(np.percentile(wait, 99)), "solve_p50_s": float(np.percentile(serve, 50)),
+           "solve_p99_s": float(np.percentile(serve, 99)), "makespan_s": float(span), "solves_per_s": len(ok) / span}
+    if requests is not None:
+        by_id = {q.rid: q for q in requests}
+        groups: dict[str, list[float]] = {}
+        for r in ok:
+            q = by_id[r.rid]
+            groups.setdefault(f"d={q.d} nu={q.nu:g}", []).append(r.latency)
+        out["by_variant"] = {k: {"n": len(v), "p50_s": float(np.percentile(v, 50)),
+                                 "p99_s": float(np.percentile(v, 99))} for k, v in sorted(groups.items())}
+        p99 = out["p99_s"]
+        tail: dict[str, int] = {}
+        for r in ok:
+            if r.latency >= p99:
+                q = by_id[r.rid]
+                key = f"d={q.d} nu={q.nu:g}"
+                tail[key] = tail.get(key, 0) + 1
+        out["at_or_above_p99"] = tail
+    return out
 
 
 def to_requests(problems, tol: float = 1e-8, kind: str = "product") -> list[Request]:
