@@ -154,37 +154,44 @@ class GlsFit:
 
 def gls_outer_loop(descend, beta_gls, H, y, theta0, sigma2_0: float, eps_beta: float = 1e-3,
                    max_rep: int = 20) -> GlsFit:
-    """Algorithm 1 around its gradient descents, on host values.
-    descend(y_c, theta, sigma2) runs one descent on the centred data y_c and
-    returns (theta, sigma2, info); beta_gls(theta, sigma2) returns the GLS
-    estimate (H^T A^{-1} H)^{-1} H^T A^{-1} y, A = K(theta) + sigma2 I.
+    """Algorithm 1 (Sec. 3.1) on host values: a damped fixed-point iteration
+    between the fixed effects and the kernel parameters.
 
-    The first descent runs on y - H beta_OLS (beta_OLS from the normal
-    equations of H, an L x L system).  Each repetition r = 1, 2, ... takes
-    beta_GLS at the current parameters, folds it into the running mean of
-    all GLS estimates so far, descends on y minus H times that mean, and
-    stops once beta_GLS has moved by at most eps_beta since the previous
-    repetition (the first is compared with beta_OLS), or after max_rep."""
+    The two depend on each other.  descend(y_c, theta, sigma2) fits the
+    parameters to data centred by a mean H b and returns (theta, sigma2,
+    info); beta_gls(theta, sigma2) is the GLS estimate
+    (H^T A^{-1} H)^{-1} H^T A^{-1} y, A = K(theta) + sigma2 I, at those
+    parameters.  Writing P(b) for the parameters fitted to y - H b, a
+    consistent pair is a fixed point b = beta_gls(P(b)).  The iteration
+    starts from the least-squares mean b_0 = beta_OLS (the normal equations
+    of H) and feeds each new estimate b_r = beta_gls(P(m_{r-1})) back through
+    the mean m_r of all estimates so far, which damps it; it stops once two
+    successive estimates agree to eps_beta (b_1 is compared with beta_OLS)
+    or after max_rep estimates.  The parameters returned are P(m_r) of the
+    last repetition."""
     H = np.asarray(H, dtype=np.float64)
     y = np.asarray(y, dtype=np.float64).reshape(-1)
-    prev = np.linalg.solve(H.T @ H, H.T @ y)
-    theta, sigma2, info = descend(y - H @ prev, np.array(theta0, dtype=np.float64), float(sigma2_0))
-    fit = GlsFit(beta=prev.copy(), beta_avg=np.zeros(H.shape[1]), theta=np.asarray(theta, dtype=np.float64),
+    b_ols = np.linalg.solve(H.T @ H, H.T @ y)
+
+    def agree(b_new, b_old):
+        return float(np.linalg.norm(b_new - b_old)) <= eps_beta
+
+    theta, sigma2, info = descend(y - H @ b_ols, np.array(theta0, dtype=np.float64), float(sigma2_0))
+    fit = GlsFit(beta=b_ols.copy(), beta_avg=np.zeros(H.shape[1]), theta=np.asarray(theta, dtype=np.float64),
                  sigma2=float(sigma2), reps=0)
-    fit.history.append({"beta_ols": prev.copy(), "theta": fit.theta.copy(), "sigma2": fit.sigma2, **info})
-    total = np.zeros(H.shape[1])
-    for r in range(1, max_rep + 1):
+    fit.history.append({"beta_ols": b_ols.copy(), "theta": fit.theta.copy(), "sigma2": fit.sigma2, **info})
+    estimates = [b_ols]  # b_0, b_1, ..., b_r; the mean is over b_1 .. b_r
+    while len(estimates) <= max_rep:
         b = np.asarray(beta_gls(fit.theta, fit.sigma2), dtype=np.float64).reshape(-1)
-        total += b
-        mean = total / r
-        theta, sigma2, info = descend(y - H @ mean, fit.theta, fit.sigma2)
-        moved = float(np.linalg.norm(b - prev))
-        prev = b
-        fit.beta, fit.beta_avg, fit.reps = b.copy(), mean, r
+        estimates.append(b)
+        m = np.sum(estimates[1:], axis=0) / (len(estimates) - 1)
+        theta, sigma2, info = descend(y - H @ m, fit.theta, fit.sigma2)
+        fit.beta, fit.beta_avg, fit.reps = b.copy(), m, len(estimates) - 1
         fit.theta, fit.sigma2 = np.asarray(theta, dtype=np.float64), float(sigma2)
-        fit.history.append({"beta_gls": b.copy(), "beta_avg": mean.copy(), "change": moved,
-                            "theta": fit.theta.copy(), "sigma2": fit.sigma2, **info})
-        if moved <= eps_beta:
+        fit.history.append({"beta_gls": b.copy(), "beta_avg": m.copy(),
+                            "change": float(np.linalg.norm(b - estimates[-2])), "theta": fit.theta.copy(),
+                            "sigma2": fit.sigma2, **info})
+        if agree(b, estimates[-2]):
             break
     return fit
 
