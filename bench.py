@@ -326,6 +326,7 @@ def run_serving(args, local):
     srv.close()
     sb = serving.summarize(burst, requests)
     out["burst"] = sb
+    print(json.dumps({"phase": "burst", **sb}), file=sys.stderr, flush=True)  # progress, in case of a limit
     cap = sb.get("solves_per_s", 0.0)
     if cap > 0:
         for name, f in (("steady_0.8x", 0.8), ("overload_1.5x", 1.5)):
@@ -336,6 +337,7 @@ def run_serving(args, local):
             out[name]["arrival_rate_per_s"] = f * cap
             out[name]["peak_concurrency"] = srv.stats.peak_concurrency
             out[name]["peak_bytes"] = srv.stats.peak_bytes
+            print(json.dumps({"phase": name, **out[name]}), file=sys.stderr, flush=True)
         out["value"] = out["steady_0.8x"].get("solves_per_s")
     print(json.dumps(out), flush=True)
     return 0

@@ -78,11 +78,18 @@ constexpr int kRedThreads = 256;
 
 constexpr int variant_key(int P, int noff, int kind) { return (P * 3 + noff) * 2 + kind; }
 
-template <int MODE>
-__global__ void __launch_bounds__(kScanThreads, FGK_SCAN_MINB) k_batch_scan(BatchArgs B) {
-    const BatchItem bi = B.items[blockIdx.x];
+// One kernel per variant (P, split dimensions, kind), over that variant's
+// contiguous range of the work list (items first .. first + gridDim.x - 1):
+// each variant gets its own register allocation instead of the largest one's.
+template <int MODE, int PP, int NO, int KK>
+__global__ void __launch_bounds__(kScanThreads, FGK_SCAN_MINB) k_batch_scan(BatchArgs B, int first) {
+    const BatchItem bi = B.items[first + blockIdx.x];
     if (B.prob_active && B.prob_active[bi.prob] == 0) return;
     const BatchProb pr = B.probs[bi.prob];
+    if (pr.variant != variant_key(PP, NO, KK)) {  // the host groups the list by variant
+        if (threadIdx.x == 0) atomicExch(B.err, DEV_INTERNAL);
+        return;
+    }
     ScanArgs<float> A;
     A.lv_q = pr.lv_q;
     A.lv_dl = pr.lv_dl;
@@ -103,21 +110,38 @@ __global__ void __launch_bounds__(kScanThreads, FGK_SCAN_MINB) k_batch_scan(Batc
     A.s2 = pr.s2;
     A.err = B.err;
     A.gate = nullptr;
-    switch (pr.variant) {
-#define FGK_BCASE(PP, NO, KK) \
-    case variant_key(PP, NO, KK): scan_tile<float, PP, NO, KK, MODE, false, false>(A, bi.w, bi.r0, bi.r1); break;
-        FGK_BCASE(1, 0, FGK_L1)
-        FGK_BCASE(2, 0, FGK_L1)
-        FGK_BCASE(3, 0, FGK_L1)
-        FGK_BCASE(1, 1, FGK_L1)
-        FGK_BCASE(2, 1, FGK_L1)
-        FGK_BCASE(3, 1, FGK_L1)
-        FGK_BCASE(2, 1, FGK_PRODUCT)
-        FGK_BCASE(3, 1, FGK_PRODUCT)
+    scan_tile<float, PP, NO, KK, MODE, false, false>(A, bi.w, bi.r0, bi.r1);
+}
+
+// the variants a batch can hold (d <= 2, nu <= 5/2; nu = 1/2 and d = 1 use the L1 scans)
+constexpr int kBatchVariants = 8;
+constexpr int kBatchVariantKey[kBatchVariants] = {
+    variant_key(1, 0, FGK_L1), variant_key(2, 0, FGK_L1), variant_key(3, 0, FGK_L1), variant_key(1, 1, FGK_L1),
+    variant_key(2, 1, FGK_L1), variant_key(3, 1, FGK_L1), variant_key(2, 1, FGK_PRODUCT),
+    variant_key(3, 1, FGK_PRODUCT)};
+
+template <int MODE>
+int launch_batch_scan(int v, const BatchArgs &A, int first, int count, cudaStream_t s) {
+    switch (v) {
+#define FGK_BCASE(I, PP, NO, KK)                                                  \
+    case I:                                                                       \
+        k_batch_scan<MODE, PP, NO, KK><<<count, kScanThreads, 0, s>>>(A, first); \
+        break;
+        FGK_BCASE(0, 1, 0, FGK_L1)
+        FGK_BCASE(1, 2, 0, FGK_L1)
+        FGK_BCASE(2, 3, 0, FGK_L1)
+        FGK_BCASE(3, 1, 1, FGK_L1)
+        FGK_BCASE(4, 2, 1, FGK_L1)
+        FGK_BCASE(5, 3, 1, FGK_L1)
+        FGK_BCASE(6, 2, 1, FGK_PRODUCT)
+        FGK_BCASE(7, 3, 1, FGK_PRODUCT)
 #undef FGK_BCASE
         default:
-            if (threadIdx.x == 0) atomicExch(B.err, DEV_INTERNAL);
+            set_error("batch: unknown scan variant %d", v);
+            return FGK_ERR_INTERNAL;
     }
+    FGK_LAUNCH_CHECK();
+    return FGK_OK;
 }
 
 // one warp per (segment, direction, rhs, pass); passes beyond a variant's own
@@ -413,6 +437,9 @@ struct Batch {
     BatchProb *probs = nullptr;
     BatchItem *long_items = nullptr, *all_items = nullptr;
     int n_long_items = 0, n_all_items = 0;
+    // per variant (kBatchVariantKey order), its range of each list: [first, first + count)
+    int long_first[kBatchVariants] = {}, long_count[kBatchVariants] = {};
+    int all_first[kBatchVariants] = {}, all_count[kBatchVariants] = {};
     BatchSeg *segs = nullptr;
     int nseg = 0;
     Chunk *chunks = nullptr;
@@ -454,16 +481,16 @@ static int batch_product(Batch *b, const float *V, float *Y, const int *prob_act
     A.err = b->err;
     if (b->n_long_items > 0) {
         A.items = b->long_items;
-        k_batch_scan<SCAN_AGG><<<b->n_long_items, kScanThreads, 0, s>>>(A);
-        FGK_LAUNCH_CHECK();
+        for (int v = 0; v < kBatchVariants; ++v)
+            if (b->long_count[v] > 0) FGK_TRY(launch_batch_scan<SCAN_AGG>(v, A, b->long_first[v], b->long_count[v], s));
         const int64_t nthr = (int64_t)b->nseg * 2 * b->nrhs * kMaxBatchNPT * 32;
         k_batch_carry<<<grid_for(nthr, 256), 256, 0, s>>>(A);
         FGK_LAUNCH_CHECK();
     }
     if (b->n_all_items > 0) {
         A.items = b->all_items;
-        k_batch_scan<SCAN_OUT><<<b->n_all_items, kScanThreads, 0, s>>>(A);
-        FGK_LAUNCH_CHECK();
+        for (int v = 0; v < kBatchVariants; ++v)
+            if (b->all_count[v] > 0) FGK_TRY(launch_batch_scan<SCAN_OUT>(v, A, b->all_first[v], b->all_count[v], s));
     }
     return FGK_OK;
 }
@@ -534,6 +561,25 @@ int fgk_batch_create(const fgk_handle *handles, int n, int nrhs, int rhs_per_cta
                                    r0 == 0 ? 1 : 0});
         b->h_prob_nc.push_back((int)chunks.size() - b->h_prob_c0.back());
         row += p->N;
+    }
+    // group each list by variant (stable: each problem's items keep their order)
+    auto group = [&](std::vector<BatchItem> &list, int *first, int *count) -> bool {
+        std::vector<BatchItem> out;
+        out.reserve(list.size());
+        for (int v = 0; v < kBatchVariants; ++v) {
+            first[v] = (int)out.size();
+            for (const BatchItem &bi : list)
+                if (probs[bi.prob].variant == kBatchVariantKey[v]) out.push_back(bi);
+            count[v] = (int)out.size() - first[v];
+        }
+        const bool all_placed = out.size() == list.size();
+        list.swap(out);
+        return all_placed;
+    };
+    if (!group(longs, b->long_first, b->long_count) || !group(all, b->all_first, b->all_count)) {
+        set_error("fgk_batch_create: a problem's scan variant has no batched kernel (internal)");
+        delete b;
+        return FGK_ERR_INTERNAL;
     }
     b->rows = row;
     b->n_long_items = (int)longs.size();

@@ -55,7 +55,6 @@ namespace {
 constexpr int kPcThreads = 256;
 constexpr int kPcMaxRank = 1024;
 constexpr int kGramTile = 16;
-constexpr size_t kCholSmemMax = 200 * 1024;  // C's packed lower triangle in shared memory up to here
 constexpr double kExhausted = 1e-12;  // stop once the residual diagonal is at most this x s2
 
 struct PivPart {
@@ -179,7 +178,8 @@ __global__ void k_pc_init(int64_t N, double s2, const int32_t *__restrict__ perm
 }
 
 // step m of the pivoted Cholesky (see the file comment)
-__global__ void k_pc_step(int m, int64_t N, int64_t ldN, KernArgs ka, const int32_t *__restrict__ perm0,
+__global__ void __launch_bounds__(kPcThreads, 3) k_pc_step(int m, int64_t N, int64_t ldN, KernArgs ka,
+                                                          const int32_t *__restrict__ perm0,
                           const PivPart *__restrict__ prev, int nprev, PivPart *__restrict__ next,
                           float *__restrict__ L, double *__restrict__ dres, int32_t *__restrict__ piv_q,
                           int *__restrict__ rank, double floor) {
@@ -214,15 +214,27 @@ __global__ void k_pc_step(int m, int64_t N, int64_t ldN, KernArgs ka, const int3
          i0 += 2 * (int64_t)gridDim.x * blockDim.x) {
         const bool two = i0 + 1 < N;
         // sum_t L_t[i] L_t[pivot]: each product of two FP32 values made exact
-        // by the two-product, the running sum a float pair
-        F2 acc0{0.f, 0.f}, acc1{0.f, 0.f};
-#pragma unroll 8
-        for (int t = 0; t < m; ++t) {
+        // by the two-product, the running sums float pairs (two per row, even
+        // and odd t, so that consecutive terms do not wait on each other)
+        F2 acc0{0.f, 0.f}, acc1{0.f, 0.f}, acc0b{0.f, 0.f}, acc1b{0.f, 0.f};
+        int t = 0;
+#pragma unroll 4
+        for (; t + 1 < m; t += 2) {
             const float2 a = *reinterpret_cast<const float2 *>(L + (size_t)t * ldN + i0);
-            const float ph = s_lp[t];
+            const float2 b = *reinterpret_cast<const float2 *>(L + (size_t)(t + 1) * ldN + i0);
+            const float ph = s_lp[t], ph1 = s_lp[t + 1];
             f2_fma(acc0, a.x, ph, 0.f);
             f2_fma(acc1, a.y, ph, 0.f);
+            f2_fma(acc0b, b.x, ph1, 0.f);
+            f2_fma(acc1b, b.y, ph1, 0.f);
         }
+        if (t < m) {
+            const float2 a = *reinterpret_cast<const float2 *>(L + (size_t)t * ldN + i0);
+            f2_fma(acc0, a.x, s_lp[t], 0.f);
+            f2_fma(acc1, a.y, s_lp[t], 0.f);
+        }
+        acc0 = f2_add(acc0, acc0b);
+        acc1 = f2_add(acc1, acc1b);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             if (h == 1 && !two) break;
@@ -276,58 +288,134 @@ __global__ void k_pc_gram(const float *__restrict__ L, int64_t ldN, int64_t N, i
     if (a < r && b < r) Gp[((size_t)z * r + a) * r + b] = acc;
 }
 
-// C = I + G / sigma2 (G summed over the z partials, mirrored), its lower
-// Cholesky factor F (row-major r x r, upper part untouched), and log det P by
-// Sylvester: N log sigma2 + 2 sum_j log F_jj.  err = 1 if C is not positive
-// definite.  One CTA; right-looking: per column j the pivot's square root,
-// the scaled column, then the rank-1 update of the trailing lower triangle
-// (one warp per row).  SMEM: C's lower triangle packed in shared memory
-// (row i at i(i+1)/2) plus the current column; otherwise C in global memory.
-template <bool SMEM>
-__global__ void __launch_bounds__(1024) k_pc_chol(const double *__restrict__ Gp, int nz, int r, double sigma2,
-                                                   int64_t N, double *__restrict__ C, double *__restrict__ logdet,
-                                                   int *__restrict__ err) {
-    extern __shared__ __align__(16) double s_c[];
-    double *col = s_c + (SMEM ? (size_t)r * (r + 1) / 2 : 0);  // r
+// C = I + G / sigma2 (G summed over the z partials, mirrored) and its lower
+// Cholesky factor F (row-major r x r, upper part untouched), blocked and
+// right-looking over the whole GPU: per panel of kCholB columns, the
+// diagonal block is factored by one CTA (k_chol_diag), the rows below it are
+// solved against that block (k_chol_panel, one thread per row), and the
+// trailing lower triangle takes the panel's rank-kCholB update in 32 x 32
+// tiles (k_chol_update, one CTA per tile).  GB300 issues FP64 at about two
+// multiply-adds per cycle per SM, so the factorisation of C (r^3 / 3
+// multiply-adds) belongs on all SMs, not one.  log det P by Sylvester:
+// N log sigma2 + 2 sum_j log F_jj (k_chol_logdet).  err = 1 if C is not
+// positive definite.
+constexpr int kCholB = 32;
+
+__global__ void k_chol_init(const double *__restrict__ Gp, int nz, int r, double sigma2, double *__restrict__ C) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)r * r) return;
+    const int i = (int)(e / r), l = (int)(e % r);
+    if (l > i) return;
+    double g = 0.0;
+    for (int z = 0; z < nz; ++z) g += Gp[((size_t)z * r + l) * r + i];  // partial tiles hold l <= i
+    C[(size_t)i * r + l] = (i == l ? 1.0 : 0.0) + g / sigma2;
+}
+
+// the diagonal block [j0, j0 + b) in place, right-looking (one CTA)
+__global__ void __launch_bounds__(1024) k_chol_diag(double *__restrict__ C, int r, int j0, int *__restrict__ err) {
+    __shared__ double a[kCholB][kCholB + 1];
     __shared__ int s_bad;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    auto at = [&](int i, int l) -> double & { return SMEM ? s_c[(size_t)i * (i + 1) / 2 + l] : C[(size_t)i * r + l]; };
-    for (int i = warp; i < r; i += nw)
-        for (int l = lane; l <= i; l += 32) {
-            double g = 0.0;
-            for (int z = 0; z < nz; ++z) g += Gp[((size_t)z * r + l) * r + i];  // partial tiles hold l <= i
-            at(i, l) = (i == l ? 1.0 : 0.0) + g / sigma2;
-        }
-    if (threadIdx.x == 0) s_bad = 0;
+    const int b = min(kCholB, r - j0);
+    const int tid = threadIdx.x;
+    if (tid == 0) s_bad = 0;
+    for (int e = tid; e < b * b; e += blockDim.x) {
+        const int i = e / b, l = e % b;
+        if (l <= i) a[i][l] = C[(size_t)(j0 + i) * r + j0 + l];
+    }
     __syncthreads();
-    for (int j = 0; j < r; ++j) {
-        const double v = at(j, j);  // every thread: no write-back race (read before the barrier below)
+    for (int j = 0; j < b; ++j) {
+        const double v = a[j][j];  // every thread, before the barrier below
         const bool ok = v > 0.0;
         const double djj = ok ? sqrt(v) : 1.0;
-        for (int i = j + 1 + threadIdx.x; i < r; i += blockDim.x) {
-            const double x = at(i, j) / djj;
-            at(i, j) = x;
-            col[i] = x;
-        }
+        for (int i = j + 1 + tid; i < b; i += blockDim.x) a[i][j] /= djj;
         __syncthreads();
-        if (threadIdx.x == 0) {
-            at(j, j) = djj;
+        if (tid == 0) {
+            a[j][j] = djj;
             if (!ok) s_bad = 1;
         }
-        for (int i = j + 1 + warp; i < r; i += nw) {
-            const double ci = col[i];
-            for (int l = j + 1 + lane; l <= i; l += 32) at(i, l) -= ci * col[l];
+        for (int e = tid; e < b * b; e += blockDim.x) {
+            const int i = e / b, l = e % b;
+            if (l > j && l <= i) a[i][l] -= a[i][j] * a[l][j];
         }
         __syncthreads();
     }
-    if (SMEM)  // the factor out to global memory
-        for (int i = warp; i < r; i += nw)
-            for (int l = lane; l <= i; l += 32) C[(size_t)i * r + l] = s_c[(size_t)i * (i + 1) / 2 + l];
+    for (int e = tid; e < b * b; e += blockDim.x) {
+        const int i = e / b, l = e % b;
+        if (l <= i) C[(size_t)(j0 + i) * r + j0 + l] = a[i][l];
+    }
+    if (tid == 0) {
+        if (j0 == 0) *err = 0;
+        if (s_bad) *err = 1;
+    }
+}
+
+// rows i >= j0 + b: F[i][j0 .. j0+b) = C[i][j0 .. j0+b) F_diag^{-T}, forward
+// substitution along the row (one thread per row)
+__global__ void k_chol_panel(double *__restrict__ C, int r, int j0) {
+    __shared__ double d[kCholB][kCholB + 1];
+    const int b = min(kCholB, r - j0);
+    for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+        const int k = e / b, t = e % b;
+        if (t <= k) d[k][t] = C[(size_t)(j0 + k) * r + j0 + t];
+    }
+    __syncthreads();
+    const int i = j0 + b + blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= r) return;
+    double x[kCholB];
+    double *row = C + (size_t)i * r + j0;
+#pragma unroll
+    for (int k = 0; k < kCholB; ++k) x[k] = k < b ? row[k] : 0.0;
+#pragma unroll
+    for (int k = 0; k < kCholB; ++k) {
+        if (k < b) {
+            double v = x[k];
+#pragma unroll
+            for (int t = 0; t < k; ++t) v -= x[t] * d[k][t];
+            x[k] = v / d[k][k];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kCholB; ++k)
+        if (k < b) row[k] = x[k];
+}
+
+// the trailing lower triangle, rows and columns from m0 = j0 + b: tile
+// (blockIdx.y, blockIdx.x) of 32 x 32 entries, skipped above the diagonal
+__global__ void __launch_bounds__(1024) k_chol_update(double *__restrict__ C, int r, int j0) {
+    __shared__ double pi[32][kCholB + 1], pl[32][kCholB + 1];
+    const int b = min(kCholB, r - j0);
+    const int m0 = j0 + b;
+    const int bi = blockIdx.y, bl = blockIdx.x;
+    if (bl > bi) return;
+    const int y = threadIdx.x / 32, x = threadIdx.x % 32;
+    {
+        const int k = threadIdx.x % 32, row = threadIdx.x / 32;
+        const int ii = m0 + bi * 32 + row, ll = m0 + bl * 32 + row;
+        pi[row][k] = (ii < r && k < b) ? C[(size_t)ii * r + j0 + k] : 0.0;
+        pl[row][k] = (ll < r && k < b) ? C[(size_t)ll * r + j0 + k] : 0.0;
+    }
+    __syncthreads();
+    const int i = m0 + bi * 32 + y, l = m0 + bl * 32 + x;
+    if (i >= r || l > i) return;
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < kCholB; ++k) acc = fma(pi[y][k], pl[x][k], acc);
+    C[(size_t)i * r + l] -= acc;
+}
+
+__global__ void k_chol_logdet(const double *__restrict__ C, int r, int64_t N, double sigma2,
+                              double *__restrict__ logdet) {
+    __shared__ double part[32];
+    double ld = 0.0;
+    for (int j = threadIdx.x; j < r; j += blockDim.x) ld += 2.0 * log(C[(size_t)j * r + j]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ld += __shfl_xor_sync(0xffffffffu, ld, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = ld;
+    __syncthreads();
     if (threadIdx.x == 0) {
-        double ld = (double)N * log(sigma2);
-        for (int j = 0; j < r; ++j) ld += 2.0 * log(at(j, j));
-        *logdet = ld;
-        *err = s_bad;
+        double t = (double)N * log(sigma2);
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+        *logdet = t;
     }
 }
 
@@ -999,7 +1087,13 @@ static int pc_build(Precond *pc, cudaStream_t s) {
         }
         return q;
     };
-    const int steps_blocks = (int)std::min<int64_t>(2 * 152, (N + kPcThreads - 1) / kPcThreads);
+    // the pivot steps: every row pair in one pass while that fits three CTAs
+    // per SM (a thread left with a second pair makes every step wait for its
+    // second pass over the factor), else three CTAs per SM, several passes
+    int n_sm = 152;
+    FGK_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, p->device));
+    const int steps_blocks =
+        (int)std::max<int64_t>(1, std::min<int64_t>(3 * (int64_t)n_sm, (N + 2 * kPcThreads - 1) / (2 * kPcThreads)));
     pc->chunk = kTR;
     FGK_TRY(set_pc_attrs<1>(k));
     FGK_TRY(set_pc_attrs<2>(k));
@@ -1079,17 +1173,22 @@ static int pc_build(Precond *pc, cudaStream_t s) {
     if (r > 0) {
         k_pc_gram<<<dim3(ntile, ntile, nz), kPcThreads, 0, s>>>(pc->L32, ldN, N, r, rows_per_z, Gp);
         FGK_LAUNCH_CHECK();
-        const size_t chol_smem = ((size_t)r * (r + 1) / 2 + (size_t)r) * 8;
-        if (chol_smem <= kCholSmemMax) {
-            FGK_CUDA(cudaFuncSetAttribute(k_pc_chol<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)chol_smem));
-            k_pc_chol<true><<<1, 1024, chol_smem, s>>>(Gp, nz, r, pc->sigma2, N, pc->Cf, pc->scal + 1, pc->ints + 1);
-        } else {
-            FGK_CUDA(cudaFuncSetAttribute(k_pc_chol<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)((size_t)r * 8)));
-            k_pc_chol<false><<<1, 1024, (size_t)r * 8, s>>>(Gp, nz, r, pc->sigma2, N, pc->Cf, pc->scal + 1,
-                                                            pc->ints + 1);
+        k_chol_init<<<grid_for((int64_t)r * r, 256), 256, 0, s>>>(Gp, nz, r, pc->sigma2, pc->Cf);
+        FGK_LAUNCH_CHECK();
+        for (int j0 = 0; j0 < r; j0 += kCholB) {
+            const int b = std::min(kCholB, r - j0);
+            k_chol_diag<<<1, 1024, 0, s>>>(pc->Cf, r, j0, pc->ints + 1);
+            FGK_LAUNCH_CHECK();
+            const int rest = r - j0 - b;
+            if (rest > 0) {
+                k_chol_panel<<<(rest + 127) / 128, 128, 0, s>>>(pc->Cf, r, j0);
+                FGK_LAUNCH_CHECK();
+                const int nt = (rest + 31) / 32;
+                k_chol_update<<<dim3(nt, nt), 1024, 0, s>>>(pc->Cf, r, j0);
+                FGK_LAUNCH_CHECK();
+            }
         }
+        k_chol_logdet<<<1, 256, 0, s>>>(pc->Cf, r, N, pc->sigma2, pc->scal + 1);
         FGK_LAUNCH_CHECK();
         // Gp (nz * k * k >= k * k doubles) as the scratch of F^{-1}
         k_pc_finv<<<(r + 3) / 4, 128, 0, s>>>(pc->Cf, r, Gp);
