@@ -112,16 +112,60 @@ struct KernArgs {
     const double *x0, *x1, *x2;  // scaled coordinates in q order
     int d, two_nu, kind;
     double s2;
+    // e^{+x} and e^{-x} of each scaled coordinate (block k of N per
+    // dimension), 0 where |x| > kExpTableMax; NULL: no tables
+    const double *ep, *em;
+    int64_t N;
 };
 
+// |x| up to which the tables hold e^{+-x}: e^{700} < DBL_MAX and e^{-700} >
+// DBL_MIN, so neither factor nor their product (at most 1) overflows
+constexpr double kExpTableMax = 700.0;
+
+__global__ void k_pc_exptab(KernArgs ka, double *__restrict__ ep, double *__restrict__ em) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= ka.N) return;
+    for (int k = 0; k < ka.d; ++k) {
+        const double x = (k == 0 ? ka.x0 : (k == 1 ? ka.x1 : ka.x2))[i];
+        const bool in = fabs(x) <= kExpTableMax;
+        ep[(size_t)k * ka.N + i] = in ? exp(x) : 0.0;
+        em[(size_t)k * ka.N + i] = in ? exp(-x) : 0.0;
+    }
+}
+
 // K(x_i, x_p): both kinds share the exponential e^{-sum_k |u_k|} (L1: of the
-// summed distance; product: the product of the per-dimension factors), so one
-// exp per entry
-__device__ __forceinline__ double kern_q(const KernArgs &k, int64_t i, const double *xp) {
-    const double u0 = fabs(k.x0[i] - xp[0]);
-    const double u1 = k.d > 1 ? fabs(k.x1[i] - xp[1]) : 0.0;
-    const double u2 = k.d > 2 ? fabs(k.x2[i] - xp[2]) : 0.0;
-    const double e = exp(-(u0 + u1 + u2));
+// summed distance; product: the product of the per-dimension factors).  With
+// the tables, e^{-|x_i - x_p|} = e^{-x_i} e^{+x_p} (x_i >= x_p) or e^{+x_i}
+// e^{-x_p}: d multiplications instead of an FP64 exponential, whose long
+// instruction sequence on GB300's FP64 pipe bounds each pivot step's row pass.
+// pex[k] = e^{+x_p,k}, pex[3 + k] = e^{-x_p,k}; tab: the pivot is inside the
+// tables (rows outside them take the exponential).
+__device__ __forceinline__ double kern_q(const KernArgs &k, int64_t i, const double *xp, const double *pex,
+                                         bool tab) {
+    const double d0 = k.x0[i] - xp[0];
+    const double d1 = k.d > 1 ? k.x1[i] - xp[1] : 0.0;
+    const double d2 = k.d > 2 ? k.x2[i] - xp[2] : 0.0;
+    const double u0 = fabs(d0), u1 = fabs(d1), u2 = fabs(d2);
+    double e;
+    bool done = false;
+    if (tab) {
+        const double em0 = k.em[i], ep0 = k.ep[i];
+        double f = d0 >= 0.0 ? em0 * pex[0] : ep0 * pex[3];
+        bool in = em0 != 0.0;
+        if (k.d > 1) {
+            const double em1 = k.em[k.N + i], ep1 = k.ep[k.N + i];
+            f *= d1 >= 0.0 ? em1 * pex[1] : ep1 * pex[4];
+            in = in && em1 != 0.0;
+        }
+        if (k.d > 2) {
+            const double em2 = k.em[2 * k.N + i], ep2 = k.ep[2 * k.N + i];
+            f *= d2 >= 0.0 ? em2 * pex[2] : ep2 * pex[5];
+            in = in && em2 != 0.0;
+        }
+        e = f;
+        done = in;
+    }
+    if (!done) e = exp(-(u0 + u1 + u2));
     if (k.d == 1 || k.kind == FGK_L1) return k.s2 * matern_poly(k.two_nu, u0 + u1 + u2) * e;
     double v = matern_poly(k.two_nu, u0) * matern_poly(k.two_nu, u1);
     if (k.d == 3) v *= matern_poly(k.two_nu, u2);
@@ -185,6 +229,7 @@ __global__ void __launch_bounds__(kPcThreads, 3) k_pc_step(int m, int64_t N, int
                           int *__restrict__ rank, double floor) {
     __shared__ float s_lp[kPcMaxRank];
     __shared__ double s_xp[3];
+    __shared__ double s_pex[6];  // the pivot's e^{+x_k}, e^{-x_k}
     PivPart best = piv_none();
     for (int b = threadIdx.x; b < nprev; b += blockDim.x)
         if (piv_better(prev[b], best)) best = prev[b];
@@ -203,8 +248,13 @@ __global__ void __launch_bounds__(kPcThreads, 3) k_pc_step(int m, int64_t N, int
         s_xp[0] = ka.x0[piv];
         s_xp[1] = ka.d > 1 ? ka.x1[piv] : 0.0;
         s_xp[2] = ka.d > 2 ? ka.x2[piv] : 0.0;
+        for (int k = 0; k < 3; ++k) {
+            s_pex[k] = (ka.ep && k < ka.d) ? ka.ep[(size_t)k * ka.N + piv] : 1.0;
+            s_pex[3 + k] = (ka.em && k < ka.d) ? ka.em[(size_t)k * ka.N + piv] : 1.0;
+        }
     }
     __syncthreads();
+    const bool tab = ka.ep != nullptr && s_pex[3] != 0.0 && s_pex[4] != 0.0 && s_pex[5] != 0.0;
     const double isq = 1.0 / sqrt(best.val);  // one division per CTA (GB300's FP64 divide is costly)
     PivPart mine = piv_none();
     // two consecutive rows per thread (8-byte vector loads of L; the column
@@ -240,7 +290,7 @@ __global__ void __launch_bounds__(kPcThreads, 3) k_pc_step(int m, int64_t N, int
             if (h == 1 && !two) break;
             const int64_t i = i0 + h;
             const F2 acc = h == 0 ? acc0 : acc1;
-            const double kv = kern_q(ka, i, s_xp);
+            const double kv = kern_q(ka, i, s_xp, s_pex, tab);
             const double dot = (double)acc.hi + (double)acc.lo;
             const float lf = (float)((kv - dot) * isq);
             L[(size_t)m * ldN + i] = lf;
@@ -311,38 +361,37 @@ __global__ void k_chol_init(const double *__restrict__ Gp, int nz, int r, double
     C[(size_t)i * r + l] = (i == l ? 1.0 : 0.0) + g / sigma2;
 }
 
-// the diagonal block [j0, j0 + b) in place, right-looking (one CTA)
+// the diagonal block [j0, j0 + b) in place, right-looking (one CTA): per
+// column one thread forms the pivot's square root and reciprocal (GB300's FP64
+// square root and divide are long dependent chains on a slow pipe), the rows
+// below are scaled by the reciprocal, and the block's remaining lower
+// triangle takes the rank-1 update, one entry per thread
 __global__ void __launch_bounds__(1024) k_chol_diag(double *__restrict__ C, int r, int j0, int *__restrict__ err) {
     __shared__ double a[kCholB][kCholB + 1];
+    __shared__ double s_inv;
     __shared__ int s_bad;
     const int b = min(kCholB, r - j0);
     const int tid = threadIdx.x;
+    const int ti = tid >> 5, tl = tid & 31;  // this thread's entry of the block
     if (tid == 0) s_bad = 0;
-    for (int e = tid; e < b * b; e += blockDim.x) {
-        const int i = e / b, l = e % b;
-        if (l <= i) a[i][l] = C[(size_t)(j0 + i) * r + j0 + l];
-    }
+    if (ti < b && tl <= ti) a[ti][tl] = C[(size_t)(j0 + ti) * r + j0 + tl];
     __syncthreads();
     for (int j = 0; j < b; ++j) {
-        const double v = a[j][j];  // every thread, before the barrier below
-        const bool ok = v > 0.0;
-        const double djj = ok ? sqrt(v) : 1.0;
-        for (int i = j + 1 + tid; i < b; i += blockDim.x) a[i][j] /= djj;
-        __syncthreads();
         if (tid == 0) {
+            const double v = a[j][j];
+            const bool ok = v > 0.0;
+            const double djj = ok ? sqrt(v) : 1.0;
             a[j][j] = djj;
+            s_inv = 1.0 / djj;
             if (!ok) s_bad = 1;
         }
-        for (int e = tid; e < b * b; e += blockDim.x) {
-            const int i = e / b, l = e % b;
-            if (l > j && l <= i) a[i][l] -= a[i][j] * a[l][j];
-        }
         __syncthreads();
+        if (tid > j && tid < b) a[tid][j] *= s_inv;
+        __syncthreads();
+        if (ti < b && tl > j && tl <= ti) a[ti][tl] -= a[ti][j] * a[tl][j];
+        __syncthreads();  // the next pivot reads an updated entry
     }
-    for (int e = tid; e < b * b; e += blockDim.x) {
-        const int i = e / b, l = e % b;
-        if (l <= i) C[(size_t)(j0 + i) * r + j0 + l] = a[i][l];
-    }
+    if (ti < b && tl <= ti) C[(size_t)(j0 + ti) * r + j0 + tl] = a[ti][tl];
     if (tid == 0) {
         if (j0 == 0) *err = 0;
         if (s_bad) *err = 1;
@@ -350,14 +399,19 @@ __global__ void __launch_bounds__(1024) k_chol_diag(double *__restrict__ C, int 
 }
 
 // rows i >= j0 + b: F[i][j0 .. j0+b) = C[i][j0 .. j0+b) F_diag^{-T}, forward
-// substitution along the row (one thread per row)
-__global__ void k_chol_panel(double *__restrict__ C, int r, int j0) {
+// substitution along the row (one thread per row; one-warp CTAs, so that the
+// FP64 work of the rows spreads over many SMs)
+constexpr int kCholPanelThreads = 32;
+
+__global__ void __launch_bounds__(kCholPanelThreads) k_chol_panel(double *__restrict__ C, int r, int j0) {
     __shared__ double d[kCholB][kCholB + 1];
+    __shared__ double rd[kCholB];  // reciprocals of the diagonal
     const int b = min(kCholB, r - j0);
     for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
         const int k = e / b, t = e % b;
         if (t <= k) d[k][t] = C[(size_t)(j0 + k) * r + j0 + t];
     }
+    if (threadIdx.x < b) rd[threadIdx.x] = 1.0 / C[(size_t)(j0 + threadIdx.x) * r + j0 + threadIdx.x];
     __syncthreads();
     const int i = j0 + b + blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= r) return;
@@ -368,10 +422,16 @@ __global__ void k_chol_panel(double *__restrict__ C, int r, int j0) {
 #pragma unroll
     for (int k = 0; k < kCholB; ++k) {
         if (k < b) {
-            double v = x[k];
+            // four partial sums: the FP64 chain of a row is a quarter as long
+            double v0 = x[k], v1 = 0.0, v2 = 0.0, v3 = 0.0;
 #pragma unroll
-            for (int t = 0; t < k; ++t) v -= x[t] * d[k][t];
-            x[k] = v / d[k][k];
+            for (int t = 0; t < k; t += 4) {
+                v0 -= x[t] * d[k][t];
+                if (t + 1 < k) v1 -= x[t + 1] * d[k][t + 1];
+                if (t + 2 < k) v2 -= x[t + 2] * d[k][t + 2];
+                if (t + 3 < k) v3 -= x[t + 3] * d[k][t + 3];
+            }
+            x[k] = ((v0 + v1) + (v2 + v3)) * rd[k];
         }
     }
 #pragma unroll
@@ -404,10 +464,14 @@ __global__ void __launch_bounds__(1024) k_chol_update(double *__restrict__ C, in
 }
 
 __global__ void k_chol_logdet(const double *__restrict__ C, int r, int64_t N, double sigma2,
-                              double *__restrict__ logdet) {
+                              double *__restrict__ logdet, double *__restrict__ rdiag) {
     __shared__ double part[32];
     double ld = 0.0;
-    for (int j = threadIdx.x; j < r; j += blockDim.x) ld += 2.0 * log(C[(size_t)j * r + j]);
+    for (int j = threadIdx.x; j < r; j += blockDim.x) {
+        const double f = C[(size_t)j * r + j];
+        ld += 2.0 * log(f);
+        rdiag[j] = 1.0 / f;  // for the columns of F^{-1}
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ld += __shfl_xor_sync(0xffffffffu, ld, o);
     if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = ld;
@@ -422,7 +486,8 @@ __global__ void k_chol_logdet(const double *__restrict__ C, int r, int64_t N, do
 // Columns of F^{-1} (F lower, row-major r x r) by forward substitution, one
 // warp per column c: FinvT[c][i] = (F^{-1})[i][c] (zero for i < c).  The
 // dots run across the lanes; the column being solved sits in shared memory.
-__global__ void k_pc_finv(const double *__restrict__ F, int r, double *__restrict__ FinvT) {
+__global__ void k_pc_finv(const double *__restrict__ F, const double *__restrict__ rdiag, int r,
+                          double *__restrict__ FinvT) {
     __shared__ double s_x[4][kPcMaxRank];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int c = blockIdx.x * 4 + w;
@@ -433,7 +498,7 @@ __global__ void k_pc_finv(const double *__restrict__ F, int r, double *__restric
         for (int k = c + lane; k < i; k += 32) part = fma(F[(size_t)i * r + k], x[k], part);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-        const double xi = ((i == c ? 1.0 : 0.0) - part) / F[(size_t)i * r + i];
+        const double xi = ((i == c ? 1.0 : 0.0) - part) * rdiag[i];
         if (lane == 0) x[i] = xi;
         __syncwarp();
     }
@@ -1138,7 +1203,17 @@ static int pc_build(Precond *pc, cudaStream_t s) {
     FGK_CUDA(cudaMemsetAsync(pc->L32, 0, (size_t)k * ldN * 4, s));
     const int init[4] = {k, 0, 0, 0};
     FGK_CUDA(cudaMemcpyAsync(pc->ints, init, sizeof(init), cudaMemcpyHostToDevice, s));
-    KernArgs ka{p->xq[0], p->xq[1], p->xq[2], p->d, p->two_nu, p->kind, p->s2};
+    KernArgs ka{p->xq[0], p->xq[1], p->xq[2], p->d, p->two_nu, p->kind, p->s2, nullptr, nullptr, N};
+    // the exponential tables of the kernel columns, for the pivot steps only
+    double *exptab = (double *)dev_alloc((size_t)2 * p->d * N * 8, s);
+    if (!exptab) {
+        set_error("fgk_precond_build: device allocation failed");
+        return FGK_ERR_OOM;
+    }
+    ka.ep = exptab;
+    ka.em = exptab + (size_t)p->d * N;
+    k_pc_exptab<<<grid_for(N, 256), 256, 0, s>>>(ka, exptab, exptab + (size_t)p->d * N);
+    FGK_LAUNCH_CHECK();
     k_pc_init<<<steps_blocks, kPcThreads, 0, s>>>(N, p->s2, p->perm[0], pc->dres, part0);
     FGK_LAUNCH_CHECK();
     PivPart *bufs[2] = {part0, part1};
@@ -1148,6 +1223,7 @@ static int pc_build(Precond *pc, cudaStream_t s) {
                                                       kExhausted * p->s2);
         FGK_LAUNCH_CHECK();
     }
+    dev_free(exptab, s);
     int hints[4];
     FGK_CUDA(cudaMemcpyAsync(hints, pc->ints, sizeof(hints), cudaMemcpyDeviceToHost, s));
     FGK_CUDA(cudaStreamSynchronize(s));
@@ -1181,17 +1257,19 @@ static int pc_build(Precond *pc, cudaStream_t s) {
             FGK_LAUNCH_CHECK();
             const int rest = r - j0 - b;
             if (rest > 0) {
-                k_chol_panel<<<(rest + 127) / 128, 128, 0, s>>>(pc->Cf, r, j0);
+                k_chol_panel<<<(rest + kCholPanelThreads - 1) / kCholPanelThreads, kCholPanelThreads, 0, s>>>(
+                    pc->Cf, r, j0);
                 FGK_LAUNCH_CHECK();
                 const int nt = (rest + 31) / 32;
                 k_chol_update<<<dim3(nt, nt), 1024, 0, s>>>(pc->Cf, r, j0);
                 FGK_LAUNCH_CHECK();
             }
         }
-        k_chol_logdet<<<1, 256, 0, s>>>(pc->Cf, r, N, pc->sigma2, pc->scal + 1);
+        // the diagonal's reciprocals go to C^{-1}'s storage until k_pc_cinv fills it
+        k_chol_logdet<<<1, 256, 0, s>>>(pc->Cf, r, N, pc->sigma2, pc->scal + 1, pc->Cinv);
         FGK_LAUNCH_CHECK();
         // Gp (nz * k * k >= k * k doubles) as the scratch of F^{-1}
-        k_pc_finv<<<(r + 3) / 4, 128, 0, s>>>(pc->Cf, r, Gp);
+        k_pc_finv<<<(r + 3) / 4, 128, 0, s>>>(pc->Cf, pc->Cinv, r, Gp);
         FGK_LAUNCH_CHECK();
         k_pc_cinv<<<grid_for((int64_t)r * r * 32, 256), 256, 0, s>>>(Gp, r, pc->Cinv);
         FGK_LAUNCH_CHECK();
