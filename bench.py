@@ -46,9 +46,9 @@ WORKLOAD = ("d=2 N=200000 nu=3/2 ell=(0.1,0.3) x~U[0,1]^2 product kernel; "
 # missing here has no capture of its current version)
 TRAFFIC_BYTES = {
     350: {
-        "k_level_scan<float,P=2,NOFF=1,product,OUT>": 44142464 + 12672,
-        "k_pc_ltr (t = L^T r)": 281732864 + 808576,
-        "k_pc_apply (z = r/s2 - L c)": 281718400 + 702592,
+        "k_level_scan<float,P=2,NOFF=1,product,OUT>": 44105728 + 2816,
+        "k_pc_ltr (t = L^T r)": 281704704 + 856064,
+        "k_pc_apply (z = r/s2 - L c)": 281727744 + 893568,
     },
 }
 FALLBACK_HBM_GBS = 6800.0
@@ -805,8 +805,9 @@ def main():
         "avg_launch_ms": scan_avg_ms, "algorithmic_bytes_per_launch": bytes_per_launch,
         "achieved_gbs": bytes_per_launch / (scan_avg_ms * 1e-3) / 1e9}}
     kernels.update(pc_kernels)
-    for k in kernels.values():
+    for name, k in kernels.items():
         k["frac"] = k["achieved_gbs"] / pk["hbm_gbs"]
+        k["traffic"] = TRAFFIC_BYTES.get(args.precond_rank, {}).get(name)  # DRAM bytes per launch (ncu)
     # each kernel launches once per CG iteration: the dominant one takes the longest
     dom = max(kernels, key=lambda k: kernels[k]["avg_launch_ms"])
     kd = kernels[dom]

@@ -63,8 +63,17 @@ struct PivPart {
     int64_t q;
 };
 
+// an integer key with the order of the doubles (negative values flipped
+// except for the sign bit; -0 sorts just below +0), so that the pivot
+// comparisons, a dozen per row of every step, stay off GB300's slow FP64 pipe
+__device__ __forceinline__ long long piv_key(double v) {
+    const long long b = __double_as_longlong(v);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+
 __device__ __forceinline__ bool piv_better(const PivPart &a, const PivPart &b) {
-    return a.val > b.val || (a.val == b.val && a.orig < b.orig);
+    const long long ka = piv_key(a.val), kb = piv_key(b.val);
+    return ka > kb || (ka == kb && a.orig < b.orig);
 }
 
 __device__ __forceinline__ PivPart piv_none() { return PivPart{-INFINITY, INT64_MAX, -1}; }
@@ -149,18 +158,19 @@ __device__ __forceinline__ double kern_q(const KernArgs &k, int64_t i, const dou
     double e;
     bool done = false;
     if (tab) {
+        // the signs and the table's zero markers tested on the integer pipe
         const double em0 = k.em[i], ep0 = k.ep[i];
-        double f = d0 >= 0.0 ? em0 * pex[0] : ep0 * pex[3];
-        bool in = em0 != 0.0;
+        double f = __double2hiint(d0) >= 0 ? em0 * pex[0] : ep0 * pex[3];
+        bool in = __double_as_longlong(em0) != 0;
         if (k.d > 1) {
             const double em1 = k.em[k.N + i], ep1 = k.ep[k.N + i];
-            f *= d1 >= 0.0 ? em1 * pex[1] : ep1 * pex[4];
-            in = in && em1 != 0.0;
+            f *= __double2hiint(d1) >= 0 ? em1 * pex[1] : ep1 * pex[4];
+            in = in && __double_as_longlong(em1) != 0;
         }
         if (k.d > 2) {
             const double em2 = k.em[2 * k.N + i], ep2 = k.ep[2 * k.N + i];
-            f *= d2 >= 0.0 ? em2 * pex[2] : ep2 * pex[5];
-            in = in && em2 != 0.0;
+            f *= __double2hiint(d2) >= 0 ? em2 * pex[2] : ep2 * pex[5];
+            in = in && __double_as_longlong(em2) != 0;
         }
         e = f;
         done = in;
@@ -230,6 +240,7 @@ __global__ void __launch_bounds__(kPcThreads, 3) k_pc_step(int m, int64_t N, int
     __shared__ float s_lp[kPcMaxRank];
     __shared__ double s_xp[3];
     __shared__ double s_pex[6];  // the pivot's e^{+x_k}, e^{-x_k}
+    __shared__ double s_isq;     // 1 / sqrt(the pivot's residual)
     PivPart best = piv_none();
     for (int b = threadIdx.x; b < nprev; b += blockDim.x)
         if (piv_better(prev[b], best)) best = prev[b];
@@ -252,10 +263,13 @@ __global__ void __launch_bounds__(kPcThreads, 3) k_pc_step(int m, int64_t N, int
             s_pex[k] = (ka.ep && k < ka.d) ? ka.ep[(size_t)k * ka.N + piv] : 1.0;
             s_pex[3 + k] = (ka.em && k < ka.d) ? ka.em[(size_t)k * ka.N + piv] : 1.0;
         }
+        // one square root and one division per CTA, not per thread: both are long
+        // dependent sequences on GB300's FP64 pipe
+        s_isq = 1.0 / sqrt(best.val);
     }
     __syncthreads();
     const bool tab = ka.ep != nullptr && s_pex[3] != 0.0 && s_pex[4] != 0.0 && s_pex[5] != 0.0;
-    const double isq = 1.0 / sqrt(best.val);  // one division per CTA (GB300's FP64 divide is costly)
+    const double isq = s_isq;
     PivPart mine = piv_none();
     // two consecutive rows per thread (8-byte vector loads of L; the column
     // stride ldN is a multiple of 64, so row i0 + 1 < ldN is always inside the
@@ -819,9 +833,9 @@ __global__ void k_pc_cmul(const double *__restrict__ t, int r, int ncols, const 
 // c is split into float pairs in shared memory per pass of up to kColsPass
 // columns; L c is summed in float pairs.
 template <int NC>
-__global__ void __launch_bounds__(kTR) k_pc_apply(const __grid_constant__ CUtensorMap map, int r,
+__global__ void __launch_bounds__(kTR, kPcCtasPerSm) k_pc_apply(const __grid_constant__ CUtensorMap map, int r,
                                                    const double *__restrict__ R, int64_t N, int ncols,
-                                                   const double *__restrict__ c, double sigma2,
+                                                   const double *__restrict__ c, double inv,
                                                    double *__restrict__ Z, double *__restrict__ rz_partial,
                                                    int *__restrict__ err, const int *__restrict__ gate) {
     if (gate && *gate == 0) return;
@@ -843,7 +857,8 @@ __global__ void __launch_bounds__(kTR) k_pc_apply(const __grid_constant__ CUtens
     const int ntile = tiles_of_cta(N);
     const ChunkStream cs{buf, bar, &map, nchunk, ntile};
     const int total = nchunk * ntile;
-    const double inv = 1.0 / sigma2;
+    // inv = 1 / sigma2, formed once on the host (a division per thread would
+    // put a few microseconds of FP64 work on every launch)
     int c_base = 0;
     for (int j0 = 0; j0 < ncols; j0 += NC) {
         const int nc = min(NC, ncols - j0);
@@ -1129,7 +1144,7 @@ static int launch_pc_apply(const Precond *pc, int r, const double *R, int ncols,
                            int *err, cudaStream_t s, const int *gate) {
     TimedLaunch tl(kTimedPcApply, s);
     k_pc_apply<NC><<<pc->nb_ltr, kTR, apply_smem(r, NC), s>>>(pc->tmap, r, R, pc->plan->N, ncols, pc->cvec,
-                                                              pc->sigma2, Z, rz_partial, err, gate);
+                                                              1.0 / pc->sigma2, Z, rz_partial, err, gate);
     FGK_LAUNCH_CHECK();
     tl.end();
     return FGK_OK;
