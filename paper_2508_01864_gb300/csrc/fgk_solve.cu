@@ -613,13 +613,10 @@ int cg_solve(Plan *p, Precond *pc, const double *y, int nrhs, double sigma2, con
         } else {
             FGK_CUDA(cudaMemcpyAsync(Pv, B, vec * 8, cudaMemcpyDeviceToDevice, s));
         }
-        // warm the products once so their workspace exists before graph capture,
-        // then set the product's starting point W = s2 p
-        if ((rc = init_p())) break;
-        if (mixed) {
-            if ((rc = mvm_q_f32(p, P32, ncols, W32, s, nullptr))) break;
-        }
-        if ((rc = mvm_q_f64(p, Pv, ncols, W64, s, nullptr))) break;
+        // the products' workspace at its largest (the FP64 products of the residual
+        // replacements run between graph launches and must not move the buffer the
+        // captured FP32 products use); no product is run for it
+        if ((rc = ensure_ws(p, std::max(mvm_ws_bytes(p, ncols, true), mvm_ws_bytes(p, ncols, false)), s))) break;
         // A residual replacement (one FP64 product) is allowed once the FP32
         // iterations since the last one have cost about as much, so that
         // replacements take at most about half of the solve: kReplacementGap
