@@ -216,9 +216,10 @@ __device__ __forceinline__ float rcp_approx(float x) {
 __device__ __forceinline__ double rcp_approx(double x) { return 1.0 / x; }
 
 // a thread's anchored walk is used when the gaps between its entries sum to
-// at most this (scaled units): e^{+X} <= e^{30} ~ 1e13 keeps every anchored
-// moment far from the FP32 range limit
-constexpr float kAnchorSpan = 30.0f;
+// at most this (scaled units): e^{+X} <= e^{20} ~ 5e8, so an anchored moment
+// reaches the FP32 range limit only for operands near 1e29, where the product
+// itself overflows FP32 anyway
+constexpr float kAnchorSpan = 20.0f;
 
 // coefficients u_j(o) = e^{-o} sum_{p>=j} c_p C(p,j) o^{p-j}
 template <class R, int P>

@@ -241,3 +241,26 @@ def test_mvm_higher_nu_c2_shape_sampled(fgk_mod, orc):
         y32 = fgk.fgk_matvec(h, to_dev(V, torch.float32), "f32").cpu().numpy()[rows]
     assert (colwise_relerr(y64, ref) <= TOL64).all()
     assert (colwise_relerr(y32, ref) <= TOL32).all()
+
+
+@pytest.mark.parametrize("d,nu,kind", [(1, 1.5, "l1"), (2, 1.5, "product"), (2, 2.5, "l1"), (2, 0.5, "l1")])
+def test_mvm_parity_mixed_gap_scales(fgk_mod, orc, d, nu, kind):
+    """Dense clusters next to points spaced three scaled units apart along
+    every coordinate: some threads' eight entries span more than the FP32
+    scans' anchored-walk limit (20 scaled units) and take the plain walk,
+    others take the anchored one, within the same product."""
+    fgk = fgk_mod
+    rng = np.random.default_rng(4242 + 10 * d)
+    ell = np.full(d, 0.25)
+    a = np.sqrt(2 * nu) / ell[0]
+    n_sparse, n_dense = 1500, 2500
+    sparse = (3.0 / a) * np.arange(n_sparse)[:, None] + rng.uniform(0, 0.1 / a, size=(n_sparse, d))
+    dense = rng.uniform(0, 0.05, size=(n_dense, d)) + sparse[n_sparse // 2]
+    X = np.concatenate([sparse, dense])[rng.permutation(n_sparse + n_dense)]
+    V = rng.standard_normal((X.shape[0], 2)) * np.exp(rng.uniform(-3, 3, size=(X.shape[0], 1)))
+    ref = orc.mvm_brute(X, V, nu, ell, kind=0 if kind == "l1" else 1)
+    with fgk.fgk_build(to_dev(X), nu, ell, kind=kind) as h:
+        y32 = fgk.fgk_matvec(h, to_dev(V, torch.float32), "f32").cpu().numpy()
+        y64 = fgk.fgk_matvec(h, to_dev(V), "f64").cpu().numpy()
+    assert (colwise_relerr(y64, ref) <= TOL64).all()
+    assert (colwise_relerr(y32, ref) <= TOL32).all(), colwise_relerr(y32, ref)
