@@ -42,8 +42,24 @@ def oracle_factor(orc, p, kind, rank, forced):
 
 @pytest.mark.parametrize("d,nu,kind,N,pattern", CASES)
 def test_factor_pivots_trace_logdet(fgk_mod, orc, d, nu, kind, N, pattern):
-    fgk = fgk_mod
     p = workloads.small(700 + d * 10 + N % 7, N, d, nu=nu, ell=[0.2, 0.35, 0.5][:d], pattern=pattern, s2=1.3)
+    check_factor(fgk_mod, orc, p, kind, pattern, free_pivots=pattern == "uniform" and nu <= 2.5)
+
+
+@pytest.mark.parametrize("kind", ["product", "l1"])
+def test_factor_with_coordinates_beyond_the_exponential_tables(fgk_mod, orc, kind):
+    """Points on [-50, 50]^2 with lengthscales (0.1, 0.12): scaled
+    coordinates reach 866 and 722, beyond the 700 up to which the pivot steps
+    take e^{-|x_i - x_p|} from tables of e^{+-x}, so rows (and pivots) outside
+    them fall back to the exponential within the same factorisation."""
+    p = workloads.small(9001, 1200, 2, nu=1.5, ell=[0.1, 0.12], pattern="wide", s2=1.3)
+    a = np.sqrt(3.0) / np.array([0.1, 0.12])
+    out = np.abs(p.X * a).max(axis=1) > 700.0
+    assert 0.05 < out.mean() < 0.5  # both kinds of rows are present
+    check_factor(fgk_mod, orc, p, kind, "wide", free_pivots=False)
+
+
+def check_factor(fgk, orc, p, kind, pattern, free_pivots):
     rank, s2n = 60, 0.02
     with fgk.fgk_build(to_dev(p.X), p.nu, p.ell, outscale2=p.s2, kind=kind) as h:
         with fgk.fgk_precond_build(h, rank, s2n) as pc:
@@ -62,7 +78,7 @@ def test_factor_pivots_trace_logdet(fgk_mod, orc, d, nu, kind, N, pattern):
     d_min = min(Lo[piv[m], m] ** 2 for m in range(len(piv)))
     tol_L = 1e-5 * np.sqrt(p.s2) * max(1.0, np.sqrt(1e-4 * p.s2 / d_min))
     assert np.abs(L - Lo).max() <= tol_L, (np.abs(L - Lo).max(), tol_L)
-    if pattern == "uniform" and nu <= 2.5:  # generic positions: the same pivots without forcing
+    if free_pivots:  # generic positions: the same pivots without forcing
         # (the smoother kernels leave near-ties between residual diagonals, which
         # two roundings may order differently; the forced comparison above covers them)
         _, free, _ = oracle_factor(orc, p, kind, rank, forced=None)
