@@ -262,6 +262,7 @@ size_t plan_bytes_estimate(int64_t N, int d, int two_nu, int kind, int nrhs) {
     b += (size_t)nlev * ntiles * sizeof(WorkItem) + (size_t)ntiles * 8;  // work lists
     b += (size_t)2 * nlev * ntiles * 2 * nrhs * 4 * 29 * 8;             // scan aggregates (upper bound)
     b += (size_t)nlev * N * nrhs * 8;                                      // level rows of an FP64 product
+    b += (size_t)d * E * 8;                                                // stored FP64 decays
     b += (size_t)N * nrhs * 8 * 10 + (size_t)N * 8 * 12;                 // solver vectors
     (void)two_nu;
     (void)kind;

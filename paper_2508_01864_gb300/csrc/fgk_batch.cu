@@ -94,6 +94,8 @@ __global__ void __launch_bounds__(kScanThreads, FGK_SCAN_MINB) k_batch_scan(Batc
     A.lv_q = pr.lv_q;
     A.lv_dl = pr.lv_dl;
     A.lv_off = pr.lv_off;
+    A.lv_edl = nullptr;  // FP32: decays computed per entry
+    A.lv_eoff = nullptr;
     A.N = pr.N;
     A.ldN = pr.ldN;
     A.nlev = pr.nlev;

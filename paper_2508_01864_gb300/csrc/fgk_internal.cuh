@@ -134,6 +134,8 @@ struct Plan {
     double *lv_dl64 = nullptr;
     float *lv_off32 = nullptr;   // (d-1) arrays of nlev x ldN, dimension-major
     double *lv_off64 = nullptr;
+    double *lv_edl64 = nullptr;   // e^{-gap} of every FP64 gap (1 past each level's end)
+    double *lv_eoff64 = nullptr;  // e^{-offset} of every FP64 offset (1 past each level's end)
     std::vector<int> lev_log2S;  // host
 
     // scan work lists (device + host copies)

@@ -64,6 +64,10 @@ enum { SCAN_AGG = 0, SCAN_OUT = 1 };
 #ifndef FGK_SCAN_MINB
 #define FGK_SCAN_MINB 2
 #endif
+// the same for the FP64 scans (bound by GB300's FP64 pipe rather than by latency)
+#ifndef FGK_SCAN_MINB_F64
+#define FGK_SCAN_MINB_F64 FGK_SCAN_MINB
+#endif
 
 // Channels: a source of role c feeds the queries of the complementary role
 // c ^ (NCH-1), so a pass handles one complementary pair {cA, cB} (d = 2: one
@@ -95,6 +99,10 @@ struct ScanArgs {
     const uint32_t *lv_q;
     const R *lv_dl;
     const R *lv_off;  // (d-1) blocks of nlev x ldN
+    // FP64 only: the decays e^{-gap} and e^{-offset} of every entry, stored by
+    // the structure build (1 past each level's end); NULL: computed per entry
+    const R *lv_edl;
+    const R *lv_eoff;
     int64_t N;
     int64_t ldN;
     int nlev;
@@ -440,14 +448,17 @@ __device__ __forceinline__ void set_identity(R *x) {
 // its threads' gaps sum to at most kAnchorSpan; the step into the first entry
 // is always the plain one.
 // The arithmetic of one tile, from this thread's entries (q, gaps, offsets,
-// the first column's operands, and for lane 31 the gap into the entry after
-// its last one) already in registers; entries past the level's end carry
-// q = 0, zero gaps and offsets and zero operands.
+// their decays e^{-gap}, e^{-offset}, the first column's operands, and for
+// lane 31 the gap into the entry after its last one and its decay) already in
+// registers; entries past the level's end carry q = 0, zero gaps and offsets,
+// unit decays and zero operands.
 template <class R, int P, int NOFF, int KIND, int MODE, bool GEN = false, bool ROWS = true>
 __device__ __forceinline__ void scan_compute(const ScanArgs<R> &A, const WorkItem wi, int r0, int r1,
                                              const uint32_t (&q)[kScanEPT], const R (&g)[kScanEPT],
                                              const R (&o)[NOFF > 0 ? NOFF : 1][kScanEPT],
-                                             const R (&vpre)[kScanEPT], R gn31) {
+                                             const R (&vpre)[kScanEPT], R gn31,
+                                             const R (&eg)[kScanEPT], const R (&eo)[NOFF > 0 ? NOFF : 1][kScanEPT],
+                                             R egn31) {
     using Tr = Traits<P, NOFF, KIND>;
     constexpr int GM = Tr::GM, CP = Tr::CP, SMM = Tr::SM, AG = Tr::AG, NCH = Tr::NCH;
     constexpr int NGP = Tr::NGP, NPT = Tr::NPT, NWC = Tr::NWC;
@@ -472,19 +483,12 @@ __device__ __forceinline__ void scan_compute(const ScanArgs<R> &A, const WorkIte
     const int64_t p0 = base + j0;
     const int nvalid = (int)(N - p0 < 0 ? 0 : (N - p0 > EPT ? EPT : N - p0));
 
-    R eg[EPT], eo[NO][EPT];
-#pragma unroll
-    for (int i = 0; i < EPT; ++i) {
-        eg[i] = exp_neg<R>(g[i]);
-#pragma unroll
-        for (int k = 0; k < NOFF; ++k) eo[k][i] = exp_neg<R>(o[k][i]);
-    }
     // gap into my last entry when walking backward: the next entry's forward gap
     R gn = __shfl_down_sync(0xffffffffu, g[0], 1);
     R egn = __shfl_down_sync(0xffffffffu, eg[0], 1);
     if (lane == 31) {
         gn = gn31;
-        egn = exp_neg<R>(gn);
+        egn = egn31;
     }
     // the gaps between this thread's entries (the same in both walk directions)
     R span = R(0);
@@ -874,13 +878,60 @@ __device__ __forceinline__ void scan_tile(const ScanArgs<R> &A, const WorkItem w
 #pragma unroll
     for (int i = 0; i < EPT; ++i)
         vpre[i] = (i < nvalid && r0 < r1) ? A.V[(size_t)(q[i] & 0x3fffffffu) * A.nrhs + r0] : R(0);
-    R gn31 = R(0);
-    if (lane == 31) {
-        const int64_t pn = p0 + EPT;
-        gn31 = pn < N ? A.lv_dl[lo + pn] : R(0);
+    R gn31 = R(0), egn31 = R(1);
+    R eg[EPT], eo[NO][EPT];
+    if (sizeof(R) == 8 && A.lv_edl) {
+        // FP64: the stored decays (an FP64 exponential per entry and offset would
+        // be most of the product's FP64 work on GB300); 1 past the level's end
+        if (nvalid > 0) {
+            const double2 *ep = reinterpret_cast<const double2 *>(A.lv_edl + lo + p0);
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const double2 x = ep[h];
+                eg[2 * h] = (R)x.x;
+                eg[2 * h + 1] = (R)x.y;
+            }
+#pragma unroll
+            for (int k = 0; k < NOFF; ++k) {
+                const double2 *op = reinterpret_cast<const double2 *>(A.lv_eoff + ((size_t)k * A.nlev) * A.ldN + lo + p0);
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const double2 x = op[h];
+                    eo[k][2 * h] = (R)x.x;
+                    eo[k][2 * h + 1] = (R)x.y;
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < EPT; ++i) {
+            if (i >= nvalid) {
+                eg[i] = R(1);
+#pragma unroll
+                for (int k = 0; k < NOFF; ++k) eo[k][i] = R(1);
+            }
+        }
+        if (lane == 31) {
+            const int64_t pn = p0 + EPT;
+            if (pn < N) {
+                gn31 = A.lv_dl[lo + pn];
+                egn31 = A.lv_edl[lo + pn];
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < EPT; ++i) {
+            eg[i] = exp_neg<R>(g[i]);
+#pragma unroll
+            for (int k = 0; k < NOFF; ++k) eo[k][i] = exp_neg<R>(o[k][i]);
+        }
+        if (lane == 31) {
+            const int64_t pn = p0 + EPT;
+            gn31 = pn < N ? A.lv_dl[lo + pn] : R(0);
+            egn31 = exp_neg<R>(gn31);
+        }
     }
     if (!gate_on) return;  // uniform over the CTA
-    scan_compute<R, P, NOFF, KIND, MODE, GEN, ROWS>(A, wi, r0, r1, q, g, o, vpre, gn31);
+    scan_compute<R, P, NOFF, KIND, MODE, GEN, ROWS>(A, wi, r0, r1, q, g, o, vpre, gn31, eg, eo, egn31);
 }
 
 // the work item of list position k (block rows of ntiles tiles per level, the
@@ -900,7 +951,8 @@ __device__ __forceinline__ WorkItem item_of(const ScanArgs<R> &A, int k) {
 }
 
 template <class R, int P, int NOFF, int KIND, int MODE, bool GEN = false>
-__global__ void __launch_bounds__(kScanThreads, GEN ? 1 : FGK_SCAN_MINB) k_level_scan(ScanArgs<R> A) {
+__global__ void __launch_bounds__(kScanThreads, GEN ? 1 : (sizeof(R) == 8 ? FGK_SCAN_MINB_F64 : FGK_SCAN_MINB))
+    k_level_scan(ScanArgs<R> A) {
     scan_tile<R, P, NOFF, KIND, MODE, GEN>(A, item_of(A, blockIdx.x), 0, A.nrhs);
 }
 
@@ -1070,6 +1122,8 @@ int run_levels(Plan *p, const R *Vq, int nrhs, R *Yq, R *ws, cudaStream_t s, con
     A.lv_q = p->lv_q;
     A.lv_dl = std::is_same<R, float>::value ? (const R *)p->lv_dl32 : (const R *)p->lv_dl64;
     A.lv_off = std::is_same<R, float>::value ? (const R *)p->lv_off32 : (const R *)p->lv_off64;
+    A.lv_edl = std::is_same<R, float>::value ? nullptr : (const R *)p->lv_edl64;
+    A.lv_eoff = std::is_same<R, float>::value ? nullptr : (const R *)p->lv_eoff64;
     A.N = p->N;
     A.ldN = p->ldN;
     A.nlev = p->nlev;

@@ -231,6 +231,31 @@ int partition(const uint32_t *in, uint32_t *out, int64_t N, int log2S, const uin
 
 }  // namespace
 
+// e^{-x} of every entry of nblk blocks of ldN values (the levels of the FP64
+// gaps or of one offset dimension), 1 for the padding past N in each block:
+// the FP64 scans read these instead of taking an FP64 exponential per entry
+// and product
+__global__ void k_decays(const double *__restrict__ x, int64_t nblk, int64_t N, int64_t ldN,
+                         double *__restrict__ ex) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= nblk * ldN) return;
+    ex[e] = (e % ldN) < N ? exp(-x[e]) : 1.0;
+}
+
+static int build_decays(Plan *p) {
+    cudaStream_t s = p->stream;
+    const int64_t nb = p->nlev, nbo = (int64_t)(p->d - 1) * p->nlev;
+    FGK_TRY(plan_alloc(p, (void **)&p->lv_edl64, (size_t)nb * p->ldN * sizeof(double)));
+    k_decays<<<grid_for(nb * p->ldN, 256), 256, 0, s>>>(p->lv_dl64, nb, p->N, p->ldN, p->lv_edl64);
+    FGK_LAUNCH_CHECK();
+    if (nbo > 0) {
+        FGK_TRY(plan_alloc(p, (void **)&p->lv_eoff64, (size_t)nbo * p->ldN * sizeof(double)));
+        k_decays<<<grid_for(nbo * p->ldN, 256), 256, 0, s>>>(p->lv_off64, nbo, p->N, p->ldN, p->lv_eoff64);
+        FGK_LAUNCH_CHECK();
+    }
+    return FGK_OK;
+}
+
 int build_levels(Plan *p) {
     cudaStream_t s = p->stream;
     const int64_t N = p->N;
@@ -250,7 +275,7 @@ int build_levels(Plan *p) {
         p->lev_log2S[0] = L;
         k_attrs_d1<<<grid_for(N, 256), 256, 0, s>>>(p->xq[0], N, p->lv_q, p->lv_dl64, p->lv_dl32);
         FGK_LAUNCH_CHECK();
-        return FGK_OK;
+        return build_decays(p);
     }
     PartWS ws;
     ws.ntiles = (N + kPartTile - 1) / kPartTile;
@@ -313,7 +338,7 @@ int build_levels(Plan *p) {
         }
     }
     dev_free(tmp, s);
-    return FGK_OK;
+    return build_decays(p);
 }
 
 }  // namespace fgk
