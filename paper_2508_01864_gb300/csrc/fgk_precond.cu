@@ -54,7 +54,7 @@ namespace {
 
 constexpr int kPcThreads = 256;
 constexpr int kPcMaxRank = 1024;
-constexpr int kGramTile = 16;
+constexpr int kGramTile = 32;  // Gram tile side (columns)
 constexpr double kExhausted = 1e-12;  // stop once the residual diagonal is at most this x s2
 
 struct PivPart {
@@ -320,36 +320,72 @@ __global__ void __launch_bounds__(kPcThreads, 3) k_pc_step(int m, int64_t N, int
 }
 
 // partial Gram blocks: Gp[z][a][b] = sum over rows of chunk z of L32[a][i] L32[b][i]
-// (products of FP32 values are exact; float-pair sums per 256 rows, then
-// FP64); tiles (ta <= tb) of 16 x 16
-__global__ void k_pc_gram(const float *__restrict__ L, int64_t ldN, int64_t N, int r, int64_t rows_per_z,
-                          double *__restrict__ Gp) {
-    __shared__ float sa[kGramTile][kPcThreads + 1];
-    __shared__ float sb[kGramTile][kPcThreads + 1];
+// (products of FP32 values are exact; float-pair sums over 256 rows, then
+// FP64).  A CTA takes a 32 x 32 tile (ta <= tb) of column pairs, each thread
+// a 2 x 2 block of it, over rows staged 64 at a time in shared memory: two
+// 8-byte shared loads feed four exact multiply-adds.
+constexpr int kGramRows = 64;   // rows staged per round
+constexpr int kGramFlush = 4;   // rounds between the FP64 flushes of the float-pair sums
+
+// acc += a * b, the product exact (two-product), the sum a float pair
+__device__ __forceinline__ void f2_mac(F2 &acc, float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float pe = fmaf(a, b, -p);  // a * b = p + pe exactly
+    float sum, err;
+    two_sum(acc.hi, p, sum, err);
+    acc.hi = sum;
+    acc.lo += err + pe;
+}
+
+__global__ void __launch_bounds__(kPcThreads) k_pc_gram(const float *__restrict__ L, int64_t ldN, int64_t N, int r,
+                                                        int64_t rows_per_z, double *__restrict__ Gp) {
+    __shared__ __align__(16) float sa[kGramRows][kGramTile + 2];
+    __shared__ __align__(16) float sb[kGramRows][kGramTile + 2];
     const int ta = blockIdx.x, tb = blockIdx.y;
     if (ta > tb) return;
     const int z = blockIdx.z;
-    const int a = ta * kGramTile + (threadIdx.x / kGramTile), b = tb * kGramTile + (threadIdx.x % kGramTile);
+    const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;  // 16 x 16 threads, 2 x 2 entries each
     const int64_t i0 = (int64_t)z * rows_per_z, i1 = min(N, i0 + rows_per_z);
-    double acc = 0.0;
-    for (int64_t c0 = i0; c0 < i1; c0 += kPcThreads) {
-        const int64_t i = c0 + threadIdx.x;
-#pragma unroll
-        for (int u = 0; u < kGramTile; ++u) {
-            const int ca = ta * kGramTile + u, cb = tb * kGramTile + u;
-            sa[u][threadIdx.x] = (i < i1 && ca < r) ? L[(size_t)ca * ldN + i] : 0.f;
-            sb[u][threadIdx.x] = (i < i1 && cb < r) ? L[(size_t)cb * ldN + i] : 0.f;
+    double tot[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+    F2 f[2][2] = {{{0.f, 0.f}, {0.f, 0.f}}, {{0.f, 0.f}, {0.f, 0.f}}};
+    int round = 0;
+    for (int64_t c0 = i0; c0 < i1; c0 += kGramRows, ++round) {
+        for (int e = threadIdx.x; e < kGramTile * kGramRows; e += blockDim.x) {
+            const int col = e / kGramRows, row = e % kGramRows;  // consecutive threads: consecutive rows
+            const int64_t i = c0 + row;
+            const int ca = ta * kGramTile + col, cb = tb * kGramTile + col;
+            sa[row][col] = (i < i1 && ca < r) ? L[(size_t)ca * ldN + i] : 0.f;
+            sb[row][col] = (i < i1 && cb < r) ? L[(size_t)cb * ldN + i] : 0.f;
         }
         __syncthreads();
-        const int la = threadIdx.x / kGramTile, lb = threadIdx.x % kGramTile;
-        const int n = (int)(i1 - c0 < kPcThreads ? i1 - c0 : kPcThreads);
-        F2 f{0.f, 0.f};  // exact float products summed in float pairs
+        const int n = (int)(i1 - c0 < kGramRows ? i1 - c0 : kGramRows);
 #pragma unroll 4
-        for (int k = 0; k < n; ++k) f2_fma(f, sa[la][k], sb[lb][k], 0.f);
-        acc += (double)f.hi + (double)f.lo;
+        for (int k = 0; k < n; ++k) {
+            const float2 a = *reinterpret_cast<const float2 *>(&sa[k][ty * 2]);
+            const float2 b = *reinterpret_cast<const float2 *>(&sb[k][tx * 2]);
+            f2_mac(f[0][0], a.x, b.x);
+            f2_mac(f[0][1], a.x, b.y);
+            f2_mac(f[1][0], a.y, b.x);
+            f2_mac(f[1][1], a.y, b.y);
+        }
         __syncthreads();
+        if (round % kGramFlush == kGramFlush - 1 || c0 + kGramRows >= i1) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+#pragma unroll
+                for (int v = 0; v < 2; ++v) {
+                    tot[u][v] += (double)f[u][v].hi + (double)f[u][v].lo;
+                    f[u][v] = F2{0.f, 0.f};
+                }
+        }
     }
-    if (a < r && b < r) Gp[((size_t)z * r + a) * r + b] = acc;
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+            const int a = ta * kGramTile + ty * 2 + u, b = tb * kGramTile + tx * 2 + v;
+            if (a < r && b < r) Gp[((size_t)z * r + a) * r + b] = tot[u][v];
+        }
 }
 
 // C = I + G / sigma2 (G summed over the z partials, mirrored) and its lower
