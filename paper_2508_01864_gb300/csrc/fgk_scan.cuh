@@ -739,7 +739,6 @@ __device__ __forceinline__ void scan_compute(const ScanArgs<R> &A, const WorkIte
                                 } else {
                                     step_all<R, P, SMM>(st[dd], gg, ee);
                                 }
-                                const int role = NOFF == 0 ? 0 : (int)(q[i] >> (32 - NOFF));
                                 R oi[NO], eoi[NO], w[NWC], u[NWC];
 #pragma unroll
                                 for (int k = 0; k < NO; ++k) {
@@ -754,6 +753,7 @@ __device__ __forceinline__ void scan_compute(const ScanArgs<R> &A, const WorkIte
                                     out[i] = AN ? fma(Rr[dd], rd, out[i]) : out[i] + rd;
                                     add_pass<R, P, NOFF, KIND>(st[dd], vi, w);
                                 } else {
+                                    const int role = (int)(q[i] >> (32 - NOFF));
                                     const bool sa = role == cA, sb = role == cB;
                                     R msel[GM];
 #pragma unroll
@@ -799,23 +799,14 @@ __device__ __forceinline__ void scan_compute(const ScanArgs<R> &A, const WorkIte
 
 template <class R, int P, int NOFF, int KIND, int MODE, bool GEN = false, bool ROWS = true>
 __device__ __forceinline__ void scan_tile(const ScanArgs<R> &A, const WorkItem wi, int r0, int r1) {
-    using Tr = Traits<P, NOFF, KIND>;
-    constexpr int GM = Tr::GM, CP = Tr::CP, SMM = Tr::SM, AG = Tr::AG, NCH = Tr::NCH;
-    constexpr int NGP = Tr::NGP, NPT = Tr::NPT, NWC = Tr::NWC;
-    constexpr int ND = Tr::NDIR, NDP = 2 / ND;  // directions per walk, direction passes
-    constexpr int EPT = kScanEPT, NT = kScanThreads, NW = NT / 32;
-    constexpr int LOG2EPT = (EPT == 8) ? 3 : (EPT == 4 ? 2 : (EPT == 16 ? 4 : 0));
+    constexpr int EPT = kScanEPT;
     constexpr int NO = NOFF > 0 ? NOFF : 1;
-    constexpr bool ANCH = std::is_same<R, float>::value && !GEN && NOFF < 2;
-    static_assert((1 << LOG2EPT) == EPT, "EPT must be 4, 8 or 16");
     static_assert(EPT == 8, "vector loads assume 8 entries per thread");
 
     const int64_t N = A.N;
     const int64_t base = (int64_t)wi.tile * kTile;
-    const int log2S = wi.log2S;
-    const int64_t S = int64_t(1) << log2S;
     const size_t lo = (size_t)wi.level * A.ldN;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int j0 = tid * EPT;
     const int64_t p0 = base + j0;
     const int nvalid = (int)(N - p0 < 0 ? 0 : (N - p0 > EPT ? EPT : N - p0));
