@@ -321,7 +321,9 @@ def run_serving(args, local):
            "requests": len(requests), "slots": args.slots, "budget_bytes": 150e9,
            "workload": (f"first {len(requests)} requests of the seeded serving stream: N log-uniform 2k-300k, "
                         "d in 1..3, nu in {1/2,3/2,5/2}, x~U[0,1]^d, product kernel, sigma^2=0.01, mixed CG")}
-    srv = serving.Server(budget_bytes=150e9, slots=args.slots)
+    mk = lambda: serving.Server(budget_bytes=150e9, slots=args.slots, batch_max=args.serve_batch)  # noqa: E731
+    out["serve_batch"] = args.serve_batch
+    srv = mk()
     burst = serving.replay(srv, requests, np.zeros(len(requests)), rate=1.0)
     srv.close()
     sb = serving.summarize(burst, requests)
@@ -330,13 +332,15 @@ def run_serving(args, local):
     cap = sb.get("solves_per_s", 0.0)
     if cap > 0:
         for name, f in (("steady_0.8x", 0.8), ("overload_1.5x", 1.5)):
-            srv = serving.Server(budget_bytes=150e9, slots=args.slots)
+            srv = mk()
             res = serving.replay(srv, requests, gaps[:len(requests)], rate=f * cap)
             srv.close()
             out[name] = serving.summarize(res, requests)
             out[name]["arrival_rate_per_s"] = f * cap
             out[name]["peak_concurrency"] = srv.stats.peak_concurrency
             out[name]["peak_bytes"] = srv.stats.peak_bytes
+            out[name]["batches"] = srv.stats.batches
+            out[name]["batched_requests"] = srv.stats.batched
             print(json.dumps({"phase": name, **out[name]}), file=sys.stderr, flush=True)
         out["value"] = out["steady_0.8x"].get("solves_per_s")
     print(json.dumps(out), flush=True)
@@ -583,6 +587,8 @@ def main():
     ap.add_argument("--serving", type=int, default=0,
                     help="replay the first K requests of the serving stream (burst, then 0.8x its capacity)")
     ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--serve-batch", type=int, default=0,
+                    help="--serving: solve up to this many small requests queued together as one batch (0: off)")
     ap.add_argument("--batched", type=int, default=0,
                     help="solve the first K problems of the batched workload (16 rhs each) in one batch")
     ap.add_argument("--batched-rank", type=int, default=100,

@@ -14,8 +14,18 @@ device; a request leaves as soon as its own solve converges, freeing its slot
 and memory for the next arrival.  Latency is measured from arrival to the
 result being on the host.
 
+With ``batch_max`` > 1 the server also shares launches between small
+requests: when the request at the head of the queue is batchable (d <= 2,
+nu <= 5/2, N <= ``batch_max_n``), the dispatcher admits it together with the
+batchable requests queued right behind it (up to ``batch_max``, within the
+budget; FIFO order is kept), and one worker solves the group as one libfgk
+batch -- one launch per phase of the product for all of them, one captured
+CG iteration -- each with its own preconditioner.  A batched request's
+product sums its levels with atomics, so its alpha can differ in the last
+bits from the same request solved alone; it meets the same tolerance.
+
 All GPU work happens inside libfgk's kernels; this module only schedules.  The
-executor is injectable so the scheduling logic can be exercised without a GPU.
+executors are injectable so the scheduling logic can be exercised without a GPU.
 """
 
 from __future__ import annotations
@@ -75,6 +85,8 @@ class Stats:
     cancelled: int = 0
     peak_bytes: int = 0
     peak_concurrency: int = 0
+    batches: int = 0   # groups solved as one batch
+    batched: int = 0   # requests in those groups
     results: list = field(default_factory=list)
 
 
@@ -112,6 +124,53 @@ def gpu_executor(mode: str = "mixed", maxit: int = 200000, precond_rank: int = 1
     return run
 
 
+def batchable(req: Request, max_n: int) -> bool:
+    """Whether the batched engine takes the request (d <= 2, nu <= 5/2)."""
+    return req.d <= 2 and req.nu <= 2.5 and req.N <= max_n and req.sigma2 > 0
+
+
+def gpu_batch_executor(maxit: int = 200000, precond_rank: int = 100):
+    """Several small requests at once: one plan and one preconditioner each,
+    one libfgk batch for their products, one mixed batched CG solve; returns
+    one (alpha, info, status) per request, in order."""
+    import torch
+
+    from . import fgk
+
+    def run(reqs: list):
+        stream = torch.cuda.Stream()
+        handles, pcs, b = [], [], None
+        with torch.cuda.stream(stream):
+            try:
+                ys = []
+                for req in reqs:
+                    X = torch.as_tensor(np.ascontiguousarray(req.X)).pin_memory().to("cuda", non_blocking=True)
+                    ys.append(torch.as_tensor(np.ascontiguousarray(req.y).reshape(-1, 1)).pin_memory().to(
+                        "cuda", non_blocking=True))
+                    handles.append(fgk.fgk_build(X, req.nu, req.ell, kind=req.kind, stream=stream))
+                b = fgk.fgk_batch_create(handles, 1, 1, stream=stream)
+                for h, req in zip(handles, reqs):
+                    pcs.append(fgk.fgk_precond_build(h, precond_rank_for(req.N, precond_rank), req.sigma2,
+                                                     stream=stream))
+                tol = min(req.tol for req in reqs)
+                alphas, infos, _ = fgk.fgk_batch_cg_solve(b, ys, [req.sigma2 for req in reqs], tol=tol, maxit=maxit,
+                                                           stream=stream, precs=pcs)
+                out = []
+                for a, info, req in zip(alphas, infos, reqs):
+                    ok = max(info["true_resid"]) <= req.tol
+                    out.append((a.cpu().numpy().reshape(-1), info, 0 if ok else 1))
+            finally:
+                for q in pcs:
+                    fgk.fgk_precond_destroy(q)
+                if b is not None:
+                    fgk.fgk_batch_destroy(b)
+                for h in handles:
+                    fgk.fgk_destroy(h)
+        return out
+
+    return run
+
+
 def gpu_estimator(nrhs_cols: int = 1, precond_rank: int = 100):
     from . import fgk
 
@@ -130,11 +189,18 @@ def gpu_estimator(nrhs_cols: int = 1, precond_rank: int = 100):
 class Server:
     """FIFO admission by slots and a device-memory budget; workers overlap."""
 
-    def __init__(self, budget_bytes: float = 150e9, slots: int = 8, executor=None, estimator=None):
+    def __init__(self, budget_bytes: float = 150e9, slots: int = 8, executor=None, estimator=None,
+                 batch_max: int = 0, batch_max_n: int = 20000, batch_executor=None):
         self.budget = int(budget_bytes)
         self.slots = int(slots)
         self.executor = executor or gpu_executor()
         self.estimator = estimator or gpu_estimator()
+        # batch_max > 1: small requests queued together share one batched solve
+        self.batch_max = int(batch_max)
+        self.batch_max_n = int(batch_max_n)
+        self.batch_executor = batch_executor or (gpu_batch_executor() if self.batch_max > 1 else None)
+        self._carry = None  # an item taken from the queue while forming a group, next in line
+        self._has_carry = False  # (the item may be the end marker None)
         self.stats = Stats()
         self._pending: queue.Queue = queue.Queue()
         self._lock = threading.Condition()
@@ -195,9 +261,15 @@ class Server:
         self._pool.shutdown(wait=wait)
 
     # ------------------------------------------------------------ scheduling
+    def _next_item(self):
+        if self._has_carry:
+            item, self._carry, self._has_carry = self._carry, None, False
+            return item
+        return self._pending.get()
+
     def _dispatch(self):
         while True:
-            item = self._pending.get()
+            item = self._next_item()
             if item is None:
                 return
             req, need = item
@@ -208,14 +280,39 @@ class Server:
                 if req.rid in self._cancelled:
                     self._cancelled.discard(req.rid)
                     continue
-                self._admitted.add(req.rid)
+                group = [(req, need)]
+                if self.batch_max > 1 and batchable(req, self.batch_max_n):
+                    # the batchable requests already queued right behind it, in order
+                    total = need
+                    while len(group) < self.batch_max:
+                        try:
+                            nxt = self._pending.get_nowait()
+                        except queue.Empty:
+                            break
+                        if nxt is None or not batchable(nxt[0], self.batch_max_n) or \
+                                self._used + total + nxt[1] > self.budget:
+                            self._carry, self._has_carry = nxt, True  # next in line, in its turn
+                            break
+                        if nxt[0].rid in self._cancelled:
+                            self._cancelled.discard(nxt[0].rid)
+                            continue
+                        group.append(nxt)
+                        total += nxt[1]
+                for r, n in group:
+                    self._admitted.add(r.rid)
+                    self._used += n
+                    self.stats.admitted += 1
                 self._running += 1
-                self._used += need
-                self.stats.admitted += 1
                 self.stats.peak_bytes = max(self.stats.peak_bytes, self._used)
                 self.stats.peak_concurrency = max(self.stats.peak_concurrency, self._running)
+                if len(group) > 1:
+                    self.stats.batches += 1
+                    self.stats.batched += len(group)
             admitted = time.perf_counter()
-            self._pool.submit(self._work, req, need, admitted)
+            if len(group) == 1:
+                self._pool.submit(self._work, req, need, admitted)
+            else:
+                self._pool.submit(self._work_group, group, admitted)
 
     def _work(self, req: Request, need: int, admitted: float):
         err = None
@@ -236,6 +333,32 @@ class Server:
             self._lock.notify_all()
         if fut is not None:
             fut.set_result(res)
+
+    def _work_group(self, group: list, admitted: float):
+        reqs = [r for r, _ in group]
+        outs, err = None, None
+        try:
+            outs = self.batch_executor(reqs)
+        except Exception as e:  # the whole group is reported failed, the server keeps going
+            err = f"{type(e).__name__}: {e}"
+        finished = time.perf_counter()
+        results = []
+        for i, req in enumerate(reqs):
+            alpha, info, rc = outs[i] if outs is not None else (None, {}, -1)
+            results.append(Result(req.rid, alpha, info, rc, req.arrival, admitted, finished, err))
+        futs = []
+        with self._lock:
+            self._running -= 1
+            for (req, need), res in zip(group, results):
+                self._used -= need
+                self._admitted.discard(req.rid)
+                self.stats.completed += 1
+                self.stats.results.append(res)
+                futs.append(self._futures.pop(req.rid, None))
+            self._lock.notify_all()
+        for fut, res in zip(futs, results):
+            if fut is not None:
+                fut.set_result(res)
 
 
 def replay(server: Server, requests: list[Request], gaps: np.ndarray, rate: float) -> list[Result]:
@@ -295,5 +418,5 @@ def to_requests(problems, tol: float = 1e-8, kind: str = "product") -> list[Requ
     return out
 
 
-__all__ = ["Request", "Result", "Server", "Stats", "gpu_executor", "gpu_estimator", "replay", "summarize",
-           "to_requests"]
+__all__ = ["Request", "Result", "Server", "Stats", "batchable", "gpu_batch_executor", "gpu_executor", "gpu_estimator",
+           "replay", "summarize", "to_requests"]

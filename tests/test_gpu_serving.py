@@ -36,3 +36,21 @@ def test_results_alone_and_in_the_mix(fgk_mod, orc):
         assert np.array_equal(np.asarray(res.alpha).view(np.uint64), np.asarray(a_alone).view(np.uint64)), r.rid
     s = serving.summarize(mixed)
     assert s["completed"] == len(requests) and s["p99_s"] >= s["p50_s"]
+
+
+def test_small_requests_solved_in_shared_batches(fgk_mod, orc):
+    """batch_max > 1: the small requests queued together are solved as one
+    libfgk batch (one launch per product phase for all of them, each with its
+    own preconditioner); every one meets the tolerance by the oracle's
+    product, and the large ones still run alone."""
+    reqs, gaps = workloads.c5(seed=11, n_requests=16, n_min=2000, n_max=30000)
+    requests = serving.to_requests(reqs, tol=1e-8)
+    srv = serving.Server(budget_bytes=150e9, slots=1, batch_max=6, batch_max_n=12000)
+    results = serving.replay(srv, requests, np.zeros(len(requests)), rate=1.0)  # a burst: they queue
+    srv.close()
+    assert srv.stats.completed == len(requests) and srv.stats.batches >= 1
+    for r, res in zip(requests, results):
+        assert res.error is None and res.status == 0, (r.rid, res.error, res.info)
+        Ka = orc.mvm_brute(r.X, res.alpha, r.nu, r.ell, kind=orc.PRODUCT if r.d > 1 else orc.L1)
+        resid = np.linalg.norm(r.y - Ka - r.sigma2 * res.alpha) / np.linalg.norm(r.y)
+        assert resid <= 1e-8, (r.rid, resid)

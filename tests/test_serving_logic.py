@@ -186,3 +186,61 @@ def test_submissions_racing_close_either_run_or_are_refused():
     assert len(taken) + len(refused) == len(reqs)
     assert all(f.result(timeout=30).error is None for f in taken)
     assert srv.stats.completed == len(taken)
+
+
+class FakeBatchDevice(FakeDevice):
+    """Records the groups the server hands to the batch executor."""
+
+    def __init__(self, per_point=2e-5):
+        super().__init__(per_point)
+        self.groups = []
+
+    def run_group(self, reqs):
+        with self.lock:
+            self.groups.append([r.rid for r in reqs])
+        time.sleep(sum(r.N for r in reqs) * self.per_point * 0.3)
+        return [(r.y.copy(), {"iterations": 1}, 0) for r in reqs]
+
+
+def test_small_requests_queued_together_share_a_batch_in_fifo_order():
+    dev = FakeBatchDevice()
+    reqs = make_requests(40, seed=3)
+    big = {4, 17, 30}  # not batchable: above batch_max_n
+    for r in reqs:
+        if r.rid in big:
+            r.X = np.random.default_rng(r.rid).uniform(size=(900, 2))
+            r.y = np.zeros(900)
+    srv = serving.Server(budget_bytes=1e12, slots=1, executor=dev.run, estimator=dev.estimate,
+                         batch_max=5, batch_max_n=500, batch_executor=dev.run_group)
+    futs = [srv.submit(r) for r in reqs]
+    res = [f.result(timeout=60) for f in futs]
+    srv.close()
+    assert [r.rid for r in res] == list(range(40))
+    assert all(r.error is None or r.rid == 5 for r in res)  # rid 5 fails only when it runs alone
+    # every request ran exactly once, singles and groups together
+    ran = [rid for rid in dev.order] + [rid for g in dev.groups for rid in g]
+    assert sorted(ran) == list(range(40))
+    # groups: at most batch_max, only batchable requests, consecutive and in submission order
+    assert dev.groups and all(2 <= len(g) <= 5 for g in dev.groups)
+    for g in dev.groups:
+        assert not set(g) & big
+        assert g == list(range(g[0], g[0] + len(g)))
+    # with one slot, work starts in submission order
+    starts = sorted(dev.groups + [[rid] for rid in dev.order], key=lambda g: g[0])
+    assert [rid for g in starts for rid in g] == list(range(40))
+    assert srv.stats.batches == len(dev.groups) and srv.stats.batched == sum(map(len, dev.groups))
+
+
+def test_batched_groups_respect_the_budget_and_close_cleanly():
+    dev = FakeBatchDevice()
+    reqs = make_requests(30, seed=4)
+    budget = 1200 * 1000  # a group's summed estimate must fit
+    srv = serving.Server(budget_bytes=budget, slots=2, executor=dev.run, estimator=dev.estimate,
+                         batch_max=8, batch_max_n=1000, batch_executor=dev.run_group)
+    futs = [srv.submit(r) for r in reqs]
+    srv.close()  # the end marker may be drawn while a group forms
+    res = [f.result(timeout=60) for f in futs]
+    assert len(res) == 30 and srv.stats.completed == 30
+    for g in dev.groups:
+        assert sum(reqs[i].N * 1000 for i in g) <= budget
+    assert srv.stats.peak_bytes <= budget
