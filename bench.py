@@ -47,7 +47,6 @@ WORKLOAD = ("d=2 N=200000 nu=3/2 ell=(0.1,0.3) x~U[0,1]^2 product kernel; "
 TRAFFIC_BYTES = {
     350: {
         "k_level_scan<float,P=2,NOFF=1,product,OUT>": 44105344 + 5504,
-        "k_pc_ltr (t = L^T r)": 281705216 + 808576,
         "k_pc_apply (z = r/s2 - L c)": 281716992 + 631936,
     },
 }

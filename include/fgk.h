@@ -272,7 +272,8 @@ typedef struct {
  *   h       a built plan; it must outlive the preconditioner.
  *   rank    0 <= rank <= 1024 (the paper uses 100); rank 0 gives P = sigma2 I.
  *   sigma2  > 0, the noise variance of the systems it will precondition.
- * Device memory: about N x rank x 4 bytes plus O(rank^2) held; during the
+ * Device memory: about N x rank x 4 bytes plus O(rank^2) held, and 8 x N bytes
+ * per column the applies have taken (the float pairs of R's rows); during the
  * build also 16 x d x N bytes of exponential tables and the Gram partials.  Synchronises
  * `stream`.  Errors: FGK_ERR_INVALID (arguments), FGK_ERR_OOM. */
 int fgk_precond_build(fgk_handle h, int rank, double sigma2, fgk_stream_t stream, fgk_precond *out);

@@ -708,14 +708,21 @@ __device__ __forceinline__ int tiles_of_cta(int64_t N) {
 // rank index and column across all the CTA's tiles, so sums cross lanes
 // (shuffles) only once per rank block, after its last tile.  The rows of R
 // for the next chunk are fetched into registers while the current chunk is
-// summed, then split into float pairs in shared memory.
+// summed, then put in shared memory as float pairs.  The split of an FP64
+// row into its float pair is FP64 work (conversions on GB300's slow FP64
+// pipe), so it is done once per row and pass: in the first rank block, whose
+// chunks cover each of the CTA's tiles once, every thread keeps its rows'
+// pairs in Rsp (N x ncols, the layout of R) and the later rank blocks load
+// them from there (8 bytes, as for the FP64 row; each row is written and
+// read back by the same thread).  Per-chunk splits had cost about 10 % of
+// the pass at rank 350.
 // NC: columns per pass (1, 2, 4 or 8); a pass with fewer real columns pads
 // with zero columns.
 template <int NC>
-__global__ void __launch_bounds__(kTR) k_pc_ltr(const __grid_constant__ CUtensorMap map, int r,
+__global__ void __launch_bounds__(kTR, NC <= 4 ? kPcCtasPerSm : 2) k_pc_ltr(const __grid_constant__ CUtensorMap map, int r,
                                                  const double *__restrict__ R, int64_t N, int ncols,
-                                                 double *__restrict__ t_part, int *__restrict__ err,
-                                                 const int *__restrict__ gate) {
+                                                 double *__restrict__ t_part, F2 *__restrict__ Rsp,
+                                                 int *__restrict__ err, const int *__restrict__ gate) {
     if (gate && *gate == 0) return;
     constexpr int NW = kTR / 32, OWN = kMC / NW, RPL = kTR / 32;  // warps, rank indices per warp, rows per lane
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -743,29 +750,50 @@ __global__ void __launch_bounds__(kTR) k_pc_ltr(const __grid_constant__ CUtensor
         for (int o = 0; o < OWN; ++o)
 #pragma unroll
             for (int u = 0; u < NC; ++u) acc[o][u] = F2{0.f, 0.f};
-        double rn[NC];  // this thread's row of R for the chunk about to be used
+        // this thread's row for the chunk about to be used, as raw 8 bytes: the
+        // FP64 row of R in the first rank block (c < ntile), its float pair
+        // from Rsp after that
+        unsigned long long rn[NC];
 #pragma unroll
-        for (int u = 0; u < NC; ++u) rn[u] = 0.0;
+        for (int u = 0; u < NC; ++u) rn[u] = 0ull;
         if (total > 0) {
             const int64_t i = cs.tile_row0(0) + threadIdx.x;
 #pragma unroll
             for (int u = 0; u < NC; ++u)
-                if (u < nc && i < N) rn[u] = R[i * ncols + j0 + u];
+                if (u < nc && i < N) rn[u] = reinterpret_cast<const unsigned long long *>(R)[i * ncols + j0 + u];
             if (threadIdx.x == 0) cs.issue(c_base, 0);
         }
         for (int c = 0; c < total; ++c) {
             const int cc = c_base + c;
             if (threadIdx.x == 0 && c + 1 < total) cs.issue(cc + 1, c + 1);
+            if (c < ntile) {
+                const int64_t i = cs.tile_row0(c) + threadIdx.x;
 #pragma unroll
-            for (int u = 0; u < NC; ++u) {
-                float hi, lo;
-                split_f2(rn[u], hi, lo);
-                Rs[threadIdx.x * NC + u] = F2{hi, lo};
+                for (int u = 0; u < NC; ++u) {
+                    F2 f;
+                    split_f2(__longlong_as_double((long long)rn[u]), f.hi, f.lo);
+                    Rs[threadIdx.x * NC + u] = f;
+                    if (u < nc && i < N) Rsp[i * ncols + j0 + u] = f;
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < NC; ++u)
+                    Rs[threadIdx.x * NC + u] =
+                        F2{__uint_as_float((unsigned)(rn[u] & 0xffffffffull)), __uint_as_float((unsigned)(rn[u] >> 32))};
             }
             if (c + 1 < total) {
                 const int64_t i = cs.tile_row0(c + 1) + threadIdx.x;
+                if (c + 1 < ntile) {
 #pragma unroll
-                for (int u = 0; u < NC; ++u) rn[u] = (u < nc && i < N) ? R[i * ncols + j0 + u] : 0.0;
+                    for (int u = 0; u < NC; ++u)
+                        rn[u] = (u < nc && i < N) ? reinterpret_cast<const unsigned long long *>(R)[i * ncols + j0 + u]
+                                                  : 0ull;
+                } else {
+#pragma unroll
+                    for (int u = 0; u < NC; ++u)
+                        rn[u] = (u < nc && i < N) ? reinterpret_cast<const unsigned long long *>(Rsp)[i * ncols + j0 + u]
+                                                  : 0ull;
+                }
             }
             if (!cs.wait(cc, &s_bad, err, c + 1 < total)) return;  // (its barrier also publishes Rs)
             const uint32_t la = smem_u32(cs.chunk(cc)) + (uint32_t)(warp * kTR + lane) * 4u;
@@ -1022,6 +1050,7 @@ struct Precond {
     int64_t ldN = 0;
     double *dres = nullptr, *Cf = nullptr, *Cinv = nullptr, *t_part = nullptr, *cvec = nullptr,
            *scal = nullptr;
+    F2 *rsp = nullptr;  // the float pairs of R's rows, N x cap_cols (written and read by k_pc_ltr)
     float *L32 = nullptr;  // the factor, k columns of ldN (q order)
     int32_t *piv_q = nullptr;
     int *ints = nullptr;  // [0] rank, [1] error flag
@@ -1041,19 +1070,22 @@ int pc_reserve(Precond *pc, int ncols, cudaStream_t s) {
     }
     if (ncols <= pc->cap_cols) return FGK_OK;
     const size_t kk = (size_t)std::max(pc->k_req, 1);
+    const size_t nrow = (size_t)std::max<int64_t>(pc->plan->N, 1);
     void *t = dev_alloc((size_t)pc->nb_ltr * kk * ncols * 8, s);
     void *c = dev_alloc(kk * ncols * 8, s);
     void *tv = dev_alloc(kk * ncols * 8, s);
-    if (!t || !c || !tv) {
+    void *rs = dev_alloc(nrow * ncols * 8, s);
+    if (!t || !c || !tv || !rs) {
         if (t) dev_free(t, s);
         if (c) dev_free(c, s);
         if (tv) dev_free(tv, s);
+        if (rs) dev_free(rs, s);
         set_error("preconditioner: scratch allocation failed");
         return FGK_ERR_OOM;
     }
     FGK_CUDA(cudaMemsetAsync(c, 0, kk * ncols * 8, s));
     for (auto &q : pc->owned)
-        if (q == pc->t_part || q == pc->cvec || q == pc->tvec) {
+        if (q == pc->t_part || q == pc->cvec || q == pc->tvec || q == pc->rsp) {
             dev_free(q, s);
             q = nullptr;
         }
@@ -1061,10 +1093,13 @@ int pc_reserve(Precond *pc, int ncols, cudaStream_t s) {
     pc->t_part = (double *)t;
     pc->cvec = (double *)c;
     pc->tvec = (double *)tv;
+    pc->rsp = (F2 *)rs;
     pc->owned.push_back(t);
     pc->owned.push_back(c);
     pc->owned.push_back(tv);
-    pc->bytes += (size_t)pc->nb_ltr * kk * (ncols - pc->cap_cols) * 8 + 2 * kk * (ncols - pc->cap_cols) * 8;
+    pc->owned.push_back(rs);
+    pc->bytes += (size_t)pc->nb_ltr * kk * (ncols - pc->cap_cols) * 8 + 2 * kk * (ncols - pc->cap_cols) * 8 +
+                 nrow * (ncols - pc->cap_cols) * 8;
     pc->cap_cols = ncols;
     return FGK_OK;
 }
@@ -1168,8 +1203,8 @@ template <int NC>
 static int launch_pc_ltr(const Precond *pc, int r, const double *R, int ncols, int *err, cudaStream_t s,
                          const int *gate) {
     TimedLaunch tl(kTimedPcLtr, s);
-    k_pc_ltr<NC><<<pc->nb_ltr, kTR, ltr_smem(r, NC), s>>>(pc->tmap, r, R, pc->plan->N, ncols, pc->t_part, err,
-                                                          gate);
+    k_pc_ltr<NC><<<pc->nb_ltr, kTR, ltr_smem(r, NC), s>>>(pc->tmap, r, R, pc->plan->N, ncols, pc->t_part,
+                                                          pc->rsp, err, gate);
     FGK_LAUNCH_CHECK();
     tl.end();
     return FGK_OK;

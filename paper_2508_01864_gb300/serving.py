@@ -177,9 +177,9 @@ def gpu_estimator(nrhs_cols: int = 1, precond_rank: int = 100):
     def est(req: Request) -> int:
         k = precond_rank_for(req.N, precond_rank)
         # factor (FP32), residual diagonal, the build's exponential tables and Gram partials
-        # (<= 64 x k x k), apply scratch
-        pc_bytes = (req.N * k * 4 + req.N * 8 + 16 * req.d * req.N + 66 * k * k * 8 + 304 * k * 8 + (1 << 20)
-                    if k > 0 else 0)
+        # (<= 64 x k x k), apply scratch (the float pairs of R's rows and the per-CTA partials)
+        pc_bytes = (req.N * k * 4 + req.N * 8 + 16 * req.d * req.N + 66 * k * k * 8 + 304 * k * 8
+                    + req.N * 8 * nrhs_cols + (1 << 20) if k > 0 else 0)
         return (int(fgk.fgk_bytes_estimate(req.N, req.d, req.nu, req.kind, nrhs_cols)) + req.N * (req.d + 3) * 8
                 + pc_bytes)
 
