@@ -289,7 +289,10 @@ int fgk_precond_factor(fgk_precond pc, double *L, fgk_stream_t stream);
 /* Z = P^{-1} R by the Woodbury formula of App. A.3,
  * P^{-1} R = R / sigma2 - L (I_k + L^T L / sigma2)^{-1} L^T R / sigma2^2.
  * R, Z: device, N x ncols FP64 row-major, original point order,
- * 1 <= ncols <= 64.  Asynchronous (allocates scratch on `stream`). */
+ * 1 <= ncols <= 64.  Asynchronous (allocates scratch on `stream`).  The
+ * scratch belongs to pc, as a plan's workspace belongs to its handle: the
+ * calls that use one preconditioner (its applies and the solves it
+ * preconditions) must be ordered on one stream. */
 int fgk_precond_apply(fgk_precond pc, const double *R, int ncols, double *Z, fgk_stream_t stream);
 
 int fgk_precond_destroy(fgk_precond pc);
