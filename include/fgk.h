@@ -331,8 +331,8 @@ int fgk_cg_solve_pc(fgk_handle h, fgk_precond pc, const double *y, int nrhs, dou
 int fgk_minres_solve(fgk_handle h, const double *y, int nrhs, double sigma2, double tol, int maxit, double *alpha,
                      fgk_cg_info *info, fgk_stream_t stream);
 
-/* One d = 1 problem over several devices (SURVEY's sharded form of the d = 1
- * product): each device holds a shard, a contiguous range of the points in
+/* One d = 1 problem over several devices (the d = 1 product split by point
+ * ranges): each device holds a shard, a contiguous range of the points in
  * sorted order, and a plan of its own points; the plan's product covers the
  * pairs inside the shard, and the pairs between shards act through P
  * moments per shard and direction (Sec. 2.1, the fast sum updating of
